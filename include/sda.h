@@ -1,0 +1,235 @@
+/*
+ * sda.h - C ABI of libsda, the GB300 (sm_103a) library for fast binary
+ * semi-supervised discriminant analysis (FSDA) of Tavernier et al., arXiv
+ * 1709.04794.
+ *
+ * The library solves, for one or many binary targets sharing one sparse
+ * sample x feature matrix X (N x D, rows = samples, Sec. 2.1) and one
+ * similarity graph S (N x N, Sec. 2.3-2.4), the regularised SDA systems
+ *
+ *     (B + beta I) w = b     for every beta of a shift sweep,
+ *     B = (X - 1 mu_l^T)^T [ omega P_l + alpha L ] X                 (Alg. 7 step 4)
+ *       = omega S_t^l + alpha X^T L X,   L = diag(S 1) - S,  omega = 1 - alpha  (eq. 7)
+ *
+ * with one shifted conjugate-gradient run per target (Algorithm 3) and the
+ * centring applied implicitly as a rank-1 correction (Sec. 3.2.3), so X is
+ * never densified.  mu_l is the mean labelled sample (Alg. 7 step 3), P_l
+ * the diagonal 0/1 matrix of the labelled rows.
+ *
+ * Conventions for every call:
+ *  - Return value 0 (SDA_OK) on success, a positive warning code, or a
+ *    negative error code; sda_status_string() names it and
+ *    sda_last_error_detail() gives the calling thread's last message.
+ *    No C++ exception crosses this boundary.
+ *  - Inputs are borrowed for the duration of the call only; an operator
+ *    keeps its own device copies.  Outputs are allocated by the caller.
+ *  - Pointers are host or device pointers as the accompanying flag says;
+ *    device pointers belong to the current CUDA device.
+ *  - Device work is ordered on the caller's stream (cudaStream_t passed as
+ *    void*, NULL = legacy default stream); calls that return host results
+ *    synchronise that stream before returning.
+ */
+#ifndef SDA_H
+#define SDA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SDA_API __attribute__((visibility("default")))
+#else
+#define SDA_API
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+    SDA_OK = 0,
+    SDA_NOT_CONVERGED = 1,        /* warning: a shift reached max_iter before tol (see the report) */
+    SDA_ERR_INVALID_ARG = -1,     /* NULL pointer, bad flag, n_shifts out of range, shift <= 0 ...  */
+    SDA_ERR_SHAPE = -2,           /* inconsistent sizes between X, S, labels and vectors            */
+    SDA_ERR_INDEX = -3,           /* row pointers not monotone, or a column index out of range or
+                                     not strictly increasing within its row                          */
+    SDA_ERR_VALUE_NOT_EXACT = -4, /* a value of X would change when stored in the compute dtype      */
+    SDA_ERR_NO_POSITIVE = -5,     /* a target has no labelled positive sample: mu_+ undefined        */
+    SDA_ERR_NO_NEGATIVE = -6,     /* a target has no labelled negative sample: mu_- undefined        */
+    SDA_ERR_NOT_SYMMETRIC = -7,   /* S differs from S^T, or holds a negative or non-finite weight    */
+    SDA_ERR_BREAKDOWN = -8,       /* <p, (B + sigma0 I) p> <= 0 or not finite during the solve       */
+    SDA_ERR_TIMEOUT = -9,         /* a bounded device-side wait ran out                              */
+    SDA_ERR_CUDA = -10,           /* a CUDA runtime call failed (detail in sda_last_error_detail)    */
+    SDA_ERR_OOM = -11,            /* device allocation failed                                        */
+    SDA_ERR_UNSUPPORTED = -12     /* a combination of options this build does not provide            */
+};
+
+/* Storage type of the values of X.  SDA_F64 selects the plain FP64 path
+ * (values, vectors and sums in FP64).  The other types select the mixed
+ * path: X stored in that type (binary / small-count fingerprint data is
+ * exact in FP16 and FP8 e4m3), FP32 vectors and FP32 sparse sums, FP64
+ * scalar recurrences, FP64 true-residual check.  SDA_PATTERN stores no
+ * values at all (every stored entry is 1). */
+typedef enum {
+    SDA_F64 = 0,
+    SDA_F32 = 1,
+    SDA_F16 = 2,
+    SDA_F8E4M3 = 3,
+    SDA_PATTERN = 4
+} sda_dtype;
+
+/* A CSR matrix.  row_ptr has n_rows + 1 entries starting at 0 and ending at
+ * nnz; col_idx has nnz entries, strictly increasing within each row and in
+ * [0, n_cols).  values has nnz entries of `dtype` (SDA_F64 or SDA_F32 as
+ * input types), or is NULL when dtype is SDA_PATTERN. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const void *values;
+    sda_dtype dtype;
+    int32_t on_device;            /* 1: the three arrays are device pointers; 0: host pointers */
+} sda_csr;
+
+/* Labels of n_targets binary targets over the N samples, row-major
+ * [n_targets][N]: +1 (positive), -1 (negative), 0 (unlabelled).  Each
+ * target's labelled rows form its P_l (eq. 7). */
+typedef struct {
+    int32_t n_targets;
+    const int8_t *labels;
+    int32_t on_device;
+} sda_labels;
+
+typedef struct sda_operator sda_operator;   /* opaque, owned by the library */
+
+/*
+ * sda_build_operator - copy X and S to the device and prepare everything
+ * the solves share (Alg. 7 steps 1-3): a feature order by descending column
+ * count, CSR and CSC copies of X in the compute dtype, the degrees
+ * D_ii = sum_j s_ij of the graph Laplacian L = D - S (Sec. 2.3), and per
+ * target l, N+, N-, mu_l = X^T 1_l / l (Alg. 7 step 3) and
+ * d = mu_+ - mu_- (the direction of the rank-1 right-hand side of Alg. 7
+ * step 4, (X - 1 mu_l^T)^T [W 0; 0 0] X r = (N+ N- / l)(d^T r) d).
+ *
+ *   X              N x D sample x feature matrix (F64/F32 values, or PATTERN)
+ *   S              N x N similarity graph, symmetric, weights >= 0 (diagonal ignored by L)
+ *   y              labels of the targets
+ *   alpha          weight of the manifold term alpha X^T L X, in [0, 1] (eq. 7)
+ *   scatter_weight weight omega of the labelled total scatter; NaN selects the
+ *                  paper's 1 - alpha
+ *   compute        storage dtype of X on the device (see sda_dtype)
+ *   cuda_stream    stream for the device work; the call synchronises it
+ *   out            receives the operator; release it with sda_destroy_operator
+ *
+ * Errors: INVALID_ARG, SHAPE, INDEX, VALUE_NOT_EXACT, NOT_SYMMETRIC,
+ * NO_POSITIVE / NO_NEGATIVE (per target), CUDA, OOM.  *out is NULL on error.
+ */
+SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, const sda_labels *y,
+                               double alpha, double scatter_weight, sda_dtype compute,
+                               void *cuda_stream, sda_operator **out);
+
+/* Right-hand side of the solve (Alg. 7 step 4). */
+enum {
+    SDA_RHS_CANONICAL = 0,  /* b = d = mu_+ - mu_- (positives score high)                          */
+    SDA_RHS_FROM_R = 1,     /* b = (X - 1 mu_l^T)^T [W 0; 0 0] X r for the given r in R^D
+                               (= (N+ N- / l)(d^T r) d); `rhs` holds r (D doubles, shared by all
+                               targets of the call)                                                */
+    SDA_RHS_GIVEN = 2       /* b given in `rhs`: [target_count][D] doubles                          */
+};
+
+typedef struct {
+    double tol;             /* shift s stops when |zeta_s| ||r|| < tol ||b|| (Alg. 3, relative)     */
+    int32_t max_iter;       /* iteration cap for every shift                                       */
+    int32_t fixed_iters;    /* > 0: run exactly this many iterations, ignore tol (Sec. 5.2: 70)     */
+    int32_t rhs_mode;       /* SDA_RHS_*                                                           */
+    const double *rhs;      /* see rhs_mode; NULL for SDA_RHS_CANONICAL                            */
+    int32_t rhs_on_device;  /* 1: `rhs` is a device pointer                                        */
+    int32_t target_begin;   /* first target solved by this call                                    */
+    int32_t target_count;   /* number of targets solved by this call (-1: all from target_begin)   */
+    int32_t check_residual; /* 1: compute the FP64 true relative residual of every shift           */
+    int32_t out_on_device;  /* 1: w_out is a device pointer; 0: host pointer                       */
+    int32_t use_graph;      /* 1: replay the iteration loop as captured CUDA graphs                */
+    int32_t iter_batch;     /* iterations launched between two host convergence checks (0: auto)   */
+} sda_solve_opts;
+
+/* Fills *opt with: tol 1e-6, max_iter 10000, fixed_iters 0, canonical RHS,
+ * all targets, FP64 residual check on, device output, graphs on, auto batch. */
+SDA_API void sda_default_opts(sda_solve_opts *opt);
+
+/* Per target and shift outcome of sda_solve_shifts. */
+typedef struct {
+    int32_t iters;          /* iteration at which the shift stopped (Alg. 3 stop test)             */
+    int32_t status;         /* SDA_OK, SDA_NOT_CONVERGED or SDA_ERR_BREAKDOWN                      */
+    double est_residual;    /* |zeta| ||r|| / ||b|| when it stopped                                */
+    double true_residual;   /* ||b - (B + beta I) w|| / ||b|| in FP64, or -1 when not computed     */
+} sda_shift_report;
+
+/*
+ * sda_solve_shifts - solve (B + beta_s I) w_s = b for every shift of every
+ * target in the call's range with one shifted-CG run per target
+ * (Algorithm 3; base system B + sigma0 I, sigma0 = min beta, recurrences on
+ * the relative shifts; the shift coefficient uses the new CG coefficient,
+ * alpha^b_{i+1} = alpha_{i+1} (zeta^b_{i+1} / zeta^b_i)^2).
+ *
+ *   shifts     n_shifts values > 0 (host), 1 <= n_shifts <= 64
+ *   opt        options (NULL: sda_default_opts)
+ *   w_out      [target_count][n_shifts][D] doubles in the caller's feature order, or NULL
+ *   report     host array [target_count][n_shifts], or NULL
+ *
+ * Returns SDA_OK, SDA_NOT_CONVERGED (some shift hit max_iter; its report
+ * says which), or an error: INVALID_ARG, SHAPE, BREAKDOWN, TIMEOUT, CUDA,
+ * OOM.  Synchronises the stream.
+ */
+SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, int32_t n_shifts,
+                             const sda_solve_opts *opt, double *w_out, sda_shift_report *report,
+                             void *cuda_stream);
+
+/*
+ * sda_project - ratings s = X w of the samples (Sec. 4, Alg. 7 step 5), or
+ * the centred ratings (X - 1 mu_l^T) w when `centred` is 1 (uses mu_l of
+ * `target`).  FP64 sums.
+ *
+ *   w        [n_vec][D] doubles in the caller's feature order (device)
+ *   scores   [n_vec][N] doubles (device)
+ */
+SDA_API int sda_project(const sda_operator *op, const double *w, int64_t n_vec, double *scores,
+                        int32_t centred, int32_t target, void *cuda_stream);
+
+/*
+ * sda_operator_apply - q = (B + sigma I) p for one target in FP64 (the
+ * operator of Alg. 7 step 4 in its centred symmetric form
+ * (X - 1 mu_l^T)^T M (X - 1 mu_l^T), equal to the paper's form because
+ * M 1 = omega 1_l and (X - 1 mu_l^T)^T 1_l = 0).  p and q are device arrays
+ * of D doubles in the caller's feature order.
+ */
+SDA_API int sda_operator_apply(const sda_operator *op, int32_t target, double sigma,
+                               const double *p, double *q, void *cuda_stream);
+
+/* Sizes of an operator. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz, graph_nnz;
+    int32_t n_targets;
+    sda_dtype compute;
+    double alpha, omega;
+    int64_t device_bytes;   /* device memory held by the operator (without solve workspace) */
+} sda_operator_info;
+
+SDA_API int sda_get_operator_info(const sda_operator *op, sda_operator_info *info);
+
+/* Per-target counts (l, N+, N-) as doubles, host array [n_targets][3]. */
+SDA_API int sda_get_target_counts(const sda_operator *op, double *counts);
+
+/* Releases the operator and its device memory (NULL is a no-op). */
+SDA_API void sda_destroy_operator(sda_operator *op);
+
+/* Static string naming a status code. */
+SDA_API const char *sda_status_string(int code);
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len); returns the code of that error (0 if none). */
+SDA_API int sda_last_error_detail(char *buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDA_H */

@@ -1,0 +1,351 @@
+"""Pins of the FP64 CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test names the passage it follows.  None of them re-types the oracle's
+own formula: the dense checks build B from the sample sums of eq. (7) and
+the regulariser of Sec. 2.3, the eigenproblem goes through a library
+generalised-eigen routine, and the rest are closed forms, invariances,
+special cases and brute force.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from paper_1709_04794_gb300 import synth
+
+
+def _dense(prob, t=0):
+    return oracle.dense_x(prob.x_ptr, prob.x_col, prob.x_val, prob.d)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# --------------------------------------------------------------------------
+# Operator (eq. 7, Alg. 7 step 4, Sec. 3.2.3)
+# --------------------------------------------------------------------------
+
+def test_operator_equals_sample_sum_definition(tiny):
+    """B p from the matrix-free paper form equals (1-a) S_t^l + a X^T L X built from
+    sums over samples (eq. 7) and over graph edges (regulariser, Sec. 2.3)."""
+    o = oracle.from_problem(tiny)
+    X = _dense(tiny)
+    B = oracle.dense_operator(X, tiny.s_ptr, tiny.s_col, tiny.s_val, tiny.labels[0], tiny.alpha)
+    rng = np.random.default_rng(0)
+    for sigma in (0.0, 0.37):
+        p = rng.standard_normal(tiny.d)
+        assert _rel(o.apply(p, sigma), B @ p + sigma * p) < 1e-12
+
+
+def test_operator_symmetric_psd(cfg1):
+    """B is symmetric positive semi-definite (Sec. 3.2.1: 'symmetric ... SDA')."""
+    o = oracle.from_problem(cfg1)
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        x, y = rng.standard_normal(cfg1.d), rng.standard_normal(cfg1.d)
+        bx, by = o.apply(x), o.apply(y)
+        assert abs(x @ by - bx @ y) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(by)
+        assert x @ bx >= -1e-12 * (x @ x)
+
+
+def test_centred_operator_kills_nondiscriminative_direction(tiny):
+    """Sec. 3.2.3: with centring around mu_l, the vector w_nd with X w_nd = 1 is in
+    the null space: B w_nd = 0.  Make w_nd exist by adding an all-ones feature."""
+    n, d = tiny.n, tiny.d
+    counts = np.diff(tiny.x_ptr)
+    x_ptr = np.concatenate([[0], np.cumsum(counts + 1)]).astype(np.int64)
+    x_col = np.empty(x_ptr[-1], dtype=np.int32)
+    x_val = np.empty(x_ptr[-1])
+    for i in range(n):
+        a, b = tiny.x_ptr[i], tiny.x_ptr[i + 1]
+        x_col[x_ptr[i]:x_ptr[i + 1]] = np.concatenate([tiny.x_col[a:b], [d]])
+        x_val[x_ptr[i]:x_ptr[i + 1]] = np.concatenate([tiny.x_val[a:b], [1.0]])
+    o = oracle.Oracle(x_ptr, x_col, x_val, tiny.s_ptr, tiny.s_col, tiny.s_val, tiny.labels[0],
+                      d + 1, tiny.alpha)
+    e = np.zeros(d + 1)
+    e[d] = 1.0
+    q = o.apply(e)
+    scale = np.linalg.norm(o.apply(np.random.default_rng(2).standard_normal(d + 1)))
+    assert np.linalg.norm(q) <= 1e-13 * scale
+    # without the centring correction it is not in the null space: the uncentred
+    # operator X^T M X maps w_nd to (1 - alpha) X^T 1_l = (1 - alpha) l mu_l != 0
+    X = oracle.dense_x(x_ptr, x_col, x_val, d + 1)
+    y = tiny.labels[0]
+    unc = (1 - tiny.alpha) * X.T @ ((y != 0) * (X @ e))
+    assert np.linalg.norm(unc) > 1.0
+
+
+def test_paper_form_equals_symmetric_centred_form(tiny):
+    """(X - 1 mu^T)^T M X = (X - 1 mu^T)^T M (X - 1 mu^T) because M 1 = (1-a) 1_l
+    (L 1 = 0, Sec. 2.5.2) and (X - 1 mu^T)^T 1_l = 0."""
+    o = oracle.from_problem(tiny)
+    X = _dense(tiny)
+    y = tiny.labels[0]
+    mu = X[y != 0].mean(axis=0)
+    Xc = X - mu
+    n = tiny.n
+    S = np.zeros((n, n))
+    S[np.repeat(np.arange(n), np.diff(tiny.s_ptr)), tiny.s_col] = tiny.s_val
+    L = np.diag(S.sum(axis=1)) - S
+    M = (1 - tiny.alpha) * np.diag((y != 0).astype(float)) + tiny.alpha * L
+    p = np.random.default_rng(3).standard_normal(tiny.d)
+    assert _rel(o.apply(p), Xc.T @ (M @ (Xc @ p))) < 1e-12
+
+
+def test_class_means(tiny):
+    """l mu_l = X^T 1_l (Alg. 7 step 3) and the class means, against dense sums."""
+    o = oracle.from_problem(tiny)
+    X = _dense(tiny)
+    y = tiny.labels[0]
+    mu, mp, mn, cnt = o.class_means()
+    assert np.allclose(mu, X[y != 0].mean(axis=0), rtol=0, atol=1e-14)
+    assert np.allclose(mp, X[y > 0].mean(axis=0), rtol=0, atol=1e-14)
+    assert np.allclose(mn, X[y < 0].mean(axis=0), rtol=0, atol=1e-14)
+    assert list(cnt) == [(y != 0).sum(), (y > 0).sum(), (y < 0).sum()]
+
+
+def test_rhs_rank_one_closed_form(tiny):
+    """Alg. 7 step 4 RHS (X - 1 mu^T)^T [W 0; 0 0] X r equals (N+ N- / l)(d^T r) d:
+    the between-class scatter of two classes has rank one (Sec. 2.2.1, Sec. 3.1)."""
+    o = oracle.from_problem(tiny)
+    _, mp, mn, cnt = o.class_means()
+    dvec = mp - mn
+    r = synth.random_r(5, tiny.d)
+    b = o.rhs_from_r(r)
+    expect = cnt[1] * cnt[2] / cnt[0] * (dvec @ r) * dvec
+    assert _rel(b, expect) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Solvers (Alg. 2, Alg. 3, eq. 10-12)
+# --------------------------------------------------------------------------
+
+def test_shifted_cg_equals_dense_direct_solve(tiny):
+    """w_beta = (B + beta I)^{-1} b by Cholesky of the dense B, for every shift."""
+    o = oracle.from_problem(tiny)
+    X = _dense(tiny)
+    B = oracle.dense_operator(X, tiny.s_ptr, tiny.s_col, tiny.s_val, tiny.labels[0], tiny.alpha)
+    b = o.rhs_canonical()
+    res = o.shifted_cg(b, tiny.shifts, tol=1e-14, max_iter=5000)
+    assert res.status == 0
+    for s, beta in enumerate(tiny.shifts):
+        A = B + beta * np.eye(tiny.d)
+        w = scipy.linalg.cho_solve(scipy.linalg.cho_factor(A), b)
+        kappa = np.linalg.cond(A)
+        assert _rel(res.W[s], w) < max(1e-12, 1e-14 * kappa * 10), (beta, kappa)
+
+
+def test_cg_equals_dense_direct_solve(tiny):
+    o = oracle.from_problem(tiny)
+    X = _dense(tiny)
+    B = oracle.dense_operator(X, tiny.s_ptr, tiny.s_col, tiny.s_val, tiny.labels[0], tiny.alpha)
+    b = o.rhs_canonical()
+    beta = tiny.shifts[1]
+    w, it, r, rc = o.cg(b, beta, tol=1e-14, max_iter=5000)
+    assert rc == 0
+    assert _rel(w, np.linalg.solve(B + beta * np.eye(tiny.d), b)) < 1e-10
+
+
+def test_generalised_eigenproblem_rank_one(tiny):
+    """Eq. (7)/(10): S_B v = lambda (B + beta I) v with rank-1 S_B has one nonzero
+    eigenvalue (N+N-/l) d^T (B+beta I)^{-1} d, eigenvector ∝ the solve's w."""
+    o = oracle.from_problem(tiny)
+    X = _dense(tiny)
+    y = tiny.labels[0]
+    B = oracle.dense_operator(X, tiny.s_ptr, tiny.s_col, tiny.s_val, y, tiny.alpha)
+    SB = oracle.dense_between(X, y)
+    beta = tiny.shifts[2]
+    lam, V = scipy.linalg.eigh(SB, B + beta * np.eye(tiny.d))
+    b = o.rhs_canonical()
+    res = o.shifted_cg(b, [beta], tol=1e-14, max_iter=5000)
+    w = res.W[0]
+    _, _, _, cnt = o.class_means()
+    lam_max = cnt[1] * cnt[2] / cnt[0] * (b @ w)
+    assert abs(lam[-1] - lam_max) <= 1e-10 * lam_max
+    assert np.all(np.abs(lam[:-1]) <= 1e-10 * lam_max)
+    v = V[:, -1]
+    cos = abs(v @ w) / (np.linalg.norm(v) * np.linalg.norm(w))
+    assert cos > 1 - 1e-12
+
+
+def test_subspace_iteration_converges_in_one_step(tiny):
+    """Sec. 3.1 / Alg. 1: with j = C - 1 = 1 one step of subspace iteration gives the
+    eigenvector: V solves (B + beta I) V = S_B R for a random R."""
+    o = oracle.from_problem(tiny)
+    X = _dense(tiny)
+    y = tiny.labels[0]
+    B = oracle.dense_operator(X, tiny.s_ptr, tiny.s_col, tiny.s_val, y, tiny.alpha)
+    SB = oracle.dense_between(X, y)
+    beta = tiny.shifts[0]
+    R = synth.random_r(9, tiny.d)
+    V = np.linalg.solve(B + beta * np.eye(tiny.d), SB @ R)
+    w = o.shifted_cg(o.rhs_canonical(), [beta], tol=1e-14, max_iter=5000).W[0]
+    cos = abs(V @ w) / (np.linalg.norm(V) * np.linalg.norm(w))
+    assert cos > 1 - 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 12, 40])
+def test_shifted_iterates_equal_per_shift_cg(cfg1, k):
+    """Sec. 3.2.2: the Krylov space does not depend on the shift, so after k steps the
+    shifted-CG iterate of every shift equals k steps of plain CG (Alg. 2) on B + beta I.
+    Fails with the printed alpha_i in the shift-coefficient update (index slip)."""
+    o = oracle.from_problem(cfg1)
+    b = o.rhs_canonical()
+    res = o.shifted_cg(b, cfg1.shifts, fixed_iters=k)
+    assert res.status == 0
+    for s, beta in enumerate(cfg1.shifts):
+        w, it, _, rc = o.cg(b, beta, fixed_iters=k)
+        assert rc == 0 and it == k
+        # exact in exact arithmetic; FP64 rounding grows with k on the ill-conditioned shifts
+        tol = 1e-10 if k <= 12 else 1e-7
+        assert _rel(res.W[s], w) < tol, (k, beta, _rel(res.W[s], w))
+
+
+def test_residual_collinear_and_monotone_in_shift(cfg1):
+    """r^beta_k = zeta^beta_k r_k: the explicit residual of every shift has norm
+    |zeta| ||r|| (Alg. 3 stop test), and |zeta| does not grow with the shift."""
+    o = oracle.from_problem(cfg1)
+    b = o.rhs_canonical()
+    for k in (4, 15, 30):
+        res = o.shifted_cg(b, cfg1.shifts, fixed_iters=k)
+        for s, beta in enumerate(cfg1.shifts):
+            tr = o.true_residual(b, beta, res.W[s])
+            assert abs(tr - res.res_est[s]) <= 1e-8 * max(tr, 1e-12) + 1e-13, (k, beta)
+        assert np.all(np.diff(res.res_est) <= 1e-15)
+
+
+def test_converged_solve_meets_tolerance(cfg1):
+    o = oracle.from_problem(cfg1)
+    b = o.rhs_canonical()
+    res = o.shifted_cg(b, cfg1.shifts, tol=1e-10, max_iter=20000)
+    assert res.status == 0
+    for s, beta in enumerate(cfg1.shifts):
+        assert res.res_est[s] < 1e-10
+        assert o.true_residual(b, beta, res.W[s]) < 2e-10
+    # larger shifts converge in no more iterations (Sec. 5.1, Table 6 discussion)
+    assert np.all(np.diff(res.iters) <= 0)
+
+
+# --------------------------------------------------------------------------
+# Special cases and invariances
+# --------------------------------------------------------------------------
+
+def test_alpha_zero_ignores_unlabelled_rows(tiny):
+    """alpha = 0: the Laplacian is off and only labelled rows enter B and b, so w is
+    regularised LDA on the labelled rows (eq. 1): dropping unlabelled rows keeps w."""
+    y = tiny.labels[0]
+    o = oracle.from_problem(tiny, alpha=0.0)
+    w = o.shifted_cg(o.rhs_canonical(), tiny.shifts, tol=1e-14, max_iter=5000).W
+    keep = np.nonzero(y != 0)[0]
+    cnt = np.diff(tiny.x_ptr)[keep]
+    x_ptr = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    x_col = np.concatenate([tiny.x_col[tiny.x_ptr[i]:tiny.x_ptr[i + 1]] for i in keep])
+    x_val = np.concatenate([tiny.x_val[tiny.x_ptr[i]:tiny.x_ptr[i + 1]] for i in keep])
+    m = keep.size
+    o2 = oracle.Oracle(x_ptr, x_col, x_val, np.zeros(m + 1, np.int64), np.zeros(0, np.int32),
+                       np.zeros(0), y[keep], tiny.d, 0.0)
+    w2 = o2.shifted_cg(o2.rhs_canonical(), tiny.shifts, tol=1e-14, max_iter=5000).W
+    for s in range(len(tiny.shifts)):
+        assert _rel(w2[s], w[s]) < 1e-10
+    # and it is the ridge solution of the labelled total scatter
+    X = oracle.dense_x(x_ptr, x_col, x_val, tiny.d)
+    St, _ = oracle.dense_scatter_labelled(X, y[keep])
+    b = o2.rhs_canonical()
+    for s, beta in enumerate(tiny.shifts):
+        assert _rel(w2[s], np.linalg.solve(St + beta * np.eye(tiny.d), b)) < 1e-9
+
+
+def test_alpha_one_is_pure_manifold_term(tiny):
+    """alpha = 1 (omega = 0): the labelled scatter drops out, B = X^T L X."""
+    o = oracle.from_problem(tiny, alpha=1.0)
+    X = _dense(tiny)
+    XLX = oracle.dense_manifold(X, tiny.s_ptr, tiny.s_col, tiny.s_val)
+    p = np.random.default_rng(4).standard_normal(tiny.d)
+    assert _rel(o.apply(p), XLX @ p) < 1e-12
+
+
+def test_large_shift_expansion(tiny):
+    """(B + beta I)^{-1} b = b/beta - B b/beta^2 + O(beta^-3) for large beta."""
+    o = oracle.from_problem(tiny)
+    b = o.rhs_canonical()
+    beta = 1e7
+    w = o.shifted_cg(b, [beta], tol=1e-15, max_iter=100).W[0]
+    approx = b / beta - o.apply(b) / beta ** 2
+    assert _rel(w, approx) < 1e-6 * 10
+
+
+def test_translation_invariance(tiny):
+    """Centring (Sec. 2.5.2): X -> X + 1 t^T leaves B, d and w unchanged (graph fixed)."""
+    X = _dense(tiny)
+    t = np.random.default_rng(6).uniform(0.5, 2.0, size=tiny.d)
+    n, d = X.shape
+    full_ptr = (np.arange(n + 1) * d).astype(np.int64)
+    full_col = np.tile(np.arange(d, dtype=np.int32), n)
+    y = tiny.labels[0]
+    o1 = oracle.Oracle(full_ptr, full_col, X.reshape(-1), tiny.s_ptr, tiny.s_col, tiny.s_val, y, d,
+                       tiny.alpha)
+    o2 = oracle.Oracle(full_ptr, full_col, (X + t).reshape(-1), tiny.s_ptr, tiny.s_col, tiny.s_val,
+                       y, d, tiny.alpha)
+    b1, b2 = o1.rhs_canonical(), o2.rhs_canonical()
+    assert _rel(b2, b1) < 1e-12
+    w1 = o1.shifted_cg(b1, tiny.shifts, tol=1e-14, max_iter=5000).W
+    w2 = o2.shifted_cg(b2, tiny.shifts, tol=1e-14, max_iter=5000).W
+    for s in range(len(tiny.shifts)):
+        assert _rel(w2[s], w1[s]) < 1e-8
+
+
+def test_linearity_in_rhs(cfg1):
+    o = oracle.from_problem(cfg1)
+    b = o.rhs_canonical()
+    w1 = o.shifted_cg(b, cfg1.shifts, fixed_iters=20).W
+    # scaling by a power of two is exact in every operation: bit-identical iterates
+    w2 = o.shifted_cg(-4.0 * b, cfg1.shifts, fixed_iters=20).W
+    assert np.array_equal(w2, -4.0 * w1)
+    w3 = o.shifted_cg(3.0 * b, cfg1.shifts, fixed_iters=20).W
+    assert _rel(w3, 3.0 * w1) < 1e-6      # rounding, amplified on the ill-conditioned shifts
+
+
+def test_thread_count_does_not_change_results(cfg1):
+    o = oracle.from_problem(cfg1)
+    b = o.rhs_canonical()
+    before = oracle.set_threads(1)
+    w1 = o.shifted_cg(b, cfg1.shifts, fixed_iters=25).W
+    oracle.set_threads(4)
+    w4 = o.shifted_cg(b, cfg1.shifts, fixed_iters=25).W
+    oracle.set_threads(before)
+    assert np.array_equal(w1, w4)
+
+
+# --------------------------------------------------------------------------
+# Evaluation (Sec. 4: rating s = X w, AUC-ROC)
+# --------------------------------------------------------------------------
+
+def test_auc_rank_formula_equals_pairwise_bruteforce():
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        s = np.round(rng.standard_normal(60), 1)        # ties on purpose
+        y = np.where(rng.random(60) < 0.4, 1, -1)
+        pos, neg = s[y > 0], s[y < 0]
+        brute = ((pos[:, None] > neg[None, :]).sum() + 0.5 * (pos[:, None] == neg[None, :]).sum())
+        brute /= pos.size * neg.size
+        assert abs(oracle.auc(s, y) - brute) < 1e-15
+    assert oracle.auc([3, 2, 1, 0], [1, 1, -1, -1]) == 1.0
+    assert oracle.auc([0, 1, 2, 3], [1, 1, -1, -1]) == 0.0
+    assert oracle.auc([1, 1, 1, 1], [1, -1, 1, -1]) == 0.5
+
+
+def test_projection(tiny):
+    o = oracle.from_problem(tiny)
+    w = np.random.default_rng(8).standard_normal(tiny.d)
+    assert _rel(o.project(w), _dense(tiny) @ w) < 1e-14
+
+
+def test_planted_direction_is_found(cfg1):
+    """Sanity of the method on the planted workload: the AUC of the rating over
+    the 1,800 unlabelled rows is well above chance (0.5) for the best shift."""
+    o = oracle.from_problem(cfg1)
+    res = o.shifted_cg(o.rhs_canonical(), cfg1.shifts, tol=1e-8, max_iter=5000)
+    unl = np.nonzero(cfg1.labels[0] == 0)[0]
+    aucs = [oracle.auc(o.project(res.W[s])[unl], cfg1.truth[0][unl]) for s in range(len(cfg1.shifts))]
+    assert max(aucs) > 0.65
