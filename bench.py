@@ -1,0 +1,356 @@
+"""Benchmark: SDA solves per second (a solve = one binary target, all its
+beta shifts, converged) on the single-target 200,000 x 131,072 workload
+(FP16 count values, 32 shifts 1e-5..1e3, kNN Jaccard graph k=10), plus the
+achieved HBM bandwidth of the dominant kernel against the measured peak.
+
+One step = one pass of the whole hot path over the inputs resident in HBM:
+operator build (CSR->CSC, feature order, degrees, class means), shifted CG
+to tol for every shift, FP64 true-residual check of every shift, and the
+ratings s = X w of every shift.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one process per GPU) runs independent replicas: the
+single-target solve does not shard.  --impl reference times the FP64 CPU
+oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "single_mixed_200k"
+METRIC = "SDA solves/s (all shifts)"
+UNIT = "solves/s"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cg_phase3_xt_shift_update_single_mixed_200k.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--compute", default=None, help="storage dtype of X (default: the workload's)")
+    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--max-iter", type=int, default=4000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=300, help="oracle iterations per CPU sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, name in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def sources_hash() -> str:
+    csrc = os.path.join(ROOT, "paper_1709_04794_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "sda.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    txt = open(PROFILE_SUMMARY).read()
+    m = re.search(r"sources_sha256:\s*([0-9a-f]+)", txt)
+    t = re.search(r"%s_dram_bytes_per_launch:\s*([0-9.eE+]+)" % kernel, txt)
+    if not m or not t or m.group(1) != sources_hash():
+        return None
+    return float(t.group(1))
+
+
+def algorithmic_bytes(prob, compute: str, iters: int, shift_iters: int):
+    """Algorithmic bytes of all launches of each phase kernel over one solve.
+
+    Phase 1 (rows of X): CSR indices + values + row pointers, two gathers'
+    worth of the D-vectors r, p (each element once), ut written.
+    Phase 2 (rows of S): CSR of S (FP32 weights), ut read once, degrees,
+    labels, v written.
+    Phase 3 (columns of X): CSC indices + values + column pointers, v read
+    once, r and p read and written, mu_l (FP64) read, and per active shift
+    P and W read and written (FP32)."""
+    n, d = prob.n, prob.d
+    nnz = int(prob.x_ptr[-1])
+    snz = int(prob.s_ptr[-1])
+    vsz = {"f64": 8, "f32": 4, "f16": 2, "f8e4m3": 1, "pattern": 0}[compute]
+    fsz = 8 if compute == "f64" else 4
+    p1 = nnz * (4 + vsz) + (n + 1) * 8 + 2 * d * fsz + n * fsz
+    p2 = snz * (4 + fsz) + (n + 1) * 8 + n * fsz + n * fsz + n + n * fsz
+    p3_fixed = nnz * (4 + vsz) + (d + 1) * 8 + n * fsz + 4 * d * fsz + d * 8
+    per_launch = {"phase1": p1, "phase2": p2, "phase3": p3_fixed + shift_iters * d * 4 * fsz / max(iters, 1)}
+    return per_launch
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        pk = json.load(open(path))
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle as it stands
+# ---------------------------------------------------------------------------
+
+def run_reference(args, prob, rank):
+    import oracle
+    if rank != 0:
+        return
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    o = oracle.from_problem(prob)
+    b = o.rhs_canonical()
+    # iterations of the full solve (setup, untimed): the oracle's own run to tol
+    full = o.shifted_cg(b, prob.shifts, tol=args.tol, max_iter=args.max_iter)
+    iters_full = int(full.total_iters)
+    k = max(1, min(args.cpu_iters, iters_full))
+    for _ in range(args.warmup):
+        o.shifted_cg(b, prob.shifts, fixed_iters=k)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.shifted_cg(b, prob.shifts, fixed_iters=k)
+        times.append(time.perf_counter() - t0)
+    per_solve = statistics.mean(times) * iters_full / k
+    value = 1.0 / per_solve
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "tol": args.tol, "shifts": len(prob.shifts)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d of the %d shifted-CG iterations of the full solve per step, "
+                                       "extrapolated linearly" % (k, iters_full)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1709_04794_gb300 import synth
+    prob = synth.make_problem(WORKLOAD)
+    compute = args.compute or prob.workload.value_dtype
+    if args.impl == "reference":
+        run_reference(args, prob, rank)
+        return
+
+    import torch
+    from paper_1709_04794_gb300 import sda
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k))).cuda()
+           for k in ("x_ptr", "x_col", "x_val", "s_ptr", "s_col", "s_val", "labels")}
+    ns, d, n = len(prob.shifts), prob.d, prob.n
+    w = torch.empty((1, ns, d), dtype=torch.float64, device="cuda")
+    scores = torch.empty((ns, n), dtype=torch.float64, device="cuda")
+
+    def opts(profile=0, out_dev=1):
+        o = sda.sda_default_opts()
+        o.tol, o.max_iter, o.check_residual, o.profile = args.tol, args.max_iter, 1, profile
+        o.out_on_device = out_dev
+        return o
+
+    def step(profile=0):
+        h = sda.sda_build_operator(dev["x_ptr"], dev["x_col"], dev["x_val"], d, dev["s_ptr"], dev["s_col"],
+                                   dev["s_val"], dev["labels"], prob.alpha, float("nan"), compute, stream)
+        try:
+            code, rep = sda.sda_solve_shifts(h, prob.shifts, opts(profile), w_out=w, n_report=1, stream=stream)
+            sda.sda_project(h, w[0], ns, scores, 0, 0, stream)
+            stats = sda.sda_get_solve_stats(h)
+        finally:
+            sda.sda_destroy_operator(h)
+        return code, rep, stats
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sda.sda_kernel_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    ev0.record(stream)
+    reports = []
+    for _ in range(args.steps):
+        reports.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = sda.sda_kernel_launch_count() - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t_local = ms / 1e3
+    if dist is not None:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = world * args.steps / t_max
+    code, rep, stats = reports[-1]
+
+    # per-kernel durations: one profiled solve (events around every phase kernel)
+    pcode, prep, pstats = step(profile=1)
+    iters = max(1, pstats["iterations"])
+    per_launch = algorithmic_bytes(prob, compute, pstats["iterations"], pstats["shift_iterations"])
+    durs = {"phase1": pstats["ms"][1] / iters, "phase2": pstats["ms"][2] / iters, "phase3": pstats["ms"][3] / iters}
+    dominant = max(durs, key=durs.get)
+    peak, peak_kind = load_peaks()
+    achieved = per_launch[dominant] / (durs[dominant] * 1e-3) / 1e9
+    kernel_names = {"phase1": "k_cg_phase1", "phase2": "k_cg_phase2", "phase3": "k_cg_phase3"}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(kernel_names[dominant]),
+                "kernel": kernel_names[dominant], "peak_kind": peak_kind,
+                "bytes_per_launch": per_launch[dominant], "ms_per_launch": durs[dominant],
+                "all_kernels": {kernel_names[k]: {"ms_per_launch": durs[k], "GB/s": per_launch[k] / (durs[k] * 1e-3) / 1e9}
+                                for k in durs}}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {k: np.ascontiguousarray(getattr(prob, k)) for k in
+                ("x_ptr", "x_col", "x_val", "s_ptr", "s_col", "s_val", "labels")}
+        w_host = np.empty((1, ns, d))
+        h2d = sum(a.nbytes for a in host.values())
+        d2h = w_host.nbytes + ns * 24
+        e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            h = sda.sda_build_operator(host["x_ptr"], host["x_col"], host["x_val"], d, host["s_ptr"], host["s_col"],
+                                       host["s_val"], host["labels"], prob.alpha, float("nan"), compute, stream)
+            try:
+                sda.sda_solve_shifts(h, prob.shifts, opts(0, 0), w_out=w_host, n_report=1, stream=stream)
+            finally:
+                sda.sda_destroy_operator(h)
+        el = time.perf_counter() - t0
+        e2e = {"value": world * e_steps / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e_steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        cores = oracle.set_threads(os.cpu_count() or 1)
+        o = oracle.from_problem(prob)
+        b = o.rhs_canonical()
+        k = min(args.cpu_iters, iters)
+        o.shifted_cg(b, prob.shifts, fixed_iters=3)
+        t0 = time.perf_counter()
+        o.shifted_cg(b, prob.shifts, fixed_iters=k)
+        el = time.perf_counter() - t0
+        cpu = {"value": 1.0 / (el * stats["iterations"] / k), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d of the %d shifted-CG iterations of one solve (FP64 oracle), extrapolated linearly"
+                         % (k, stats["iterations"])}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if compute != "f64" else "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": n, "d": d, "nnz": int(prob.x_ptr[-1]),
+                           "graph_nnz": int(prob.s_ptr[-1]), "x_storage": compute, "shifts": ns, "tol": args.tol,
+                           "alpha": prob.alpha, "iterations": stats["iterations"],
+                           "shift_iterations": stats["shift_iterations"],
+                           "max_true_residual": max(r["true_residual"] for r in rep[0]),
+                           "status": code, "parallelism": "replicas" if world > 1 else "single",
+                           "l2": "no flush: one iteration streams ~%d MB (> 126 MB L2)"
+                                 % int(sum(per_launch.values()) / 1e6)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

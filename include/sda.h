@@ -149,6 +149,8 @@ typedef struct {
     int32_t out_on_device;  /* 1: w_out is a device pointer; 0: host pointer                       */
     int32_t use_graph;      /* 1: replay the iteration loop as captured CUDA graphs                */
     int32_t iter_batch;     /* iterations launched between two host convergence checks (0: auto)   */
+    int32_t profile;        /* 1: launch without graphs and time every phase kernel with CUDA
+                               events (sda_get_solve_stats); slower, for measurement only         */
 } sda_solve_opts;
 
 /* Fills *opt with: tol 1e-6, max_iter 10000, fixed_iters 0, canonical RHS,
@@ -203,6 +205,21 @@ SDA_API int sda_project(const sda_operator *op, const double *w, int64_t n_vec, 
  */
 SDA_API int sda_operator_apply(const sda_operator *op, int32_t target, double sigma,
                                const double *p, double *q, void *cuda_stream);
+
+/* Counters of the last sda_solve_shifts call on an operator. */
+typedef struct {
+    int64_t iterations;        /* Krylov iterations summed over the call's targets                  */
+    int64_t shift_iterations;  /* sum over targets and shifts of the iterations each shift ran      */
+    int64_t launches[4];       /* kernel launches: [0] start, [1] X rows, [2] S rows, [3] X columns */
+    double ms[4];              /* device time of those launches in ms (profile mode, else 0)        */
+    double solve_ms;           /* device time of the whole call in ms                               */
+} sda_solve_stats;
+
+SDA_API int sda_get_solve_stats(const sda_operator *op, sda_solve_stats *stats);
+
+/* Number of kernels libsda has launched in this process (graph replays count
+ * every kernel of the graph).  Instrumentation for benchmarks. */
+SDA_API int64_t sda_kernel_launch_count(void);
 
 /* Sizes of an operator. */
 typedef struct {

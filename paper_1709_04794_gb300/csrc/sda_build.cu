@@ -1,0 +1,547 @@
+// sda_build_operator: everything the solves of one (X, S, labels) share.
+//
+//  - X is validated, its features relabelled by descending column count
+//    (stable in the feature id), and stored twice in the compute dtype: CSR
+//    with the new column ids and CSC (new column order, rows ascending), the
+//    CSC built by a stable radix sort of the nonzeros by column.
+//  - S is validated (CSR, weights >= 0) and checked to equal its transpose;
+//    the degrees D_ii = sum_j s_ij of L = D - S (Sec. 2.3) are formed.
+//  - For every target: l, N+, N-, and from the exact column sums
+//    X^T 1_+ and X^T 1_- (Alg. 7 step 3): mu_l = (X^T 1_+ + X^T 1_-) / l and
+//    d = X^T 1_+ / N+ - X^T 1_- / N-.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sda_kernels.cuh"
+
+namespace sda {
+
+enum : int {
+    kErrIndex = 1,
+    kErrInexact = 2,
+    kErrNonFinite = 4,
+    kErrWeight = 8,
+    kErrAsym = 16,
+    kErrLabel = 32,
+    kErrRowPtr = 64,
+};
+
+// ---------------------------------------------------------------------------
+// conversions
+// ---------------------------------------------------------------------------
+template <class T>
+struct Store;
+template <>
+struct Store<double> {
+    static __device__ __forceinline__ double make(double x) { return x; }
+    static __device__ __forceinline__ double back(double x) { return x; }
+};
+template <>
+struct Store<float> {
+    static __device__ __forceinline__ float make(double x) { return (float)x; }
+    static __device__ __forceinline__ double back(float x) { return (double)x; }
+};
+template <>
+struct Store<__half> {
+    static __device__ __forceinline__ __half make(double x) { return __double2half(x); }
+    static __device__ __forceinline__ double back(__half x) { return (double)__half2float(x); }
+};
+template <>
+struct Store<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ __nv_fp8_e4m3 make(double x) { return __nv_fp8_e4m3((float)x); }
+    static __device__ __forceinline__ double back(__nv_fp8_e4m3 x) { return (double)float(x); }
+};
+
+__device__ __forceinline__ double load_in(const void *v, int dtype, int64_t e) {
+    if (dtype == SDA_F64) return ((const double *)v)[e];
+    if (dtype == SDA_F32) return (double)((const float *)v)[e];
+    return 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+__global__ void k_check_csr(int64_t n, int64_t ncols, const int64_t *rp, const int32_t *col, const void *val,
+                            int dtype, int nonneg, int *err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = rp[i], b = rp[i + 1];
+        if (b < a) {
+            atomicOr(err, kErrRowPtr);
+            continue;
+        }
+        int32_t prev = -1;
+        for (int64_t e = a; e < b; ++e) {
+            const int32_t c = col[e];
+            if (c < 0 || c >= ncols || c <= prev) atomicOr(err, kErrIndex);
+            prev = c;
+            if (val) {
+                const double x = load_in(val, dtype, e);
+                if (!isfinite(x)) atomicOr(err, kErrNonFinite);
+                if (nonneg && x < 0.0) atomicOr(err, kErrWeight);
+            }
+        }
+    }
+}
+
+__global__ void k_col_count(int64_t nnz, const int32_t *col, unsigned long long *cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[col[e]], 1ull);
+}
+
+__global__ void k_perm_keys(int64_t d, const unsigned long long *cnt, unsigned long long maxc, uint32_t *keys,
+                            uint32_t *vals) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+        keys[j] = (uint32_t)(maxc - cnt[j]);
+        vals[j] = (uint32_t)j;
+    }
+}
+
+__global__ void k_perm_finish(int64_t d, const uint32_t *old_sorted, const unsigned long long *cnt,
+                              int32_t *old_of_new, int32_t *new_of_old, int64_t *cp) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < d; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = (int32_t)old_sorted[k];
+        old_of_new[k] = o;
+        new_of_old[o] = (int32_t)k;
+        cp[k] = (int64_t)cnt[o];
+    }
+}
+
+__global__ void k_relabel(int64_t nnz, const int32_t *col_in, const int32_t *new_of_old, int32_t *col_out,
+                          uint32_t *keys, uint32_t *vals) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = new_of_old ? new_of_old[col_in[e]] : col_in[e];
+        col_out[e] = c;
+        keys[e] = (uint32_t)c;
+        vals[e] = (uint32_t)e;
+    }
+}
+
+__global__ void k_expand_rows(int64_t n, const int64_t *rp, int32_t *row_of) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) row_of[e] = (int32_t)i;
+}
+
+__global__ void k_gather_rows(int64_t nnz, const uint32_t *src, const int32_t *row_of, int32_t *out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = row_of[src[k]];
+}
+
+// out[k] = store(in[src ? src[k] : k]); flags values that do not survive the round trip
+template <class OUT>
+__global__ void k_convert(int64_t m, const void *in, int dtype, const uint32_t *src, OUT *out, int *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = src ? (int64_t)src[k] : k;
+        const double x = load_in(in, dtype, e);
+        const OUT y = Store<OUT>::make(x);
+        if (Store<OUT>::back(y) != x) atomicOr(err, kErrInexact);
+        out[k] = y;
+    }
+}
+
+// pattern storage: every value must be exactly one
+__global__ void k_check_ones(int64_t m, const void *in, int dtype, int *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        if (load_in(in, dtype, k) != 1.0) atomicOr(err, kErrInexact);
+}
+
+// S == S^T: the k-th nonzero of S^T (sorted by column of S, stable) must match the k-th of S
+__global__ void k_check_sym(int64_t nnz, const uint32_t *tkey, const uint32_t *tsrc, const int32_t *row_of,
+                            const int32_t *col, const void *val, int dtype, int *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = tsrc[k];
+        const bool same = ((int32_t)tkey[k] == row_of[k]) && (row_of[e] == col[k]) &&
+                          (!val || load_in(val, dtype, e) == load_in(val, dtype, k));
+        if (!same) atomicOr(err, kErrAsym);
+    }
+}
+
+// degrees from the stored weights (FP64 sums), FP64 and vector-type copies
+template <class FT>
+__global__ void k_degrees(int64_t n, const int64_t *rp, const void *val, int dtype, double *s64, FT *sft,
+                          double *deg64, FT *degft) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0, sf = 0.0;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const double x = load_in(val, dtype, e);
+            s64[e] = x;
+            if (sft) {
+                const FT xf = (FT)x;
+                sft[e] = xf;
+                sf += (double)xf;
+            }
+            s += x;
+        }
+        deg64[i] = s;
+        if (degft) degft[i] = (FT)sf;
+    }
+}
+
+__global__ void k_check_labels(int64_t m, const int8_t *y, int *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        if (y[k] < -1 || y[k] > 1) atomicOr(err, kErrLabel);
+}
+
+__global__ void k_indicators(int64_t n, const int8_t *y, double *ip, double *in_, unsigned long long *cnt) {
+    unsigned long long cp = 0, cn = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        ip[i] = y[i] > 0 ? 1.0 : 0.0;
+        in_[i] = y[i] < 0 ? 1.0 : 0.0;
+        cp += y[i] > 0;
+        cn += y[i] < 0;
+    }
+    cp = warp_sum(cp);
+    cn = warp_sum(cn);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&cnt[0], cp);
+        atomicAdd(&cnt[1], cn);
+    }
+}
+
+__global__ void k_means(int64_t d, const double *sp, const double *sn, double npos, double nneg, double *mu,
+                        double *dv) {
+    const double ell = npos + nneg;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+        mu[j] = (sp[j] + sn[j]) / ell;
+        dv[j] = sp[j] / npos - sn[j] / nneg;
+    }
+}
+
+static int grid1(int64_t work, int sms) {
+    int64_t g = (work + kBlock - 1) / kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
+}
+
+static int bits_for(unsigned long long v) {
+    int b = 0;
+    while (b < 64 && (v >> b) != 0ull) ++b;
+    return b;
+}
+
+static int read_err(DevBuf<int> &err, cudaStream_t s, int *host) {
+    SDA_CUDA(cudaMemcpyAsync(host, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    return SDA_OK;
+}
+
+// copies a host or device array to a new device buffer
+template <class T>
+static int to_device(DevBuf<T> &dst, const void *src, int64_t count, int on_device, cudaStream_t s) {
+    SDA_TRY(dst.alloc((size_t)std::max<int64_t>(count, 1)));
+    if (count > 0)
+        SDA_CUDA(cudaMemcpyAsync(dst.p, src, (size_t)count * sizeof(T),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return SDA_OK;
+}
+
+static size_t dtype_size(int dt) {
+    switch (dt) {
+    case SDA_F64: return 8;
+    case SDA_F32: return 4;
+    case SDA_F16: return 2;
+    case SDA_F8E4M3: return 1;
+    default: return 0;
+    }
+}
+
+template <class OUT>
+static int convert(int64_t m, const void *in, int dtype, const uint32_t *src, void *out, int *err, int sms,
+                   cudaStream_t s) {
+    k_convert<OUT><<<grid1(m, sms), kBlock, 0, s>>>(m, in, dtype, src, (OUT *)out, err);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
+static int convert_any(int compute, int64_t m, const void *in, int dtype, const uint32_t *src, void *out, int *err,
+                       int sms, cudaStream_t s) {
+    switch (compute) {
+    case SDA_F64: return convert<double>(m, in, dtype, src, out, err, sms, s);
+    case SDA_F32: return convert<float>(m, in, dtype, src, out, err, sms, s);
+    case SDA_F16: return convert<__half>(m, in, dtype, src, out, err, sms, s);
+    case SDA_F8E4M3: return convert<__nv_fp8_e4m3>(m, in, dtype, src, out, err, sms, s);
+    default: return fail(SDA_ERR_INVALID_ARG, "unknown compute dtype %d", compute);
+    }
+}
+
+static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double alpha, double omega,
+                 sda_dtype compute, cudaStream_t s, sda_operator *op) {
+    const int64_t n = X->n_rows, d = X->n_cols, nnz = X->nnz, snz = S->nnz;
+    const int sms = op->sm_count;
+    const int x_in_dt = X->values ? X->dtype : SDA_PATTERN;
+    const int s_in_dt = S->values ? S->dtype : SDA_PATTERN;
+    const bool fp64 = compute == SDA_F64;
+    int herr = 0;
+    DevBuf<int> err;
+    SDA_TRY(err.alloc(1));
+    SDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+
+    // ---- X: copy and validate ----------------------------------------------
+    DevBuf<int32_t> col_in;
+    DevBuf<char> val_in;
+    SDA_TRY(to_device(op->x_rp, X->row_ptr, n + 1, X->on_device, s));
+    SDA_TRY(to_device(col_in, X->col_idx, nnz, X->on_device, s));
+    if (X->values) {
+        const size_t vb = dtype_size(X->dtype);
+        SDA_TRY(val_in.alloc((size_t)std::max<int64_t>(nnz, 1) * vb));
+        if (nnz > 0)
+            SDA_CUDA(cudaMemcpyAsync(val_in.p, X->values, (size_t)nnz * vb,
+                                     X->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
+    int64_t ends[2];
+    SDA_CUDA(cudaMemcpyAsync(&ends[0], op->x_rp.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaMemcpyAsync(&ends[1], op->x_rp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || ends[1] != nnz)
+        return fail(SDA_ERR_INDEX, "X row_ptr must start at 0 and end at nnz (got %lld .. %lld, nnz %lld)",
+                    (long long)ends[0], (long long)ends[1], (long long)nnz);
+    k_check_csr<<<grid1(n, sms), kBlock, 0, s>>>(n, d, op->x_rp.p, col_in.p, X->values ? val_in.p : nullptr,
+                                                 x_in_dt, 0, err.p);
+    SDA_LAUNCHED();
+    SDA_TRY(read_err(err, s, &herr));
+    if (herr & (kErrIndex | kErrRowPtr))
+        return fail(SDA_ERR_INDEX, "X: row pointers not monotone or a column index out of range / not strictly "
+                                   "increasing within its row");
+    if (herr & kErrNonFinite) return fail(SDA_ERR_VALUE_NOT_EXACT, "X holds a non-finite value");
+
+    // ---- feature order by descending column count ---------------------------
+    DevBuf<unsigned long long> cnt;
+    SDA_TRY(cnt.alloc((size_t)std::max<int64_t>(d, 1)));
+    SDA_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)d * sizeof(unsigned long long), s));
+    k_col_count<<<grid1(nnz, sms), kBlock, 0, s>>>(nnz, col_in.p, cnt.p);
+    SDA_LAUNCHED();
+    std::vector<unsigned long long> hcnt((size_t)d);
+    SDA_CUDA(cudaMemcpyAsync(hcnt.data(), cnt.p, (size_t)d * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    unsigned long long maxc = 0;
+    for (auto c : hcnt) maxc = std::max(maxc, c);
+    SDA_TRY(op->new_of_old.alloc((size_t)d));
+    SDA_TRY(op->old_of_new.alloc((size_t)d));
+    SDA_TRY(op->x_cp.alloc((size_t)d + 1));
+    {
+        DevBuf<uint32_t> keys, vals;
+        SDA_TRY(keys.alloc((size_t)d));
+        SDA_TRY(vals.alloc((size_t)d));
+        k_perm_keys<<<grid1(d, sms), kBlock, 0, s>>>(d, cnt.p, maxc, keys.p, vals.p);
+        SDA_LAUNCHED();
+        SDA_TRY(radix_sort_pairs(keys.p, vals.p, d, bits_for(maxc), s));
+        k_perm_finish<<<grid1(d, sms), kBlock, 0, s>>>(d, vals.p, cnt.p, op->old_of_new.p, op->new_of_old.p,
+                                                       op->x_cp.p);
+        SDA_LAUNCHED();
+        SDA_CUDA(cudaMemsetAsync(op->x_cp.p + d, 0, sizeof(int64_t), s));
+        SDA_TRY(scan_exclusive_i64(op->x_cp.p, d + 1, s));
+    }
+
+    // ---- CSR with new column ids, CSC by stable sort on the column ------------
+    SDA_TRY(op->x_col.alloc((size_t)std::max<int64_t>(nnz, 1)));
+    SDA_TRY(op->x_row.alloc((size_t)std::max<int64_t>(nnz, 1)));
+    const size_t vsz = compute == SDA_PATTERN ? 0 : dtype_size(compute);
+    if (vsz) {
+        SDA_TRY(op->x_val_r.alloc((size_t)std::max<int64_t>(nnz, 1) * vsz));
+        SDA_TRY(op->x_val_c.alloc((size_t)std::max<int64_t>(nnz, 1) * vsz));
+    }
+    {
+        DevBuf<uint32_t> keys, vals;
+        DevBuf<int32_t> row_of;
+        SDA_TRY(keys.alloc((size_t)std::max<int64_t>(nnz, 1)));
+        SDA_TRY(vals.alloc((size_t)std::max<int64_t>(nnz, 1)));
+        SDA_TRY(row_of.alloc((size_t)std::max<int64_t>(nnz, 1)));
+        k_relabel<<<grid1(nnz, sms), kBlock, 0, s>>>(nnz, col_in.p, op->new_of_old.p, op->x_col.p, keys.p, vals.p);
+        SDA_LAUNCHED();
+        SDA_TRY(radix_sort_pairs(keys.p, vals.p, nnz, bits_for((unsigned long long)std::max<int64_t>(d - 1, 1)), s));
+        k_expand_rows<<<grid1(n, sms), kBlock, 0, s>>>(n, op->x_rp.p, row_of.p);
+        SDA_LAUNCHED();
+        k_gather_rows<<<grid1(nnz, sms), kBlock, 0, s>>>(nnz, vals.p, row_of.p, op->x_row.p);
+        SDA_LAUNCHED();
+        if (vsz) {
+            SDA_TRY(convert_any(compute, nnz, X->values ? (const void *)val_in.p : nullptr, x_in_dt, nullptr,
+                                op->x_val_r.p, err.p, sms, s));
+            SDA_TRY(convert_any(compute, nnz, X->values ? (const void *)val_in.p : nullptr, x_in_dt, vals.p,
+                                op->x_val_c.p, err.p, sms, s));
+        } else if (X->values) {
+            k_check_ones<<<grid1(nnz, sms), kBlock, 0, s>>>(nnz, val_in.p, x_in_dt, err.p);
+            SDA_LAUNCHED();
+        }
+        SDA_TRY(read_err(err, s, &herr));
+        if (herr & kErrInexact)
+            return fail(SDA_ERR_VALUE_NOT_EXACT, "a value of X is not exact in the compute dtype %d", (int)compute);
+    }
+
+    // ---- S -------------------------------------------------------------------
+    DevBuf<int32_t> s_col_in;
+    DevBuf<char> s_val_in;
+    SDA_TRY(to_device(op->s_rp, S->row_ptr, n + 1, S->on_device, s));
+    SDA_TRY(to_device(op->s_col, S->col_idx, snz, S->on_device, s));
+    if (S->values) {
+        const size_t vb = dtype_size(S->dtype);
+        SDA_TRY(s_val_in.alloc((size_t)std::max<int64_t>(snz, 1) * vb));
+        if (snz > 0)
+            SDA_CUDA(cudaMemcpyAsync(s_val_in.p, S->values, (size_t)snz * vb,
+                                     S->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
+    SDA_CUDA(cudaMemcpyAsync(&ends[0], op->s_rp.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaMemcpyAsync(&ends[1], op->s_rp.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    if (ends[0] != 0 || ends[1] != snz)
+        return fail(SDA_ERR_INDEX, "S row_ptr must start at 0 and end at nnz");
+    k_check_csr<<<grid1(n, sms), kBlock, 0, s>>>(n, n, op->s_rp.p, op->s_col.p, S->values ? s_val_in.p : nullptr,
+                                                 s_in_dt, 1, err.p);
+    SDA_LAUNCHED();
+    SDA_TRY(read_err(err, s, &herr));
+    if (herr & (kErrIndex | kErrRowPtr)) return fail(SDA_ERR_INDEX, "S: bad row pointers or column indices");
+    if (herr & (kErrWeight | kErrNonFinite)) return fail(SDA_ERR_NOT_SYMMETRIC, "S holds a negative or non-finite weight");
+    {
+        DevBuf<uint32_t> keys, vals;
+        DevBuf<int32_t> row_of;
+        SDA_TRY(keys.alloc((size_t)std::max<int64_t>(snz, 1)));
+        SDA_TRY(vals.alloc((size_t)std::max<int64_t>(snz, 1)));
+        SDA_TRY(row_of.alloc((size_t)std::max<int64_t>(snz, 1)));
+        k_relabel<<<grid1(snz, sms), kBlock, 0, s>>>(snz, op->s_col.p, nullptr, op->s_col.p, keys.p, vals.p);
+        SDA_LAUNCHED();
+        SDA_TRY(radix_sort_pairs(keys.p, vals.p, snz, bits_for((unsigned long long)std::max<int64_t>(n - 1, 1)), s));
+        k_expand_rows<<<grid1(n, sms), kBlock, 0, s>>>(n, op->s_rp.p, row_of.p);
+        SDA_LAUNCHED();
+        k_check_sym<<<grid1(snz, sms), kBlock, 0, s>>>(snz, keys.p, vals.p, row_of.p, op->s_col.p,
+                                                       S->values ? s_val_in.p : nullptr, s_in_dt, err.p);
+        SDA_LAUNCHED();
+        SDA_TRY(read_err(err, s, &herr));
+        if (herr & kErrAsym) return fail(SDA_ERR_NOT_SYMMETRIC, "S is not equal to its transpose");
+    }
+    SDA_TRY(op->s_val64.alloc((size_t)std::max<int64_t>(snz, 1)));
+    SDA_TRY(op->deg64.alloc((size_t)std::max<int64_t>(n, 1)));
+    if (fp64) {
+        k_degrees<double><<<grid1(n, sms), kBlock, 0, s>>>(n, op->s_rp.p, S->values ? s_val_in.p : nullptr, s_in_dt,
+                                                           op->s_val64.p, nullptr, op->deg64.p, nullptr);
+    } else {
+        SDA_TRY(op->s_val32.alloc((size_t)std::max<int64_t>(snz, 1)));
+        SDA_TRY(op->deg32.alloc((size_t)std::max<int64_t>(n, 1)));
+        k_degrees<float><<<grid1(n, sms), kBlock, 0, s>>>(n, op->s_rp.p, S->values ? s_val_in.p : nullptr, s_in_dt,
+                                                          op->s_val64.p, op->s_val32.p, op->deg64.p, op->deg32.p);
+    }
+    SDA_LAUNCHED();
+
+    // ---- labels ----------------------------------------------------------------
+    const int64_t T = y->n_targets;
+    SDA_TRY(to_device(op->labels, y->labels, T * n, y->on_device, s));
+    k_check_labels<<<grid1(T * n, sms), kBlock, 0, s>>>(T * n, op->labels.p, err.p);
+    SDA_LAUNCHED();
+    SDA_TRY(read_err(err, s, &herr));
+    if (herr & kErrLabel) return fail(SDA_ERR_INVALID_ARG, "labels must be -1, 0 or +1");
+
+    // ---- column schedule of the X^T pass -----------------------------------------
+    {
+        std::vector<int64_t> hcp((size_t)d + 1);
+        SDA_CUDA(cudaMemcpyAsync(hcp.data(), op->x_cp.p, ((size_t)d + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SDA_CUDA(cudaStreamSynchronize(s));
+        SDA_TRY(build_col_schedule(hcp, op->col));
+    }
+    SDA_TRY(op->slots.alloc((size_t)std::max(op->col.nslots, 1)));
+    SDA_TRY(op->lcount.alloc((size_t)std::max(op->col.nsplits, 1)));
+    SDA_CUDA(cudaMemsetAsync(op->lcount.p, 0, op->lcount.bytes(), s));
+    SDA_TRY(op->part.alloc((size_t)op->grid * 4));
+    SDA_TRY(op->cnt.alloc(4));
+    SDA_CUDA(cudaMemsetAsync(op->cnt.p, 0, op->cnt.bytes(), s));
+    SDA_TRY(op->scal.alloc(8));
+
+    // ---- per-target counts and means (Alg. 7 step 3) ---------------------------------
+    SDA_TRY(op->mu.alloc((size_t)(T * d)));
+    SDA_TRY(op->dvec.alloc((size_t)(T * d)));
+    op->counts.assign((size_t)T * 3, 0.0);
+    {
+        DevBuf<double> ip, in_, sp, sn;
+        DevBuf<unsigned long long> c2;
+        SDA_TRY(ip.alloc((size_t)n));
+        SDA_TRY(in_.alloc((size_t)n));
+        SDA_TRY(sp.alloc((size_t)d));
+        SDA_TRY(sn.alloc((size_t)d));
+        SDA_TRY(c2.alloc(2));
+        for (int64_t t = 0; t < T; ++t) {
+            SDA_CUDA(cudaMemsetAsync(c2.p, 0, 2 * sizeof(unsigned long long), s));
+            k_indicators<<<grid1(n, sms), kBlock, 0, s>>>(n, op->labels.p + t * n, ip.p, in_.p, c2.p);
+            SDA_LAUNCHED();
+            SDA_TRY(op_xtmul_f64(op, ip.p, sp.p, s));
+            SDA_TRY(op_xtmul_f64(op, in_.p, sn.p, s));
+            unsigned long long hc[2];
+            SDA_CUDA(cudaMemcpyAsync(hc, c2.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+            SDA_CUDA(cudaStreamSynchronize(s));
+            if (hc[0] == 0) return fail(SDA_ERR_NO_POSITIVE, "target %lld has no labelled positive sample", (long long)t);
+            if (hc[1] == 0) return fail(SDA_ERR_NO_NEGATIVE, "target %lld has no labelled negative sample", (long long)t);
+            op->counts[t * 3 + 0] = (double)(hc[0] + hc[1]);
+            op->counts[t * 3 + 1] = (double)hc[0];
+            op->counts[t * 3 + 2] = (double)hc[1];
+            k_means<<<grid1(d, sms), kBlock, 0, s>>>(d, sp.p, sn.p, (double)hc[0], (double)hc[1], op->mu.p + t * d,
+                                                     op->dvec.p + t * d);
+            SDA_LAUNCHED();
+        }
+        SDA_CUDA(cudaStreamSynchronize(s));
+    }
+    return SDA_OK;
+}
+
+static int lanes_for_rows(int64_t nnz, int64_t n) {
+    const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+    int g = 2;
+    while (g < 32 && 2 * g < avg) g <<= 1;
+    return g;
+}
+
+}  // namespace sda
+
+using namespace sda;
+
+extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, const sda_labels *y, double alpha,
+                                          double scatter_weight, sda_dtype compute, void *cuda_stream,
+                                          sda_operator **out) {
+    clear_error();
+    if (!out) return fail(SDA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!X || !S || !y) return fail(SDA_ERR_INVALID_ARG, "X, S and y must not be NULL");
+    if (!X->row_ptr || (X->nnz > 0 && !X->col_idx) || !S->row_ptr || (S->nnz > 0 && !S->col_idx) || !y->labels)
+        return fail(SDA_ERR_INVALID_ARG, "missing array");
+    if (X->n_rows <= 0 || X->n_cols <= 0 || X->nnz < 0 || S->nnz < 0 || y->n_targets <= 0)
+        return fail(SDA_ERR_SHAPE, "empty X or no targets");
+    if (S->n_rows != X->n_rows || S->n_cols != X->n_rows)
+        return fail(SDA_ERR_SHAPE, "S must be N x N with N = rows of X");
+    if (X->n_cols > INT32_MAX || X->n_rows > INT32_MAX || X->nnz > (int64_t)UINT32_MAX || S->nnz > (int64_t)UINT32_MAX)
+        return fail(SDA_ERR_SHAPE, "sizes beyond 32-bit indexing");
+    if (X->values && X->dtype != SDA_F64 && X->dtype != SDA_F32)
+        return fail(SDA_ERR_INVALID_ARG, "X values must be F64 or F32 (or NULL for a pattern)");
+    if (S->values && S->dtype != SDA_F64 && S->dtype != SDA_F32)
+        return fail(SDA_ERR_INVALID_ARG, "S values must be F64 or F32 (or NULL for all-ones weights)");
+    if (compute < SDA_F64 || compute > SDA_PATTERN) return fail(SDA_ERR_INVALID_ARG, "bad compute dtype");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(SDA_ERR_INVALID_ARG, "alpha must be in [0, 1]");
+    const double omega = isnan(scatter_weight) ? 1.0 - alpha : scatter_weight;
+    if (!(omega >= 0.0) || !isfinite(omega)) return fail(SDA_ERR_INVALID_ARG, "scatter weight must be >= 0");
+    sda_operator *op = new (std::nothrow) sda_operator();
+    if (!op) return fail(SDA_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&op->device);
+    op->n = X->n_rows;
+    op->d = X->n_cols;
+    op->nnz = X->nnz;
+    op->s_nnz = S->nnz;
+    op->n_targets = y->n_targets;
+    op->compute = compute;
+    op->alpha = alpha;
+    op->omega = omega;
+    op->sm_count = device_sm_count();
+    if (op->sm_count <= 0) {
+        delete op;
+        return fail(SDA_ERR_CUDA, "no CUDA device");
+    }
+    op->grid = op->sm_count * 4;
+    op->x_lanes = lanes_for_rows(X->nnz, X->n_rows);
+    op->s_lanes = lanes_for_rows(S->nnz, X->n_rows);
+    int rc = build(X, S, y, alpha, omega, compute, (cudaStream_t)cuda_stream, op);
+    if (rc < 0) {
+        cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        delete op;
+        return rc;
+    }
+    op->bytes = (int64_t)(op->new_of_old.bytes() + op->old_of_new.bytes() + op->x_rp.bytes() + op->x_cp.bytes() +
+                          op->x_col.bytes() + op->x_row.bytes() + op->x_val_r.bytes() + op->x_val_c.bytes() +
+                          op->s_rp.bytes() + op->s_col.bytes() + op->s_val64.bytes() + op->s_val32.bytes() +
+                          op->deg64.bytes() + op->deg32.bytes() + op->labels.bytes() + op->mu.bytes() +
+                          op->dvec.bytes() + op->col.tiles.bytes() + op->col.splits.bytes());
+    *out = op;
+    return SDA_OK;
+}

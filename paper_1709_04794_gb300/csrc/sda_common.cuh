@@ -1,0 +1,203 @@
+// Internal definitions shared by the translation units of libsda.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sda.h"
+
+namespace sda {
+
+constexpr int kBlock = 256;          // threads per block of every pass kernel
+constexpr int kMaxShifts = 64;       // shifts per solve
+constexpr int kTileNnz = 4096;       // nonzeros per column tile / split chunk
+constexpr int kTileSegs = 1024;      // columns per multi-column tile
+constexpr int kBigSeg = 256;         // columns longer than this get whole-block tiles
+
+// ---------------------------------------------------------------------------
+// errors (thread-local last error, no exceptions across the ABI)
+// ---------------------------------------------------------------------------
+int fail(int code, const char *fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define SDA_CUDA(expr)                                                          \
+    do {                                                                        \
+        cudaError_t e_ = (expr);                                                \
+        if (e_ != cudaSuccess) return ::sda::cuda_fail(e_, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+// kernel launch accounting (instrumentation): every launch site calls
+// SDA_LAUNCHED() right after the launch; launches recorded into a graph
+// capture are not counted, graph replays count their kernels
+void note_launch(int64_t n);
+void set_capturing(bool on);
+#define SDA_LAUNCHED()                                                          \
+    do {                                                                        \
+        ::sda::note_launch(1);                                                  \
+        SDA_CUDA(cudaGetLastError());                                           \
+    } while (0)
+
+#define SDA_TRY(expr)                   \
+    do {                                \
+        int rc_ = (expr);               \
+        if (rc_ < 0) return rc_;        \
+    } while (0)
+
+// device allocation helper: frees on destruction
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    int alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();
+            return fail(SDA_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
+                        cudaGetErrorString(e));
+        }
+        n = count;
+        return SDA_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+// ---------------------------------------------------------------------------
+// column tiles of the X^T pass (built on the host from the column pointers)
+// ---------------------------------------------------------------------------
+struct Tile {
+    int64_t nz0, nz1;   // nonzero range (whole-block tiles)
+    int32_t seg0, seg1; // column range
+    int32_t lanes;      // > 0: multi-column tile, lanes per column; 0: whole-block tile
+    int32_t slot;       // split chunk: slot of its partial sum; -1: the tile holds the whole column
+    int32_t lseg;       // split chunk: index of its long column in the split tables
+    int32_t pad;
+};
+
+struct SplitSeg {
+    int32_t slot0;      // first slot of the column's chunks
+    int32_t nchunks;
+};
+
+struct ColSchedule {
+    DevBuf<Tile> tiles;
+    DevBuf<SplitSeg> splits;
+    int32_t ntiles = 0, nsplits = 0, nslots = 0;
+};
+
+int build_col_schedule(const std::vector<int64_t> &colptr, ColSchedule &out);
+
+// ---------------------------------------------------------------------------
+// value storage types
+// ---------------------------------------------------------------------------
+struct Pattern {};  // no stored values: every entry is one
+
+template <class VT>
+struct Val;
+template <>
+struct Val<double> {
+    static __device__ __forceinline__ double get(const double *v, int64_t e) { return v[e]; }
+};
+template <>
+struct Val<float> {
+    static __device__ __forceinline__ float get(const float *v, int64_t e) { return v[e]; }
+};
+template <>
+struct Val<__half> {
+    static __device__ __forceinline__ float get(const __half *v, int64_t e) { return __half2float(v[e]); }
+};
+template <>
+struct Val<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ float get(const __nv_fp8_e4m3 *v, int64_t e) { return float(v[e]); }
+};
+template <>
+struct Val<Pattern> {
+    static __device__ __forceinline__ float get(const Pattern *, int64_t) { return 1.0f; }
+};
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block in a fixed order; the result is returned to every thread.
+// `red` holds kBlock/32 entries.  Contains __syncthreads().
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T *red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < kBlock / 32; ++i) s += red[i];
+    return s;
+}
+
+// Grid-wide "last block" protocol: every block stores its NDOT partials, the
+// block that arrives last sees all of them.  Returns true in that block only
+// (for every thread of it).  The counter is reset by the caller.
+template <int NDOT>
+__device__ __forceinline__ bool arrive_last(const double *mine, double *partials, unsigned *counter) {
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) partials[(int64_t)blockIdx.x * NDOT + k] = mine[k];
+        __threadfence();
+        unsigned prev = atomicAdd(counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last != 0;
+}
+
+// Fixed-order sum of the grid's partials (called by every thread of the last block).
+template <int NDOT>
+__device__ __forceinline__ void reduce_partials(const double *partials, int nblocks, double *out,
+                                                double *red) {
+#pragma unroll
+    for (int k = 0; k < NDOT; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += kBlock) s += __ldcg(partials + (int64_t)b * NDOT + k);
+        s = block_sum(s, red);
+        out[k] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// primitives (sda_primitives.cu)
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (key, value) pairs on the low `key_bits` bits of
+// the keys.  Sorted data ends in keys/vals.  Temporary buffers are allocated
+// by the call.
+int radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, cudaStream_t s);
+// Exclusive prefix sum in place (int64).
+int scan_exclusive_i64(int64_t *data, int64_t n, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace sda

@@ -1,0 +1,119 @@
+// The operator object behind the opaque sda_operator handle, and the solve
+// state shared between the host driver and the kernels.
+#pragma once
+
+#include "sda_common.cuh"
+
+namespace sda {
+
+// Per-shift recurrence state of Algorithm 3 (FP64), indexed by shift.
+struct ShiftState {
+    double delta;    // beta_s - sigma0 (shift relative to the base system)
+    double z_prev;   // zeta_{k-1}
+    double z;        // zeta_k
+    double z_next;   // zeta_{k+1} (set when gamma_k is known)
+    double g;        // gamma^s_k = gamma_k zeta_{k+1} / zeta_k
+    double a;        // alpha^s_k: P_k = zeta_k r_k + alpha^s_k P_{k-1}
+    double res;      // |zeta| ||r|| / ||b|| after the last update
+    int32_t active;  // 0 once the shift has stopped
+    int32_t iters;   // iteration count when it stopped (or so far)
+};
+
+// Scalars of one shifted-CG run, read by every phase kernel, written by the
+// last block of the phase that completes them.
+struct SolveState {
+    // fixed for the run
+    double sigma0, omega, alpha_l, tol, bnorm;
+    int32_t n_shifts, limit, fixed;
+    int32_t pad0;
+    const int8_t *labels;   // labels of the target being solved
+    const double *mu;       // its mu_l (permuted feature order)
+    // iteration
+    int32_t k;              // iterations completed
+    int32_t done;
+    int32_t status;         // SDA_OK or SDA_ERR_BREAKDOWN
+    int32_t nactive;
+    double rr;              // <r_k, r_k>
+    double alpha;           // alpha_k: p_k = r_k + alpha_k p_{k-1}
+    double c;               // <mu_l, p_k>
+    double pp;              // <p_k, p_k>
+    double gamma;           // gamma_k = -<r_k, r_k> / <p_k, (B + sigma0) p_k>
+    double gamma_prev;      // gamma_{k-1}
+    double t;               // 1^T v_k
+    ShiftState sh[kMaxShifts];
+};
+
+struct Workspace {
+    int fp64 = -1;
+    int64_t d = 0, n = 0;
+    int n_shifts = 0;
+    DevBuf<char> vec;        // r, p (D), ut, v (N) in the vector type
+    DevBuf<char> shift;      // W, P ([S][D] each) in the vector type
+    DevBuf<SolveState> st;
+    DevBuf<double> part;     // [3][grid][4] block partials of init / phase 2 / phase 3
+    DevBuf<unsigned> cnt;    // grid arrival counters of init / phase 2 / phase 3
+    DevBuf<double> f64;      // FP64 scratch: b (D), w (D), q (D)
+    DevBuf<double> dev_b;    // right-hand sides of the call's targets [T][D]
+    SolveState *h_st = nullptr;   // pinned host mirror of the state
+    std::vector<cudaEvent_t> prof_ev;  // profile mode: start/end event of every phase launch of a batch
+    cudaEvent_t call_ev[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    cudaStream_t cap_stream = nullptr;
+};
+
+}  // namespace sda
+
+struct sda_operator {
+    int device = 0;
+    int64_t n = 0, d = 0, nnz = 0, s_nnz = 0;
+    int32_t n_targets = 0;
+    sda_dtype compute = SDA_F64;
+    double alpha = 0.0, omega = 1.0;
+    int sm_count = 0;
+
+    // feature order: columns sorted by descending count (new index = rank)
+    sda::DevBuf<int32_t> new_of_old, old_of_new;
+    // X in CSR (columns renumbered) and CSC (new column order, rows ascending)
+    sda::DevBuf<int64_t> x_rp, x_cp;
+    sda::DevBuf<int32_t> x_col, x_row;
+    sda::DevBuf<char> x_val_r, x_val_c;   // compute dtype (empty for PATTERN)
+    // graph S (CSR) and degrees D_ii; FP32 copies for the mixed path
+    sda::DevBuf<int64_t> s_rp;
+    sda::DevBuf<int32_t> s_col;
+    sda::DevBuf<double> s_val64, deg64;
+    sda::DevBuf<float> s_val32, deg32;
+    // targets
+    sda::DevBuf<int8_t> labels;          // [T][N]
+    sda::DevBuf<double> mu;              // [T][D] mu_l, permuted order
+    sda::DevBuf<double> dvec;            // [T][D] mu_+ - mu_-, permuted order
+    std::vector<double> counts;          // [T][3]: l, N+, N-
+    // schedule of the X^T pass
+    sda::ColSchedule col;
+    int x_lanes = 32, s_lanes = 8;       // lanes per row of the X and S row passes
+    int grid = 0;                         // blocks of every persistent-style pass
+    int64_t bytes = 0;
+    // scratch of the column pass and of the FP64 reductions
+    sda::DevBuf<double> slots;            // split-column partial sums
+    sda::DevBuf<unsigned> lcount;         // split-column arrival counters (kept at zero)
+    sda::DevBuf<double> part;             // block partials of the FP64 reductions
+    sda::DevBuf<unsigned> cnt;            // their arrival counters (kept at zero)
+    sda::DevBuf<double> scal;             // device scalars of the FP64 operator apply
+
+    sda::Workspace ws;
+    sda_solve_stats stats{};
+};
+
+namespace sda {
+// launchers implemented in sda_solve.cu / sda_build.cu
+int op_apply_f64(const sda_operator *op, int target, double sigma, const double *p_perm, double *q_perm,
+                 cudaStream_t s);
+int op_xmul_f64(const sda_operator *op, const double *w_perm, double *u, const double *csub_dev, cudaStream_t s);
+int op_xtmul_f64(const sda_operator *op, const double *v, double *q, cudaStream_t s);
+int permute_to_new(const sda_operator *op, const double *old_order, double *new_order, int64_t count,
+                   cudaStream_t s);
+int permute_to_old(const sda_operator *op, const double *new_order, double *old_order, int64_t count,
+                   cudaStream_t s);
+void release_workspace(sda_operator *op);
+int64_t launch_count();
+}  // namespace sda

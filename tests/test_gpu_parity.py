@@ -1,0 +1,332 @@
+"""CUDA path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (derivation in DESIGN.md, "Parity bar"):
+* FP64 path, same iterations: the two sides differ only in summation order,
+  ~1e-16 per operation, amplified along the Krylov recurrence on the
+  ill-conditioned shifts: 1e-9 relative after <= 40 iterations.
+* FP64 path, converged to tol 1e-10: 1e-6 relative on w per shift (the
+  spec bar), AUC equal to 4 decimals.
+* Mixed path (FP32 vectors, FP64 scalars): converged to tol, its FP64 true
+  residual stays within a small factor of tol; w within kappa_s x residual of
+  the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_04794_gb300 import sda, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_solve(prob, compute="f64", tol=1e-10, max_iter=20000, fixed=0, graph=1, batch=0, rhs_mode=0,
+              rhs=None, targets=None, check=1, profile=0):
+    op = sda.Operator(prob, compute=compute, targets=targets)
+    T = op.info["n_targets"]
+    ns, d = len(prob.shifts), prob.d
+    w = torch.empty((T, ns, d), dtype=torch.float64, device="cuda")
+    o = sda.sda_default_opts()
+    o.tol, o.max_iter, o.fixed_iters = tol, max_iter, fixed
+    o.use_graph, o.iter_batch, o.rhs_mode, o.check_residual, o.profile = graph, batch, rhs_mode, check, profile
+    code, rep = sda.sda_solve_shifts(op.handle, prob.shifts, o, w_out=w, n_report=T, rhs=rhs)
+    return op, code, rep, w.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def skewed():
+    """9,000 rows: the most common features have > 4,096 nonzeros, so their
+    columns are split over several tiles; ragged sizes everywhere."""
+    return synth.custom_problem(9001, 3001, 22, seed=5, values="counts", n_labelled=700, k=6,
+                                shifts=(1e-3, 1e2, 7))
+
+
+# ---------------------------------------------------------------------------
+# operator
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("compute", ["f64", "f32", "f16", "f8e4m3"])
+def test_operator_apply_matches_oracle(skewed, compute):
+    op = sda.Operator(skewed, compute=compute)
+    o = oracle.from_problem(skewed)
+    rng = np.random.default_rng(0)
+    for sigma in (0.0, 0.5):
+        p = rng.standard_normal(skewed.d)
+        q = torch.empty(skewed.d, dtype=torch.float64, device="cuda")
+        sda.sda_operator_apply(op.handle, 0, sigma, torch.from_numpy(p).cuda(), q)
+        assert _rel(q.cpu().numpy(), o.apply(p, sigma)) < 1e-12
+
+
+def test_operator_apply_cfg1_pattern(cfg1):
+    op = sda.Operator(cfg1, compute="pattern")
+    o = oracle.from_problem(cfg1)
+    p = np.random.default_rng(1).standard_normal(cfg1.d)
+    q = torch.empty(cfg1.d, dtype=torch.float64, device="cuda")
+    sda.sda_operator_apply(op.handle, 0, 0.25, torch.from_numpy(p).cuda(), q)
+    assert _rel(q.cpu().numpy(), o.apply(p, 0.25)) < 1e-12
+
+
+def test_target_counts_and_info(cfg1):
+    op = sda.Operator(cfg1, compute="f64")
+    c = sda.sda_get_target_counts(op.handle, 1)[0]
+    y = cfg1.labels[0]
+    assert list(c) == [(y != 0).sum(), (y > 0).sum(), (y < 0).sum()]
+    assert op.info["n_rows"] == cfg1.n and op.info["nnz"] == cfg1.x_ptr[-1]
+
+
+# ---------------------------------------------------------------------------
+# solves
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 7, 40])
+def test_fixed_iterations_fp64_match_oracle(cfg1, k):
+    _, code, rep, w = gpu_solve(cfg1, "f64", fixed=k)
+    assert code == sda.SDA_OK
+    o = oracle.from_problem(cfg1)
+    ref = o.shifted_cg(o.rhs_canonical(), cfg1.shifts, fixed_iters=k)
+    for s in range(len(cfg1.shifts)):
+        assert rep[0][s]["iters"] == k
+        assert _rel(w[0, s], ref.W[s]) < 1e-9, (k, s, _rel(w[0, s], ref.W[s]))
+        assert abs(rep[0][s]["est_residual"] - ref.res_est[s]) <= 1e-9 * ref.res_est[s] + 1e-15
+
+
+def test_converged_fp64_matches_oracle(cfg1):
+    _, code, rep, w = gpu_solve(cfg1, "f64", tol=1e-10)
+    assert code == sda.SDA_OK
+    o = oracle.from_problem(cfg1)
+    ref = o.shifted_cg(o.rhs_canonical(), cfg1.shifts, tol=1e-10, max_iter=20000)
+    unl = np.nonzero(cfg1.labels[0] == 0)[0]
+    for s in range(len(cfg1.shifts)):
+        assert _rel(w[0, s], ref.W[s]) < 1e-6, (s, _rel(w[0, s], ref.W[s]))
+        assert abs(rep[0][s]["iters"] - int(ref.iters[s])) <= 2
+        assert rep[0][s]["true_residual"] < 2e-10
+        a_gpu = oracle.auc(o.project(w[0, s])[unl], cfg1.truth[0][unl])
+        a_ref = oracle.auc(o.project(ref.W[s])[unl], cfg1.truth[0][unl])
+        assert abs(a_gpu - a_ref) < 5e-5
+
+
+@pytest.mark.parametrize("compute", ["f32", "f16", "f8e4m3", "pattern"])
+def test_mixed_paths_reach_tolerance(cfg1, compute):
+    tol = 1e-5
+    _, code, rep, w = gpu_solve(cfg1, compute, tol=tol)
+    assert code == sda.SDA_OK
+    o = oracle.from_problem(cfg1)
+    ref = o.shifted_cg(o.rhs_canonical(), cfg1.shifts, tol=1e-12, max_iter=20000)
+    for s, beta in enumerate(cfg1.shifts):
+        tr = rep[0][s]["true_residual"]
+        assert tr < 20 * tol, (s, tr)
+        # the oracle's own check of the GPU solution
+        assert abs(o.true_residual(o.rhs_canonical(), beta, w[0, s]) - tr) <= 1e-3 * tr + 1e-14
+
+
+def test_graph_and_plain_launches_identical(cfg1):
+    _, c1, r1, w1 = gpu_solve(cfg1, "f16", tol=1e-6, graph=1, batch=8)
+    _, c2, r2, w2 = gpu_solve(cfg1, "f16", tol=1e-6, graph=0, batch=8)
+    _, c3, r3, w3 = gpu_solve(cfg1, "f16", tol=1e-6, graph=1, batch=8)
+    assert np.array_equal(w1, w2) and np.array_equal(w1, w3)   # deterministic kernels
+    assert [r["iters"] for r in r1[0]] == [r["iters"] for r in r2[0]]
+
+
+def test_rhs_from_r_matches_paper_form(cfg1):
+    r = synth.random_r(77, cfg1.d)
+    _, code, rep, w = gpu_solve(cfg1, "f64", fixed=25, rhs_mode=sda.SDA_RHS_FROM_R, rhs=r)
+    o = oracle.from_problem(cfg1)
+    b = o.rhs_from_r(r)     # literal (X - 1 mu^T)^T [W 0; 0 0] X r
+    ref = o.shifted_cg(b, cfg1.shifts, fixed_iters=25)
+    for s in range(len(cfg1.shifts)):
+        assert _rel(w[0, s], ref.W[s]) < 1e-9
+
+
+def test_rhs_given(cfg1):
+    b = np.random.default_rng(3).standard_normal(cfg1.d)
+    _, code, rep, w = gpu_solve(cfg1, "f64", fixed=12, rhs_mode=sda.SDA_RHS_GIVEN, rhs=b[None, :])
+    o = oracle.from_problem(cfg1)
+    ref = o.shifted_cg(b, cfg1.shifts, fixed_iters=12)
+    for s in range(len(cfg1.shifts)):
+        assert _rel(w[0, s], ref.W[s]) < 1e-9
+
+
+def test_split_columns_and_ragged_tiles(skewed):
+    _, code, rep, w = gpu_solve(skewed, "f64", fixed=15)
+    o = oracle.from_problem(skewed)
+    ref = o.shifted_cg(o.rhs_canonical(), skewed.shifts, fixed_iters=15)
+    for s in range(len(skewed.shifts)):
+        assert _rel(w[0, s], ref.W[s]) < 1e-9
+
+
+def test_several_targets():
+    prob = synth.custom_problem(1500, 900, 15, seed=8, values="counts", n_targets=3, n_labelled=150, k=5,
+                                shifts=(1e-2, 1e1, 4))
+    _, code, rep, w = gpu_solve(prob, "f64", fixed=20)
+    for t in range(3):
+        o = oracle.Oracle(prob.x_ptr, prob.x_col, prob.x_val, prob.s_ptr, prob.s_col, prob.s_val,
+                          prob.labels[t], prob.d, prob.alpha)
+        ref = o.shifted_cg(o.rhs_canonical(), prob.shifts, fixed_iters=20)
+        for s in range(len(prob.shifts)):
+            assert _rel(w[t, s], ref.W[s]) < 1e-9
+
+
+def test_projection(cfg1):
+    op = sda.Operator(cfg1, compute="f16")
+    o = oracle.from_problem(cfg1)
+    W = np.random.default_rng(4).standard_normal((3, cfg1.d))
+    sc = torch.empty((3, cfg1.n), dtype=torch.float64, device="cuda")
+    sda.sda_project(op.handle, torch.from_numpy(W).cuda(), 3, sc)
+    for v in range(3):
+        assert _rel(sc[v].cpu().numpy(), o.project(W[v])) < 1e-14
+    mu, _, _, _ = o.class_means()
+    sda.sda_project(op.handle, torch.from_numpy(W).cuda(), 3, sc, centred=1, target=0)
+    for v in range(3):
+        assert _rel(sc[v].cpu().numpy(), o.project(W[v]) - mu @ W[v]) < 1e-13
+
+
+def test_host_output_and_inputs(cfg1):
+    """Host arrays in and out (the end-to-end path)."""
+    op = sda.Operator(cfg1, compute="f64")
+    ns = len(cfg1.shifts)
+    w = np.empty((1, ns, cfg1.d))
+    o = sda.sda_default_opts()
+    o.fixed_iters = 9
+    code, rep = sda.sda_solve_shifts(op.handle, cfg1.shifts, o, w_out=w, n_report=1)
+    orc = oracle.from_problem(cfg1)
+    ref = orc.shifted_cg(orc.rhs_canonical(), cfg1.shifts, fixed_iters=9)
+    for s in range(ns):
+        assert _rel(w[0, s], ref.W[s]) < 1e-10
+
+
+def test_device_inputs(cfg1):
+    op = sda.Operator(cfg1, compute="f64", device_inputs=True)
+    o = oracle.from_problem(cfg1)
+    p = np.random.default_rng(5).standard_normal(cfg1.d)
+    q = torch.empty(cfg1.d, dtype=torch.float64, device="cuda")
+    sda.sda_operator_apply(op.handle, 0, 0.0, torch.from_numpy(p).cuda(), q)
+    assert _rel(q.cpu().numpy(), o.apply(p)) < 1e-12
+
+
+def test_profile_stats(cfg1):
+    op, code, rep, w = gpu_solve(cfg1, "f16", tol=1e-6, profile=1)
+    st = sda.sda_get_solve_stats(op.handle)
+    assert st["iterations"] == max(r["iters"] for r in rep[0])
+    assert st["shift_iterations"] == sum(r["iters"] for r in rep[0])
+    assert all(m > 0 for m in st["ms"][1:]) and st["launches"][3] >= st["iterations"]
+
+
+# ---------------------------------------------------------------------------
+# errors and edge cases
+# ---------------------------------------------------------------------------
+
+def _expect(code, fn):
+    with pytest.raises(sda.SDAError) as e:
+        fn()
+    assert e.value.code == code
+
+
+def test_errors(tiny):
+    p = tiny
+    base = dict(x_ptr=p.x_ptr, x_col=p.x_col, x_val=p.x_val, n_cols=p.d, s_ptr=p.s_ptr, s_col=p.s_col,
+                s_val=p.s_val, labels=p.labels)
+
+    def build(compute="f64", **kw):
+        a = dict(base)
+        a.update(kw)
+        return sda.Operator(None, compute=compute, alpha=0.1, **a)
+
+    y = p.labels.copy()
+    y[y > 0] = -1
+    _expect(sda.SDA_ERR_NO_POSITIVE, lambda: build(labels=y))
+    y = p.labels.copy()
+    y[y < 0] = 1
+    _expect(sda.SDA_ERR_NO_NEGATIVE, lambda: build(labels=y))
+    col = p.x_col.copy()
+    col[3] = p.d
+    _expect(sda.SDA_ERR_INDEX, lambda: build(x_col=col))
+    col = p.x_col.copy()
+    i = int(np.argmax(np.diff(p.x_ptr) >= 2))
+    a = p.x_ptr[i]
+    col[a], col[a + 1] = col[a + 1], col[a]
+    _expect(sda.SDA_ERR_INDEX, lambda: build(x_col=col))
+    sv = p.s_val.copy()
+    sv[0] *= 2.0
+    _expect(sda.SDA_ERR_NOT_SYMMETRIC, lambda: build(s_val=sv))
+    xv = p.x_val.copy()
+    xv[5] = 0.3
+    _expect(sda.SDA_ERR_VALUE_NOT_EXACT, lambda: build(x_val=xv, compute="f16"))
+    yv = p.labels.copy()
+    yv[0, 0] = 2
+    _expect(sda.SDA_ERR_INVALID_ARG, lambda: build(labels=yv))
+    op = sda.Operator(p, compute="f64")
+    _expect(sda.SDA_ERR_INVALID_ARG, lambda: sda.sda_solve_shifts(op.handle, [1.0, -1.0]))
+    _expect(sda.SDA_ERR_INVALID_ARG, lambda: sda.sda_solve_shifts(op.handle, np.ones(65)))
+
+
+def test_empty_rows_and_columns():
+    """Rows without nonzeros or neighbours, and features nobody has."""
+    p = synth.custom_problem(300, 200, 6, seed=9, n_labelled=60, k=4, shifts=(1e-2, 1e1, 3))
+    n = p.n
+    # insert 5 empty rows at the front and append 7 empty feature columns
+    x_ptr = np.concatenate([np.zeros(5, np.int64), p.x_ptr])
+    s_ptr = np.concatenate([np.zeros(5, np.int64), p.s_ptr])
+    s_col = p.s_col + 5
+    labels = np.concatenate([np.zeros((1, 5), np.int8), p.labels], axis=1)
+    d = p.d + 7
+    op = sda.Operator(None, compute="f64", alpha=p.alpha, x_ptr=x_ptr, x_col=p.x_col, x_val=p.x_val, n_cols=d,
+                      s_ptr=s_ptr, s_col=s_col, s_val=p.s_val, labels=labels)
+    o = oracle.Oracle(x_ptr, p.x_col, p.x_val, s_ptr, s_col, p.s_val, labels[0], d, p.alpha)
+    w = torch.empty((1, 3, d), dtype=torch.float64, device="cuda")
+    opts = sda.sda_default_opts()
+    opts.fixed_iters = 10
+    sda.sda_solve_shifts(op.handle, p.shifts, opts, w_out=w, n_report=1)
+    ref = o.shifted_cg(o.rhs_canonical(), p.shifts, fixed_iters=10)
+    for s in range(3):
+        assert _rel(w[0, s].cpu().numpy(), ref.W[s]) < 1e-10
+        assert np.all(w[0, s, p.d:].cpu().numpy() == 0.0)
+
+
+def test_single_shift_and_zero_alpha(tiny):
+    op = sda.Operator(tiny, compute="f64", alpha=0.0)
+    o = oracle.from_problem(tiny, alpha=0.0)
+    w = torch.empty((1, 1, tiny.d), dtype=torch.float64, device="cuda")
+    opts = sda.sda_default_opts()
+    opts.tol = 1e-12
+    code, rep = sda.sda_solve_shifts(op.handle, [0.3], opts, w_out=w, n_report=1)
+    ref = o.shifted_cg(o.rhs_canonical(), [0.3], tol=1e-12, max_iter=5000)
+    assert _rel(w[0, 0].cpu().numpy(), ref.W[0]) < 1e-9
+
+
+def test_not_converged_reported(cfg1):
+    _, code, rep, w = gpu_solve(cfg1, "f64", tol=1e-12, max_iter=5)
+    assert code == sda.SDA_NOT_CONVERGED
+    assert rep[0][0]["status"] == sda.SDA_NOT_CONVERGED and rep[0][0]["iters"] == 5
+
+
+# ---------------------------------------------------------------------------
+# full-size single-target workload (200k x 131k, FP16 counts), as the benchmark runs it
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return synth.make_problem("single_mixed_200k")
+
+
+def test_cfg2_fixed_iterations_fp64_and_mixed(cfg2):
+    k = 20
+    o = oracle.from_problem(cfg2)
+    ref = o.shifted_cg(o.rhs_canonical(), cfg2.shifts, fixed_iters=k)
+    _, code, rep, w = gpu_solve(cfg2, "f64", fixed=k, check=0)
+    for s in range(len(cfg2.shifts)):
+        assert _rel(w[0, s], ref.W[s]) < 1e-9
+    _, code, rep, w = gpu_solve(cfg2, "f16", fixed=k, check=0)
+    for s in range(len(cfg2.shifts)):
+        assert _rel(w[0, s], ref.W[s]) < 1e-3, (s, _rel(w[0, s], ref.W[s]))
+
+
+def test_cfg2_converged_mixed_true_residuals(cfg2):
+    tol = 1e-3
+    _, code, rep, w = gpu_solve(cfg2, "f16", tol=tol, max_iter=4000)
+    assert code == sda.SDA_OK
+    for r in rep[0]:
+        assert r["true_residual"] < 1.5 * tol, r
