@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 WORKLOAD = "single_mixed_200k"
 METRIC = "SDA solves/s (all shifts)"
 UNIT = "solves/s"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cg_phase3_xt_shift_update_single_mixed_200k.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cg_kernels_single_mixed_200k.md")
 
 
 def parse():
@@ -133,25 +133,27 @@ def recorded_traffic(kernel: str):
 
 
 def algorithmic_bytes(prob, compute: str, iters: int, shift_iters: int):
-    """Algorithmic bytes of all launches of each phase kernel over one solve.
+    """Algorithmic bytes per launch of each iteration kernel, averaged over one solve.
 
-    Phase 1 (rows of X): CSR indices + values + row pointers, two gathers'
-    worth of the D-vectors r, p (each element once), ut written.
-    Phase 2 (rows of S): CSR of S (FP32 weights), ut read once, degrees,
-    labels, v written.
-    Phase 3 (columns of X): CSC indices + values + column pointers, v read
-    once, r and p read and written, mu_l (FP64) read, and per active shift
-    P and W read and written (FP32)."""
+    phase1  (rows of X):    CSR indices + values + row pointers, the D-vectors
+                            r_k and p_{k-1} once each, ut written.
+    phase2  (rows of S):    CSR of S (vector-type weights) + row pointers, ut
+                            read once, degrees, labels, v written.
+    phase3a (columns of X): CSC indices + values + column pointers, v read
+                            once, s written.
+    phase3b (stream):       r_k, p, s, mu_l (FP64) read, r_{k+1} and p written,
+                            and per active shift P and W read and written."""
     n, d = prob.n, prob.d
     nnz = int(prob.x_ptr[-1])
     snz = int(prob.s_ptr[-1])
     vsz = {"f64": 8, "f32": 4, "f16": 2, "f8e4m3": 1, "pattern": 0}[compute]
     fsz = 8 if compute == "f64" else 4
-    p1 = nnz * (4 + vsz) + (n + 1) * 8 + 2 * d * fsz + n * fsz
-    p2 = snz * (4 + fsz) + (n + 1) * 8 + n * fsz + n * fsz + n + n * fsz
-    p3_fixed = nnz * (4 + vsz) + (d + 1) * 8 + n * fsz + 4 * d * fsz + d * 8
-    per_launch = {"phase1": p1, "phase2": p2, "phase3": p3_fixed + shift_iters * d * 4 * fsz / max(iters, 1)}
-    return per_launch
+    return {
+        "phase1": nnz * (4 + vsz) + (n + 1) * 8 + 2 * d * fsz + n * fsz,
+        "phase2": snz * (4 + fsz) + (n + 1) * 8 + 3 * n * fsz + n,
+        "phase3a": nnz * (4 + vsz) + (d + 1) * 8 + n * fsz + d * fsz,
+        "phase3b": d * (5 * fsz + 8) + (shift_iters / max(iters, 1)) * d * 4 * fsz,
+    }
 
 
 def load_peaks():
@@ -284,11 +286,12 @@ def main():
     pcode, prep, pstats = step(profile=1)
     iters = max(1, pstats["iterations"])
     per_launch = algorithmic_bytes(prob, compute, pstats["iterations"], pstats["shift_iterations"])
-    durs = {"phase1": pstats["ms"][1] / iters, "phase2": pstats["ms"][2] / iters, "phase3": pstats["ms"][3] / iters}
+    durs = {k: pstats["ms"][i + 1] / iters for i, k in enumerate(("phase1", "phase2", "phase3a", "phase3b"))}
     dominant = max(durs, key=durs.get)
     peak, peak_kind = load_peaks()
     achieved = per_launch[dominant] / (durs[dominant] * 1e-3) / 1e9
-    kernel_names = {"phase1": "k_cg_phase1", "phase2": "k_cg_phase2", "phase3": "k_cg_phase3"}
+    kernel_names = {"phase1": "k_cg_phase1", "phase2": "k_cg_phase2", "phase3a": "k_cg_phase3a",
+                    "phase3b": "k_cg_phase3b"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(kernel_names[dominant]),
                 "kernel": kernel_names[dominant], "peak_kind": peak_kind,

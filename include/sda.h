@@ -210,8 +210,9 @@ SDA_API int sda_operator_apply(const sda_operator *op, int32_t target, double si
 typedef struct {
     int64_t iterations;        /* Krylov iterations summed over the call's targets                  */
     int64_t shift_iterations;  /* sum over targets and shifts of the iterations each shift ran      */
-    int64_t launches[4];       /* kernel launches: [0] start, [1] X rows, [2] S rows, [3] X columns */
-    double ms[4];              /* device time of those launches in ms (profile mode, else 0)        */
+    int64_t launches[5];       /* kernel launches: [0] start, [1] X rows (X p), [2] S rows (L u),
+                                  [3] X columns (X^T v), [4] vector and shift-state update          */
+    double ms[5];              /* device time of those launches in ms (profile mode, else 0)        */
     double solve_ms;           /* device time of the whole call in ms                               */
 } sda_solve_stats;
 

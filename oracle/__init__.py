@@ -44,8 +44,12 @@ _i64p = ctypes.c_void_p
 
 def build(force: bool = False, extra_flags: tuple = (), out: str | None = None) -> str:
     """Compile the C oracle in place (gcc, OpenMP, strict IEEE FP64)."""
+    import platform
     out = out or _SO
-    if force or extra_flags or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+    stamp = out + ".arch"
+    stale = (not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC)
+             or not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine())
+    if force or extra_flags or stale:
         tmp = out + ".tmp%d" % os.getpid()
         cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", *extra_flags, _SRC,
                "-o", tmp, "-lm"]
@@ -53,6 +57,8 @@ def build(force: bool = False, extra_flags: tuple = (), out: str | None = None) 
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stderr)
         os.replace(tmp, out)
+        with open(stamp, "w") as f:
+            f.write(platform.machine() + "\n")
     return out
 
 

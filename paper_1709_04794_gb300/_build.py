@@ -9,6 +9,7 @@ Everything is compiled in place next to its sources; nothing is installed.
 from __future__ import annotations
 
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -17,17 +18,27 @@ PKG_DIR = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG_DIR, "csrc")
 LIBSDA = os.path.join(PKG_DIR, "libsda.so")
 SYNTH_SO = os.path.join(PKG_DIR, "_synth_knn.so")
-BUILD_DIR = os.path.join(PKG_DIR, "_build")
+MACHINE = platform.machine()
+BUILD_DIR = os.path.join(PKG_DIR, "_build", MACHINE)
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def _newer(target: str, sources: list[str]) -> bool:
+    """True if `target` is missing, older than a source, or built for another machine."""
     if not os.path.exists(target):
+        return True
+    stamp = target + ".arch"
+    if not os.path.exists(stamp) or open(stamp).read().strip() != MACHINE:
         return True
     t = os.path.getmtime(target)
     return any(os.path.getmtime(s) > t for s in sources)
+
+
+def _stamp(target: str) -> None:
+    with open(target + ".arch", "w") as f:
+        f.write(MACHINE + "\n")
 
 
 def _run(cmd: list[str]) -> None:
@@ -42,6 +53,7 @@ def build_synth(force: bool = False) -> str:
         tmp = SYNTH_SO + ".tmp%d" % os.getpid()
         _run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", src, "-o", tmp])
         os.replace(tmp, SYNTH_SO)
+        _stamp(SYNTH_SO)
     return SYNTH_SO
 
 
@@ -68,6 +80,7 @@ def build_libsda(force: bool = False, verbose_ptxas: bool = False) -> str:
         obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
         if force or _newer(obj, [src] + hdr):
             _run([NVCC] + common + ["-c", src, "-o", obj])
+            _stamp(obj)
         return obj
 
     with ThreadPoolExecutor(max_workers=min(8, len(cu))) as ex:
@@ -75,6 +88,7 @@ def build_libsda(force: bool = False, verbose_ptxas: bool = False) -> str:
     tmp = LIBSDA + ".tmp%d" % os.getpid()
     _run([NVCC] + ARCH_FLAGS + ["-shared", "-o", tmp] + objs)
     os.replace(tmp, LIBSDA)
+    _stamp(LIBSDA)
     return LIBSDA
 
 

@@ -18,6 +18,10 @@ constexpr int kMaxShifts = 64;       // shifts per solve
 constexpr int kTileNnz = 4096;       // nonzeros per column tile / split chunk
 constexpr int kTileSegs = 1024;      // columns per multi-column tile
 constexpr int kBigSeg = 256;         // columns longer than this get whole-block tiles
+constexpr int kStreamSeg = 32;       // tiles whose columns are all this short are streamed
+constexpr int kHeadF32 = 8192;       // features of p_k staged in shared memory (FP32 vectors)
+constexpr int kHeadF64 = 4096;       // same, FP64 vectors
+constexpr int kMaxBlocksPerSm = 8;   // cap of resident blocks per SM used to size grids
 
 // ---------------------------------------------------------------------------
 // errors (thread-local last error, no exceptions across the ABI)
@@ -85,7 +89,8 @@ struct DevBuf {
 struct Tile {
     int64_t nz0, nz1;   // nonzero range (whole-block tiles)
     int32_t seg0, seg1; // column range
-    int32_t lanes;      // > 0: multi-column tile, lanes per column; 0: whole-block tile
+    int32_t lanes;      // > 0: multi-column tile, lanes per column; 0: whole-block tile;
+                        // -1: multi-column tile of short columns, nonzeros streamed
     int32_t slot;       // split chunk: slot of its partial sum; -1: the tile holds the whole column
     int32_t lseg;       // split chunk: index of its long column in the split tables
     int32_t pad;

@@ -45,10 +45,12 @@ struct SolveState {
 
 struct Workspace {
     int fp64 = -1;
-    int64_t d = 0, n = 0;
+    int64_t d = 0, n = 0, ldw = 0;   // ldw: D rounded up to 8 (leading dimension of D-vectors)
     int n_shifts = 0;
-    DevBuf<char> vec;        // r, p (D), ut, v (N) in the vector type
-    DevBuf<char> shift;      // W, P ([S][D] each) in the vector type
+    int vt = -1;                     // compute dtype the grids below were sized for
+    int grid1 = 0, grid2 = 0, grid3a = 0, grid3b = 0, head = 0;
+    DevBuf<char> vec;        // r[2][ldw], p[ldw], s[ldw], ut[N], v[N] in the vector type
+    DevBuf<char> shift;      // W[S][ldw], P[S][ldw] in the vector type
     DevBuf<SolveState> st;
     DevBuf<double> part;     // [3][grid][4] block partials of init / phase 2 / phase 3
     DevBuf<unsigned> cnt;    // grid arrival counters of init / phase 2 / phase 3

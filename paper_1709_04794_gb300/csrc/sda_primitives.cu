@@ -263,7 +263,9 @@ int build_col_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
             maxlen = std::max(maxlen, l);
             ++j;
         }
-        tiles.push_back(Tile{colptr[start], colptr[j], (int32_t)start, (int32_t)j, lanes_for(maxlen), -1, -1, 0});
+        // short columns: stream the tile's nonzeros (lanes -1); else a group of lanes per column
+        const int32_t lanes = maxlen <= kStreamSeg ? -1 : lanes_for(maxlen);
+        tiles.push_back(Tile{colptr[start], colptr[j], (int32_t)start, (int32_t)j, lanes, -1, -1, 0});
     }
     if (slots > INT32_MAX || (int64_t)tiles.size() > INT32_MAX)
         return fail(SDA_ERR_UNSUPPORTED, "column schedule too large");

@@ -71,11 +71,11 @@ __global__ void k_to_old(int64_t d, int64_t count, const int32_t *new_of_old, co
 
 // out[s][old] = W[s][new(old)] as FP64
 template <class FT>
-__global__ void k_w_out(int64_t d, int ns, const int32_t *new_of_old, const FT *W, double *out) {
+__global__ void k_w_out(int64_t d, int64_t ldw, int ns, const int32_t *new_of_old, const FT *W, double *out) {
     const int64_t m = d * ns;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = i / d, o = i - s * d;
-        out[i] = (double)W[s * d + new_of_old[o]];
+        out[i] = (double)W[s * ldw + new_of_old[o]];
     }
 }
 
@@ -231,15 +231,16 @@ static int ensure_workspace(sda_operator *op, int ns) {
     Workspace &w = op->ws;
     const int fp64 = op->compute == SDA_F64;
     const size_t fsz = fp64 ? sizeof(double) : sizeof(float);
+    const int64_t ldw = (op->d + 7) / 8 * 8;
     const bool realloc = w.fp64 != fp64 || w.d != op->d || w.n != op->n || w.n_shifts < ns;
     if (!realloc) return SDA_OK;
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
     w.graph_iters = 0;
-    SDA_TRY(w.vec.alloc((size_t)(2 * op->d + 2 * op->n) * fsz));
-    SDA_TRY(w.shift.alloc((size_t)(2 * (int64_t)ns * op->d) * fsz));
+    SDA_TRY(w.vec.alloc((size_t)(4 * ldw + 2 * op->n) * fsz));
+    SDA_TRY(w.shift.alloc((size_t)(2 * (int64_t)ns * ldw) * fsz));
     SDA_TRY(w.st.alloc(1));
-    SDA_TRY(w.part.alloc((size_t)3 * op->grid * 4));
+    SDA_TRY(w.part.alloc((size_t)3 * kMaxBlocksPerSm * op->sm_count * 4));
     SDA_TRY(w.cnt.alloc(4));
     SDA_CUDA(cudaMemset(w.cnt.p, 0, w.cnt.bytes()));
     SDA_TRY(ensure_apply_scratch(op));
@@ -247,13 +248,15 @@ static int ensure_workspace(sda_operator *op, int ns) {
     w.fp64 = fp64;
     w.d = op->d;
     w.n = op->n;
+    w.ldw = ldw;
     w.n_shifts = ns;
+    w.vt = -1;
     return SDA_OK;
 }
 
 template <class FT>
 struct WsView {
-    FT *r, *p, *ut, *v, *W, *P;
+    FT *r, *p, *s, *ut, *v, *W, *P;
 };
 
 template <class FT>
@@ -261,12 +264,43 @@ static WsView<FT> view(const sda_operator *op) {
     const Workspace &w = op->ws;
     FT *base = (FT *)w.vec.p;
     FT *sb = (FT *)w.shift.p;
-    return WsView<FT>{base, base + op->d, base + 2 * op->d, base + 2 * op->d + op->n, sb,
-                      sb + (int64_t)w.n_shifts * op->d};
+    const int64_t l = w.ldw;
+    return WsView<FT>{base, base + 2 * l, base + 3 * l, base + 4 * l, base + 4 * l + op->n, sb,
+                      sb + (int64_t)w.n_shifts * l};
 }
 
-// the three phase kernels of one iteration; `ev` (profile mode) holds a
-// start and an end event for each of them
+static int grid_of(const void *kernel, size_t dyn, int sms) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, dyn) != cudaSuccess || nb <= 0) {
+        (void)cudaGetLastError();
+        nb = 1;
+    }
+    return std::min(nb, kMaxBlocksPerSm) * sms;
+}
+
+// sizes the grids of the iteration kernels for this operator's dtypes
+template <class VT, class FT>
+static int size_grids(sda_operator *op) {
+    Workspace &w = op->ws;
+    if (w.vt == (int)op->compute) return SDA_OK;
+    const int sms = op->sm_count;
+    w.head = (int)std::min<int64_t>(op->d, std::is_same<FT, double>::value ? kHeadF64 : kHeadF32);
+    SDA_TRY(with_lanes(op->x_lanes, [&](auto G) -> int {
+        w.grid1 = grid_of((const void *)k_cg_phase1<VT, FT, decltype(G)::value>, (size_t)w.head * sizeof(FT), sms);
+        return SDA_OK;
+    }));
+    SDA_TRY(with_lanes(op->s_lanes, [&](auto G) -> int {
+        w.grid2 = grid_of((const void *)k_cg_phase2<FT, decltype(G)::value>, 0, sms);
+        return SDA_OK;
+    }));
+    w.grid3a = grid_of((const void *)k_cg_phase3a<VT, FT>, 0, sms);
+    w.grid3b = grid_of((const void *)k_cg_phase3b<FT>, 0, sms);
+    w.vt = (int)op->compute;
+    return SDA_OK;
+}
+
+// the four kernels of one iteration; `ev` (profile mode) holds a start and an
+// end event for each of them
 template <class VT, class FT>
 static int launch_iteration(const sda_operator *op, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     const Workspace &w = op->ws;
@@ -275,27 +309,32 @@ static int launch_iteration(const sda_operator *op, cudaStream_t s, cudaEvent_t 
     const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
     if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
     SDA_TRY(with_lanes(op->x_lanes, [&](auto G) -> int {
-        k_cg_phase1<VT, FT, decltype(G)::value><<<op->grid, kBlock, 0, s>>>(
-            op->n, op->x_rp.p, op->x_col.p, (const VT *)op->x_val_r.p, b.r, b.p, b.ut, w.st.p);
+        k_cg_phase1<VT, FT, decltype(G)::value><<<w.grid1, kBlock, (size_t)w.head * sizeof(FT), s>>>(
+            op->n, w.head, op->x_rp.p, op->x_col.p, (const VT *)op->x_val_r.p, b.r, w.ldw, b.p, b.ut, w.st.p);
         SDA_LAUNCHED();
         return SDA_OK;
     }));
     if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[2], s));
     SDA_TRY(with_lanes(op->s_lanes, [&](auto G) -> int {
-        k_cg_phase2<FT, decltype(G)::value><<<op->grid, kBlock, 0, s>>>(
-            op->n, op->s_rp.p, op->s_col.p, sv, dg, b.ut, b.v, w.st.p, w.part.p + (size_t)op->grid * 4, w.cnt.p + 1);
+        k_cg_phase2<FT, decltype(G)::value><<<w.grid2, kBlock, 0, s>>>(
+            op->n, op->s_rp.p, op->s_col.p, sv, dg, b.ut, b.v, w.st.p, w.part.p + (size_t)kMaxBlocksPerSm * op->sm_count * 4,
+            w.cnt.p + 1);
         SDA_LAUNCHED();
         return SDA_OK;
     }));
     if (ev) SDA_CUDA(cudaEventRecord(ev[3], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[4], s));
-    k_cg_phase3<VT, FT><<<op->grid, kBlock, 0, s>>>(
-        op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p, (const VT *)op->x_val_c.p, b.v, b.r, b.p, b.W,
-        b.P, op->d, w.st.p, w.part.p + (size_t)op->grid * 8, w.cnt.p + 2, (FT *)op->slots.p, op->lcount.p,
-        op->col.splits.p);
+    k_cg_phase3a<VT, FT><<<w.grid3a, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
+                                                    (const VT *)op->x_val_c.p, b.v, b.s, w.st.p, (FT *)op->slots.p,
+                                                    op->lcount.p, op->col.splits.p);
     SDA_LAUNCHED();
     if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
+    if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
+    k_cg_phase3b<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b.s, b.r, b.p, b.W, b.P, w.st.p,
+                                                 w.part.p + (size_t)kMaxBlocksPerSm * op->sm_count * 8, w.cnt.p + 2);
+    SDA_LAUNCHED();
+    if (ev) SDA_CUDA(cudaEventRecord(ev[7], s));
     return SDA_OK;
 }
 
@@ -303,26 +342,26 @@ template <class VT, class FT>
 static int run_iterations(sda_operator *op, int nb, bool use_graph, bool profile, cudaStream_t s) {
     Workspace &w = op->ws;
     if (profile) {
-        const size_t need = (size_t)nb * 6;
+        const size_t need = (size_t)nb * 8;
         while (w.prof_ev.size() < need) {
             cudaEvent_t e;
             SDA_CUDA(cudaEventCreate(&e));
             w.prof_ev.push_back(e);
         }
-        for (int i = 0; i < nb; ++i) SDA_TRY((launch_iteration<VT, FT>(op, s, w.prof_ev.data() + 6 * i)));
+        for (int i = 0; i < nb; ++i) SDA_TRY((launch_iteration<VT, FT>(op, s, w.prof_ev.data() + 8 * i)));
         SDA_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < nb; ++i)
-            for (int ph = 0; ph < 3; ++ph) {
+            for (int ph = 0; ph < 4; ++ph) {
                 float ms = 0.f;
-                SDA_CUDA(cudaEventElapsedTime(&ms, w.prof_ev[6 * i + 2 * ph], w.prof_ev[6 * i + 2 * ph + 1]));
+                SDA_CUDA(cudaEventElapsedTime(&ms, w.prof_ev[8 * i + 2 * ph], w.prof_ev[8 * i + 2 * ph + 1]));
                 op->stats.ms[1 + ph] += ms;
             }
-        for (int ph = 1; ph <= 3; ++ph) op->stats.launches[ph] += nb;
+        for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb;
         return SDA_OK;
     }
     if (!use_graph) {
         for (int i = 0; i < nb; ++i) SDA_TRY((launch_iteration<VT, FT>(op, s)));
-        for (int ph = 1; ph <= 3; ++ph) op->stats.launches[ph] += nb;
+        for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb;
         return SDA_OK;
     }
     if (!w.graph || w.graph_iters != nb) {
@@ -347,8 +386,8 @@ static int run_iterations(sda_operator *op, int nb, bool use_graph, bool profile
         w.graph_iters = nb;
     }
     SDA_CUDA(cudaGraphLaunch(w.graph, s));
-    note_launch(3 * (int64_t)nb);
-    for (int ph = 1; ph <= 3; ++ph) op->stats.launches[ph] += nb;
+    note_launch(4 * (int64_t)nb);
+    for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb;
     return SDA_OK;
 }
 
@@ -365,6 +404,7 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
                         const sda_solve_opts &o, double *w_out_t, sda_shift_report *rep_t, cudaStream_t s,
                         int *worst) {
     Workspace &w = op->ws;
+    SDA_TRY((size_grids<VT, FT>(op)));
     WsView<FT> bv = view<FT>(op);
     SolveState &h = *w.h_st;
     memset(&h, 0, sizeof(SolveState));
@@ -381,7 +421,8 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
     h.mu = op->mu.p + (int64_t)t * op->d;
     for (int i = 0; i < ns; ++i) h.sh[i].delta = shifts[i] - sigma0;
     SDA_CUDA(cudaMemcpyAsync(w.st.p, &h, sizeof(SolveState), cudaMemcpyHostToDevice, s));
-    k_cg_init<FT><<<op->grid, kBlock, 0, s>>>(op->d, b_perm, bv.r, bv.p, bv.W, bv.P, w.st.p, w.part.p, w.cnt.p + 0);
+    k_cg_init<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b_perm, bv.r, bv.p, bv.W, bv.P, w.st.p, w.part.p,
+                                              w.cnt.p + 0);
     SDA_LAUNCHED();
     op->stats.launches[0] += 1;
     SDA_TRY(read_header(op, s));
@@ -410,8 +451,8 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
             tmp = hostbuf.p;
             dst = tmp;
         }
-        k_w_out<FT><<<grid_elems((int64_t)ns * op->d, op->sm_count), kBlock, 0, s>>>(op->d, ns, op->new_of_old.p,
-                                                                                      bv.W, dst);
+        k_w_out<FT><<<grid_elems((int64_t)ns * op->d, op->sm_count), kBlock, 0, s>>>(op->d, w.ldw, ns,
+                                                                                      op->new_of_old.p, bv.W, dst);
         SDA_LAUNCHED();
         if (!o.out_on_device) {
             SDA_CUDA(cudaMemcpyAsync(w_out_t, tmp, (size_t)ns * op->d * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -426,7 +467,7 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
         SDA_TRY(rs.alloc((size_t)ns + 1));
         SDA_TRY(dot_f64(op, op->d, b_perm, b_perm, rs.p + ns, s));
         for (int i = 0; i < ns; ++i) {
-            k_w_f64<FT><<<grid_elems(op->d, op->sm_count), kBlock, 0, s>>>(op->d, bv.W + (int64_t)i * op->d, w64);
+            k_w_f64<FT><<<grid_elems(op->d, op->sm_count), kBlock, 0, s>>>(op->d, bv.W + (int64_t)i * w.ldw, w64);
             SDA_LAUNCHED();
             SDA_TRY(op_apply_f64(op, t, shifts[i], w64, q, s));
             k_resid_f64<<<op->grid, kBlock, 0, s>>>(op->d, b_perm, q, rs.p + i, op->part.p, op->cnt.p);

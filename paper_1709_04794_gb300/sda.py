@@ -62,7 +62,7 @@ class sda_shift_report(ctypes.Structure):
 
 class sda_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("shift_iterations", ctypes.c_int64),
-                ("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4), ("solve_ms", ctypes.c_double)]
+                ("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5), ("solve_ms", ctypes.c_double)]
 
 
 class sda_operator_info(ctypes.Structure):

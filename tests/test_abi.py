@@ -43,4 +43,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sda.sda_shift_report) == 24
     assert sda.sda_solve_opts.rhs.offset == 24
     assert ctypes.sizeof(sda.sda_solve_opts) == 64
-    assert ctypes.sizeof(sda.sda_solve_stats) == 88
+    assert ctypes.sizeof(sda.sda_solve_stats) == 104
