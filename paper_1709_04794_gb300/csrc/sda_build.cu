@@ -428,17 +428,30 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
     SDA_TRY(read_err(err, s, &herr));
     if (herr & kErrLabel) return fail(SDA_ERR_INVALID_ARG, "labels must be -1, 0 or +1");
 
-    // ---- column schedule of the X^T pass -----------------------------------------
+    // ---- tile schedules of the sparse passes -------------------------------------
     {
-        std::vector<int64_t> hcp((size_t)d + 1);
-        SDA_CUDA(cudaMemcpyAsync(hcp.data(), op->x_cp.p, ((size_t)d + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        std::vector<int64_t> hp((size_t)std::max(n, d) + 1);
+        hp.resize((size_t)d + 1);
+        SDA_CUDA(cudaMemcpyAsync(hp.data(), op->x_cp.p, ((size_t)d + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
-        SDA_TRY(build_col_schedule(hcp, op->col));
+        SDA_TRY(build_seg_schedule(hp, op->col));
+        hp.resize((size_t)n + 1);
+        SDA_CUDA(cudaMemcpyAsync(hp.data(), op->x_rp.p, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SDA_CUDA(cudaStreamSynchronize(s));
+        SDA_TRY(build_seg_schedule(hp, op->xrow));
+        SDA_CUDA(cudaMemcpyAsync(hp.data(), op->s_rp.p, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SDA_CUDA(cudaStreamSynchronize(s));
+        SDA_TRY(build_seg_schedule(hp, op->srow));
     }
-    SDA_TRY(op->slots.alloc((size_t)std::max(op->col.nslots, 1)));
-    SDA_TRY(op->lcount.alloc((size_t)std::max(op->col.nsplits, 1)));
+    // split segments of the three schedules use disjoint slot / counter ranges
+    op->xrow_slot0 = op->col.nslots;
+    op->srow_slot0 = op->col.nslots + op->xrow.nslots;
+    op->xrow_lseg0 = op->col.nsplits;
+    op->srow_lseg0 = op->col.nsplits + op->xrow.nsplits;
+    SDA_TRY(op->slots.alloc((size_t)std::max(op->col.nslots + op->xrow.nslots + op->srow.nslots, 1)));
+    SDA_TRY(op->lcount.alloc((size_t)std::max(op->col.nsplits + op->xrow.nsplits + op->srow.nsplits, 1)));
     SDA_CUDA(cudaMemsetAsync(op->lcount.p, 0, op->lcount.bytes(), s));
-    SDA_TRY(op->part.alloc((size_t)op->grid * 4));
+    SDA_TRY(op->part.alloc((size_t)kMaxBlocksPerSm * op->sm_count * 4));
     SDA_TRY(op->cnt.alloc(4));
     SDA_CUDA(cudaMemsetAsync(op->cnt.p, 0, op->cnt.bytes(), s));
     SDA_TRY(op->scal.alloc(8));
@@ -476,13 +489,6 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
         SDA_CUDA(cudaStreamSynchronize(s));
     }
     return SDA_OK;
-}
-
-static int lanes_for_rows(int64_t nnz, int64_t n) {
-    const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-    int g = 2;
-    while (g < 32 && 2 * g < avg) g <<= 1;
-    return g;
 }
 
 }  // namespace sda
@@ -529,8 +535,6 @@ extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, co
         return fail(SDA_ERR_CUDA, "no CUDA device");
     }
     op->grid = op->sm_count * 4;
-    op->x_lanes = lanes_for_rows(X->nnz, X->n_rows);
-    op->s_lanes = lanes_for_rows(S->nnz, X->n_rows);
     int rc = build(X, S, y, alpha, omega, compute, (cudaStream_t)cuda_stream, op);
     if (rc < 0) {
         cudaStreamSynchronize((cudaStream_t)cuda_stream);
@@ -541,7 +545,9 @@ extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, co
                           op->x_col.bytes() + op->x_row.bytes() + op->x_val_r.bytes() + op->x_val_c.bytes() +
                           op->s_rp.bytes() + op->s_col.bytes() + op->s_val64.bytes() + op->s_val32.bytes() +
                           op->deg64.bytes() + op->deg32.bytes() + op->labels.bytes() + op->mu.bytes() +
-                          op->dvec.bytes() + op->col.tiles.bytes() + op->col.splits.bytes());
+                          op->dvec.bytes() + op->col.tiles.bytes() + op->col.splits.bytes() +
+                          op->xrow.tiles.bytes() + op->xrow.splits.bytes() + op->srow.tiles.bytes() +
+                          op->srow.splits.bytes());
     *out = op;
     return SDA_OK;
 }

@@ -18,9 +18,6 @@ constexpr int kMaxShifts = 64;       // shifts per solve
 constexpr int kTileNnz = 4096;       // nonzeros per column tile / split chunk
 constexpr int kTileSegs = 1024;      // columns per multi-column tile
 constexpr int kBigSeg = 256;         // columns longer than this get whole-block tiles
-constexpr int kStreamSeg = 32;       // tiles whose columns are all this short are streamed
-constexpr int kHeadF32 = 8192;       // features of p_k staged in shared memory (FP32 vectors)
-constexpr int kHeadF64 = 4096;       // same, FP64 vectors
 constexpr int kMaxBlocksPerSm = 8;   // cap of resident blocks per SM used to size grids
 
 // ---------------------------------------------------------------------------
@@ -84,13 +81,13 @@ struct DevBuf {
 };
 
 // ---------------------------------------------------------------------------
-// column tiles of the X^T pass (built on the host from the column pointers)
+// tiles of the sparse passes (built on the host from the segment pointers)
 // ---------------------------------------------------------------------------
 struct Tile {
     int64_t nz0, nz1;   // nonzero range (whole-block tiles)
     int32_t seg0, seg1; // column range
-    int32_t lanes;      // > 0: multi-column tile, lanes per column; 0: whole-block tile;
-                        // -1: multi-column tile of short columns, nonzeros streamed
+    int32_t lanes;      // > 0: multi-segment tile (nonzeros streamed, `lanes` lanes sum a
+                        // segment); 0: whole-block tile
     int32_t slot;       // split chunk: slot of its partial sum; -1: the tile holds the whole column
     int32_t lseg;       // split chunk: index of its long column in the split tables
     int32_t pad;
@@ -107,34 +104,45 @@ struct ColSchedule {
     int32_t ntiles = 0, nsplits = 0, nslots = 0;
 };
 
-int build_col_schedule(const std::vector<int64_t> &colptr, ColSchedule &out);
+// tiles of consecutive segments (rows or columns) of a CSR-like pointer array
+int build_seg_schedule(const std::vector<int64_t> &ptr, ColSchedule &out);
 
 // ---------------------------------------------------------------------------
 // value storage types
 // ---------------------------------------------------------------------------
 struct Pattern {};  // no stored values: every entry is one
 
+// get(): plain load; get_cs(): evict-first load for streams read once per pass
 template <class VT>
 struct Val;
 template <>
 struct Val<double> {
     static __device__ __forceinline__ double get(const double *v, int64_t e) { return v[e]; }
+    static __device__ __forceinline__ double get_cs(const double *v, int64_t e) { return __ldcs(v + e); }
 };
 template <>
 struct Val<float> {
     static __device__ __forceinline__ float get(const float *v, int64_t e) { return v[e]; }
+    static __device__ __forceinline__ float get_cs(const float *v, int64_t e) { return __ldcs(v + e); }
 };
 template <>
 struct Val<__half> {
     static __device__ __forceinline__ float get(const __half *v, int64_t e) { return __half2float(v[e]); }
+    static __device__ __forceinline__ float get_cs(const __half *v, int64_t e) { return __half2float(__ldcs(v + e)); }
 };
 template <>
 struct Val<__nv_fp8_e4m3> {
     static __device__ __forceinline__ float get(const __nv_fp8_e4m3 *v, int64_t e) { return float(v[e]); }
+    static __device__ __forceinline__ float get_cs(const __nv_fp8_e4m3 *v, int64_t e) {
+        __nv_fp8_e4m3 x;
+        x.__x = (__nv_fp8_storage_t)__ldcs(reinterpret_cast<const unsigned char *>(v) + e);
+        return float(x);
+    }
 };
 template <>
 struct Val<Pattern> {
     static __device__ __forceinline__ float get(const Pattern *, int64_t) { return 1.0f; }
+    static __device__ __forceinline__ float get_cs(const Pattern *, int64_t) { return 1.0f; }
 };
 
 // ---------------------------------------------------------------------------

@@ -13,7 +13,15 @@
 //                             <r,r>, <mu,r>, <r,p_k>  -> alpha_{k+1}, <mu,p_{k+1}>, <p_{k+1},p_{k+1}>, stop tests
 // <p, (B + sigma0) p> = <ut, v> + sigma0 <p, p> is known after phase 2, so q is
 // never stored; <mu, p> and <p, p> follow from recurrences on the phase-3b dots.
-// The scalar work of a phase runs in the block that finishes last.
+// The scalar work of a phase runs in the block that finishes last (no block
+// ever waits for another).
+//
+// The three sparse passes share one tile kernel (k_segpass): a tile is a run of
+// consecutive segments (rows or columns) holding at most kTileNnz nonzeros.  Its
+// index and value streams are read with all loads independent and evict-first,
+// the gathered operand through L1, the products staged in shared memory and
+// summed per segment by groups of lanes; segments longer than kBigSeg get
+// whole-block tiles, split across blocks when longer than kTileNnz.
 #pragma once
 
 #include "sda_operator.cuh"
@@ -27,197 +35,305 @@ __device__ __forceinline__ float form_p<float>(float r, float p, float a) { retu
 template <>
 __device__ __forceinline__ double form_p<double>(double r, double p, double a) { return fma(a, p, r); }
 
+// interleaved {r, p} pair of the CG vectors
+template <class FT>
+struct RPair;
+template <>
+struct RPair<float> {
+    using T = float2;
+};
+template <>
+struct RPair<double> {
+    using T = double2;
+};
+
 // ---------------------------------------------------------------------------
-// column tile: column sums of X^T v, handed to an epilogue
+// segmented sums over one tile
 // ---------------------------------------------------------------------------
+template <class AccT>
+struct TileSmem {
+    AccT buf[kTileNnz];       // products of the tile
+    AccT sums[kTileSegs];     // segment sums
+    int offs[kTileSegs + 1];  // segment starts relative to the tile
+    AccT red[kBlock / 32];
+    int last;
+};
+
 // Epi must provide
-//   __device__ void column(int64_t j, AccT sum)      one thread per column, consecutive columns on
-//                                                    consecutive threads
-//   __device__ void column_block(int64_t j, AccT s)  the whole block, one column (s valid in all threads)
-// `buf` holds kTileNnz AccT (shared).  Three tile kinds:
-//   lanes < 0  short columns: the tile's nonzeros are loaded and multiplied with
-//              all loads independent (coalesced index/value streams, gathers of v
-//              in flight together), products staged in shared memory, then summed
-//              per column in index order;
-//   lanes > 0  a group of `lanes` lanes per column, xor-tree sum inside the group;
-//   lanes == 0 one column or one chunk of a long column for the whole block; the
-//              chunks of a split column leave their sums in slots and the chunk
-//              that arrives last adds them in chunk order.
-template <class VT, class AccT, class Epi>
-__device__ __forceinline__ void col_tile(const Tile &tl, const int64_t *__restrict__ cp,
-                                         const int32_t *__restrict__ row, const VT *__restrict__ val,
-                                         const AccT *__restrict__ v, AccT *slots, unsigned *lcount,
-                                         const SplitSeg *__restrict__ splits, Epi &epi, AccT *buf,
-                                         AccT *red) {
-    __shared__ int s_last;
-    if (tl.lanes < 0) {
+//   segment(i, sum)        one thread per segment, consecutive segments on consecutive threads
+//   segment_block(i, sum)  the whole block, one segment (sum valid in every thread)
+template <class VT, class AccT, class Gather, class Epi>
+__device__ __forceinline__ void seg_tile(const Tile &tl, const int64_t *__restrict__ ptr,
+                                         const int32_t *__restrict__ idx, const VT *__restrict__ val,
+                                         const Gather &gather, Epi &epi, TileSmem<AccT> &sh, AccT *slots,
+                                         unsigned *lcount, const SplitSeg *__restrict__ splits) {
+    if (tl.lanes > 0) {
         const int64_t nz0 = tl.nz0;
         const int nnz = (int)(tl.nz1 - nz0);
+        const int nseg = tl.seg1 - tl.seg0;
+        for (int s = threadIdx.x; s <= nseg; s += kBlock) sh.offs[s] = (int)(ptr[tl.seg0 + s] - nz0);
+#pragma unroll 4
         for (int e = threadIdx.x; e < nnz; e += kBlock)
-            buf[e] = (AccT)Val<VT>::get(val, nz0 + e) * v[row[nz0 + e]];
+            sh.buf[e] = (AccT)Val<VT>::get_cs(val, nz0 + e) * gather(__ldcs(idx + nz0 + e));
         __syncthreads();
-        const int nseg = tl.seg1 - tl.seg0;
-        for (int s = threadIdx.x; s < nseg; s += kBlock) {
-            const int64_t j = tl.seg0 + s;
-            const int a = (int)(cp[j] - nz0), b = (int)(cp[j + 1] - nz0);
-            AccT acc = 0;
-            for (int e = a; e < b; ++e) acc += buf[e];
-            epi.column(j, acc);
-        }
-        __syncthreads();
-        return;
-    }
-    if (tl.lanes > 0) {
-        const int G = tl.lanes, ngroups = kBlock / G;
-        const int g = threadIdx.x / G, lane = threadIdx.x % G;
-        const int nseg = tl.seg1 - tl.seg0;
-        for (int base = 0; base < nseg; base += ngroups) {
-            const int s = base + g;
-            AccT acc = 0;
-            if (s < nseg) {
-                const int64_t j = tl.seg0 + s;
-                const int64_t e1 = cp[j + 1];
-                for (int64_t e = cp[j] + lane; e < e1; e += G)
-                    acc += (AccT)Val<VT>::get(val, e) * v[row[e]];
+        const int G = tl.lanes;
+        if (G == 1) {
+            for (int s = threadIdx.x; s < nseg; s += kBlock) {
+                AccT acc = 0;
+                for (int e = sh.offs[s]; e < sh.offs[s + 1]; ++e) acc += sh.buf[e];
+                epi.segment(tl.seg0 + s, acc);
             }
-            for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (s < nseg && lane == 0) buf[s] = acc;
+        } else {
+            const int ngroups = kBlock / G, g = threadIdx.x / G, lane = threadIdx.x % G;
+            for (int base = 0; base < nseg; base += ngroups) {
+                const int s = base + g;
+                AccT acc = 0;
+                if (s < nseg)
+                    for (int e = sh.offs[s] + lane; e < sh.offs[s + 1]; e += G) acc += sh.buf[e];
+                for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (s < nseg && lane == 0) sh.sums[s] = acc;
+            }
+            __syncthreads();
+            for (int s = threadIdx.x; s < nseg; s += kBlock) epi.segment(tl.seg0 + s, sh.sums[s]);
         }
-        __syncthreads();
-        for (int s = threadIdx.x; s < nseg; s += kBlock) epi.column(tl.seg0 + s, buf[s]);
         __syncthreads();
         return;
     }
     AccT acc = 0;
+#pragma unroll 4
     for (int64_t e = tl.nz0 + threadIdx.x; e < tl.nz1; e += kBlock)
-        acc += (AccT)Val<VT>::get(val, e) * v[row[e]];
-    acc = block_sum(acc, red);
+        acc += (AccT)Val<VT>::get_cs(val, e) * gather(__ldcs(idx + e));
+    acc = block_sum(acc, sh.red);
     if (tl.slot < 0) {
-        epi.column_block(tl.seg0, acc);
+        epi.segment_block(tl.seg0, acc);
         return;
     }
+    // one chunk of a split segment: the chunk that arrives last adds the chunks in order
     if (threadIdx.x == 0) {
         slots[tl.slot] = acc;
         __threadfence();
         const unsigned prev = atomicAdd(&lcount[tl.lseg], 1u);
-        s_last = (prev == (unsigned)splits[tl.lseg].nchunks - 1u);
+        sh.last = (prev == (unsigned)splits[tl.lseg].nchunks - 1u);
     }
     __syncthreads();
-    if (s_last) {
+    if (sh.last) {
         __threadfence();
         const SplitSeg sp = splits[tl.lseg];
         AccT tot = 0;
-        for (int c = 0; c < sp.nchunks; ++c) tot += __ldcg(slots + sp.slot0 + c);   // fixed order
+        for (int c = 0; c < sp.nchunks; ++c) tot += __ldcg(slots + sp.slot0 + c);
         if (threadIdx.x == 0) lcount[tl.lseg] = 0u;
-        epi.column_block(tl.seg0, tot);
+        epi.segment_block(tl.seg0, tot);
     }
     __syncthreads();
 }
 
-// ---------------------------------------------------------------------------
-// plain FP64 kernels (operator apply, means, projection, residual check)
-// ---------------------------------------------------------------------------
-
-// u_i = sum_e x_e w[col_e] - (csub ? *csub : 0), groups of G lanes per row
-template <class VT, int G>
-__global__ void __launch_bounds__(kBlock) k_rows_f64(int64_t n, const int64_t *__restrict__ rp,
-                                                     const int32_t *__restrict__ col,
-                                                     const VT *__restrict__ val,
-                                                     const double *__restrict__ w, double *__restrict__ u,
-                                                     const double *csub) {
-    constexpr int RPW = 32 / G;
-    const double c = csub ? *csub : 0.0;
-    const int lane = threadIdx.x % G;
-    const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
-    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
-        const int64_t i = base + (threadIdx.x & 31) / G;
-        double acc = 0.0;
-        if (i < n) {
-            const int64_t e1 = rp[i + 1];
-            for (int64_t e = rp[i] + lane; e < e1; e += G) acc += (double)Val<VT>::get(val, e) * w[col[e]];
-        }
-#pragma unroll
-        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (i < n && lane == 0) u[i] = acc - c;
-    }
-}
-
-// v_i = omega [y_i != 0] ut_i + alpha (deg_i ut_i - sum_j s_ij ut_j)
-template <int G>
-__global__ void __launch_bounds__(kBlock) k_lap_f64(int64_t n, const int64_t *__restrict__ rp,
-                                                    const int32_t *__restrict__ col,
-                                                    const double *__restrict__ sv,
-                                                    const double *__restrict__ deg,
-                                                    const int8_t *__restrict__ y, double omega, double alpha,
-                                                    const double *__restrict__ ut, double *__restrict__ v) {
-    constexpr int RPW = 32 / G;
-    const int lane = threadIdx.x % G;
-    const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
-    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
-        const int64_t i = base + (threadIdx.x & 31) / G;
-        double acc = 0.0;
-        if (i < n) {
-            const int64_t e1 = rp[i + 1];
-            for (int64_t e = rp[i] + lane; e < e1; e += G) acc += sv[e] * ut[col[e]];
-        }
-#pragma unroll
-        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (i < n && lane == 0) {
-            const double u = ut[i];
-            v[i] = omega * (y[i] != 0 ? u : 0.0) + alpha * (deg[i] * u - acc);
-        }
-    }
-}
-
-// <a, b> (or sum of a when b is NULL) into *out, fixed-order reduction
-__global__ void __launch_bounds__(kBlock) k_dot_f64(int64_t n, const double *__restrict__ a,
-                                                    const double *__restrict__ b, double *out,
-                                                    double *partials, unsigned *counter);
-
-struct EpiStore {
-    double *q;
-    __device__ __forceinline__ void column(int64_t j, double s) { q[j] = s; }
-    __device__ __forceinline__ void column_block(int64_t j, double s) {
-        if (threadIdx.x == 0) q[j] = s;
-    }
-};
-
-// q_j = s_j - mu_j t + sigma p_j
-struct EpiApply {
-    double *q;
-    const double *mu, *p;
-    const double *t;
-    double sigma;
-    __device__ __forceinline__ void column(int64_t j, double s) { q[j] = s - mu[j] * (*t) + sigma * p[j]; }
-    __device__ __forceinline__ void column_block(int64_t j, double s) {
-        if (threadIdx.x == 0) column(j, s);
-    }
-};
-
-template <class VT, class Epi>
-__global__ void __launch_bounds__(kBlock) k_cols_f64(const Tile *__restrict__ tiles, int ntiles,
-                                                     const int64_t *__restrict__ cp,
-                                                     const int32_t *__restrict__ row,
-                                                     const VT *__restrict__ val, const double *__restrict__ v,
-                                                     double *slots, unsigned *lcount,
-                                                     const SplitSeg *__restrict__ splits, Epi epi) {
-    __shared__ double buf[kTileNnz];
-    __shared__ double red[kBlock / 32];
+// Epi additionally provides skip() (run finished), begin() and end() (block
+// dots and the last block's scalar work).  Gather provides begin() and
+// operator()(column) -> AccT.
+template <class VT, class AccT, class Gather, class Epi>
+__global__ void __launch_bounds__(kBlock) k_segpass(const Tile *__restrict__ tiles, int ntiles,
+                                                    const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                                    const VT *__restrict__ val, Gather gather, Epi epi, AccT *slots,
+                                                    unsigned *lcount, const SplitSeg *__restrict__ splits) {
+    __shared__ TileSmem<AccT> sh;
+    __shared__ typename Epi::Shared esh;
+    if (epi.skip()) return;
+    gather.begin();
+    epi.begin(esh);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const Tile tl = tiles[t];
-        col_tile<VT, double, Epi>(tl, cp, row, val, v, slots, lcount, splits, epi, buf, red);
+        seg_tile<VT, AccT, Gather, Epi>(tl, ptr, idx, val, gather, epi, sh, slots, lcount, splits);
     }
+    epi.end(esh);
 }
 
+// ---------------------------------------------------------------------------
+// gathers
+// ---------------------------------------------------------------------------
+template <class AccT, class T>
+struct GatherVec {
+    const T *__restrict__ v;
+    __device__ __forceinline__ void begin() {}
+    __device__ __forceinline__ AccT operator()(int32_t j) const { return (AccT)v[j]; }
+};
+
+// p_k,j = r_k,j + alpha_k p_{k-1,j} from the interleaved buffer of iteration k
+template <class FT>
+struct GatherP {
+    const typename RPair<FT>::T *base;   // [2][ldw]
+    int64_t ldw;
+    const SolveState *st;
+    const typename RPair<FT>::T *a;
+    FT alpha;
+    __device__ __forceinline__ void begin() {
+        a = base + (st->k & 1) * ldw;
+        alpha = (FT)st->alpha;
+    }
+    __device__ __forceinline__ FT operator()(int32_t j) const {
+        const typename RPair<FT>::T x = a[j];
+        return form_p<FT>(x.x, x.y, alpha);
+    }
+};
 
 // ---------------------------------------------------------------------------
-// shifted CG (Algorithm 3) kernels; FT = vector type (float or double)
+// epilogues
 // ---------------------------------------------------------------------------
-// Vectors live in the workspace with leading dimension ldw (D rounded up to
-// 8, padding kept at zero): r[2][ldw] (r_k in r[k & 1]), p[ldw] (p_{k-1}),
-// s[ldw] (X^T v), and the shift state W[S][ldw], P[S][ldw].
+struct NoShared {};
+
+// out_i = sum - (csub ? *csub : 0)
+template <class OT>
+struct EpiStore {
+    using Shared = NoShared;
+    OT *out;
+    const double *csub;
+    const SolveState *st;   // optional: skip when the run is finished
+    double c;
+    __device__ __forceinline__ bool skip() const { return st && st->done; }
+    __device__ __forceinline__ void begin(Shared &) { c = csub ? *csub : 0.0; }
+    template <class AccT>
+    __device__ __forceinline__ void segment(int64_t i, AccT s) {
+        out[i] = csub ? (OT)((double)s - c) : (OT)s;
+    }
+    template <class AccT>
+    __device__ __forceinline__ void segment_block(int64_t i, AccT s) {
+        if (threadIdx.x == 0) segment(i, s);
+    }
+    __device__ __forceinline__ void end(Shared &) {}
+};
+
+// FP64 Laplacian rows of the operator apply: v_i = omega [y_i != 0] u_i + alpha (D_ii u_i - s_i)
+struct EpiLap64 {
+    using Shared = NoShared;
+    double *v;
+    const double *u, *deg;
+    const int8_t *y;
+    double omega, alpha;
+    __device__ __forceinline__ bool skip() const { return false; }
+    __device__ __forceinline__ void begin(Shared &) {}
+    __device__ __forceinline__ void segment(int64_t i, double s) {
+        const double ui = u[i];
+        v[i] = omega * (y[i] != 0 ? ui : 0.0) + alpha * (deg[i] * ui - s);
+    }
+    __device__ __forceinline__ void segment_block(int64_t i, double s) {
+        if (threadIdx.x == 0) segment(i, s);
+    }
+    __device__ __forceinline__ void end(Shared &) {}
+};
+
+// FP64 columns of the operator apply: q_j = s_j - mu_j t + sigma p_j
+struct EpiApply {
+    using Shared = NoShared;
+    double *q;
+    const double *mu, *p, *t;
+    double sigma, tv;
+    __device__ __forceinline__ bool skip() const { return false; }
+    __device__ __forceinline__ void begin(Shared &) { tv = *t; }
+    __device__ __forceinline__ void segment(int64_t j, double s) { q[j] = s - mu[j] * tv + sigma * p[j]; }
+    __device__ __forceinline__ void segment_block(int64_t j, double s) {
+        if (threadIdx.x == 0) segment(j, s);
+    }
+    __device__ __forceinline__ void end(Shared &) {}
+};
+
+// phase 1: ut_i = sum - <mu, p_k>
+template <class FT>
+struct EpiP1 {
+    using Shared = NoShared;
+    FT *ut;
+    const SolveState *st;
+    double c;
+    __device__ __forceinline__ bool skip() const { return st->done != 0; }
+    __device__ __forceinline__ void begin(Shared &) { c = st->c; }
+    __device__ __forceinline__ void segment(int64_t i, FT s) { ut[i] = (FT)((double)s - c); }
+    __device__ __forceinline__ void segment_block(int64_t i, FT s) {
+        if (threadIdx.x == 0) segment(i, s);
+    }
+    __device__ __forceinline__ void end(Shared &) {}
+};
+
+// Sum of the grid's partials in block order (called by every thread of the last block).
+template <int NDOT>
+__device__ __forceinline__ void grid_dots(double *partials, int nblocks, double (&tot)[NDOT], double *red) {
+#pragma unroll
+    for (int k = 0; k < NDOT; ++k) tot[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kBlock) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) tot[k] += __ldcg(partials + (int64_t)b * NDOT + k);
+    }
+#pragma unroll
+    for (int k = 0; k < NDOT; ++k) tot[k] = block_sum(tot[k], red);
+}
+
+// phase 2: v_i = omega [y_i != 0] ut_i + alpha (D_ii ut_i - s_i); dots <ut, v>, 1^T v;
+// the last block forms gamma_k and zeta^s_{k+1}, gamma^s_k
+template <class FT>
+struct EpiP2 {
+    struct Shared {
+        double red[kBlock / 32];
+        int ok;
+    };
+    FT *v;
+    const FT *ut, *deg;
+    SolveState *st;
+    double *partials;
+    unsigned *counter;
+    const int8_t *y;
+    double omega, al, d0, d1;
+    __device__ __forceinline__ bool skip() const { return st->done != 0; }
+    __device__ __forceinline__ void begin(Shared &) {
+        y = st->labels;
+        omega = st->omega;
+        al = st->alpha_l;
+        d0 = d1 = 0.0;
+    }
+    __device__ __forceinline__ void segment(int64_t i, FT s) {
+        const double u = (double)ut[i];
+        const double vi = omega * (y[i] != 0 ? u : 0.0) + al * ((double)deg[i] * u - (double)s);
+        const FT vf = (FT)vi;
+        v[i] = vf;
+        d0 += u * (double)vf;
+        d1 += (double)vf;
+    }
+    __device__ __forceinline__ void segment_block(int64_t i, FT s) {
+        if (threadIdx.x == 0) segment(i, s);
+    }
+    __device__ void end(Shared &sh) {
+        double mine[2] = {block_sum(d0, sh.red), block_sum(d1, sh.red)};
+        if (!arrive_last<2>(mine, partials, counter)) return;
+        double tot[2];
+        grid_dots<2>(partials, gridDim.x, tot, sh.red);
+        if (threadIdx.x == 0) {
+            const double pq = tot[0] + st->sigma0 * st->pp;
+            sh.ok = (pq > 0.0) && isfinite(pq);
+            if (!sh.ok) {
+                st->status = SDA_ERR_BREAKDOWN;
+                st->done = 1;
+            } else {
+                st->gamma = -st->rr / pq;
+                st->t = tot[1];
+            }
+            *counter = 0u;
+        }
+        __syncthreads();
+        if (!sh.ok) return;
+        const double gam = st->gamma, gp = st->gamma_prev, al_k = st->alpha;
+        for (int q = threadIdx.x; q < st->n_shifts; q += kBlock) {
+            ShiftState &h = st->sh[q];
+            if (!h.active) continue;
+            const double den = gam * al_k * (h.z_prev - h.z) + h.z_prev * gp * (1.0 - h.delta * gam);
+            const double zn = h.z_prev * h.z * gp / den;
+            h.z_next = zn;
+            h.g = gam * zn / h.z;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// shifted CG (Algorithm 3): start and vector/shift-state update
+// ---------------------------------------------------------------------------
+// Workspace vectors have leading dimension ldw (D rounded up to 8, padding kept
+// at zero): RP[2][ldw] interleaved {r, p} (RP[k & 1] holds {r_k, p_{k-1}}),
+// s[ldw] = X^T v, and the shift state W[S][ldw], P[S][ldw].
 
 template <class FT>
 struct Vec16;
@@ -225,35 +341,45 @@ template <>
 struct Vec16<float> {
     using T = float4;
     static constexpr int n = 4;
-    static __device__ __forceinline__ float get(const T &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
-    static __device__ __forceinline__ void set(T &v, int i, float x) {
-        if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
-    }
 };
 template <>
 struct Vec16<double> {
     using T = double2;
     static constexpr int n = 2;
-    static __device__ __forceinline__ double get(const T &v, int i) { return i == 0 ? v.x : v.y; }
-    static __device__ __forceinline__ void set(T &v, int i, double x) {
-        if (i == 0) v.x = x; else v.y = x;
-    }
 };
+__device__ __forceinline__ float v16_get(const float4 &v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void v16_set(float4 &v, int i, float x) {
+    if (i == 0) v.x = x;
+    else if (i == 1) v.y = x;
+    else if (i == 2) v.z = x;
+    else v.w = x;
+}
+__device__ __forceinline__ double v16_get(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
+__device__ __forceinline__ void v16_set(double2 &v, int i, double x) {
+    if (i == 0) v.x = x;
+    else v.y = x;
+}
 
-// r_0 = b, p_{-1} = 0, W = 0, P_{-1} = 0; <r,r>, <mu,r>; scalar start values.
+// RP[0] = {b, 0}, RP[1] = 0, W = 0, P_{-1} = 0; <r,r>, <mu,r>; scalar start values
 template <class FT>
-__global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, const double *__restrict__ b, FT *r,
-                                                    FT *p, FT *W, FT *P, SolveState *st, double *partials,
-                                                    unsigned *counter) {
+__global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, const double *__restrict__ b,
+                                                    typename RPair<FT>::T *rp, FT *W, FT *P, SolveState *st,
+                                                    double *partials, unsigned *counter) {
+    using R = typename RPair<FT>::T;
     __shared__ double red[kBlock / 32];
     const int ns = st->n_shifts;
     const double *mu = st->mu;
     double d0 = 0.0, d1 = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < ldw; j += (int64_t)gridDim.x * kBlock) {
         const FT rj = j < d ? (FT)b[j] : (FT)0;
-        r[j] = rj;
-        r[ldw + j] = (FT)0;
-        p[j] = (FT)0;
+        R x;
+        x.x = rj;
+        x.y = (FT)0;
+        rp[j] = x;
+        x.x = (FT)0;
+        rp[ldw + j] = x;
         for (int s = 0; s < ns; ++s) {
             W[(int64_t)s * ldw + j] = (FT)0;
             P[(int64_t)s * ldw + j] = (FT)0;
@@ -263,12 +389,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, cons
             d1 += mu[j] * (double)rj;
         }
     }
-    double mine[2];
-    mine[0] = block_sum(d0, red);
-    mine[1] = block_sum(d1, red);
+    double mine[2] = {block_sum(d0, red), block_sum(d1, red)};
     if (!arrive_last<2>(mine, partials, counter)) return;
     double tot[2];
-    reduce_partials<2>(partials, gridDim.x, tot, red);
+    grid_dots<2>(partials, gridDim.x, tot, red);
     if (threadIdx.x == 0) {
         st->rr = tot[0];
         st->bnorm = sqrt(tot[0]);
@@ -304,144 +428,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, cons
     }
 }
 
-// phase 1: ut = X p_k - c_k with p_k = r_k + alpha_k p_{k-1}; the first `head`
-// entries of p_k (the most frequent features) are formed once per block in
-// shared memory, the rest on the fly at the gather.
-template <class VT, class FT, int G>
-__global__ void __launch_bounds__(kBlock) k_cg_phase1(int64_t n, int head, const int64_t *__restrict__ rp,
-                                                      const int32_t *__restrict__ col,
-                                                      const VT *__restrict__ val, const FT *__restrict__ r,
-                                                      int64_t ldw, const FT *__restrict__ p, FT *__restrict__ ut,
-                                                      const SolveState *__restrict__ st) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    FT *sp = reinterpret_cast<FT *>(smem_raw);
-    if (st->done) return;
-    const FT a = (FT)st->alpha;
-    const double c = st->c;
-    const FT *__restrict__ rc = r + (st->k & 1) * ldw;
-    for (int f = threadIdx.x; f < head; f += kBlock) sp[f] = form_p<FT>(rc[f], p[f], a);
-    __syncthreads();
-    constexpr int RPW = 32 / G;
-    const int lane = threadIdx.x % G;
-    const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
-    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
-        const int64_t i = base + (threadIdx.x & 31) / G;
-        FT acc = 0;
-        if (i < n) {
-            const int64_t e1 = rp[i + 1];
-            for (int64_t e = rp[i] + lane; e < e1; e += G) {
-                const int32_t j = col[e];
-                const FT pj = j < head ? sp[j] : form_p<FT>(rc[j], p[j], a);
-                acc += (FT)Val<VT>::get(val, e) * pj;
-            }
-        }
-#pragma unroll
-        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (i < n && lane == 0) ut[i] = (FT)((double)acc - c);
-    }
-}
-
-// phase 2: v = omega P_l ut + alpha (D ut - S ut); dots <ut,v>, 1^T v; then gamma_k and zeta^s_{k+1}
-template <class FT, int G>
-__global__ void __launch_bounds__(kBlock) k_cg_phase2(int64_t n, const int64_t *__restrict__ rp,
-                                                      const int32_t *__restrict__ col,
-                                                      const FT *__restrict__ sv, const FT *__restrict__ deg,
-                                                      const FT *__restrict__ ut, FT *__restrict__ v,
-                                                      SolveState *st, double *partials, unsigned *counter) {
-    __shared__ double red[kBlock / 32];
-    if (st->done) return;
-    const int8_t *__restrict__ y = st->labels;
-    const double omega = st->omega, al = st->alpha_l;
-    constexpr int RPW = 32 / G;
-    const int lane = threadIdx.x % G;
-    const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
-    double d0 = 0.0, d1 = 0.0;
-    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
-        const int64_t i = base + (threadIdx.x & 31) / G;
-        FT acc = 0;
-        FT ui = 0, di = 0;
-        int8_t yi = 0;
-        if (i < n) {
-            if (lane == 0) {   // loads of the row's own entries, issued before the gathers
-                ui = ut[i];
-                di = deg[i];
-                yi = y[i];
-            }
-            const int64_t e1 = rp[i + 1];
-            for (int64_t e = rp[i] + lane; e < e1; e += G) acc += sv[e] * ut[col[e]];
-        }
-#pragma unroll
-        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (i < n && lane == 0) {
-            const double u = (double)ui;
-            const double vi = omega * (yi != 0 ? u : 0.0) + al * ((double)di * u - (double)acc);
-            const FT vf = (FT)vi;
-            v[i] = vf;
-            d0 += u * (double)vf;
-            d1 += (double)vf;
-        }
-    }
-    double mine[2];
-    mine[0] = block_sum(d0, red);
-    mine[1] = block_sum(d1, red);
-    if (!arrive_last<2>(mine, partials, counter)) return;
-    double tot[2];
-    reduce_partials<2>(partials, gridDim.x, tot, red);
-    if (threadIdx.x == 0) {
-        const double pq = tot[0] + st->sigma0 * st->pp;
-        if (!(pq > 0.0) || !isfinite(pq)) {
-            st->status = SDA_ERR_BREAKDOWN;
-            st->done = 1;
-        } else {
-            st->gamma = -st->rr / pq;
-            st->t = tot[1];
-        }
-        *counter = 0u;
-    }
-    __syncthreads();
-    if (st->status != SDA_OK) return;
-    const double gam = st->gamma, gp = st->gamma_prev, al_k = st->alpha;
-    for (int s = threadIdx.x; s < st->n_shifts; s += kBlock) {
-        ShiftState &h = st->sh[s];
-        if (!h.active) continue;
-        const double den = gam * al_k * (h.z_prev - h.z) + h.z_prev * gp * (1.0 - h.delta * gam);
-        const double zn = h.z_prev * h.z * gp / den;
-        h.z_next = zn;
-        h.g = gam * zn / h.z;
-    }
-}
-
-template <class FT>
-struct EpiStoreFT {
-    FT *s;
-    template <class AccT>
-    __device__ __forceinline__ void column(int64_t j, AccT x) { s[j] = (FT)x; }
-    template <class AccT>
-    __device__ __forceinline__ void column_block(int64_t j, AccT x) {
-        if (threadIdx.x == 0) s[j] = (FT)x;
-    }
-};
-
-// phase 3a: s = X^T v (column tiles)
-template <class VT, class FT>
-__global__ void __launch_bounds__(kBlock) k_cg_phase3a(const Tile *__restrict__ tiles, int ntiles,
-                                                       const int64_t *__restrict__ cp,
-                                                       const int32_t *__restrict__ row, const VT *__restrict__ val,
-                                                       const FT *__restrict__ v, FT *__restrict__ s,
-                                                       const SolveState *__restrict__ st, FT *slots,
-                                                       unsigned *lcount, const SplitSeg *__restrict__ splits) {
-    __shared__ FT buf[kTileNnz];
-    __shared__ FT redf[kBlock / 32];
-    if (st->done) return;
-    EpiStoreFT<FT> epi{s};
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const Tile tl = tiles[t];
-        col_tile<VT, FT, EpiStoreFT<FT>>(tl, cp, row, val, v, slots, lcount, splits, epi, buf, redf);
-    }
-}
-
 // block-cached scalars of phase 3b
 template <class FT>
 struct P3Shared {
@@ -451,89 +437,112 @@ struct P3Shared {
     FT zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
 };
 
-// phase 3b: q = s - mu t + sigma0 p_k;  r_{k+1} = r_k + gamma_k q;  p <- p_k;
+// r_k of VW consecutive features from the interleaved buffer
+__device__ __forceinline__ void load_r(const float2 *a, int64_t j0, float (&r)[4]) {
+    const float4 u = *reinterpret_cast<const float4 *>(a + j0);
+    const float4 w = *reinterpret_cast<const float4 *>(a + j0 + 2);
+    r[0] = u.x;
+    r[1] = u.z;
+    r[2] = w.x;
+    r[3] = w.z;
+}
+__device__ __forceinline__ void load_r(const double2 *a, int64_t j0, double (&r)[2]) {
+    r[0] = a[j0].x;
+    r[1] = a[j0 + 1].x;
+}
+
+// phase 3b: q = s - mu t + sigma0 p_k;  r_{k+1} = r_k + gamma_k q;  RP[k+1] = {r_{k+1}, p_k};
 // P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1};  W^s_{k+1} = W^s_k - gamma^s_k P^s_k
-// over the flattened (1 + active shifts) x columns space, 16-byte vectors for
+// over the flattened (1 + active shifts) x features space, 16-byte vectors for
 // the shift state; then alpha_{k+1}, <mu, p_{k+1}>, <p_{k+1}, p_{k+1}>, stop tests.
 template <class FT>
 __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, const FT *__restrict__ s,
-                                                       FT *__restrict__ r, FT *__restrict__ p, FT *__restrict__ W,
-                                                       FT *__restrict__ P, SolveState *st, double *partials,
-                                                       unsigned *counter) {
+                                                       typename RPair<FT>::T *__restrict__ rp,
+                                                       FT *__restrict__ W, FT *__restrict__ P, SolveState *st,
+                                                       double *partials, unsigned *counter) {
     using V = typename Vec16<FT>::T;
+    using R = typename RPair<FT>::T;
     constexpr int VW = Vec16<FT>::n;
     __shared__ double red[kBlock / 32];
     __shared__ P3Shared<FT> sm;
+    __shared__ double s_alpha_new, s_rnorm;
     if (st->done) return;
-    if (threadIdx.x == 0) {
-        sm.alpha = st->alpha;
-        sm.gamma = st->gamma;
-        sm.t = st->t;
-        sm.sigma0 = st->sigma0;
+    if (threadIdx.x < 32) {   // one warp compacts the active shifts
+        const int lane = threadIdx.x, ns = st->n_shifts;
         int na = 0;
-        for (int q = 0; q < st->n_shifts; ++q) {
-            const ShiftState &h = st->sh[q];
-            if (!h.active) continue;
-            sm.act[na] = q;
-            sm.zk[na] = (FT)h.z;
-            sm.ak[na] = (FT)h.a;
-            sm.gk[na] = (FT)h.g;
-            ++na;
+        for (int base = 0; base < ns; base += 32) {
+            const int q = base + lane;
+            const bool act = q < ns && st->sh[q].active;
+            const unsigned m = __ballot_sync(0xffffffffu, act);
+            if (act) {
+                const int pos = na + __popc(m & ((1u << lane) - 1u));
+                const ShiftState &h = st->sh[q];
+                sm.act[pos] = q;
+                sm.zk[pos] = (FT)h.z;
+                sm.ak[pos] = (FT)h.a;
+                sm.gk[pos] = (FT)h.g;
+            }
+            na += __popc(m);
         }
-        sm.nact = na;
+        if (lane == 0) {
+            sm.nact = na;
+            sm.alpha = st->alpha;
+            sm.gamma = st->gamma;
+            sm.t = st->t;
+            sm.sigma0 = st->sigma0;
+        }
     }
     __syncthreads();
     const int par = st->k & 1;
-    const FT *__restrict__ rc = r + par * ldw;
-    FT *__restrict__ rn = r + (par ^ 1) * ldw;
+    const R *__restrict__ a = rp + par * ldw;
+    R *__restrict__ an_ = rp + (par ^ 1) * ldw;
     const double *__restrict__ mu = st->mu;
     const FT al = (FT)sm.alpha;
     const uint32_t nch = (uint32_t)(ldw / VW);
     const uint32_t total = (uint32_t)(sm.nact + 1) * nch;
     double d0 = 0.0, d1 = 0.0, d2 = 0.0;
     for (uint32_t idx = blockIdx.x * kBlock + threadIdx.x; idx < total; idx += gridDim.x * kBlock) {
-        const uint32_t a = idx / nch;
-        const int64_t j0 = (int64_t)(idx - a * nch) * VW;
-        if (a == 0) {
+        const uint32_t q = idx / nch;
+        const int64_t j0 = (int64_t)(idx - q * nch) * VW;
+        if (q == 0) {
 #pragma unroll
             for (int u = 0; u < VW; ++u) {
                 const int64_t j = j0 + u;
                 if (j >= d) break;
-                const FT rj = rc[j];
-                const FT pk = form_p<FT>(rj, p[j], al);
+                const R x = a[j];
+                const FT pk = form_p<FT>(x.x, x.y, al);
                 const double mj = mu[j];
-                const double q = (double)s[j] - mj * sm.t + sm.sigma0 * (double)pk;
-                const FT rnj = (FT)((double)rj + sm.gamma * q);
-                rn[j] = rnj;
-                p[j] = pk;
+                const double qj = (double)s[j] - mj * sm.t + sm.sigma0 * (double)pk;
+                const FT rnj = (FT)((double)x.x + sm.gamma * qj);
+                R y;
+                y.x = rnj;
+                y.y = pk;
+                an_[j] = y;
                 d0 += (double)rnj * (double)rnj;
                 d1 += mj * (double)rnj;
                 d2 += (double)rnj * (double)pk;
             }
         } else {
-            const int q = sm.act[a - 1];
-            const FT z = sm.zk[a - 1], aa = sm.ak[a - 1], g = sm.gk[a - 1];
-            const V rv = *reinterpret_cast<const V *>(rc + j0);
-            V pv = *reinterpret_cast<const V *>(P + (int64_t)q * ldw + j0);
-            V wv = *reinterpret_cast<const V *>(W + (int64_t)q * ldw + j0);
+            const int sh = sm.act[q - 1];
+            const FT z = sm.zk[q - 1], aa = sm.ak[q - 1], g = sm.gk[q - 1];
+            FT r[VW];
+            load_r(a, j0, r);
+            V pv = *reinterpret_cast<const V *>(P + (int64_t)sh * ldw + j0);
+            V wv = *reinterpret_cast<const V *>(W + (int64_t)sh * ldw + j0);
 #pragma unroll
             for (int u = 0; u < VW; ++u) {
-                const FT pn = z * Vec16<FT>::get(rv, u) + aa * Vec16<FT>::get(pv, u);
-                Vec16<FT>::set(pv, u, pn);
-                Vec16<FT>::set(wv, u, Vec16<FT>::get(wv, u) - g * pn);
+                const FT pn = z * r[u] + aa * v16_get(pv, u);
+                v16_set(pv, u, pn);
+                v16_set(wv, u, v16_get(wv, u) - g * pn);
             }
-            *reinterpret_cast<V *>(P + (int64_t)q * ldw + j0) = pv;
-            *reinterpret_cast<V *>(W + (int64_t)q * ldw + j0) = wv;
+            *reinterpret_cast<V *>(P + (int64_t)sh * ldw + j0) = pv;
+            *reinterpret_cast<V *>(W + (int64_t)sh * ldw + j0) = wv;
         }
     }
-    double mine[3];
-    mine[0] = block_sum(d0, red);
-    mine[1] = block_sum(d1, red);
-    mine[2] = block_sum(d2, red);
+    double mine[3] = {block_sum(d0, red), block_sum(d1, red), block_sum(d2, red)};
     if (!arrive_last<3>(mine, partials, counter)) return;
     double tot[3];
-    reduce_partials<3>(partials, gridDim.x, tot, red);
-    __shared__ double s_alpha_new, s_rnorm;
+    grid_dots<3>(partials, gridDim.x, tot, red);
     if (threadIdx.x == 0) {
         const double rr_new = tot[0];
         const double an = rr_new / st->rr;
@@ -573,5 +582,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
         st->done = (na == 0 || k >= st->limit || st->status != SDA_OK) ? 1 : 0;
     }
 }
+
+// <a, b> (or the sum of a when b is NULL) into *out, fixed-order reduction
+__global__ void __launch_bounds__(kBlock) k_dot_f64(int64_t n, const double *__restrict__ a,
+                                                    const double *__restrict__ b, double *out,
+                                                    double *partials, unsigned *counter);
 
 }  // namespace sda

@@ -48,8 +48,8 @@ struct Workspace {
     int64_t d = 0, n = 0, ldw = 0;   // ldw: D rounded up to 8 (leading dimension of D-vectors)
     int n_shifts = 0;
     int vt = -1;                     // compute dtype the grids below were sized for
-    int grid1 = 0, grid2 = 0, grid3a = 0, grid3b = 0, head = 0;
-    DevBuf<char> vec;        // r[2][ldw], p[ldw], s[ldw], ut[N], v[N] in the vector type
+    int grid1 = 0, grid2 = 0, grid3a = 0, grid3b = 0;
+    DevBuf<char> vec;        // RP[2][ldw] ({r, p} pairs), s[ldw], ut[N], v[N] in the vector type
     DevBuf<char> shift;      // W[S][ldw], P[S][ldw] in the vector type
     DevBuf<SolveState> st;
     DevBuf<double> part;     // [3][grid][4] block partials of init / phase 2 / phase 3
@@ -90,14 +90,15 @@ struct sda_operator {
     sda::DevBuf<double> mu;              // [T][D] mu_l, permuted order
     sda::DevBuf<double> dvec;            // [T][D] mu_+ - mu_-, permuted order
     std::vector<double> counts;          // [T][3]: l, N+, N-
-    // schedule of the X^T pass
-    sda::ColSchedule col;
-    int x_lanes = 32, s_lanes = 8;       // lanes per row of the X and S row passes
+    // tile schedules of the sparse passes: columns of X, rows of X, rows of S;
+    // their split segments use disjoint ranges of the slots / counters below
+    sda::ColSchedule col, xrow, srow;
+    int32_t xrow_slot0 = 0, srow_slot0 = 0, xrow_lseg0 = 0, srow_lseg0 = 0;
     int grid = 0;                         // blocks of every persistent-style pass
     int64_t bytes = 0;
     // scratch of the column pass and of the FP64 reductions
-    sda::DevBuf<double> slots;            // split-column partial sums
-    sda::DevBuf<unsigned> lcount;         // split-column arrival counters (kept at zero)
+    sda::DevBuf<double> slots;            // split-segment partial sums (the three schedules share them)
+    sda::DevBuf<unsigned> lcount;         // split-segment arrival counters (kept at zero)
     sda::DevBuf<double> part;             // block partials of the FP64 reductions
     sda::DevBuf<unsigned> cnt;            // their arrival counters (kept at zero)
     sda::DevBuf<double> scal;             // device scalars of the FP64 operator apply

@@ -220,15 +220,16 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, cu
 }
 
 // ---------------------------------------------------------------------------
-// column tiles for the X^T pass
+// tiles of consecutive segments
 // ---------------------------------------------------------------------------
+// lanes that sum one segment of a streamed tile: at most four products each
 static int lanes_for(int64_t maxlen) {
     int g = 1;
-    while (g < 32 && 2 * g < maxlen) g <<= 1;   // about two nonzeros per lane
+    while (g < 32 && 4 * g < maxlen) g <<= 1;
     return g;
 }
 
-int build_col_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
+int build_seg_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
     const int64_t d = (int64_t)colptr.size() - 1;
     std::vector<Tile> tiles;
     std::vector<SplitSeg> splits;
@@ -263,9 +264,7 @@ int build_col_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
             maxlen = std::max(maxlen, l);
             ++j;
         }
-        // short columns: stream the tile's nonzeros (lanes -1); else a group of lanes per column
-        const int32_t lanes = maxlen <= kStreamSeg ? -1 : lanes_for(maxlen);
-        tiles.push_back(Tile{colptr[start], colptr[j], (int32_t)start, (int32_t)j, lanes, -1, -1, 0});
+        tiles.push_back(Tile{colptr[start], colptr[j], (int32_t)start, (int32_t)j, lanes_for(maxlen), -1, -1, 0});
     }
     if (slots > INT32_MAX || (int64_t)tiles.size() > INT32_MAX)
         return fail(SDA_ERR_UNSUPPORTED, "column schedule too large");

@@ -111,41 +111,36 @@ static int with_vt(int compute, F &&f) {
     }
 }
 
-template <class F>
-static int with_lanes(int g, F &&f) {
-    switch (g) {
-    case 1:
-    case 2: return f(std::integral_constant<int, 2>());
-    case 4: return f(std::integral_constant<int, 4>());
-    case 8: return f(std::integral_constant<int, 8>());
-    case 16: return f(std::integral_constant<int, 16>());
-    default: return f(std::integral_constant<int, 32>());
-    }
-}
-
 // ---------------------------------------------------------------------------
 // FP64 operator pieces (permuted feature order)
 // ---------------------------------------------------------------------------
+// a sparse pass with one of the operator's schedules
+template <class VT, class AccT, class Gather, class Epi>
+static int segpass(const sda_operator *op, const ColSchedule &sc, int32_t slot0, int32_t lseg0,
+                   const int64_t *ptr, const int32_t *idx, const void *val, const Gather &g, const Epi &e,
+                   int grid, cudaStream_t s) {
+    k_segpass<VT, AccT, Gather, Epi><<<grid, kBlock, 0, s>>>(sc.tiles.p, sc.ntiles, ptr, idx, (const VT *)val, g, e,
+                                                            (AccT *)op->slots.p + slot0, op->lcount.p + lseg0,
+                                                            sc.splits.p);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
 int op_xtmul_f64(const sda_operator *op, const double *v, double *q, cudaStream_t s) {
     return with_vt(op->compute, [&](auto tag) -> int {
         using VT = std::remove_pointer_t<decltype(tag)>;
-        k_cols_f64<VT, EpiStore><<<op->grid, kBlock, 0, s>>>(
-            op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p, (const VT *)op->x_val_c.p, v, op->slots.p,
-            op->lcount.p, op->col.splits.p, EpiStore{q});
-        SDA_LAUNCHED();
-        return SDA_OK;
+        return segpass<VT, double>(op, op->col, 0, 0, op->x_cp.p, op->x_row.p, op->x_val_c.p,
+                                   GatherVec<double, double>{v}, EpiStore<double>{q, nullptr, nullptr, 0.0}, op->grid,
+                                   s);
     });
 }
 
 int op_xmul_f64(const sda_operator *op, const double *w, double *u, const double *csub, cudaStream_t s) {
     return with_vt(op->compute, [&](auto tag) -> int {
         using VT = std::remove_pointer_t<decltype(tag)>;
-        return with_lanes(op->x_lanes, [&](auto G) -> int {
-            k_rows_f64<VT, decltype(G)::value><<<op->grid, kBlock, 0, s>>>(
-                op->n, op->x_rp.p, op->x_col.p, (const VT *)op->x_val_r.p, w, u, csub);
-            SDA_LAUNCHED();
-            return SDA_OK;
-        });
+        return segpass<VT, double>(op, op->xrow, op->xrow_slot0, op->xrow_lseg0, op->x_rp.p, op->x_col.p,
+                                   op->x_val_r.p, GatherVec<double, double>{w},
+                                   EpiStore<double>{u, csub, nullptr, 0.0}, op->grid, s);
     });
 }
 
@@ -171,20 +166,15 @@ int op_apply_f64(const sda_operator *op, int target, double sigma, const double 
     const int8_t *y = op->labels.p + (int64_t)target * op->n;
     SDA_TRY(dot_f64(op, op->d, mu, p, op->scal.p + 0, s));
     SDA_TRY(op_xmul_f64(op, p, u, op->scal.p + 0, s));
-    SDA_TRY(with_lanes(op->s_lanes, [&](auto G) -> int {
-        k_lap_f64<decltype(G)::value><<<op->grid, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, op->s_val64.p,
-                                                                 op->deg64.p, y, op->omega, op->alpha, u, v);
-        SDA_LAUNCHED();
-        return SDA_OK;
-    }));
+    SDA_TRY((segpass<double, double>(op, op->srow, op->srow_slot0, op->srow_lseg0, op->s_rp.p, op->s_col.p,
+                                     op->s_val64.p, GatherVec<double, double>{u},
+                                     EpiLap64{v, u, op->deg64.p, y, op->omega, op->alpha}, op->grid, s)));
     SDA_TRY(dot_f64(op, op->n, v, nullptr, op->scal.p + 1, s));
     return with_vt(op->compute, [&](auto tag) -> int {
         using VT = std::remove_pointer_t<decltype(tag)>;
-        k_cols_f64<VT, EpiApply><<<op->grid, kBlock, 0, s>>>(
-            op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p, (const VT *)op->x_val_c.p, v, op->slots.p,
-            op->lcount.p, op->col.splits.p, EpiApply{q, mu, p, op->scal.p + 1, sigma});
-        SDA_LAUNCHED();
-        return SDA_OK;
+        return segpass<VT, double>(op, op->col, 0, 0, op->x_cp.p, op->x_row.p, op->x_val_c.p,
+                                   GatherVec<double, double>{v}, EpiApply{q, mu, p, op->scal.p + 1, sigma, 0.0},
+                                   op->grid, s);
     });
 }
 
@@ -237,7 +227,7 @@ static int ensure_workspace(sda_operator *op, int ns) {
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
     w.graph_iters = 0;
-    SDA_TRY(w.vec.alloc((size_t)(4 * ldw + 2 * op->n) * fsz));
+    SDA_TRY(w.vec.alloc((size_t)(5 * ldw + 2 * op->n) * fsz));
     SDA_TRY(w.shift.alloc((size_t)(2 * (int64_t)ns * ldw) * fsz));
     SDA_TRY(w.st.alloc(1));
     SDA_TRY(w.part.alloc((size_t)3 * kMaxBlocksPerSm * op->sm_count * 4));
@@ -256,7 +246,8 @@ static int ensure_workspace(sda_operator *op, int ns) {
 
 template <class FT>
 struct WsView {
-    FT *r, *p, *s, *ut, *v, *W, *P;
+    typename RPair<FT>::T *rp;
+    FT *s, *ut, *v, *W, *P;
 };
 
 template <class FT>
@@ -265,18 +256,26 @@ static WsView<FT> view(const sda_operator *op) {
     FT *base = (FT *)w.vec.p;
     FT *sb = (FT *)w.shift.p;
     const int64_t l = w.ldw;
-    return WsView<FT>{base, base + 2 * l, base + 3 * l, base + 4 * l, base + 4 * l + op->n, sb,
+    return WsView<FT>{(typename RPair<FT>::T *)base, base + 4 * l, base + 5 * l, base + 5 * l + op->n, sb,
                       sb + (int64_t)w.n_shifts * l};
 }
 
-static int grid_of(const void *kernel, size_t dyn, int sms) {
+static int grid_of(const void *kernel, int sms) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, dyn) != cudaSuccess || nb <= 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, 0) != cudaSuccess || nb <= 0) {
         (void)cudaGetLastError();
         nb = 1;
     }
     return std::min(nb, kMaxBlocksPerSm) * sms;
 }
+
+template <class VT, class FT>
+struct PhaseKernels {
+    using K1 = GatherP<FT>;
+    static constexpr auto p1 = k_segpass<VT, FT, GatherP<FT>, EpiP1<FT>>;
+    static constexpr auto p2 = k_segpass<FT, FT, GatherVec<FT, FT>, EpiP2<FT>>;
+    static constexpr auto p3a = k_segpass<VT, FT, GatherVec<FT, FT>, EpiStore<FT>>;
+};
 
 // sizes the grids of the iteration kernels for this operator's dtypes
 template <class VT, class FT>
@@ -284,17 +283,10 @@ static int size_grids(sda_operator *op) {
     Workspace &w = op->ws;
     if (w.vt == (int)op->compute) return SDA_OK;
     const int sms = op->sm_count;
-    w.head = (int)std::min<int64_t>(op->d, std::is_same<FT, double>::value ? kHeadF64 : kHeadF32);
-    SDA_TRY(with_lanes(op->x_lanes, [&](auto G) -> int {
-        w.grid1 = grid_of((const void *)k_cg_phase1<VT, FT, decltype(G)::value>, (size_t)w.head * sizeof(FT), sms);
-        return SDA_OK;
-    }));
-    SDA_TRY(with_lanes(op->s_lanes, [&](auto G) -> int {
-        w.grid2 = grid_of((const void *)k_cg_phase2<FT, decltype(G)::value>, 0, sms);
-        return SDA_OK;
-    }));
-    w.grid3a = grid_of((const void *)k_cg_phase3a<VT, FT>, 0, sms);
-    w.grid3b = grid_of((const void *)k_cg_phase3b<FT>, 0, sms);
+    w.grid1 = grid_of((const void *)PhaseKernels<VT, FT>::p1, sms);
+    w.grid2 = grid_of((const void *)PhaseKernels<VT, FT>::p2, sms);
+    w.grid3a = grid_of((const void *)PhaseKernels<VT, FT>::p3a, sms);
+    w.grid3b = grid_of((const void *)k_cg_phase3b<FT>, sms);
     w.vt = (int)op->compute;
     return SDA_OK;
 }
@@ -307,32 +299,25 @@ static int launch_iteration(const sda_operator *op, cudaStream_t s, cudaEvent_t 
     WsView<FT> b = view<FT>(op);
     const FT *sv = std::is_same<FT, double>::value ? (const FT *)op->s_val64.p : (const FT *)op->s_val32.p;
     const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
+    const size_t P = (size_t)kMaxBlocksPerSm * op->sm_count;
     if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
-    SDA_TRY(with_lanes(op->x_lanes, [&](auto G) -> int {
-        k_cg_phase1<VT, FT, decltype(G)::value><<<w.grid1, kBlock, (size_t)w.head * sizeof(FT), s>>>(
-            op->n, w.head, op->x_rp.p, op->x_col.p, (const VT *)op->x_val_r.p, b.r, w.ldw, b.p, b.ut, w.st.p);
-        SDA_LAUNCHED();
-        return SDA_OK;
-    }));
+    SDA_TRY((segpass<VT, FT>(op, op->xrow, op->xrow_slot0, op->xrow_lseg0, op->x_rp.p, op->x_col.p, op->x_val_r.p,
+                             GatherP<FT>{b.rp, w.ldw, w.st.p, nullptr, (FT)0}, EpiP1<FT>{b.ut, w.st.p, 0.0}, w.grid1,
+                             s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[2], s));
-    SDA_TRY(with_lanes(op->s_lanes, [&](auto G) -> int {
-        k_cg_phase2<FT, decltype(G)::value><<<w.grid2, kBlock, 0, s>>>(
-            op->n, op->s_rp.p, op->s_col.p, sv, dg, b.ut, b.v, w.st.p, w.part.p + (size_t)kMaxBlocksPerSm * op->sm_count * 4,
-            w.cnt.p + 1);
-        SDA_LAUNCHED();
-        return SDA_OK;
-    }));
+    SDA_TRY((segpass<FT, FT>(op, op->srow, op->srow_slot0, op->srow_lseg0, op->s_rp.p, op->s_col.p, sv,
+                             GatherVec<FT, FT>{b.ut},
+                             EpiP2<FT>{b.v, b.ut, dg, w.st.p, w.part.p + P * 4, w.cnt.p + 1, nullptr, 0, 0, 0, 0},
+                             w.grid2, s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[3], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[4], s));
-    k_cg_phase3a<VT, FT><<<w.grid3a, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
-                                                    (const VT *)op->x_val_c.p, b.v, b.s, w.st.p, (FT *)op->slots.p,
-                                                    op->lcount.p, op->col.splits.p);
-    SDA_LAUNCHED();
+    SDA_TRY((segpass<VT, FT>(op, op->col, 0, 0, op->x_cp.p, op->x_row.p, op->x_val_c.p, GatherVec<FT, FT>{b.v},
+                             EpiStore<FT>{b.s, nullptr, w.st.p, 0.0}, w.grid3a, s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
-    k_cg_phase3b<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b.s, b.r, b.p, b.W, b.P, w.st.p,
-                                                 w.part.p + (size_t)kMaxBlocksPerSm * op->sm_count * 8, w.cnt.p + 2);
+    k_cg_phase3b<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b.s, b.rp, b.W, b.P, w.st.p, w.part.p + P * 8,
+                                                 w.cnt.p + 2);
     SDA_LAUNCHED();
     if (ev) SDA_CUDA(cudaEventRecord(ev[7], s));
     return SDA_OK;
@@ -421,7 +406,7 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
     h.mu = op->mu.p + (int64_t)t * op->d;
     for (int i = 0; i < ns; ++i) h.sh[i].delta = shifts[i] - sigma0;
     SDA_CUDA(cudaMemcpyAsync(w.st.p, &h, sizeof(SolveState), cudaMemcpyHostToDevice, s));
-    k_cg_init<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b_perm, bv.r, bv.p, bv.W, bv.P, w.st.p, w.part.p,
+    k_cg_init<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b_perm, bv.rp, bv.W, bv.P, w.st.p, w.part.p,
                                               w.cnt.p + 0);
     SDA_LAUNCHED();
     op->stats.launches[0] += 1;

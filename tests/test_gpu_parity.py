@@ -142,9 +142,10 @@ def test_rhs_from_r_matches_paper_form(cfg1):
     """The GPU forms b = (N+ N- / l)(d^T r) d; the oracle evaluates the paper's
     (X - 1 mu^T)^T [W 0; 0 0] X r literally, which rounds differently (the
     centring subtracts two large column sums).  After 1 and 5 iterations the
-    iterates agree to 1e-9; after 25 the difference is amplified on the
-    ill-conditioned shifts (measured 2.5e-5 against the literal b), so the
-    longer run is compared with the oracle fed the same closed form."""
+    iterates agree to 1e-9.  The longer run is compared at 40 iterations with
+    the oracle fed the same closed form: around iteration 25 the iteration map
+    itself is ill-conditioned on the beta = 1e-4 shift (on the oracle alone a
+    2e-16 rescaling of b moves the iterate by 8e-7 there, by 5e-9 at 40)."""
     r = synth.random_r(77, cfg1.d)
     o = oracle.from_problem(cfg1)
     b_lit = o.rhs_from_r(r)
@@ -153,10 +154,10 @@ def test_rhs_from_r_matches_paper_form(cfg1):
         ref = o.shifted_cg(b_lit, cfg1.shifts, fixed_iters=k)
         for s in range(len(cfg1.shifts)):
             assert _rel(w[0, s], ref.W[s]) < 1e-9, (k, s)
-    _, code, rep, w = gpu_solve(cfg1, "f64", fixed=25, rhs_mode=sda.SDA_RHS_FROM_R, rhs=r)
+    _, code, rep, w = gpu_solve(cfg1, "f64", fixed=40, rhs_mode=sda.SDA_RHS_FROM_R, rhs=r)
     _, mp, mn, cnt = o.class_means()
     dv = mp - mn
-    ref = o.shifted_cg(cnt[1] * cnt[2] / cnt[0] * (dv @ r) * dv, cfg1.shifts, fixed_iters=25)
+    ref = o.shifted_cg(cnt[1] * cnt[2] / cnt[0] * (dv @ r) * dv, cfg1.shifts, fixed_iters=40)
     for s in range(len(cfg1.shifts)):
         assert _rel(w[0, s], ref.W[s]) < 1e-6, (s, _rel(w[0, s], ref.W[s]))
 
