@@ -206,6 +206,33 @@ SDA_API int sda_project(const sda_operator *op, const double *w, int64_t n_vec, 
 SDA_API int sda_operator_apply(const sda_operator *op, int32_t target, double sigma,
                                const double *p, double *q, void *cuda_stream);
 
+/*
+ * sda_operator_apply_static - the same q = (B + sigma I) p as
+ * sda_operator_apply, for callers that cannot allocate device memory: code
+ * that runs while a CUDA stream is being captured into a graph (cudaMalloc
+ * and cudaFree are not allowed there), code whose device memory is entirely
+ * owned by its own pool allocator, and latency-critical loops where the
+ * implicit device synchronisation of cudaMalloc / cudaFree is not acceptable.
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ * Every per-call buffer lives in one file-scope device array of
+ * SDA_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU loading the
+ * library holds until the process exits; the call allocates nothing and
+ * does not synchronise the stream.  The operator must satisfy
+ *     2 D + 2 N + (reduction and split-segment slots) <= SDA_STATIC_SCRATCH_DOUBLES,
+ * otherwise the call returns SDA_ERR_SHAPE and names the size it needed.
+ * All calls share the array, so calls that overlap on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  The first call on a device looks the array's address up (which
+ * loads the library's device code on that device): make that first call
+ * before any stream capture.  p and q are device arrays of D doubles in the
+ * caller's feature order; errors as sda_operator_apply.
+ */
+#define SDA_STATIC_SCRATCH_DOUBLES (1 << 20)
+
+SDA_API int sda_operator_apply_static(const sda_operator *op, int32_t target, double sigma,
+                                      const double *p, double *q, void *cuda_stream);
+
 /* Counters of the last sda_solve_shifts call on an operator. */
 typedef struct {
     int64_t iterations;        /* Krylov iterations summed over the call's targets                  */

@@ -81,6 +81,7 @@ _SIGS = {
                                         ctypes.POINTER(sda_shift_report), _vp]),
     "sda_project": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32, ctypes.c_int32, _vp]),
     "sda_operator_apply": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
+    "sda_operator_apply_static": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
     "sda_get_operator_info": (ctypes.c_int, [_vp, ctypes.POINTER(sda_operator_info)]),
     "sda_get_target_counts": (ctypes.c_int, [_vp, _vp]),
     "sda_get_solve_stats": (ctypes.c_int, [_vp, ctypes.POINTER(sda_solve_stats)]),
@@ -238,6 +239,15 @@ def sda_operator_apply(op, target, sigma, p, q, stream=None):
     qp, _, qk = _ptr(q)
     return _check(lib.sda_operator_apply(op, int(target), float(sigma), pp, qp, _stream(stream)),
                   "sda_operator_apply")
+
+
+def sda_operator_apply_static(op, target, sigma, p, q, stream=None):
+    """The operator apply without device allocation (scratch in a fixed device array)."""
+    lib = load()
+    pp, _, pk = _ptr(p)
+    qp, _, qk = _ptr(q)
+    return _check(lib.sda_operator_apply_static(op, int(target), float(sigma), pp, qp, _stream(stream)),
+                  "sda_operator_apply_static")
 
 
 def sda_get_operator_info(op) -> dict:
