@@ -119,14 +119,14 @@ def sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources (else None)."""
+def recorded_traffic(phase: str):
+    """DRAM bytes per launch of the `phase` kernel from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     txt = open(PROFILE_SUMMARY).read()
     m = re.search(r"sources_sha256:\s*([0-9a-f]+)", txt)
-    t = re.search(r"%s_dram_bytes_per_launch:\s*([0-9.eE+]+)" % kernel, txt)
+    t = re.search(r"%s_dram_bytes_per_launch:\s*([0-9.eE+]+)" % phase, txt)
     if not m or not t or m.group(1) != sources_hash():
         return None
     return float(t.group(1))
@@ -135,14 +135,14 @@ def recorded_traffic(kernel: str):
 def algorithmic_bytes(prob, compute: str, iters: int, shift_iters: int):
     """Algorithmic bytes per launch of each iteration kernel, averaged over one solve.
 
-    phase1  (rows of X):    CSR indices + values + row pointers, the D-vectors
-                            r_k and p_{k-1} once each, ut written.
-    phase2  (rows of S):    CSR of S (vector-type weights) + row pointers, ut
-                            read once, degrees, labels, v written.
-    phase3a (columns of X): CSC indices + values + column pointers, v read
-                            once, s written.
-    phase3b (stream):       r_k, p, s, mu_l (FP64) read, r_{k+1} and p written,
-                            and per active shift P and W read and written."""
+    phase1 (rows of X):    CSR indices + values + row pointers, the {r_k, p_{k-1}}
+                           pairs once each, ut written.
+    phase2 (rows of S):    CSR of S (vector-type weights) + row pointers, ut
+                           read once, degrees, labels, v written.
+    phase3a (columns of X): CSC indices + values + column pointers, v read once,
+                           s written.
+    phase3b (stream):      s, {r_k, p_{k-1}} and mu_l (FP64) read, {r_{k+1}, p_k}
+                           written, and per active shift P and W read and written."""
     n, d = prob.n, prob.d
     nnz = int(prob.x_ptr[-1])
     snz = int(prob.s_ptr[-1])
@@ -290,10 +290,10 @@ def main():
     dominant = max(durs, key=durs.get)
     peak, peak_kind = load_peaks()
     achieved = per_launch[dominant] / (durs[dominant] * 1e-3) / 1e9
-    kernel_names = {"phase1": "k_cg_phase1", "phase2": "k_cg_phase2", "phase3a": "k_cg_phase3a",
-                    "phase3b": "k_cg_phase3b"}
+    kernel_names = {"phase1": "k_rowpass<EpiP1> (rows of X)", "phase2": "k_rowpass<EpiP2> (rows of S)",
+                    "phase3a": "k_colpass<EpiStore> (columns of X)", "phase3b": "k_cg_phase3b (vector and shift stream)"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(kernel_names[dominant]),
+                "frac": achieved / peak, "traffic": recorded_traffic(dominant),
                 "kernel": kernel_names[dominant], "peak_kind": peak_kind,
                 "bytes_per_launch": per_launch[dominant], "ms_per_launch": durs[dominant],
                 "all_kernels": {kernel_names[k]: {"ms_per_launch": durs[k], "GB/s": per_launch[k] / (durs[k] * 1e-3) / 1e9}

@@ -151,10 +151,14 @@ typedef struct {
     int32_t iter_batch;     /* iterations launched between two host convergence checks (0: auto)   */
     int32_t profile;        /* 1: launch without graphs and time every phase kernel with CUDA
                                events (sda_get_solve_stats); slower, for measurement only         */
+    double alpha;           /* NaN: the operator's alpha; else this call's alpha in [0, 1] (eq. 7)  */
+    double scatter_weight;  /* NaN: 1 - alpha if the operator was built with a NaN scatter weight,
+                               else the operator's omega; else this call's omega >= 0              */
 } sda_solve_opts;
 
 /* Fills *opt with: tol 1e-6, max_iter 10000, fixed_iters 0, canonical RHS,
- * all targets, FP64 residual check on, device output, graphs on, auto batch. */
+ * all targets, FP64 residual check on, device output, graphs on, auto batch,
+ * the operator's alpha and omega. */
 SDA_API void sda_default_opts(sda_solve_opts *opt);
 
 /* Per target and shift outcome of sda_solve_shifts. */
@@ -183,6 +187,35 @@ typedef struct {
  */
 SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, int32_t n_shifts,
                              const sda_solve_opts *opt, double *w_out, sda_shift_report *report,
+                             void *cuda_stream);
+
+/*
+ * sda_adjoint_grad - gradient of a loss of held-out scores with respect to
+ * (alpha, beta) by one adjoint solve on the same symmetric operator (not in
+ * the paper; a training-style use of the solve).
+ *
+ * w solves (B(alpha) + beta I) w = b (Algorithm 3); the held-out scores are
+ * s_h = (X_h - 1 mu_l^T) w for the rows `rows`; the caller passes
+ * g = d loss / d s_h.  With lambda solving (B + beta I) lambda = (X_h - 1 mu_l^T)^T g,
+ *   d loss / d beta  = -lambda^T w
+ *   d loss / d alpha = -lambda^T (dB/dalpha) w
+ *                    = -[(X~ lambda)^T L (X~ w) - c (X~ lambda)^T P_l (X~ w)],
+ * X~ = X - 1 mu_l^T, c = 1 when omega follows 1 - alpha, else 0 (eq. 7).
+ *
+ *   target, alpha, beta  the point of w (alpha NaN: the operator's)
+ *   w                    D doubles, device, caller's feature order
+ *   dloss_ds, rows       n_rows doubles and n_rows int64 row ids (device); repeated
+ *                        rows add up
+ *   opt                  tolerance and iteration cap of the adjoint solve (NULL:
+ *                        defaults with tol 1e-10); its alpha/scatter_weight are ignored
+ *   d_alpha, d_beta      host doubles receiving the gradient
+ *   lambda_out           D doubles (device, caller order) receiving lambda, or NULL
+ * Errors: INVALID_ARG (a row out of range), BREAKDOWN, CUDA, OOM; SDA_NOT_CONVERGED
+ * when the adjoint solve hit its cap.  Synchronises the stream.
+ */
+SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double alpha, double beta, const double *w,
+                             const double *dloss_ds, const int64_t *rows, int64_t n_rows,
+                             const sda_solve_opts *opt, double *d_alpha, double *d_beta, double *lambda_out,
                              void *cuda_stream);
 
 /*

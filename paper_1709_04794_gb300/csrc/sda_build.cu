@@ -491,6 +491,14 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
     return SDA_OK;
 }
 
+// lanes per row of the register row pass: about four nonzeros per lane on average
+static int row_lanes(int64_t nnz, int64_t n) {
+    const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+    int g = 4;
+    while (g < 32 && 4.0 * g < avg) g <<= 1;
+    return g;
+}
+
 }  // namespace sda
 
 using namespace sda;
@@ -529,12 +537,15 @@ extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, co
     op->compute = compute;
     op->alpha = alpha;
     op->omega = omega;
+    op->omega_follows_alpha = isnan(scatter_weight);
     op->sm_count = device_sm_count();
     if (op->sm_count <= 0) {
         delete op;
         return fail(SDA_ERR_CUDA, "no CUDA device");
     }
     op->grid = op->sm_count * 4;
+    op->x_lanes = row_lanes(X->nnz, X->n_rows);
+    op->s_lanes = row_lanes(S->nnz, X->n_rows);
     int rc = build(X, S, y, alpha, omega, compute, (cudaStream_t)cuda_stream, op);
     if (rc < 0) {
         cudaStreamSynchronize((cudaStream_t)cuda_stream);

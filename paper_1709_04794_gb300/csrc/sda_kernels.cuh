@@ -16,12 +16,13 @@
 // The scalar work of a phase runs in the block that finishes last (no block
 // ever waits for another).
 //
-// The three sparse passes share one tile kernel (k_segpass): a tile is a run of
-// consecutive segments (rows or columns) holding at most kTileNnz nonzeros.  Its
-// index and value streams are read with all loads independent and evict-first,
-// the gathered operand through L1, the products staged in shared memory and
-// summed per segment by groups of lanes; segments longer than kBigSeg get
-// whole-block tiles, split across blocks when longer than kTileNnz.
+// The row passes (X, S) use k_rowpass: G lanes per row with unrolled,
+// independent loads and register sums.  The column pass (X^T, Zipf-skewed
+// column lengths, features ordered by decreasing frequency) uses k_colpass over
+// tiles of consecutive columns: register groups for short and medium columns,
+// whole-block tiles for long ones, split across blocks when longer than
+// kTileNnz.  k_segpass (shared-memory staged tiles) serves the allocation-free
+// operator apply.
 #pragma once
 
 #include "sda_operator.cuh"
@@ -60,8 +61,9 @@ struct TileSmem {
 };
 
 // Epi must provide
-//   segment(i, sum)        one thread per segment, consecutive segments on consecutive threads
+//   tile(i0, nseg, sums)   the whole block, the sums of segments i0 .. i0 + nseg - 1 (shared)
 //   segment_block(i, sum)  the whole block, one segment (sum valid in every thread)
+// EpiPerSegment supplies tile() for epilogues with a per-segment segment(i, sum).
 template <class VT, class AccT, class Gather, class Epi>
 __device__ __forceinline__ void seg_tile(const Tile &tl, const int64_t *__restrict__ ptr,
                                          const int32_t *__restrict__ idx, const VT *__restrict__ val,
@@ -81,7 +83,7 @@ __device__ __forceinline__ void seg_tile(const Tile &tl, const int64_t *__restri
             for (int s = threadIdx.x; s < nseg; s += kBlock) {
                 AccT acc = 0;
                 for (int e = sh.offs[s]; e < sh.offs[s + 1]; ++e) acc += sh.buf[e];
-                epi.segment(tl.seg0 + s, acc);
+                sh.sums[s] = acc;
             }
         } else {
             const int ngroups = kBlock / G, g = threadIdx.x / G, lane = threadIdx.x % G;
@@ -93,9 +95,9 @@ __device__ __forceinline__ void seg_tile(const Tile &tl, const int64_t *__restri
                 for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 if (s < nseg && lane == 0) sh.sums[s] = acc;
             }
-            __syncthreads();
-            for (int s = threadIdx.x; s < nseg; s += kBlock) epi.segment(tl.seg0 + s, sh.sums[s]);
         }
+        __syncthreads();
+        epi.tile(tl.seg0, nseg, sh.sums);
         __syncthreads();
         return;
     }
@@ -147,6 +149,51 @@ __global__ void __launch_bounds__(kBlock) k_segpass(const Tile *__restrict__ til
     epi.end(esh);
 }
 
+// Row pass for segments of similar, moderate length (rows of X, rows of S):
+// G lanes per row, each lane loads up to U (index, value) pairs of its row at
+// once (predicated, evict-first) and then issues their U gathers together; the
+// row sum is an xor tree over the G lanes; no shared memory.  Rows longer than
+// G * U take several rounds.  Epi::segment(i, sum) runs on the row's first lane.
+template <class VT, class AccT, int G, int U, class Gather, class Epi>
+__global__ void __launch_bounds__(kBlock) k_rowpass(int64_t n, const int64_t *__restrict__ rp,
+                                                    const int32_t *__restrict__ idx, const VT *__restrict__ val,
+                                                    Gather gather, Epi epi) {
+    __shared__ typename Epi::Shared esh;
+    if (epi.skip()) return;
+    gather.begin();
+    epi.begin(esh);
+    constexpr int RPW = 32 / G;
+    const int lane = threadIdx.x % G;
+    const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
+    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
+        const int64_t i = base + (threadIdx.x & 31) / G;
+        AccT acc = 0;
+        if (i < n) {
+            const int64_t e1 = rp[i + 1];
+            for (int64_t eb = rp[i] + lane; eb < e1; eb += G * U) {
+                int32_t jj[U];
+                AccT vv[U], gg[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t e = eb + (int64_t)u * G;
+                    const bool ok = e < e1;
+                    jj[u] = ok ? __ldcs(idx + e) : -1;
+                    vv[u] = ok ? (AccT)Val<VT>::get_cs(val, e) : (AccT)0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) gg[u] = jj[u] >= 0 ? gather(jj[u]) : (AccT)0;
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc += vv[u] * gg[u];
+            }
+        }
+#pragma unroll
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (i < n && lane == 0) epi.segment(i, acc);
+    }
+    epi.end(esh);
+}
+
 // ---------------------------------------------------------------------------
 // gathers
 // ---------------------------------------------------------------------------
@@ -180,6 +227,13 @@ struct GatherP {
 // ---------------------------------------------------------------------------
 struct NoShared {};
 
+// one thread per segment, consecutive segments on consecutive threads
+#define SDA_TILE_PER_SEGMENT                                                        \
+    template <class AccT>                                                           \
+    __device__ __forceinline__ void tile(int64_t i0, int nseg, const AccT *sums) {  \
+        for (int s = threadIdx.x; s < nseg; s += kBlock) segment(i0 + s, sums[s]);  \
+    }
+
 // out_i = sum - (csub ? *csub : 0)
 template <class OT>
 struct EpiStore {
@@ -188,6 +242,7 @@ struct EpiStore {
     const double *csub;
     const SolveState *st;   // optional: skip when the run is finished
     double c;
+    SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return st && st->done; }
     __device__ __forceinline__ void begin(Shared &) { c = csub ? *csub : 0.0; }
     template <class AccT>
@@ -208,6 +263,7 @@ struct EpiLap64 {
     const double *u, *deg;
     const int8_t *y;
     double omega, alpha;
+    SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return false; }
     __device__ __forceinline__ void begin(Shared &) {}
     __device__ __forceinline__ void segment(int64_t i, double s) {
@@ -226,6 +282,7 @@ struct EpiApply {
     double *q;
     const double *mu, *p, *t;
     double sigma, tv;
+    SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return false; }
     __device__ __forceinline__ void begin(Shared &) { tv = *t; }
     __device__ __forceinline__ void segment(int64_t j, double s) { q[j] = s - mu[j] * tv + sigma * p[j]; }
@@ -242,6 +299,7 @@ struct EpiP1 {
     FT *ut;
     const SolveState *st;
     double c;
+    SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return st->done != 0; }
     __device__ __forceinline__ void begin(Shared &) { c = st->c; }
     __device__ __forceinline__ void segment(int64_t i, FT s) { ut[i] = (FT)((double)s - c); }
@@ -271,6 +329,7 @@ struct EpiP2 {
     struct Shared {
         double red[kBlock / 32];
         int ok;
+        int flag[kBlock];
     };
     FT *v;
     const FT *ut, *deg;
@@ -279,6 +338,7 @@ struct EpiP2 {
     unsigned *counter;
     const int8_t *y;
     double omega, al, d0, d1;
+    SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return st->done != 0; }
     __device__ __forceinline__ void begin(Shared &) {
         y = st->labels;
@@ -317,13 +377,41 @@ struct EpiP2 {
         __syncthreads();
         if (!sh.ok) return;
         const double gam = st->gamma, gp = st->gamma_prev, al_k = st->alpha;
-        for (int q = threadIdx.x; q < st->n_shifts; q += kBlock) {
-            ShiftState &h = st->sh[q];
-            if (!h.active) continue;
-            const double den = gam * al_k * (h.z_prev - h.z) + h.z_prev * gp * (1.0 - h.delta * gam);
-            const double zn = h.z_prev * h.z * gp / den;
-            h.z_next = zn;
-            h.g = gam * zn / h.z;
+        const int ns = st->n_shifts;
+        StreamParams &sp = st->sp;
+        int act = 0;
+        double zk = 0.0, ak = 0.0, gk = 0.0;
+        if (threadIdx.x < ns) {
+            ShiftState &h = st->sh[threadIdx.x];
+            if (h.active) {
+                const double den = gam * al_k * (h.z_prev - h.z) + h.z_prev * gp * (1.0 - h.delta * gam);
+                const double zn = h.z_prev * h.z * gp / den;
+                h.z_next = zn;
+                h.g = gam * zn / h.z;
+                zk = h.z;
+                ak = h.a;
+                gk = h.g;
+                act = 1;
+            }
+        }
+        // compact the active shifts for the stream kernel (slot = number of active shifts before it)
+        sh.flag[threadIdx.x] = act;
+        __syncthreads();
+        if (act) {
+            int pos = 0;
+            for (int q = 0; q < (int)threadIdx.x; ++q) pos += sh.flag[q];
+            sp.act[pos] = threadIdx.x;
+            sp.zk[pos] = zk;
+            sp.ak[pos] = ak;
+            sp.gk[pos] = gk;
+        }
+        const int na = __syncthreads_count(act);
+        if (threadIdx.x == 0) {
+            sp.nact = na;
+            sp.alpha = al_k;
+            sp.gamma = gam;
+            sp.t = st->t;
+            sp.sigma0 = st->sigma0;
         }
     }
 };
@@ -408,8 +496,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, cons
     }
     __syncthreads();
     const bool zero_rhs = !(st->bnorm > 0.0);
-    for (int s = threadIdx.x; s < ns; s += kBlock) {
-        ShiftState &h = st->sh[s];
+    int act = 0;
+    if (threadIdx.x < ns) {
+        ShiftState &h = st->sh[threadIdx.x];
         h.z_prev = 1.0;
         h.z = 1.0;
         h.z_next = 1.0;
@@ -418,26 +507,113 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, cons
         h.res = zero_rhs ? 0.0 : 1.0;
         h.active = zero_rhs ? 0 : 1;
         h.iters = 0;
+        act = h.active;
     }
-    __syncthreads();
+    const int na = __syncthreads_count(act);
     if (threadIdx.x == 0) {
-        int na = 0;
-        for (int s = 0; s < ns; ++s) na += st->sh[s].active;
         st->nactive = na;
         st->done = (na == 0 || st->limit <= 0) ? 1 : 0;
     }
 }
 
-// block-cached scalars of phase 3b
+// Column pass X^T v: long columns (lanes == 0) as whole-block tiles, split
+// across blocks when longer than kTileNnz; the other tiles with `lanes` lanes per
+// column, each lane loading up to U (row, value) pairs at once and issuing their
+// gathers together; xor-tree sum over the lanes; no shared memory.
+// Epi::segment(j, sum) runs on the column's first lane, segment_block for
+// whole-block columns.
+template <class VT, class AccT, int U, class Epi>
+__global__ void __launch_bounds__(kBlock) k_colpass(const Tile *__restrict__ tiles, int ntiles,
+                                                    const int64_t *__restrict__ cp, const int32_t *__restrict__ row,
+                                                    const VT *__restrict__ val, const AccT *__restrict__ v,
+                                                    AccT *slots, unsigned *lcount, const SplitSeg *__restrict__ splits,
+                                                    Epi epi) {
+    __shared__ typename Epi::Shared esh;
+    __shared__ AccT red[kBlock / 32];
+    __shared__ int last;
+    if (epi.skip()) return;
+    epi.begin(esh);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        if (tl.lanes > 0) {
+            const int G = tl.lanes, ngroups = kBlock / G;
+            const int g = threadIdx.x / G, lane = threadIdx.x % G;
+            const int nseg = tl.seg1 - tl.seg0;
+            for (int base = 0; base < nseg; base += ngroups) {
+                const int s = base + g;
+                AccT acc = 0;
+                if (s < nseg) {
+                    const int64_t j = tl.seg0 + s;
+                    const int64_t e0 = cp[j];
+                    const int len = (int)(cp[j + 1] - e0);
+                    for (int eb = lane; eb < len; eb += G * U) {
+                        int32_t ii[U];
+                        AccT vv[U], gg[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int e = eb + u * G;
+                            const bool ok = e < len;
+                            ii[u] = ok ? __ldcs(row + e0 + e) : -1;
+                            vv[u] = ok ? (AccT)Val<VT>::get_cs(val, e0 + e) : (AccT)0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) gg[u] = ii[u] >= 0 ? v[ii[u]] : (AccT)0;
+#pragma unroll
+                        for (int u = 0; u < U; ++u) acc += vv[u] * gg[u];
+                    }
+                }
+                for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (s < nseg && lane == 0) epi.segment(tl.seg0 + s, acc);
+            }
+            continue;
+        }
+        AccT acc = 0;
+#pragma unroll 4
+        for (int64_t e = tl.nz0 + threadIdx.x; e < tl.nz1; e += kBlock)
+            acc += (AccT)Val<VT>::get_cs(val, e) * v[__ldcs(row + e)];
+        acc = block_sum(acc, red);
+        if (tl.slot < 0) {
+            epi.segment_block(tl.seg0, acc);
+            continue;
+        }
+        if (threadIdx.x == 0) {
+            slots[tl.slot] = acc;
+            __threadfence();
+            const unsigned prev = atomicAdd(&lcount[tl.lseg], 1u);
+            last = (prev == (unsigned)splits[tl.lseg].nchunks - 1u);
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            const SplitSeg sp = splits[tl.lseg];
+            AccT tot = 0;
+            for (int c = 0; c < sp.nchunks; ++c) tot += __ldcg(slots + sp.slot0 + c);
+            if (threadIdx.x == 0) lcount[tl.lseg] = 0u;
+            epi.segment_block(tl.seg0, tot);
+        }
+        __syncthreads();
+    }
+    epi.end(esh);
+}
+
+// phase 3b (stream over D), q_j = s_j - mu_j t + sigma0 p_k,j for every feature:
+//   r_{k+1} = r_k + gamma_k q;  RP[k+1] = {r_{k+1}, p_k}
+//   P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1};  W^s_{k+1} = W^s_k - gamma^s_k P^s_k  (active shifts)
+// The base vectors are one grid-stride pass; the shift state a second one over
+// (active shift, 16-byte chunk) pairs, four pairs per thread in flight.  The
+// scalars arrive in the compact block st->sp written by phase 2.  Dots
+// <r_{k+1}, r_{k+1}>, <mu, r_{k+1}>, <r_{k+1}, p_k>; the last block forms
+// alpha_{k+1}, <mu, p_{k+1}>, ||p_{k+1}||^2 and the stop tests.
 template <class FT>
-struct P3Shared {
+struct StreamSmem {
     double alpha, gamma, t, sigma0;
     int nact;
     int act[kMaxShifts];
     FT zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
+    double red[kBlock / 32];
+    double alpha_new, rnorm;
 };
 
-// r_k of VW consecutive features from the interleaved buffer
 __device__ __forceinline__ void load_r(const float2 *a, int64_t j0, float (&r)[4]) {
     const float4 u = *reinterpret_cast<const float4 *>(a + j0);
     const float4 w = *reinterpret_cast<const float4 *>(a + j0 + 2);
@@ -451,10 +627,6 @@ __device__ __forceinline__ void load_r(const double2 *a, int64_t j0, double (&r)
     r[1] = a[j0 + 1].x;
 }
 
-// phase 3b: q = s - mu t + sigma0 p_k;  r_{k+1} = r_k + gamma_k q;  RP[k+1] = {r_{k+1}, p_k};
-// P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1};  W^s_{k+1} = W^s_k - gamma^s_k P^s_k
-// over the flattened (1 + active shifts) x features space, 16-byte vectors for
-// the shift state; then alpha_{k+1}, <mu, p_{k+1}>, <p_{k+1}, p_{k+1}>, stop tests.
 template <class FT>
 __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, const FT *__restrict__ s,
                                                        typename RPair<FT>::T *__restrict__ rp,
@@ -463,33 +635,23 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
     using V = typename Vec16<FT>::T;
     using R = typename RPair<FT>::T;
     constexpr int VW = Vec16<FT>::n;
-    __shared__ double red[kBlock / 32];
-    __shared__ P3Shared<FT> sm;
-    __shared__ double s_alpha_new, s_rnorm;
+    constexpr int UNROLL = 4;
+    __shared__ StreamSmem<FT> sm;
     if (st->done) return;
-    if (threadIdx.x < 32) {   // one warp compacts the active shifts
-        const int lane = threadIdx.x, ns = st->n_shifts;
-        int na = 0;
-        for (int base = 0; base < ns; base += 32) {
-            const int q = base + lane;
-            const bool act = q < ns && st->sh[q].active;
-            const unsigned m = __ballot_sync(0xffffffffu, act);
-            if (act) {
-                const int pos = na + __popc(m & ((1u << lane) - 1u));
-                const ShiftState &h = st->sh[q];
-                sm.act[pos] = q;
-                sm.zk[pos] = (FT)h.z;
-                sm.ak[pos] = (FT)h.a;
-                sm.gk[pos] = (FT)h.g;
-            }
-            na += __popc(m);
+    {
+        const StreamParams &sp = st->sp;
+        if (threadIdx.x == 0) {
+            sm.alpha = sp.alpha;
+            sm.gamma = sp.gamma;
+            sm.t = sp.t;
+            sm.sigma0 = sp.sigma0;
+            sm.nact = sp.nact;
         }
-        if (lane == 0) {
-            sm.nact = na;
-            sm.alpha = st->alpha;
-            sm.gamma = st->gamma;
-            sm.t = st->t;
-            sm.sigma0 = st->sigma0;
+        if (threadIdx.x < kMaxShifts) {
+            sm.act[threadIdx.x] = sp.act[threadIdx.x];
+            sm.zk[threadIdx.x] = (FT)sp.zk[threadIdx.x];
+            sm.ak[threadIdx.x] = (FT)sp.ak[threadIdx.x];
+            sm.gk[threadIdx.x] = (FT)sp.gk[threadIdx.x];
         }
     }
     __syncthreads();
@@ -498,86 +660,97 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
     R *__restrict__ an_ = rp + (par ^ 1) * ldw;
     const double *__restrict__ mu = st->mu;
     const FT al = (FT)sm.alpha;
-    const uint32_t nch = (uint32_t)(ldw / VW);
-    const uint32_t total = (uint32_t)(sm.nact + 1) * nch;
+    const double t = sm.t, sigma0 = sm.sigma0, gam = sm.gamma;
+    const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
     double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-    for (uint32_t idx = blockIdx.x * kBlock + threadIdx.x; idx < total; idx += gridDim.x * kBlock) {
-        const uint32_t q = idx / nch;
-        const int64_t j0 = (int64_t)(idx - q * nch) * VW;
-        if (q == 0) {
+    for (int64_t j = tid; j < d; j += nthr) {
+        const R x = a[j];
+        const FT pk = form_p<FT>(x.x, x.y, al);
+        const double mj = mu[j];
+        const double qj = (double)s[j] - mj * t + sigma0 * (double)pk;
+        const FT rnj = (FT)((double)x.x + gam * qj);
+        R y;
+        y.x = rnj;
+        y.y = pk;
+        an_[j] = y;
+        d0 += (double)rnj * (double)rnj;
+        d1 += mj * (double)rnj;
+        d2 += (double)rnj * (double)pk;
+    }
+    const uint32_t nch = (uint32_t)(ldw / VW);
+    const int64_t total = (int64_t)sm.nact * nch;
+    for (int64_t i0 = tid; i0 < total; i0 += nthr * UNROLL) {
+        FT r[UNROLL][VW];
+        V pv[UNROLL], wv[UNROLL];
+        int64_t off[UNROLL];
+        int qq[UNROLL];
 #pragma unroll
-            for (int u = 0; u < VW; ++u) {
-                const int64_t j = j0 + u;
-                if (j >= d) break;
-                const R x = a[j];
-                const FT pk = form_p<FT>(x.x, x.y, al);
-                const double mj = mu[j];
-                const double qj = (double)s[j] - mj * sm.t + sm.sigma0 * (double)pk;
-                const FT rnj = (FT)((double)x.x + sm.gamma * qj);
-                R y;
-                y.x = rnj;
-                y.y = pk;
-                an_[j] = y;
-                d0 += (double)rnj * (double)rnj;
-                d1 += mj * (double)rnj;
-                d2 += (double)rnj * (double)pk;
+        for (int u = 0; u < UNROLL; ++u) {
+            const int64_t i = i0 + u * nthr;
+            qq[u] = -1;
+            if (i < total) {
+                const uint32_t q = (uint32_t)(i / nch);
+                const int64_t j0 = (int64_t)(i - (int64_t)q * nch) * VW;
+                qq[u] = (int)q;
+                off[u] = (int64_t)sm.act[q] * ldw + j0;
+                load_r(a, j0, r[u]);
+                pv[u] = *reinterpret_cast<const V *>(P + off[u]);
+                wv[u] = *reinterpret_cast<const V *>(W + off[u]);
             }
-        } else {
-            const int sh = sm.act[q - 1];
-            const FT z = sm.zk[q - 1], aa = sm.ak[q - 1], g = sm.gk[q - 1];
-            FT r[VW];
-            load_r(a, j0, r);
-            V pv = *reinterpret_cast<const V *>(P + (int64_t)sh * ldw + j0);
-            V wv = *reinterpret_cast<const V *>(W + (int64_t)sh * ldw + j0);
+        }
 #pragma unroll
-            for (int u = 0; u < VW; ++u) {
-                const FT pn = z * r[u] + aa * v16_get(pv, u);
-                v16_set(pv, u, pn);
-                v16_set(wv, u, v16_get(wv, u) - g * pn);
+        for (int u = 0; u < UNROLL; ++u) {
+            if (qq[u] < 0) continue;
+            const FT z = sm.zk[qq[u]], aa = sm.ak[qq[u]], g = sm.gk[qq[u]];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const FT pn = z * r[u][e] + aa * v16_get(pv[u], e);
+                v16_set(pv[u], e, pn);
+                v16_set(wv[u], e, v16_get(wv[u], e) - g * pn);
             }
-            *reinterpret_cast<V *>(P + (int64_t)sh * ldw + j0) = pv;
-            *reinterpret_cast<V *>(W + (int64_t)sh * ldw + j0) = wv;
+            *reinterpret_cast<V *>(P + off[u]) = pv[u];
+            *reinterpret_cast<V *>(W + off[u]) = wv[u];
         }
     }
-    double mine[3] = {block_sum(d0, red), block_sum(d1, red), block_sum(d2, red)};
+    double mine[3] = {block_sum(d0, sm.red), block_sum(d1, sm.red), block_sum(d2, sm.red)};
     if (!arrive_last<3>(mine, partials, counter)) return;
     double tot[3];
-    grid_dots<3>(partials, gridDim.x, tot, red);
+    grid_dots<3>(partials, gridDim.x, tot, sm.red);
     if (threadIdx.x == 0) {
         const double rr_new = tot[0];
-        const double an = rr_new / st->rr;
-        const double c_new = tot[1] + an * st->c;
-        const double pp_new = rr_new + 2.0 * an * tot[2] + an * an * st->pp;
-        if (!isfinite(rr_new) || !isfinite(an)) st->status = SDA_ERR_BREAKDOWN;
+        const double anw = rr_new / st->rr;
+        const double c_new = tot[1] + anw * st->c;
+        const double pp_new = rr_new + 2.0 * anw * tot[2] + anw * anw * st->pp;
+        if (!isfinite(rr_new) || !isfinite(anw)) st->status = SDA_ERR_BREAKDOWN;
         st->gamma_prev = st->gamma;
-        st->alpha = an;
+        st->alpha = anw;
         st->c = c_new;
         st->pp = pp_new;
         st->rr = rr_new;
         st->k = st->k + 1;
-        s_alpha_new = an;
-        s_rnorm = sqrt(rr_new);
+        sm.alpha_new = anw;
+        sm.rnorm = sqrt(rr_new);
         *counter = 0u;
     }
     __syncthreads();
-    const double an = s_alpha_new, rnorm = s_rnorm, bnorm = st->bnorm, tol = st->tol;
-    const int k = st->k, fixed = st->fixed;
-    for (int q = threadIdx.x; q < st->n_shifts; q += kBlock) {
-        ShiftState &h = st->sh[q];
-        if (!h.active) continue;
-        const double ratio = h.z_next / h.z;
-        h.a = an * ratio * ratio;
-        h.z_prev = h.z;
-        h.z = h.z_next;
-        h.iters = k;
-        const double rz = fabs(h.z) * rnorm;
-        h.res = bnorm > 0.0 ? rz / bnorm : 0.0;
-        if (!fixed && (rz < tol * bnorm || !(fabs(h.z) > 0.0))) h.active = 0;
+    const int ns = st->n_shifts, k = st->k;
+    int act = 0;
+    if (threadIdx.x < ns) {
+        ShiftState &h = st->sh[threadIdx.x];
+        if (h.active) {
+            const double ratio = h.z_next / h.z;
+            h.a = sm.alpha_new * ratio * ratio;
+            h.z_prev = h.z;
+            h.z = h.z_next;
+            h.iters = k;
+            const double rz = fabs(h.z) * sm.rnorm, bnorm = st->bnorm;
+            h.res = bnorm > 0.0 ? rz / bnorm : 0.0;
+            if (!st->fixed && (rz < st->tol * bnorm || !(fabs(h.z) > 0.0))) h.active = 0;
+            act = h.active;
+        }
     }
-    __syncthreads();
+    const int na = __syncthreads_count(act);
     if (threadIdx.x == 0) {
-        int na = 0;
-        for (int q = 0; q < st->n_shifts; ++q) na += st->sh[q].active;
         st->nactive = na;
         st->done = (na == 0 || k >= st->limit || st->status != SDA_OK) ? 1 : 0;
     }

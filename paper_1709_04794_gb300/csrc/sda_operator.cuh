@@ -19,6 +19,15 @@ struct ShiftState {
     int32_t iters;   // iteration count when it stopped (or so far)
 };
 
+// Compact scalars of the vector / shift-state stream of one iteration, written
+// by the last block of phase 2 (active shifts first, in shift order).
+struct StreamParams {
+    double alpha, gamma, t, sigma0;
+    int32_t nact, pad;
+    int32_t act[kMaxShifts];
+    double zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
+};
+
 // Scalars of one shifted-CG run, read by every phase kernel, written by the
 // last block of the phase that completes them.
 struct SolveState {
@@ -40,6 +49,7 @@ struct SolveState {
     double gamma;           // gamma_k = -<r_k, r_k> / <p_k, (B + sigma0) p_k>
     double gamma_prev;      // gamma_{k-1}
     double t;               // 1^T v_k
+    StreamParams sp;
     ShiftState sh[kMaxShifts];
 };
 
@@ -56,6 +66,7 @@ struct Workspace {
     DevBuf<unsigned> cnt;    // grid arrival counters of init / phase 2 / phase 3
     DevBuf<double> f64;      // FP64 scratch: b (D), w (D), q (D)
     DevBuf<double> dev_b;    // right-hand sides of the call's targets [T][D]
+    DevBuf<double> adj;      // adjoint scratch: 3 D + 5 N doubles
     SolveState *h_st = nullptr;   // pinned host mirror of the state
     std::vector<cudaEvent_t> prof_ev;  // profile mode: start/end event of every phase launch of a batch
     cudaEvent_t call_ev[2] = {nullptr, nullptr};
@@ -72,6 +83,7 @@ struct sda_operator {
     int32_t n_targets = 0;
     sda_dtype compute = SDA_F64;
     double alpha = 0.0, omega = 1.0;
+    bool omega_follows_alpha = true;     // built with a NaN scatter weight: omega = 1 - alpha
     int sm_count = 0;
 
     // feature order: columns sorted by descending count (new index = rank)
@@ -94,6 +106,7 @@ struct sda_operator {
     // their split segments use disjoint ranges of the slots / counters below
     sda::ColSchedule col, xrow, srow;
     int32_t xrow_slot0 = 0, srow_slot0 = 0, xrow_lseg0 = 0, srow_lseg0 = 0;
+    int x_lanes = 16, s_lanes = 4;        // lanes per row of the register row passes
     int grid = 0;                         // blocks of every persistent-style pass
     int64_t bytes = 0;
     // scratch of the column pass and of the FP64 reductions
@@ -110,7 +123,7 @@ struct sda_operator {
 namespace sda {
 // launchers implemented in sda_solve.cu / sda_build.cu
 int op_apply_f64(const sda_operator *op, int target, double sigma, const double *p_perm, double *q_perm,
-                 cudaStream_t s);
+                 cudaStream_t s, double alpha, double omega);
 int op_xmul_f64(const sda_operator *op, const double *w_perm, double *u, const double *csub_dev, cudaStream_t s);
 int op_xtmul_f64(const sda_operator *op, const double *v, double *q, cudaStream_t s);
 int permute_to_new(const sda_operator *op, const double *old_order, double *new_order, int64_t count,

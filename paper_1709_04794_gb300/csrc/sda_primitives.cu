@@ -222,10 +222,10 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, cu
 // ---------------------------------------------------------------------------
 // tiles of consecutive segments
 // ---------------------------------------------------------------------------
-// lanes that sum one segment of a streamed tile: at most four products each
+// lanes per segment of a multi-segment tile: at most eight nonzeros per lane
 static int lanes_for(int64_t maxlen) {
     int g = 1;
-    while (g < 32 && 4 * g < maxlen) g <<= 1;
+    while (g < 32 && 8 * g < maxlen) g <<= 1;
     return g;
 }
 

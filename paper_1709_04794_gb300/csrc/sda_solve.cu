@@ -91,6 +91,31 @@ __global__ void k_scale(int64_t d, const double *x, const double *coef, double m
         out[i] = c * x[i];
 }
 
+// G[rows[h]] += g[h]; a row out of range sets *err
+__global__ void k_scatter_rows(int64_t m, const int64_t *rows, const double *g, double *G, int64_t n, int *err) {
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < m; h += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = rows[h];
+        if (i < 0 || i >= n) {
+            atomicOr(err, 1);
+            continue;
+        }
+        atomicAdd(G + i, g[h]);
+    }
+}
+
+// c_j -= mu_j * (*t)
+__global__ void k_sub_mu(int64_t d, double *c, const double *mu, const double *t) {
+    const double tv = *t;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x)
+        c[j] -= mu[j] * tv;
+}
+
+// out_i = [y_i != 0] u_i  (P_l u)
+__global__ void k_mask_labelled(int64_t n, const int8_t *y, const double *u, double *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = y[i] != 0 ? u[i] : 0.0;
+}
+
 static int grid_elems(int64_t m, int sms) {
     const int64_t g = (m + kBlock - 1) / kBlock;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
@@ -111,6 +136,17 @@ static int with_vt(int compute, F &&f) {
     }
 }
 
+// lanes per row G and unrolled loads per lane U of the register row pass
+template <class F>
+static int with_row_lanes(int g, F &&f) {
+    switch (g) {
+    case 4: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 8>());
+    case 8: return f(std::integral_constant<int, 8>(), std::integral_constant<int, 8>());
+    case 16: return f(std::integral_constant<int, 16>(), std::integral_constant<int, 8>());
+    default: return f(std::integral_constant<int, 32>(), std::integral_constant<int, 4>());
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 operator pieces (permuted feature order)
 // ---------------------------------------------------------------------------
@@ -126,21 +162,42 @@ static int segpass(const sda_operator *op, const ColSchedule &sc, int32_t slot0,
     return SDA_OK;
 }
 
+// a column pass over X^T with the operator's column schedule
+template <class VT, class AccT, class Epi>
+static int colpass(const sda_operator *op, const AccT *v, const Epi &e, int grid, cudaStream_t s) {
+    k_colpass<VT, AccT, 8, Epi><<<grid, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
+                                                       (const VT *)op->x_val_c.p, v, (AccT *)op->slots.p,
+                                                       op->lcount.p, op->col.splits.p, e);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
 int op_xtmul_f64(const sda_operator *op, const double *v, double *q, cudaStream_t s) {
     return with_vt(op->compute, [&](auto tag) -> int {
         using VT = std::remove_pointer_t<decltype(tag)>;
-        return segpass<VT, double>(op, op->col, 0, 0, op->x_cp.p, op->x_row.p, op->x_val_c.p,
-                                   GatherVec<double, double>{v}, EpiStore<double>{q, nullptr, nullptr, 0.0}, op->grid,
+        return colpass<VT, double>(op, v, EpiStore<double>{q, nullptr, nullptr, 0.0}, op->sm_count * kMaxBlocksPerSm,
                                    s);
+    });
+}
+
+// a register row pass over the rows of a CSR matrix
+template <class VT, class AccT, class Gather, class Epi>
+static int rowpass(int lanes, int64_t n, const int64_t *rp, const int32_t *idx, const void *val, const Gather &g,
+                   const Epi &e, int grid, cudaStream_t s) {
+    return with_row_lanes(lanes, [&](auto G, auto U) -> int {
+        k_rowpass<VT, AccT, decltype(G)::value, decltype(U)::value, Gather, Epi>
+            <<<grid, kBlock, 0, s>>>(n, rp, idx, (const VT *)val, g, e);
+        SDA_LAUNCHED();
+        return SDA_OK;
     });
 }
 
 int op_xmul_f64(const sda_operator *op, const double *w, double *u, const double *csub, cudaStream_t s) {
     return with_vt(op->compute, [&](auto tag) -> int {
         using VT = std::remove_pointer_t<decltype(tag)>;
-        return segpass<VT, double>(op, op->xrow, op->xrow_slot0, op->xrow_lseg0, op->x_rp.p, op->x_col.p,
-                                   op->x_val_r.p, GatherVec<double, double>{w},
-                                   EpiStore<double>{u, csub, nullptr, 0.0}, op->grid, s);
+        return rowpass<VT, double>(op->x_lanes, op->n, op->x_rp.p, op->x_col.p, op->x_val_r.p,
+                                   GatherVec<double, double>{w}, EpiStore<double>{u, csub, nullptr, 0.0},
+                                   op->sm_count * kMaxBlocksPerSm, s);
     });
 }
 
@@ -157,8 +214,9 @@ static int ensure_apply_scratch(sda_operator *op) {
     return SDA_OK;
 }
 
-// q = (B + sigma I) p, FP64, centred symmetric form, permuted order
-int op_apply_f64(const sda_operator *op, int target, double sigma, const double *p, double *q, cudaStream_t s) {
+// q = (B + sigma I) p, FP64, centred symmetric form, permuted order, at (alpha, omega)
+int op_apply_f64(const sda_operator *op, int target, double sigma, const double *p, double *q, cudaStream_t s,
+                 double alpha, double omega) {
     sda_operator *mop = const_cast<sda_operator *>(op);
     SDA_TRY(ensure_apply_scratch(mop));
     double *u = op->ws.f64.p + 3 * op->d, *v = u + op->n;
@@ -166,15 +224,14 @@ int op_apply_f64(const sda_operator *op, int target, double sigma, const double 
     const int8_t *y = op->labels.p + (int64_t)target * op->n;
     SDA_TRY(dot_f64(op, op->d, mu, p, op->scal.p + 0, s));
     SDA_TRY(op_xmul_f64(op, p, u, op->scal.p + 0, s));
-    SDA_TRY((segpass<double, double>(op, op->srow, op->srow_slot0, op->srow_lseg0, op->s_rp.p, op->s_col.p,
-                                     op->s_val64.p, GatherVec<double, double>{u},
-                                     EpiLap64{v, u, op->deg64.p, y, op->omega, op->alpha}, op->grid, s)));
+    SDA_TRY((rowpass<double, double>(op->s_lanes, op->n, op->s_rp.p, op->s_col.p, op->s_val64.p,
+                                     GatherVec<double, double>{u}, EpiLap64{v, u, op->deg64.p, y, omega, alpha},
+                                     op->sm_count * kMaxBlocksPerSm, s)));
     SDA_TRY(dot_f64(op, op->n, v, nullptr, op->scal.p + 1, s));
     return with_vt(op->compute, [&](auto tag) -> int {
         using VT = std::remove_pointer_t<decltype(tag)>;
-        return segpass<VT, double>(op, op->col, 0, 0, op->x_cp.p, op->x_row.p, op->x_val_c.p,
-                                   GatherVec<double, double>{v}, EpiApply{q, mu, p, op->scal.p + 1, sigma, 0.0},
-                                   op->grid, s);
+        return colpass<VT, double>(op, v, EpiApply{q, mu, p, op->scal.p + 1, sigma, 0.0},
+                                   op->sm_count * kMaxBlocksPerSm, s);
     });
 }
 
@@ -269,23 +326,23 @@ static int grid_of(const void *kernel, int sms) {
     return std::min(nb, kMaxBlocksPerSm) * sms;
 }
 
-template <class VT, class FT>
-struct PhaseKernels {
-    using K1 = GatherP<FT>;
-    static constexpr auto p1 = k_segpass<VT, FT, GatherP<FT>, EpiP1<FT>>;
-    static constexpr auto p2 = k_segpass<FT, FT, GatherVec<FT, FT>, EpiP2<FT>>;
-    static constexpr auto p3a = k_segpass<VT, FT, GatherVec<FT, FT>, EpiStore<FT>>;
-};
-
 // sizes the grids of the iteration kernels for this operator's dtypes
 template <class VT, class FT>
 static int size_grids(sda_operator *op) {
     Workspace &w = op->ws;
     if (w.vt == (int)op->compute) return SDA_OK;
     const int sms = op->sm_count;
-    w.grid1 = grid_of((const void *)PhaseKernels<VT, FT>::p1, sms);
-    w.grid2 = grid_of((const void *)PhaseKernels<VT, FT>::p2, sms);
-    w.grid3a = grid_of((const void *)PhaseKernels<VT, FT>::p3a, sms);
+    SDA_TRY(with_row_lanes(op->x_lanes, [&](auto G, auto U) -> int {
+        w.grid1 = grid_of((const void *)k_rowpass<VT, FT, decltype(G)::value, decltype(U)::value, GatherP<FT>,
+                                                  EpiP1<FT>>, sms);
+        return SDA_OK;
+    }));
+    SDA_TRY(with_row_lanes(op->s_lanes, [&](auto G, auto U) -> int {
+        w.grid2 = grid_of((const void *)k_rowpass<FT, FT, decltype(G)::value, decltype(U)::value, GatherVec<FT, FT>,
+                                                  EpiP2<FT>>, sms);
+        return SDA_OK;
+    }));
+    w.grid3a = grid_of((const void *)k_colpass<VT, FT, 8, EpiStore<FT>>, sms);
     w.grid3b = grid_of((const void *)k_cg_phase3b<FT>, sms);
     w.vt = (int)op->compute;
     return SDA_OK;
@@ -301,19 +358,17 @@ static int launch_iteration(const sda_operator *op, cudaStream_t s, cudaEvent_t 
     const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
     const size_t P = (size_t)kMaxBlocksPerSm * op->sm_count;
     if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
-    SDA_TRY((segpass<VT, FT>(op, op->xrow, op->xrow_slot0, op->xrow_lseg0, op->x_rp.p, op->x_col.p, op->x_val_r.p,
+    SDA_TRY((rowpass<VT, FT>(op->x_lanes, op->n, op->x_rp.p, op->x_col.p, op->x_val_r.p,
                              GatherP<FT>{b.rp, w.ldw, w.st.p, nullptr, (FT)0}, EpiP1<FT>{b.ut, w.st.p, 0.0}, w.grid1,
                              s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[2], s));
-    SDA_TRY((segpass<FT, FT>(op, op->srow, op->srow_slot0, op->srow_lseg0, op->s_rp.p, op->s_col.p, sv,
-                             GatherVec<FT, FT>{b.ut},
+    SDA_TRY((rowpass<FT, FT>(op->s_lanes, op->n, op->s_rp.p, op->s_col.p, sv, GatherVec<FT, FT>{b.ut},
                              EpiP2<FT>{b.v, b.ut, dg, w.st.p, w.part.p + P * 4, w.cnt.p + 1, nullptr, 0, 0, 0, 0},
                              w.grid2, s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[3], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[4], s));
-    SDA_TRY((segpass<VT, FT>(op, op->col, 0, 0, op->x_cp.p, op->x_row.p, op->x_val_c.p, GatherVec<FT, FT>{b.v},
-                             EpiStore<FT>{b.s, nullptr, w.st.p, 0.0}, w.grid3a, s)));
+    SDA_TRY((colpass<VT, FT>(op, b.v, EpiStore<FT>{b.s, nullptr, w.st.p, 0.0}, w.grid3a, s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
     k_cg_phase3b<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b.s, b.rp, b.W, b.P, w.st.p, w.part.p + P * 8,
@@ -386,8 +441,8 @@ static int read_header(sda_operator *op, cudaStream_t s) {
 
 template <class VT, class FT>
 static int solve_target(sda_operator *op, int t, const double *b_perm, const double *shifts, int ns,
-                        const sda_solve_opts &o, double *w_out_t, sda_shift_report *rep_t, cudaStream_t s,
-                        int *worst) {
+                        const sda_solve_opts &o, double alpha, double omega, double *w_out_t,
+                        sda_shift_report *rep_t, cudaStream_t s, int *worst) {
     Workspace &w = op->ws;
     SDA_TRY((size_grids<VT, FT>(op)));
     WsView<FT> bv = view<FT>(op);
@@ -396,8 +451,8 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
     double sigma0 = shifts[0];
     for (int i = 1; i < ns; ++i) sigma0 = std::min(sigma0, shifts[i]);
     h.sigma0 = sigma0;
-    h.omega = op->omega;
-    h.alpha_l = op->alpha;
+    h.omega = omega;
+    h.alpha_l = alpha;
     h.tol = o.tol;
     h.n_shifts = ns;
     h.fixed = o.fixed_iters > 0 ? 1 : 0;
@@ -454,7 +509,7 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
         for (int i = 0; i < ns; ++i) {
             k_w_f64<FT><<<grid_elems(op->d, op->sm_count), kBlock, 0, s>>>(op->d, bv.W + (int64_t)i * w.ldw, w64);
             SDA_LAUNCHED();
-            SDA_TRY(op_apply_f64(op, t, shifts[i], w64, q, s));
+            SDA_TRY(op_apply_f64(op, t, shifts[i], w64, q, s, alpha, omega));
             k_resid_f64<<<op->grid, kBlock, 0, s>>>(op->d, b_perm, q, rs.p + i, op->part.p, op->cnt.p);
             SDA_LAUNCHED();
         }
@@ -501,6 +556,20 @@ extern "C" SDA_API void sda_default_opts(sda_solve_opts *o) {
     o->use_graph = 1;
     o->iter_batch = 0;
     o->profile = 0;
+    o->alpha = NAN;
+    o->scatter_weight = NAN;
+}
+
+// the (alpha, omega) of a call: overrides from the options, else the operator's
+static int call_weights(const sda_operator *op, const sda_solve_opts &o, double *alpha, double *omega) {
+    const double a = isnan(o.alpha) ? op->alpha : o.alpha;
+    if (!(a >= 0.0 && a <= 1.0)) return fail(SDA_ERR_INVALID_ARG, "alpha must be in [0, 1]");
+    double w = o.scatter_weight;
+    if (isnan(w)) w = op->omega_follows_alpha ? 1.0 - a : op->omega;
+    if (!(w >= 0.0) || !isfinite(w)) return fail(SDA_ERR_INVALID_ARG, "scatter weight must be >= 0");
+    *alpha = a;
+    *omega = w;
+    return SDA_OK;
 }
 
 extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, int32_t n_shifts,
@@ -522,6 +591,8 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
     if (o.rhs_mode != SDA_RHS_CANONICAL && !o.rhs) return fail(SDA_ERR_INVALID_ARG, "rhs is NULL");
     if (o.rhs_mode < 0 || o.rhs_mode > SDA_RHS_GIVEN) return fail(SDA_ERR_INVALID_ARG, "bad rhs_mode");
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    double alpha = 0.0, omega = 0.0;
+    SDA_TRY(call_weights(op, o, &alpha, &omega));
     SDA_TRY(ensure_workspace(op, n_shifts));
     Workspace &w = op->ws;
     memset(&op->stats, 0, sizeof(op->stats));
@@ -566,11 +637,11 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
         sda_shift_report *rt = report ? report + (int64_t)i * n_shifts : nullptr;
         int rc;
         if (op->compute == SDA_F64) {
-            rc = solve_target<double, double>(op, t, b, shifts, n_shifts, o, wt, rt, s, &worst);
+            rc = solve_target<double, double>(op, t, b, shifts, n_shifts, o, alpha, omega, wt, rt, s, &worst);
         } else {
             rc = with_vt(op->compute, [&](auto tag) -> int {
                 using VT = std::remove_pointer_t<decltype(tag)>;
-                return solve_target<VT, float>(op, t, b, shifts, n_shifts, o, wt, rt, s, &worst);
+                return solve_target<VT, float>(op, t, b, shifts, n_shifts, o, alpha, omega, wt, rt, s, &worst);
             });
         }
         if (rc < 0) return rc;
@@ -591,6 +662,99 @@ extern "C" SDA_API int sda_get_solve_stats(const sda_operator *op, sda_solve_sta
 
 extern "C" SDA_API int64_t sda_kernel_launch_count(void) { return launch_count(); }
 
+extern "C" SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double alpha, double beta,
+                                        const double *w, const double *dloss_ds, const int64_t *rows, int64_t n_rows,
+                                        const sda_solve_opts *opt, double *d_alpha, double *d_beta,
+                                        double *lambda_out, void *cuda_stream) {
+    clear_error();
+    if (!op || !w || !d_alpha || !d_beta) return fail(SDA_ERR_INVALID_ARG, "NULL argument");
+    if (n_rows < 0 || (n_rows > 0 && (!rows || !dloss_ds))) return fail(SDA_ERR_INVALID_ARG, "bad held-out rows");
+    if (target < 0 || target >= op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target out of range");
+    if (!(beta > 0.0) || !isfinite(beta)) return fail(SDA_ERR_INVALID_ARG, "beta must be finite and > 0");
+    sda_solve_opts o;
+    if (opt) {
+        o = *opt;
+    } else {
+        sda_default_opts(&o);
+        o.tol = 1e-10;
+    }
+    o.alpha = alpha;
+    o.scatter_weight = NAN;
+    o.rhs_mode = SDA_RHS_GIVEN;
+    double al = 0.0, om = 0.0;
+    SDA_TRY(call_weights(op, o, &al, &om));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    SDA_TRY(ensure_workspace(op, 1));
+    Workspace &ws = op->ws;
+    const int64_t d = op->d, n = op->n;
+    if (ws.adj.n < (size_t)(3 * d + 5 * n)) SDA_TRY(ws.adj.alloc((size_t)(3 * d + 5 * n)));
+    double *wp = ws.adj.p, *c = wp + d, *lam = c + d, *G = lam + d, *uw = G + n, *ul = uw + n, *v = ul + n;
+    double *v2 = G;   // G is free once c is formed
+    DevBuf<double> sc;
+    DevBuf<int> err;
+    SDA_TRY(sc.alloc(8));
+    SDA_TRY(err.alloc(1));
+    SDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    const double *mu = op->mu.p + (int64_t)target * d;
+    const int8_t *y = op->labels.p + (int64_t)target * n;
+    // right-hand side (X_h - 1 mu^T)^T g = X^T G - mu (1^T G), G = g scattered to the rows
+    SDA_TRY(permute_to_new(op, w, wp, 1, s));
+    SDA_CUDA(cudaMemsetAsync(G, 0, (size_t)n * sizeof(double), s));
+    if (n_rows > 0) {
+        k_scatter_rows<<<grid_elems(n_rows, op->sm_count), kBlock, 0, s>>>(n_rows, rows, dloss_ds, G, n, err.p);
+        SDA_LAUNCHED();
+    }
+    SDA_TRY(op_xtmul_f64(op, G, c, s));
+    SDA_TRY(dot_f64(op, n, G, nullptr, sc.p + 0, s));
+    k_sub_mu<<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, c, mu, sc.p + 0);
+    SDA_LAUNCHED();
+    int herr = 0;
+    SDA_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(SDA_ERR_INVALID_ARG, "a held-out row id is out of range");
+    // adjoint solve (B + beta I) lambda = c on the same operator
+    int worst = SDA_OK;
+    sda_shift_report rep;
+    int rc;
+    if (op->compute == SDA_F64) {
+        rc = solve_target<double, double>(op, target, c, &beta, 1, o, al, om, nullptr, &rep, s, &worst);
+        if (rc >= 0) {
+            k_w_f64<double><<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, (const double *)ws.shift.p, lam);
+            SDA_LAUNCHED();
+        }
+    } else {
+        rc = with_vt(op->compute, [&](auto tag) -> int {
+            using VT = std::remove_pointer_t<decltype(tag)>;
+            SDA_TRY((solve_target<VT, float>(op, target, c, &beta, 1, o, al, om, nullptr, &rep, s, &worst)));
+            k_w_f64<float><<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, (const float *)ws.shift.p, lam);
+            SDA_LAUNCHED();
+            return SDA_OK;
+        });
+    }
+    if (rc < 0) return rc;
+    if (worst < 0) return worst;
+    // d/d beta = -lambda^T w;  d/d alpha = -[(X~ lambda)^T L (X~ w) - c (X~ lambda)^T P_l (X~ w)]
+    SDA_TRY(dot_f64(op, d, lam, wp, sc.p + 1, s));
+    SDA_TRY(dot_f64(op, d, mu, wp, sc.p + 2, s));
+    SDA_TRY(dot_f64(op, d, mu, lam, sc.p + 3, s));
+    SDA_TRY(op_xmul_f64(op, wp, uw, sc.p + 2, s));
+    SDA_TRY(op_xmul_f64(op, lam, ul, sc.p + 3, s));
+    SDA_TRY((rowpass<double, double>(op->s_lanes, n, op->s_rp.p, op->s_col.p, op->s_val64.p,
+                                     GatherVec<double, double>{uw}, EpiLap64{v, uw, op->deg64.p, y, 0.0, 1.0},
+                                     op->sm_count * kMaxBlocksPerSm, s)));
+    SDA_TRY(dot_f64(op, n, ul, v, sc.p + 4, s));
+    k_mask_labelled<<<grid_elems(n, op->sm_count), kBlock, 0, s>>>(n, y, uw, v2);
+    SDA_LAUNCHED();
+    SDA_TRY(dot_f64(op, n, ul, v2, sc.p + 5, s));
+    if (lambda_out) SDA_TRY(permute_to_old(op, lam, lambda_out, 1, s));
+    double hs[8];
+    SDA_CUDA(cudaMemcpyAsync(hs, sc.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    *d_beta = -hs[1];
+    *d_alpha = -(hs[4] - (op->omega_follows_alpha ? hs[5] : 0.0));
+    return worst;
+}
+
 extern "C" SDA_API int sda_operator_apply(const sda_operator *op, int32_t target, double sigma, const double *p,
                                           double *q, void *cuda_stream) {
     clear_error();
@@ -601,7 +765,7 @@ extern "C" SDA_API int sda_operator_apply(const sda_operator *op, int32_t target
     SDA_TRY(ensure_apply_scratch(mop));
     double *pn = op->ws.f64.p, *qn = pn + op->d;
     SDA_TRY(permute_to_new(op, p, pn, 1, s));
-    SDA_TRY(op_apply_f64(op, target, sigma, pn, qn, s));
+    SDA_TRY(op_apply_f64(op, target, sigma, pn, qn, s, op->alpha, op->omega));
     SDA_TRY(permute_to_old(op, qn, q, 1, s));
     SDA_CUDA(cudaStreamSynchronize(s));
     return SDA_OK;

@@ -52,7 +52,8 @@ class sda_solve_opts(ctypes.Structure):
                 ("rhs_mode", ctypes.c_int32), ("rhs", ctypes.c_void_p), ("rhs_on_device", ctypes.c_int32),
                 ("target_begin", ctypes.c_int32), ("target_count", ctypes.c_int32),
                 ("check_residual", ctypes.c_int32), ("out_on_device", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("iter_batch", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("iter_batch", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("scatter_weight", ctypes.c_double)]
 
 
 class sda_shift_report(ctypes.Structure):
@@ -80,6 +81,9 @@ _SIGS = {
     "sda_solve_shifts": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(sda_solve_opts), _vp,
                                         ctypes.POINTER(sda_shift_report), _vp]),
     "sda_project": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32, ctypes.c_int32, _vp]),
+    "sda_adjoint_grad": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp,
+                                        ctypes.c_int64, ctypes.POINTER(sda_solve_opts), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), _vp, _vp]),
     "sda_operator_apply": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
     "sda_operator_apply_static": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
     "sda_get_operator_info": (ctypes.c_int, [_vp, ctypes.POINTER(sda_operator_info)]),
@@ -231,6 +235,21 @@ def sda_project(op, w, n_vec, scores, centred=0, target=0, stream=None):
     sp, _, sk = _ptr(scores)
     return _check(lib.sda_project(op, wp, int(n_vec), sp, int(centred), int(target), _stream(stream)),
                   "sda_project")
+
+
+def sda_adjoint_grad(op, target, alpha, beta, w, dloss_ds, rows, opts: sda_solve_opts | None = None,
+                     lambda_out=None, stream=None):
+    """Calls sda_adjoint_grad; returns (status, d_alpha, d_beta)."""
+    lib = load()
+    wp, _, wk = _ptr(w)
+    gp, _, gk = _ptr(dloss_ds)
+    rp, _, rk = _ptr(rows)
+    lp, _, lk = _ptr(lambda_out)
+    da, db = ctypes.c_double(), ctypes.c_double()
+    code = _check(lib.sda_adjoint_grad(op, int(target), float(alpha), float(beta), wp, gp, rp, int(rows.shape[0]),
+                                       ctypes.byref(opts) if opts is not None else None, ctypes.byref(da),
+                                       ctypes.byref(db), lp, _stream(stream)), "sda_adjoint_grad")
+    return code, da.value, db.value
 
 
 def sda_operator_apply(op, target, sigma, p, q, stream=None):

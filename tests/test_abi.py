@@ -42,5 +42,5 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sda.sda_csr) == 56
     assert ctypes.sizeof(sda.sda_shift_report) == 24
     assert sda.sda_solve_opts.rhs.offset == 24
-    assert ctypes.sizeof(sda.sda_solve_opts) == 64
+    assert ctypes.sizeof(sda.sda_solve_opts) == 80
     assert ctypes.sizeof(sda.sda_solve_stats) == 104

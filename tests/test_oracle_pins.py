@@ -349,3 +349,27 @@ def test_planted_direction_is_found(cfg1):
     unl = np.nonzero(cfg1.labels[0] == 0)[0]
     aucs = [oracle.auc(o.project(res.W[s])[unl], cfg1.truth[0][unl]) for s in range(len(cfg1.shifts))]
     assert max(aucs) > 0.65
+
+
+# --------------------------------------------------------------------------
+# Adjoint of the held-out loss (not in the paper; checks the library's adjoint)
+# --------------------------------------------------------------------------
+
+def test_dense_adjoint_gradient_equals_finite_differences(tiny):
+    """d loss / d alpha and d loss / d beta from one adjoint solve equal central
+    finite differences (h = 1e-4 on alpha and on log beta) of the loss itself."""
+    X = _dense(tiny)
+    y = tiny.labels[0]
+    rows = tiny.heldout[0]
+    yr = tiny.truth[0][rows]
+    alpha, beta = 0.3, 0.05
+    args = (X, tiny.s_ptr, tiny.s_col, tiny.s_val, y)
+    loss, da, db, _ = oracle.adjoint_grad_dense(*args, alpha, beta, rows, yr)
+    h = 1e-4
+    lp = oracle.adjoint_grad_dense(*args, alpha + h, beta, rows, yr)[0]
+    lm = oracle.adjoint_grad_dense(*args, alpha - h, beta, rows, yr)[0]
+    assert abs((lp - lm) / (2 * h) - da) <= 1e-6 * max(1.0, abs(da))
+    lp = oracle.adjoint_grad_dense(*args, alpha, beta * np.exp(h), rows, yr)[0]
+    lm = oracle.adjoint_grad_dense(*args, alpha, beta * np.exp(-h), rows, yr)[0]
+    # d/d(log beta) = beta d/d beta
+    assert abs((lp - lm) / (2 * h) - beta * db) <= 1e-6 * max(1.0, abs(beta * db))
