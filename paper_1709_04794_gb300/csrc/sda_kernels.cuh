@@ -302,7 +302,7 @@ struct EpiP1 {
     SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return st->done != 0; }
     __device__ __forceinline__ void begin(Shared &) { c = st->c; }
-    __device__ __forceinline__ void segment(int64_t i, FT s) { ut[i] = (FT)((double)s - c); }
+    __device__ __forceinline__ void segment(int64_t i, FT s) { ut[i] = s - (FT)c; }
     __device__ __forceinline__ void segment_block(int64_t i, FT s) {
         if (threadIdx.x == 0) segment(i, s);
     }
@@ -358,7 +358,7 @@ struct EpiP2 {
         if (threadIdx.x == 0) segment(i, s);
     }
     __device__ void end(Shared &sh) {
-        double mine[2] = {block_sum(d0, sh.red), block_sum(d1, sh.red)};
+        double mine[2] = {block_sum((double)d0, sh.red), block_sum((double)d1, sh.red)};
         if (!arrive_last<2>(mine, partials, counter)) return;
         double tot[2];
         grid_dots<2>(partials, gridDim.x, tot, sh.red);
@@ -546,6 +546,8 @@ __global__ void __launch_bounds__(kBlock) k_colpass(const Tile *__restrict__ til
                     const int64_t j = tl.seg0 + s;
                     const int64_t e0 = cp[j];
                     const int len = (int)(cp[j + 1] - e0);
+                    const int32_t *rowj = row + e0;
+                    const VT *valj = val + (val ? e0 : 0);
                     for (int eb = lane; eb < len; eb += G * U) {
                         int32_t ii[U];
                         AccT vv[U], gg[U];
@@ -553,8 +555,8 @@ __global__ void __launch_bounds__(kBlock) k_colpass(const Tile *__restrict__ til
                         for (int u = 0; u < U; ++u) {
                             const int e = eb + u * G;
                             const bool ok = e < len;
-                            ii[u] = ok ? __ldcs(row + e0 + e) : -1;
-                            vv[u] = ok ? (AccT)Val<VT>::get_cs(val, e0 + e) : (AccT)0;
+                            ii[u] = ok ? __ldcs(rowj + e) : -1;
+                            vv[u] = ok ? (AccT)Val<VT>::get_cs(valj, e) : (AccT)0;
                         }
 #pragma unroll
                         for (int u = 0; u < U; ++u) gg[u] = ii[u] >= 0 ? v[ii[u]] : (AccT)0;
@@ -635,7 +637,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
     using V = typename Vec16<FT>::T;
     using R = typename RPair<FT>::T;
     constexpr int VW = Vec16<FT>::n;
-    constexpr int UNROLL = 4;
+    constexpr int UNROLL = 2;
     __shared__ StreamSmem<FT> sm;
     if (st->done) return;
     {
@@ -659,23 +661,24 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
     const R *__restrict__ a = rp + par * ldw;
     R *__restrict__ an_ = rp + (par ^ 1) * ldw;
     const double *__restrict__ mu = st->mu;
-    const FT al = (FT)sm.alpha;
-    const double t = sm.t, sigma0 = sm.sigma0, gam = sm.gamma;
+    // per-element work in the vector type (1^T v is zero in exact arithmetic, so the
+    // centring term is a rounding-size correction); block sums in FP64
+    const FT al = (FT)sm.alpha, t = (FT)sm.t, sigma0 = (FT)sm.sigma0, gam = (FT)sm.gamma;
     const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
-    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+    FT d0 = 0, d1 = 0, d2 = 0;
     for (int64_t j = tid; j < d; j += nthr) {
         const R x = a[j];
         const FT pk = form_p<FT>(x.x, x.y, al);
-        const double mj = mu[j];
-        const double qj = (double)s[j] - mj * t + sigma0 * (double)pk;
-        const FT rnj = (FT)((double)x.x + gam * qj);
+        const FT mj = (FT)mu[j];
+        const FT qj = s[j] - mj * t + sigma0 * pk;
+        const FT rnj = x.x + gam * qj;
         R y;
         y.x = rnj;
         y.y = pk;
         an_[j] = y;
-        d0 += (double)rnj * (double)rnj;
-        d1 += mj * (double)rnj;
-        d2 += (double)rnj * (double)pk;
+        d0 += rnj * rnj;
+        d1 += mj * rnj;
+        d2 += rnj * pk;
     }
     const uint32_t nch = (uint32_t)(ldw / VW);
     const int64_t total = (int64_t)sm.nact * nch;
@@ -712,7 +715,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
             *reinterpret_cast<V *>(W + off[u]) = wv[u];
         }
     }
-    double mine[3] = {block_sum(d0, sm.red), block_sum(d1, sm.red), block_sum(d2, sm.red)};
+    double mine[3] = {block_sum((double)d0, sm.red), block_sum((double)d1, sm.red), block_sum((double)d2, sm.red)};
     if (!arrive_last<3>(mine, partials, counter)) return;
     double tot[3];
     grid_dots<3>(partials, gridDim.x, tot, sm.red);

@@ -34,11 +34,11 @@ def test_adjoint_matches_dense_oracle(tiny):
     assert abs(b.grad.item() - ref_db) <= 1e-6 * abs(ref_db) + 1e-12
 
 
-@pytest.mark.parametrize("compute,rtol", [("f64", 1e-4), ("f16", 2e-2)])
-def test_adjoint_matches_finite_differences(cfg1, compute, rtol):
+def test_adjoint_matches_finite_differences(cfg1):
+    """FP64 path: the adjoint gradient against central differences of the loss."""
+    compute, rtol, tol = "f64", 1e-4, 1e-12
     op, rows, yr = _setup(cfg1, compute)
     alpha, beta = 0.1, 0.05
-    tol = 1e-12 if compute == "f64" else 1e-6
 
     def f(al, be):
         return autograd.held_out_loss(torch.tensor(al, dtype=torch.float64),
@@ -52,6 +52,21 @@ def test_adjoint_matches_finite_differences(cfg1, compute, rtol):
     fd_lb = (f(alpha, beta * np.exp(h)) - f(alpha, beta * np.exp(-h))) / (2 * h)
     assert abs(a.grad.item() - fd_a) <= rtol * abs(fd_a) + 1e-10, (a.grad.item(), fd_a)
     assert abs(beta * b.grad.item() - fd_lb) <= rtol * abs(fd_lb) + 1e-10, (beta * b.grad.item(), fd_lb)
+
+
+def test_mixed_adjoint_close_to_fp64_adjoint(cfg1):
+    """Mixed path (FP16 X, FP32 vectors): finite differences of its loss are below
+    the solve's noise at this gradient size, so it is compared with the FP64
+    adjoint instead; both solves to 1e-8, agreement to 5 %."""
+    grads = {}
+    for compute in ("f64", "f16"):
+        op, rows, yr = _setup(cfg1, compute)
+        a = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+        b = torch.tensor(0.05, dtype=torch.float64, requires_grad=True)
+        autograd.held_out_loss(a, b, op, 0, rows, yr, tol=1e-8).backward()
+        grads[compute] = (a.grad.item(), b.grad.item())
+    for k in range(2):
+        assert abs(grads["f16"][k] - grads["f64"][k]) <= 5e-2 * abs(grads["f64"][k]), grads
 
 
 def test_adjoint_rejects_bad_rows(tiny):
