@@ -264,6 +264,21 @@ static int convert_any(int compute, int64_t m, const void *in, int dtype, const 
     }
 }
 
+// lanes per row of the register row pass (four loads per lane per round): the
+// 90th percentile of the row lengths fits one round
+static int row_lanes(const std::vector<int64_t> &rp) {
+    const int64_t n = (int64_t)rp.size() - 1;
+    if (n <= 0) return 4;
+    std::vector<int64_t> len((size_t)n);
+    for (int64_t i = 0; i < n; ++i) len[(size_t)i] = rp[(size_t)i + 1] - rp[(size_t)i];
+    const size_t k = (size_t)(0.9 * (double)(n - 1));
+    std::nth_element(len.begin(), len.begin() + k, len.end());
+    const int64_t p90 = len[k];
+    int g = 4;
+    while (g < 32 && 4 * g < p90) g <<= 1;
+    return g;
+}
+
 static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double alpha, double omega,
                  sda_dtype compute, cudaStream_t s, sda_operator *op) {
     const int64_t n = X->n_rows, d = X->n_cols, nnz = X->nnz, snz = S->nnz;
@@ -439,9 +454,11 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
         SDA_CUDA(cudaMemcpyAsync(hp.data(), op->x_rp.p, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
         SDA_TRY(build_seg_schedule(hp, op->xrow));
+        op->x_lanes = row_lanes(hp);
         SDA_CUDA(cudaMemcpyAsync(hp.data(), op->s_rp.p, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
         SDA_TRY(build_seg_schedule(hp, op->srow));
+        op->s_lanes = row_lanes(hp);
     }
     // split segments of the three schedules use disjoint slot / counter ranges
     op->xrow_slot0 = op->col.nslots;
@@ -491,14 +508,6 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
     return SDA_OK;
 }
 
-// lanes per row of the register row pass: about four nonzeros per lane on average
-static int row_lanes(int64_t nnz, int64_t n) {
-    const double avg = n > 0 ? (double)nnz / (double)n : 0.0;
-    int g = 4;
-    while (g < 32 && 4.0 * g < avg) g <<= 1;
-    return g;
-}
-
 }  // namespace sda
 
 using namespace sda;
@@ -544,8 +553,6 @@ extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, co
         return fail(SDA_ERR_CUDA, "no CUDA device");
     }
     op->grid = op->sm_count * 4;
-    op->x_lanes = row_lanes(X->nnz, X->n_rows);
-    op->s_lanes = row_lanes(S->nnz, X->n_rows);
     int rc = build(X, S, y, alpha, omega, compute, (cudaStream_t)cuda_stream, op);
     if (rc < 0) {
         cudaStreamSynchronize((cudaStream_t)cuda_stream);

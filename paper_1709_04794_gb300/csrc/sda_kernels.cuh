@@ -170,16 +170,19 @@ __global__ void __launch_bounds__(kBlock) k_rowpass(int64_t n, const int64_t *__
         const int64_t i = base + (threadIdx.x & 31) / G;
         AccT acc = 0;
         if (i < n) {
-            const int64_t e1 = rp[i + 1];
-            for (int64_t eb = rp[i] + lane; eb < e1; eb += G * U) {
+            const int64_t e0 = rp[i];
+            const int len = (int)(rp[i + 1] - e0);
+            const int32_t *__restrict__ ip = idx + e0;
+            const VT *__restrict__ vp = val + (val ? e0 : 0);
+            for (int eb = lane; eb < len; eb += G * U) {
                 int32_t jj[U];
                 AccT vv[U], gg[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int64_t e = eb + (int64_t)u * G;
-                    const bool ok = e < e1;
-                    jj[u] = ok ? __ldcs(idx + e) : -1;
-                    vv[u] = ok ? (AccT)Val<VT>::get_cs(val, e) : (AccT)0;
+                    const int e = eb + u * G;
+                    const bool ok = e < len;
+                    jj[u] = ok ? __ldcs(ip + e) : -1;
+                    vv[u] = ok ? (AccT)Val<VT>::get_cs(vp, e) : (AccT)0;
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) gg[u] = jj[u] >= 0 ? gather(jj[u]) : (AccT)0;
@@ -661,24 +664,25 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
     const R *__restrict__ a = rp + par * ldw;
     R *__restrict__ an_ = rp + (par ^ 1) * ldw;
     const double *__restrict__ mu = st->mu;
-    // per-element work in the vector type (1^T v is zero in exact arithmetic, so the
-    // centring term is a rounding-size correction); block sums in FP64
-    const FT al = (FT)sm.alpha, t = (FT)sm.t, sigma0 = (FT)sm.sigma0, gam = (FT)sm.gamma;
+    // the base recurrence r_{k+1} = r_k + gamma_k q is evaluated in FP64 and
+    // rounded once to the vector type (D elements per iteration)
+    const FT al = (FT)sm.alpha;
+    const double t = sm.t, sigma0 = sm.sigma0, gam = sm.gamma;
     const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
-    FT d0 = 0, d1 = 0, d2 = 0;
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
     for (int64_t j = tid; j < d; j += nthr) {
         const R x = a[j];
         const FT pk = form_p<FT>(x.x, x.y, al);
-        const FT mj = (FT)mu[j];
-        const FT qj = s[j] - mj * t + sigma0 * pk;
-        const FT rnj = x.x + gam * qj;
+        const double mj = mu[j];
+        const double qj = (double)s[j] - mj * t + sigma0 * (double)pk;
+        const FT rnj = (FT)((double)x.x + gam * qj);
         R y;
         y.x = rnj;
         y.y = pk;
         an_[j] = y;
-        d0 += rnj * rnj;
-        d1 += mj * rnj;
-        d2 += rnj * pk;
+        d0 += (double)rnj * (double)rnj;
+        d1 += mj * (double)rnj;
+        d2 += (double)rnj * (double)pk;
     }
     const uint32_t nch = (uint32_t)(ldw / VW);
     const int64_t total = (int64_t)sm.nact * nch;
@@ -715,7 +719,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
             *reinterpret_cast<V *>(W + off[u]) = wv[u];
         }
     }
-    double mine[3] = {block_sum((double)d0, sm.red), block_sum((double)d1, sm.red), block_sum((double)d2, sm.red)};
+    double mine[3] = {block_sum(d0, sm.red), block_sum(d1, sm.red), block_sum(d2, sm.red)};
     if (!arrive_last<3>(mine, partials, counter)) return;
     double tot[3];
     grid_dots<3>(partials, gridDim.x, tot, sm.red);

@@ -140,9 +140,9 @@ static int with_vt(int compute, F &&f) {
 template <class F>
 static int with_row_lanes(int g, F &&f) {
     switch (g) {
-    case 4: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 8>());
-    case 8: return f(std::integral_constant<int, 8>(), std::integral_constant<int, 8>());
-    case 16: return f(std::integral_constant<int, 16>(), std::integral_constant<int, 8>());
+    case 4: return f(std::integral_constant<int, 4>(), std::integral_constant<int, 4>());
+    case 8: return f(std::integral_constant<int, 8>(), std::integral_constant<int, 4>());
+    case 16: return f(std::integral_constant<int, 16>(), std::integral_constant<int, 4>());
     default: return f(std::integral_constant<int, 32>(), std::integral_constant<int, 4>());
     }
 }
