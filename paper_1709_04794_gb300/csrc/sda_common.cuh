@@ -1,6 +1,7 @@
 // Internal definitions shared by the translation units of libsda.
 #pragma once
 
+#include <cuda/atomic>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -170,21 +171,26 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
     return s;
 }
 
+// Arrival on a device-scope counter with release/acquire ordering: the writes
+// made before the arrival by the arriving thread are visible to the thread that
+// observes the final count.  Returns the count before this arrival.
+__device__ __forceinline__ unsigned arrive(unsigned *counter) {
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> c(*counter);
+    return c.fetch_add(1u, cuda::memory_order_acq_rel);
+}
+
 // Grid-wide "last block" protocol: every block stores its NDOT partials, the
-// block that arrives last sees all of them.  Returns true in that block only
-// (for every thread of it).  The counter is reset by the caller.
+// block that arrives last sees all of them (read them with __ldcg).  Returns true
+// in that block only (for every thread of it).  The counter is reset by the caller.
 template <int NDOT>
 __device__ __forceinline__ bool arrive_last(const double *mine, double *partials, unsigned *counter) {
     __shared__ int last;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NDOT; ++k) partials[(int64_t)blockIdx.x * NDOT + k] = mine[k];
-        __threadfence();
-        unsigned prev = atomicAdd(counter, 1u);
-        last = (prev == gridDim.x - 1);
+        last = (arrive(counter) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last) __threadfence();
     return last != 0;
 }
 

@@ -113,13 +113,10 @@ __device__ __forceinline__ void seg_tile(const Tile &tl, const int64_t *__restri
     // one chunk of a split segment: the chunk that arrives last adds the chunks in order
     if (threadIdx.x == 0) {
         slots[tl.slot] = acc;
-        __threadfence();
-        const unsigned prev = atomicAdd(&lcount[tl.lseg], 1u);
-        sh.last = (prev == (unsigned)splits[tl.lseg].nchunks - 1u);
+        sh.last = (arrive(&lcount[tl.lseg]) == (unsigned)splits[tl.lseg].nchunks - 1u);
     }
     __syncthreads();
     if (sh.last) {
-        __threadfence();
         const SplitSeg sp = splits[tl.lseg];
         AccT tot = 0;
         for (int c = 0; c < sp.nchunks; ++c) tot += __ldcg(slots + sp.slot0 + c);
@@ -583,13 +580,10 @@ __global__ void __launch_bounds__(kBlock) k_colpass(const Tile *__restrict__ til
         }
         if (threadIdx.x == 0) {
             slots[tl.slot] = acc;
-            __threadfence();
-            const unsigned prev = atomicAdd(&lcount[tl.lseg], 1u);
-            last = (prev == (unsigned)splits[tl.lseg].nchunks - 1u);
+            last = (arrive(&lcount[tl.lseg]) == (unsigned)splits[tl.lseg].nchunks - 1u);
         }
         __syncthreads();
         if (last) {
-            __threadfence();
             const SplitSeg sp = splits[tl.lseg];
             AccT tot = 0;
             for (int c = 0; c < sp.nchunks; ++c) tot += __ldcg(slots + sp.slot0 + c);
