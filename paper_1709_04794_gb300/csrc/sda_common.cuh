@@ -194,17 +194,54 @@ __device__ __forceinline__ bool arrive_last(const double *mine, double *partials
     return last != 0;
 }
 
-// Fixed-order sum of the grid's partials (called by every thread of the last block).
-template <int NDOT>
-__device__ __forceinline__ void reduce_partials(const double *partials, int nblocks, double *out,
-                                                double *red) {
+// Shared-memory doubles a block reduction of up to four sums needs.
+constexpr int kRedDoubles = 4 * (kBlock / 32);
+
+// Block sums of NDOT per-thread values, in a fixed order.  Each warp adds its
+// lanes in the values' own type (a shuffle tree, the NDOT sums interleaved); the
+// kBlock/32 warp sums are then converted and added in FP64 by the first warp
+// alone, so a block issues only a few FP64 instructions (GB300 runs FP64 at about
+// 1/60 of its FP32 rate).  The result is valid in thread 0 only.  `red` holds
+// NDOT * kBlock/32 doubles.  Contains __syncthreads().
+template <int NDOT, class AT>
+__device__ __forceinline__ void block_dots(AT (&v)[NDOT], double (&out)[NDOT], double *red) {
+    constexpr int NW = kBlock / 32;
 #pragma unroll
-    for (int k = 0; k < NDOT; ++k) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += kBlock) s += __ldcg(partials + (int64_t)b * NDOT + k);
-        s = block_sum(s, red);
-        out[k] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    AT *r = reinterpret_cast<AT *>(red);
+    __syncthreads();   // `red` may still be read by an earlier reduction
+    if (l == 0) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) r[k * NW + w] = v[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) {
+            double x = l < NW ? (double)r[k * NW + l] : 0.0;
+#pragma unroll
+            for (int o = NW / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            out[k] = x;
+        }
+    }
+}
+
+// Fixed-order sum of the grid's NDOT-wide partials (called by every thread of
+// the last block); the result is valid in thread 0 only.
+template <int NDOT>
+__device__ __forceinline__ void grid_dots(const double *partials, int nblocks, double (&out)[NDOT], double *red) {
+    double s[NDOT];
+#pragma unroll
+    for (int k = 0; k < NDOT; ++k) s[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += kBlock) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) s[k] += __ldcg(partials + (int64_t)b * NDOT + k);
+    }
+    block_dots<NDOT, double>(s, out, red);
 }
 
 // ---------------------------------------------------------------------------

@@ -298,38 +298,29 @@ struct EpiP1 {
     using Shared = NoShared;
     FT *ut;
     const SolveState *st;
-    double c;
+    FT c;
     SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return st->done != 0; }
-    __device__ __forceinline__ void begin(Shared &) { c = st->c; }
-    __device__ __forceinline__ void segment(int64_t i, FT s) { ut[i] = s - (FT)c; }
+    __device__ __forceinline__ void begin(Shared &) { c = (FT)st->c; }
+    __device__ __forceinline__ void segment(int64_t i, FT s) { ut[i] = s - c; }
     __device__ __forceinline__ void segment_block(int64_t i, FT s) {
         if (threadIdx.x == 0) segment(i, s);
     }
     __device__ __forceinline__ void end(Shared &) {}
 };
 
-// Sum of the grid's partials in block order (called by every thread of the last block).
-template <int NDOT>
-__device__ __forceinline__ void grid_dots(double *partials, int nblocks, double (&tot)[NDOT], double *red) {
-#pragma unroll
-    for (int k = 0; k < NDOT; ++k) tot[k] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += kBlock) {
-#pragma unroll
-        for (int k = 0; k < NDOT; ++k) tot[k] += __ldcg(partials + (int64_t)b * NDOT + k);
-    }
-#pragma unroll
-    for (int k = 0; k < NDOT; ++k) tot[k] = block_sum(tot[k], red);
-}
-
 // phase 2: v_i = omega [y_i != 0] ut_i + alpha (D_ii ut_i - s_i); dots <ut, v>, 1^T v;
-// the last block forms gamma_k and zeta^s_{k+1}, gamma^s_k
+// the last block forms gamma_k, then zeta^s_{k+1} / zeta^s_k and gamma^s_k of every
+// active shift, and writes the compact stream parameters.  Per-row arithmetic
+// and the per-thread dots are in the vector type (D_ii ut_i - s_i with one
+// rounding); the block and grid sums in FP64.
 template <class FT>
 struct EpiP2 {
     struct Shared {
-        double red[kBlock / 32];
+        double red[kRedDoubles];
+        double gamma;
         int ok;
-        int flag[kBlock];
+        unsigned ballot[kMaxShifts / 32];
     };
     FT *v;
     const FT *ut, *deg;
@@ -337,29 +328,45 @@ struct EpiP2 {
     double *partials;
     unsigned *counter;
     const int8_t *y;
-    double omega, al, d0, d1;
+    FT omega, al, d0, d1;
     SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return st->done != 0; }
     __device__ __forceinline__ void begin(Shared &) {
         y = st->labels;
-        omega = st->omega;
-        al = st->alpha_l;
-        d0 = d1 = 0.0;
+        omega = (FT)st->omega;
+        al = (FT)st->alpha_l;
+        d0 = d1 = (FT)0;
     }
     __device__ __forceinline__ void segment(int64_t i, FT s) {
-        const double u = (double)ut[i];
-        const double vi = omega * (y[i] != 0 ? u : 0.0) + al * ((double)deg[i] * u - (double)s);
-        const FT vf = (FT)vi;
+        const FT u = ut[i];
+        const FT lap = fma(deg[i], u, -s);
+        const FT vf = fma(al, lap, y[i] != 0 ? omega * u : (FT)0);
         v[i] = vf;
-        d0 += u * (double)vf;
-        d1 += (double)vf;
+        d0 = fma(u, vf, d0);
+        d1 += vf;
     }
     __device__ __forceinline__ void segment_block(int64_t i, FT s) {
         if (threadIdx.x == 0) segment(i, s);
     }
     __device__ void end(Shared &sh) {
-        double mine[2] = {block_sum((double)d0, sh.red), block_sum((double)d1, sh.red)};
+        FT mine_t[2] = {d0, d1};
+        double mine[2];
+        block_dots<2>(mine_t, mine, sh.red);
         if (!arrive_last<2>(mine, partials, counter)) return;
+        // the shift state is read before the grid sum so that its loads overlap it
+        const int ns = st->n_shifts;
+        const int q = threadIdx.x;
+        ShiftState *h = st->sh + q;
+        int act = 0;
+        double zp = 0.0, zk = 0.0, ak = 0.0, dl = 0.0;
+        if (q < ns) {
+            act = h->active;
+            zp = h->z_prev;
+            zk = h->z;
+            ak = h->a;
+            dl = h->delta;
+        }
+        const double gp = st->gamma_prev, al_k = st->alpha;
         double tot[2];
         grid_dots<2>(partials, gridDim.x, tot, sh.red);
         if (threadIdx.x == 0) {
@@ -369,49 +376,47 @@ struct EpiP2 {
                 st->status = SDA_ERR_BREAKDOWN;
                 st->done = 1;
             } else {
-                st->gamma = -st->rr / pq;
+                const double gam = -st->rr / pq;
+                st->gamma = gam;
                 st->t = tot[1];
+                sh.gamma = gam;
+                StreamParams &sp = st->sp;
+                sp.alpha = al_k;
+                sp.gamma = gam;
+                sp.t = tot[1];
+                sp.sigma0 = st->sigma0;
             }
             *counter = 0u;
         }
         __syncthreads();
         if (!sh.ok) return;
-        const double gam = st->gamma, gp = st->gamma_prev, al_k = st->alpha;
-        const int ns = st->n_shifts;
-        StreamParams &sp = st->sp;
-        int act = 0;
-        double zk = 0.0, ak = 0.0, gk = 0.0;
-        if (threadIdx.x < ns) {
-            ShiftState &h = st->sh[threadIdx.x];
-            if (h.active) {
-                const double den = gam * al_k * (h.z_prev - h.z) + h.z_prev * gp * (1.0 - h.delta * gam);
-                const double zn = h.z_prev * h.z * gp / den;
-                h.z_next = zn;
-                h.g = gam * zn / h.z;
-                zk = h.z;
-                ak = h.a;
-                gk = h.g;
-                act = 1;
-            }
+        // zeta_{k+1} / zeta_k = zeta_{k-1} gamma_{k-1} / den (one division per shift)
+        const double gam = sh.gamma;
+        double gk = 0.0;
+        if (act) {
+            const double den = gam * al_k * (zp - zk) + zp * gp * (1.0 - dl * gam);
+            const double ratio = zp * gp / den;
+            h->ratio = ratio;
+            gk = gam * ratio;
+            h->g = gk;
         }
-        // compact the active shifts for the stream kernel (slot = number of active shifts before it)
-        sh.flag[threadIdx.x] = act;
+        // compact the active shifts for the stream kernel (slot = active shifts before it)
+        const unsigned bal = __ballot_sync(0xffffffffu, act);
+        if (q < kMaxShifts && (q & 31) == 0) sh.ballot[q >> 5] = bal;
         __syncthreads();
         if (act) {
-            int pos = 0;
-            for (int q = 0; q < (int)threadIdx.x; ++q) pos += sh.flag[q];
-            sp.act[pos] = threadIdx.x;
+            int pos = __popc(bal & ((1u << (q & 31)) - 1u));
+            for (int w = 0; w < (q >> 5); ++w) pos += __popc(sh.ballot[w]);
+            StreamParams &sp = st->sp;
+            sp.act[pos] = q;
             sp.zk[pos] = zk;
             sp.ak[pos] = ak;
             sp.gk[pos] = gk;
         }
-        const int na = __syncthreads_count(act);
         if (threadIdx.x == 0) {
-            sp.nact = na;
-            sp.alpha = al_k;
-            sp.gamma = gam;
-            sp.t = st->t;
-            sp.sigma0 = st->sigma0;
+            int na = 0;
+            for (int w = 0; w < kMaxShifts / 32; ++w) na += __popc(sh.ballot[w]);
+            st->sp.nact = na;
         }
     }
 };
@@ -456,10 +461,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, cons
                                                     typename RPair<FT>::T *rp, FT *W, FT *P, SolveState *st,
                                                     double *partials, unsigned *counter) {
     using R = typename RPair<FT>::T;
-    __shared__ double red[kBlock / 32];
+    __shared__ double red[kRedDoubles];
     const int ns = st->n_shifts;
     const double *mu = st->mu;
-    double d0 = 0.0, d1 = 0.0;
+    double dd[2] = {0.0, 0.0};
     for (int64_t j = (int64_t)blockIdx.x * kBlock + threadIdx.x; j < ldw; j += (int64_t)gridDim.x * kBlock) {
         const FT rj = j < d ? (FT)b[j] : (FT)0;
         R x;
@@ -473,17 +478,19 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, cons
             P[(int64_t)s * ldw + j] = (FT)0;
         }
         if (j < d) {
-            d0 += (double)rj * (double)rj;
-            d1 += mu[j] * (double)rj;
+            dd[0] += (double)rj * (double)rj;
+            dd[1] += mu[j] * (double)rj;
         }
     }
-    double mine[2] = {block_sum(d0, red), block_sum(d1, red)};
+    double mine[2];
+    block_dots<2>(dd, mine, red);
     if (!arrive_last<2>(mine, partials, counter)) return;
     double tot[2];
     grid_dots<2>(partials, gridDim.x, tot, red);
     if (threadIdx.x == 0) {
         st->rr = tot[0];
         st->bnorm = sqrt(tot[0]);
+        st->inv_bnorm = st->bnorm > 0.0 ? 1.0 / st->bnorm : 0.0;
         st->c = tot[1];
         st->pp = tot[0];
         st->alpha = 0.0;
@@ -501,7 +508,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, cons
         ShiftState &h = st->sh[threadIdx.x];
         h.z_prev = 1.0;
         h.z = 1.0;
-        h.z_next = 1.0;
+        h.ratio = 1.0;
         h.g = 0.0;
         h.a = 0.0;
         h.res = zero_rhs ? 0.0 : 1.0;
@@ -609,7 +616,7 @@ struct StreamSmem {
     int nact;
     int act[kMaxShifts];
     FT zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
-    double red[kBlock / 32];
+    double red[kRedDoubles];
     double alpha_new, rnorm;
 };
 
@@ -663,7 +670,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
     const FT al = (FT)sm.alpha;
     const double t = sm.t, sigma0 = sm.sigma0, gam = sm.gamma;
     const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
-    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+    double dd[3] = {0.0, 0.0, 0.0};
     for (int64_t j = tid; j < d; j += nthr) {
         const R x = a[j];
         const FT pk = form_p<FT>(x.x, x.y, al);
@@ -674,34 +681,40 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
         y.x = rnj;
         y.y = pk;
         an_[j] = y;
-        d0 += (double)rnj * (double)rnj;
-        d1 += mj * (double)rnj;
-        d2 += (double)rnj * (double)pk;
+        dd[0] += (double)rnj * (double)rnj;
+        dd[1] += mj * (double)rnj;
+        dd[2] += (double)rnj * (double)pk;
     }
-    const uint32_t nch = (uint32_t)(ldw / VW);
-    const int64_t total = (int64_t)sm.nact * nch;
-    for (int64_t i0 = tid; i0 < total; i0 += nthr * UNROLL) {
+    // shift items i = q * nch + c (shift slot q, 16-byte chunk c), thread stride
+    // nthr; (q, c) advance by (nthr / nch, nthr % nch) without a division per item
+    const int nch = (int)(ldw / VW), nact = sm.nact;
+    int q = (int)(tid / nch), c = (int)(tid - (int64_t)q * nch);
+    const int sq = (int)(nthr / nch), sc = (int)(nthr - (int64_t)sq * nch);
+    while (q < nact) {
         FT r[UNROLL][VW];
         V pv[UNROLL], wv[UNROLL];
         int64_t off[UNROLL];
         int qq[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-            const int64_t i = i0 + u * nthr;
-            qq[u] = -1;
-            if (i < total) {
-                const uint32_t q = (uint32_t)(i / nch);
-                const int64_t j0 = (int64_t)(i - (int64_t)q * nch) * VW;
-                qq[u] = (int)q;
+            qq[u] = q;
+            if (q < nact) {
+                const int64_t j0 = (int64_t)c * VW;
                 off[u] = (int64_t)sm.act[q] * ldw + j0;
                 load_r(a, j0, r[u]);
                 pv[u] = *reinterpret_cast<const V *>(P + off[u]);
                 wv[u] = *reinterpret_cast<const V *>(W + off[u]);
             }
+            q += sq;
+            c += sc;
+            if (c >= nch) {
+                c -= nch;
+                ++q;
+            }
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) {
-            if (qq[u] < 0) continue;
+            if (qq[u] >= nact) continue;
             const FT z = sm.zk[qq[u]], aa = sm.ak[qq[u]], g = sm.gk[qq[u]];
 #pragma unroll
             for (int e = 0; e < VW; ++e) {
@@ -713,8 +726,22 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
             *reinterpret_cast<V *>(W + off[u]) = wv[u];
         }
     }
-    double mine[3] = {block_sum(d0, sm.red), block_sum(d1, sm.red), block_sum(d2, sm.red)};
+    double mine[3];
+    block_dots<3>(dd, mine, sm.red);
     if (!arrive_last<3>(mine, partials, counter)) return;
+    // the shift state is read before the grid sum so that its loads overlap it
+    const int ns = st->n_shifts, sh_q = threadIdx.x;
+    ShiftState *h = st->sh + sh_q;
+    int act = 0;
+    double zk = 0.0, ratio = 0.0;
+    if (sh_q < ns) {
+        act = h->active;
+        zk = h->z;
+        ratio = h->ratio;
+    }
+    const int k = st->k + 1;
+    const double tolb = st->tol * st->bnorm, inv_b = st->inv_bnorm;
+    const int fixed = st->fixed;
     double tot[3];
     grid_dots<3>(partials, gridDim.x, tot, sm.red);
     if (threadIdx.x == 0) {
@@ -728,27 +755,22 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
         st->c = c_new;
         st->pp = pp_new;
         st->rr = rr_new;
-        st->k = st->k + 1;
+        st->k = k;
         sm.alpha_new = anw;
         sm.rnorm = sqrt(rr_new);
         *counter = 0u;
     }
     __syncthreads();
-    const int ns = st->n_shifts, k = st->k;
-    int act = 0;
-    if (threadIdx.x < ns) {
-        ShiftState &h = st->sh[threadIdx.x];
-        if (h.active) {
-            const double ratio = h.z_next / h.z;
-            h.a = sm.alpha_new * ratio * ratio;
-            h.z_prev = h.z;
-            h.z = h.z_next;
-            h.iters = k;
-            const double rz = fabs(h.z) * sm.rnorm, bnorm = st->bnorm;
-            h.res = bnorm > 0.0 ? rz / bnorm : 0.0;
-            if (!st->fixed && (rz < st->tol * bnorm || !(fabs(h.z) > 0.0))) h.active = 0;
-            act = h.active;
-        }
+    if (act) {
+        const double zn = zk * ratio;
+        h->a = sm.alpha_new * ratio * ratio;
+        h->z_prev = zk;
+        h->z = zn;
+        h->iters = k;
+        const double rz = fabs(zn) * sm.rnorm;
+        h->res = rz * inv_b;
+        if (!fixed && (rz < tolb || !(fabs(zn) > 0.0))) act = 0;
+        h->active = act;
     }
     const int na = __syncthreads_count(act);
     if (threadIdx.x == 0) {

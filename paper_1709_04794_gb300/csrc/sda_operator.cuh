@@ -11,7 +11,7 @@ struct ShiftState {
     double delta;    // beta_s - sigma0 (shift relative to the base system)
     double z_prev;   // zeta_{k-1}
     double z;        // zeta_k
-    double z_next;   // zeta_{k+1} (set when gamma_k is known)
+    double ratio;    // zeta_{k+1} / zeta_k (set when gamma_k is known)
     double g;        // gamma^s_k = gamma_k zeta_{k+1} / zeta_k
     double a;        // alpha^s_k: P_k = zeta_k r_k + alpha^s_k P_{k-1}
     double res;      // |zeta| ||r|| / ||b|| after the last update
@@ -32,7 +32,7 @@ struct StreamParams {
 // last block of the phase that completes them.
 struct SolveState {
     // fixed for the run
-    double sigma0, omega, alpha_l, tol, bnorm;
+    double sigma0, omega, alpha_l, tol, bnorm, inv_bnorm;
     int32_t n_shifts, limit, fixed;
     int32_t pad0;
     const int8_t *labels;   // labels of the target being solved

@@ -19,14 +19,15 @@ int last_error(char *buf, int len);
 __global__ void __launch_bounds__(kBlock) k_dot_f64(int64_t n, const double *__restrict__ a,
                                                     const double *__restrict__ b, double *out,
                                                     double *partials, unsigned *counter) {
-    __shared__ double red[kBlock / 32];
-    double s = 0.0;
+    __shared__ double red[kRedDoubles];
+    double s[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
-        s += b ? a[i] * b[i] : a[i];
-    double mine[1] = {block_sum(s, red)};
+        s[0] += b ? a[i] * b[i] : a[i];
+    double mine[1];
+    block_dots<1>(s, mine, red);
     if (!arrive_last<1>(mine, partials, counter)) return;
     double tot[1];
-    reduce_partials<1>(partials, gridDim.x, tot, red);
+    grid_dots<1>(partials, gridDim.x, tot, red);
     if (threadIdx.x == 0) {
         *out = tot[0];
         *counter = 0u;
@@ -37,16 +38,17 @@ __global__ void __launch_bounds__(kBlock) k_dot_f64(int64_t n, const double *__r
 __global__ void __launch_bounds__(kBlock) k_resid_f64(int64_t n, const double *__restrict__ b,
                                                       const double *__restrict__ q, double *out,
                                                       double *partials, unsigned *counter) {
-    __shared__ double red[kBlock / 32];
-    double s = 0.0;
+    __shared__ double red[kRedDoubles];
+    double s[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
         const double e = b[i] - q[i];
-        s += e * e;
+        s[0] += e * e;
     }
-    double mine[1] = {block_sum(s, red)};
+    double mine[1];
+    block_dots<1>(s, mine, red);
     if (!arrive_last<1>(mine, partials, counter)) return;
     double tot[1];
-    reduce_partials<1>(partials, gridDim.x, tot, red);
+    grid_dots<1>(partials, gridDim.x, tot, red);
     if (threadIdx.x == 0) {
         *out = tot[0];
         *counter = 0u;
