@@ -132,27 +132,34 @@ def recorded_traffic(phase: str):
     return float(t.group(1))
 
 
-def algorithmic_bytes(prob, compute: str, iters: int, shift_iters: int):
+def algorithmic_bytes(prob, compute: str, iters: int, shift_iters: int, info: dict):
     """Algorithmic bytes per launch of each iteration kernel, averaged over one solve.
 
-    phase1 (rows of X):    CSR indices + values + row pointers, the {r_k, p_{k-1}}
-                           pairs once each, ut written.
+    Counted on the stored layouts with their nonzeros only (the zero padding of
+    segments to whole quads, and re-reads through L2, are not algorithmic):
+    phase1 (rows of X, k_rowhead):  int32 indices + values + row pointers, the
+                           {r_k, p_{k-1}} pairs once each, ut written.
     phase2 (rows of S):    CSR of S (vector-type weights) + row pointers, ut
                            read once, degrees, labels, v written.
-    phase3a (columns of X): CSC indices + values + column pointers, v read once,
-                           s written.
-    phase3b (stream):      s, {r_k, p_{k-1}} and mu_l (FP64) read, {r_{k+1}, p_k}
-                           written, and per active shift P and W read and written."""
+    phase3a (columns of X, k_colblk): 16-bit indices + values + the R ranges'
+                           column pointers, v read once, the R ranges' partial
+                           sums (pairs of the vector type) written.
+    phase3b (stream):      the R partial sums, {r_k, p_{k-1}} and mu_l read,
+                           {r_{k+1}, p_k} written, and per active shift P and W
+                           read and written."""
     n, d = prob.n, prob.d
     nnz = int(prob.x_ptr[-1])
     snz = int(prob.s_ptr[-1])
     vsz = {"f64": 8, "f32": 4, "f16": 2, "f8e4m3": 1, "pattern": 0}[compute]
     fsz = 8 if compute == "f64" else 4
+    psz = 8                       # one partial sum: an FP32 pair, or an FP64 value
+    mus = fsz                     # mu_l in the vector type
+    R = int(info["col_ranges"])
     return {
         "phase1": nnz * (4 + vsz) + (n + 1) * 8 + 2 * d * fsz + n * fsz,
         "phase2": snz * (4 + fsz) + (n + 1) * 8 + 3 * n * fsz + n,
-        "phase3a": nnz * (4 + vsz) + (d + 1) * 8 + n * fsz + d * fsz,
-        "phase3b": d * (5 * fsz + 8) + (shift_iters / max(iters, 1)) * d * 4 * fsz,
+        "phase3a": nnz * (2 + vsz) + R * (d + 1) * 8 + n * fsz + R * d * psz,
+        "phase3b": d * (R * psz + 4 * fsz + mus) + (shift_iters / max(iters, 1)) * d * 4 * fsz,
     }
 
 
@@ -247,6 +254,7 @@ def main():
             code, rep = sda.sda_solve_shifts(h, prob.shifts, opts(profile), w_out=w, n_report=1, stream=stream)
             sda.sda_project(h, w[0], ns, scores, 0, 0, stream)
             stats = sda.sda_get_solve_stats(h)
+            stats["info"] = sda.sda_get_operator_info(h)
         finally:
             sda.sda_destroy_operator(h)
         return code, rep, stats
@@ -284,14 +292,15 @@ def main():
 
     # per-kernel durations: one profiled solve (events around every phase kernel)
     pcode, prep, pstats = step(profile=1)
+    pinfo = pstats["info"]
     iters = max(1, pstats["iterations"])
-    per_launch = algorithmic_bytes(prob, compute, pstats["iterations"], pstats["shift_iterations"])
+    per_launch = algorithmic_bytes(prob, compute, pstats["iterations"], pstats["shift_iterations"], pinfo)
     durs = {k: pstats["ms"][i + 1] / iters for i, k in enumerate(("phase1", "phase2", "phase3a", "phase3b"))}
     dominant = max(durs, key=durs.get)
     peak, peak_kind = load_peaks()
     achieved = per_launch[dominant] / (durs[dominant] * 1e-3) / 1e9
-    kernel_names = {"phase1": "k_rowpass<EpiP1> (rows of X)", "phase2": "k_rowpass<EpiP2> (rows of S)",
-                    "phase3a": "k_colpass<EpiStore> (columns of X)", "phase3b": "k_cg_phase3b (vector and shift stream)"}
+    kernel_names = {"phase1": "k_rowhead (rows of X)", "phase2": "k_rowpass<EpiP2> (rows of S)",
+                    "phase3a": "k_colblk (columns of X)", "phase3b": "k_cg_phase3b (vector and shift stream)"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(dominant),
                 "kernel": kernel_names[dominant], "peak_kind": peak_kind,

@@ -289,6 +289,11 @@ typedef struct {
     sda_dtype compute;
     double alpha, omega;
     int64_t device_bytes;   /* device memory held by the operator (without solve workspace) */
+    /* layouts of the iteration's sparse passes: */
+    int32_t col_ranges;     /* ranges of rows of the column pass (X^T v partial sums per feature) */
+    int32_t row_head;       /* leading features the row pass gathers from shared memory */
+    int64_t col_entries;    /* entries of the column-pass layout, padding to quads included */
+    int64_t row_entries;    /* entries of the row-pass layout, padding to quads included */
 } sda_operator_info;
 
 SDA_API int sda_get_operator_info(const sda_operator *op, sda_operator_info *info);

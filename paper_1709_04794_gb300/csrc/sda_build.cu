@@ -200,11 +200,100 @@ __global__ void k_indicators(int64_t n, const int8_t *y, double *ip, double *in_
 }
 
 __global__ void k_means(int64_t d, const double *sp, const double *sn, double npos, double nneg, double *mu,
-                        double *dv) {
+                        float *mu32, double *dv) {
     const double ell = npos + nneg;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
-        mu[j] = (sp[j] + sn[j]) / ell;
+        const double m = (sp[j] + sn[j]) / ell;
+        mu[j] = m;
+        mu32[j] = (float)m;
         dv[j] = sp[j] / npos - sn[j] / nneg;
+    }
+}
+
+// ---- X split into ranges of rows (column pass of the iteration) ----------------
+// lb[r][j] = first entry of column j whose row is at least r * rb (rows ascend
+// within a column); cnt[r][j] = entries of column j in range r, cnt[r][d] = 0
+__global__ void k_range_bounds(int64_t d, int nr, int64_t rb, const int64_t *cp, const int32_t *row, int64_t *lb,
+                               int64_t *cnt) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = cp[j], hi = cp[j + 1];
+        int64_t prev = lo;
+        lb[j] = lo;
+        for (int r = 1; r <= nr; ++r) {
+            int64_t a = prev, b = hi;
+            if (r == nr) {
+                a = hi;
+            } else {
+                const int64_t bound = (int64_t)r * rb;
+                while (a < b) {
+                    const int64_t m = a + (b - a) / 2;
+                    if ((int64_t)row[m] < bound) a = m + 1;
+                    else b = m;
+                }
+            }
+            lb[(int64_t)r * d + j] = a;
+            cnt[(int64_t)(r - 1) * (d + 1) + j] = (a - prev + 3) / 4 * 4;   // padded to a quad
+            prev = a;
+        }
+    }
+}
+
+// entry e of the CSC goes to range r = row / rb at xb_cp[r][j] + (e - lb[r][j]);
+// the padding after each segment stays zero (row 0, value 0)
+__global__ void k_range_scatter(int64_t nnz, int64_t d, int64_t rb, const int64_t *cp, const int32_t *row,
+                                const char *val, int vsz, const int64_t *lb, const int64_t *xcp, uint16_t *xrow,
+                                char *xval) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = 0, b = d;   // largest j with cp[j] <= e
+        while (b - a > 1) {
+            const int64_t m = a + (b - a) / 2;
+            if (cp[m] <= e) a = m;
+            else b = m;
+        }
+        const int64_t j = a, i = row[e], r = i / rb;
+        const int64_t pos = xcp[r * (d + 1) + j] + (e - lb[r * d + j]);
+        xrow[pos] = (uint16_t)(i - r * rb);
+        switch (vsz) {
+        case 0: xval[pos] = (char)0x38; break;   // pattern: an FP8 E4M3 one
+        case 1: xval[pos] = val[e]; break;
+        case 2: reinterpret_cast<uint16_t *>(xval)[pos] = reinterpret_cast<const uint16_t *>(val)[e]; break;
+        case 4: reinterpret_cast<uint32_t *>(xval)[pos] = reinterpret_cast<const uint32_t *>(val)[e]; break;
+        case 8:
+            reinterpret_cast<unsigned long long *>(xval)[pos] = reinterpret_cast<const unsigned long long *>(val)[e];
+            break;
+        default: break;
+        }
+    }
+}
+
+// padded row lengths of X (quads)
+__global__ void k_row_quads(int64_t n, const int64_t *rp, int64_t *cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        cnt[i] = (rp[i + 1] - rp[i] + 3) / 4 * 4;
+}
+
+// entry e of row i goes to xrp[i] + (e - rp[i]); the padding stays zero
+__global__ void k_row_scatter(int64_t nnz, int64_t n, const int64_t *rp, const int32_t *col, const char *val, int vsz,
+                              const int64_t *xrp, int32_t *xcol, char *xval) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = 0, b = n;   // largest i with rp[i] <= e
+        while (b - a > 1) {
+            const int64_t m = a + (b - a) / 2;
+            if (rp[m] <= e) a = m;
+            else b = m;
+        }
+        const int64_t pos = xrp[a] + (e - rp[a]);
+        xcol[pos] = col[e];
+        switch (vsz) {
+        case 0: xval[pos] = (char)0x38; break;   // pattern: an FP8 E4M3 one
+        case 1: xval[pos] = val[e]; break;
+        case 2: reinterpret_cast<uint16_t *>(xval)[pos] = reinterpret_cast<const uint16_t *>(val)[e]; break;
+        case 4: reinterpret_cast<uint32_t *>(xval)[pos] = reinterpret_cast<const uint32_t *>(val)[e]; break;
+        case 8:
+            reinterpret_cast<unsigned long long *>(xval)[pos] = reinterpret_cast<const unsigned long long *>(val)[e];
+            break;
+        default: break;
+        }
     }
 }
 
@@ -277,6 +366,98 @@ static int row_lanes(const std::vector<int64_t> &rp) {
     int g = 4;
     while (g < 32 && 4 * g < p90) g <<= 1;
     return g;
+}
+
+// A matrix of nseg segments over nidx indices (CSC-like: ptr, idx, val) split
+// into ranges of the index small enough that one range's slice of an nidx-vector
+// of the iteration type fits a block's shared memory (at most 65280 indices:
+// 16-bit local indices), equal in size up to a multiple of 256.  Each (range,
+// segment) is padded with zero entries to a multiple of four (quads: one 8-byte
+// load of indices per four entries); a pattern matrix (vsz 0) gets explicit FP8
+// ones.  Indices ascend within each segment (the range bounds are found by
+// binary search).
+static int build_range_blocks(sda_operator *op, RangeBlocks &out, const int64_t *ptr, const int32_t *idx,
+                              const char *val, size_t vsz, int64_t nseg, int64_t nidx, int64_t nnz, size_t fsz,
+                              int sms, cudaStream_t s) {
+    int optin = 0, per_sm = 0;
+    SDA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, op->device));
+    SDA_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, op->device));
+    const int64_t budget = std::min<int64_t>(optin, per_sm / kColBlkPerSm) - kColBlkReserve;
+    const int64_t rb_max = std::min<int64_t>(65280, budget / (int64_t)fsz / 256 * 256);
+    if (rb_max < 256) return fail(SDA_ERR_UNSUPPORTED, "not enough shared memory per block for the range passes");
+    const int64_t nr = std::max<int64_t>(1, (nidx + rb_max - 1) / rb_max);
+    const int64_t rb = ((nidx + nr - 1) / nr + 255) / 256 * 256;
+    out.nranges = (int)nr;
+    out.rb = rb;
+    out.nseg = nseg;
+    SDA_TRY(out.cp.alloc((size_t)(nr * (nseg + 1))));
+    SDA_CUDA(cudaMemsetAsync(out.cp.p, 0, out.cp.bytes(), s));
+    DevBuf<int64_t> lb;
+    SDA_TRY(lb.alloc((size_t)((nr + 1) * nseg)));
+    k_range_bounds<<<grid1(nseg, sms), kBlock, 0, s>>>(nseg, (int)nr, rb, ptr, idx, lb.p, out.cp.p);
+    SDA_LAUNCHED();
+    SDA_TRY(scan_exclusive_i64(out.cp.p, nr * (nseg + 1), s));
+    std::vector<int64_t> hp((size_t)(nr * (nseg + 1)));
+    SDA_CUDA(cudaMemcpyAsync(hp.data(), out.cp.p, hp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    const int64_t nq = std::max<int64_t>(hp.back(), 4);   // padded entries
+    const size_t bvsz = vsz ? vsz : 1;
+    SDA_TRY(out.idx.alloc((size_t)nq));
+    SDA_TRY(out.val.alloc((size_t)nq * bvsz));
+    SDA_CUDA(cudaMemsetAsync(out.idx.p, 0, out.idx.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(out.val.p, 0, out.val.bytes(), s));
+    k_range_scatter<<<grid1(nnz, sms), kBlock, 0, s>>>(nnz, nseg, rb, ptr, idx, val, (int)vsz, lb.p, out.cp.p,
+                                                       out.idx.p, out.val.p);
+    SDA_LAUNCHED();
+    std::vector<int32_t> off;
+    out.per_range = std::max(1, sms * kColBlkPerSm / (int)nr);
+    SDA_TRY(build_range_schedule(hp, (int)nr, nseg, out.sched, off));
+    SDA_TRY(out.tile_off.alloc(off.size()));
+    SDA_CUDA(cudaMemcpy(out.tile_off.p, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    return SDA_OK;
+}
+
+// Rows of X padded to whole quads for the row pass of the iteration, and the
+// number of leading (most frequent) features it keeps in shared memory.
+static int build_row_quads(sda_operator *op, bool fp64, size_t vsz, int sms, cudaStream_t s) {
+    const int64_t n = op->n, d = op->d, nnz = op->nnz;
+    SDA_TRY(op->xr_rp.alloc((size_t)n + 1));
+    SDA_CUDA(cudaMemsetAsync(op->xr_rp.p + n, 0, sizeof(int64_t), s));
+    k_row_quads<<<grid1(n, sms), kBlock, 0, s>>>(n, op->x_rp.p, op->xr_rp.p);
+    SDA_LAUNCHED();
+    SDA_TRY(scan_exclusive_i64(op->xr_rp.p, n + 1, s));
+    std::vector<int64_t> hp((size_t)n + 1);
+    SDA_CUDA(cudaMemcpyAsync(hp.data(), op->xr_rp.p, hp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    const int64_t nq = std::max<int64_t>(hp.back(), 4);
+    const size_t bvsz = vsz ? vsz : 1;
+    SDA_TRY(op->xr_col.alloc((size_t)nq));
+    SDA_TRY(op->xr_val.alloc((size_t)nq * bvsz));
+    SDA_CUDA(cudaMemsetAsync(op->xr_col.p, 0, op->xr_col.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(op->xr_val.p, 0, op->xr_val.bytes(), s));
+    k_row_scatter<<<grid1(nnz, sms), kBlock, 0, s>>>(nnz, n, op->x_rp.p, op->x_col.p, op->x_val_r.p, (int)vsz,
+                                                     op->xr_rp.p, op->xr_col.p, op->xr_val.p);
+    SDA_LAUNCHED();
+    // lanes per row: the fewest (2..32) whose two quads per lane cover the median row
+    std::vector<int64_t> len((size_t)n);
+    for (int64_t i = 0; i < n; ++i) len[(size_t)i] = hp[(size_t)i + 1] - hp[(size_t)i];
+    int64_t med = 0;
+    if (n > 0) {
+        std::nth_element(len.begin(), len.begin() + n / 2, len.end());
+        med = len[(size_t)(n / 2)];
+    }
+    int g = 2;
+    while (g < 32 && 8 * g < med) g <<= 1;
+    op->xr_lanes = g;
+    // head of p kept in shared memory: as many features as a block's share allows
+    int optin = 0, per_sm = 0;
+    SDA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, op->device));
+    SDA_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, op->device));
+    const int64_t fsz = fp64 ? 8 : 4;
+    const int64_t budget = std::min<int64_t>(optin, per_sm / kColBlkPerSm) - kColBlkReserve;
+    const int64_t hmax = std::max<int64_t>(0, budget / fsz / 256 * 256);
+    op->xr_head = (int)std::min<int64_t>(hmax, d / 8 * 8);   // within the pair buffer, whole 16-byte vectors
+    return SDA_OK;
 }
 
 static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double alpha, double omega,
@@ -381,6 +562,9 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
         if (herr & kErrInexact)
             return fail(SDA_ERR_VALUE_NOT_EXACT, "a value of X is not exact in the compute dtype %d", (int)compute);
     }
+    SDA_TRY(build_range_blocks(op, op->xb, op->x_cp.p, op->x_row.p, op->x_val_c.p, vsz, d, n, nnz,
+                               fp64 ? sizeof(double) : sizeof(float), sms, s));
+    SDA_TRY(build_row_quads(op, fp64, vsz, sms, s));
 
     // ---- S -------------------------------------------------------------------
     DevBuf<int32_t> s_col_in;
@@ -435,6 +619,7 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
     }
     SDA_LAUNCHED();
 
+
     // ---- labels ----------------------------------------------------------------
     const int64_t T = y->n_targets;
     SDA_TRY(to_device(op->labels, y->labels, T * n, y->on_device, s));
@@ -460,13 +645,15 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
         SDA_TRY(build_seg_schedule(hp, op->srow));
         op->s_lanes = row_lanes(hp);
     }
-    // split segments of the three schedules use disjoint slot / counter ranges
+    // split segments of the four schedules use disjoint slot / counter ranges
     op->xrow_slot0 = op->col.nslots;
     op->srow_slot0 = op->col.nslots + op->xrow.nslots;
+    op->xb.slot0 = op->srow_slot0 + op->srow.nslots;
     op->xrow_lseg0 = op->col.nsplits;
     op->srow_lseg0 = op->col.nsplits + op->xrow.nsplits;
-    SDA_TRY(op->slots.alloc((size_t)std::max(op->col.nslots + op->xrow.nslots + op->srow.nslots, 1)));
-    SDA_TRY(op->lcount.alloc((size_t)std::max(op->col.nsplits + op->xrow.nsplits + op->srow.nsplits, 1)));
+    op->xb.lseg0 = op->srow_lseg0 + op->srow.nsplits;
+    SDA_TRY(op->slots.alloc((size_t)std::max(op->xb.slot0 + op->xb.sched.nslots, 1)));
+    SDA_TRY(op->lcount.alloc((size_t)std::max(op->xb.lseg0 + op->xb.sched.nsplits, 1)));
     SDA_CUDA(cudaMemsetAsync(op->lcount.p, 0, op->lcount.bytes(), s));
     SDA_TRY(op->part.alloc((size_t)kMaxBlocksPerSm * op->sm_count * 4));
     SDA_TRY(op->cnt.alloc(4));
@@ -475,6 +662,7 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
 
     // ---- per-target counts and means (Alg. 7 step 3) ---------------------------------
     SDA_TRY(op->mu.alloc((size_t)(T * d)));
+    SDA_TRY(op->mu32.alloc((size_t)(T * d)));
     SDA_TRY(op->dvec.alloc((size_t)(T * d)));
     op->counts.assign((size_t)T * 3, 0.0);
     {
@@ -500,7 +688,7 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
             op->counts[t * 3 + 1] = (double)hc[0];
             op->counts[t * 3 + 2] = (double)hc[1];
             k_means<<<grid1(d, sms), kBlock, 0, s>>>(d, sp.p, sn.p, (double)hc[0], (double)hc[1], op->mu.p + t * d,
-                                                     op->dvec.p + t * d);
+                                                     op->mu32.p + t * d, op->dvec.p + t * d);
             SDA_LAUNCHED();
         }
         SDA_CUDA(cudaStreamSynchronize(s));
@@ -561,9 +749,10 @@ extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, co
     }
     op->bytes = (int64_t)(op->new_of_old.bytes() + op->old_of_new.bytes() + op->x_rp.bytes() + op->x_cp.bytes() +
                           op->x_col.bytes() + op->x_row.bytes() + op->x_val_r.bytes() + op->x_val_c.bytes() +
+                          op->xb.bytes() + op->xr_rp.bytes() + op->xr_col.bytes() + op->xr_val.bytes() +
                           op->s_rp.bytes() + op->s_col.bytes() + op->s_val64.bytes() + op->s_val32.bytes() +
                           op->deg64.bytes() + op->deg32.bytes() + op->labels.bytes() + op->mu.bytes() +
-                          op->dvec.bytes() + op->col.tiles.bytes() + op->col.splits.bytes() +
+                          op->mu32.bytes() + op->dvec.bytes() + op->col.tiles.bytes() + op->col.splits.bytes() +
                           op->xrow.tiles.bytes() + op->xrow.splits.bytes() + op->srow.tiles.bytes() +
                           op->srow.splits.bytes());
     *out = op;

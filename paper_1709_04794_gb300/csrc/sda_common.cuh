@@ -107,6 +107,11 @@ struct ColSchedule {
 
 // tiles of consecutive segments (rows or columns) of a CSR-like pointer array
 int build_seg_schedule(const std::vector<int64_t> &ptr, ColSchedule &out);
+// warp tiles (kWarpTileNnz, kWarpTileSegs, kWarpBigSeg, chunks aligned to quads)
+// of `nranges` pointer arrays of d + 1 entries each, stored one after the other
+// in `ptr`; the tiles of range r are [tile_off[r], tile_off[r + 1])
+int build_range_schedule(const std::vector<int64_t> &ptr, int nranges, int64_t d, ColSchedule &out,
+                         std::vector<int32_t> &tile_off);
 
 // ---------------------------------------------------------------------------
 // value storage types
@@ -144,6 +149,139 @@ template <>
 struct Val<Pattern> {
     static __device__ __forceinline__ float get(const Pattern *, int64_t) { return 1.0f; }
     static __device__ __forceinline__ float get_cs(const Pattern *, int64_t) { return 1.0f; }
+};
+
+// Four consecutive stored values (a quad, 4-aligned) converted to the
+// accumulation type, read with streaming loads.
+template <class VT, class AccT>
+struct Quad;
+template <class AccT>
+struct Quad<__half, AccT> {
+    static __device__ __forceinline__ void load(const __half *v, int64_t q, AccT (&x)[4]) {
+        const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(v) + q);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        x[0] = (AccT)a.x;
+        x[1] = (AccT)a.y;
+        x[2] = (AccT)b.x;
+        x[3] = (AccT)b.y;
+    }
+};
+template <class AccT>
+struct Quad<__nv_fp8_e4m3, AccT> {
+    static __device__ __forceinline__ void load(const __nv_fp8_e4m3 *v, int64_t q, AccT (&x)[4]) {
+        const unsigned u = __ldcs(reinterpret_cast<const unsigned *>(v) + q);
+        const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
+        const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+        x[0] = (AccT)a.x;
+        x[1] = (AccT)a.y;
+        x[2] = (AccT)b.x;
+        x[3] = (AccT)b.y;
+    }
+};
+template <class AccT>
+struct Quad<float, AccT> {
+    static __device__ __forceinline__ void load(const float *v, int64_t q, AccT (&x)[4]) {
+        const float4 u = __ldcs(reinterpret_cast<const float4 *>(v) + q);
+        x[0] = (AccT)u.x;
+        x[1] = (AccT)u.y;
+        x[2] = (AccT)u.z;
+        x[3] = (AccT)u.w;
+    }
+};
+template <class AccT>
+struct Quad<double, AccT> {
+    static __device__ __forceinline__ void load(const double *v, int64_t q, AccT (&x)[4]) {
+        const double2 a = __ldcs(reinterpret_cast<const double2 *>(v) + 2 * q);
+        const double2 b = __ldcs(reinterpret_cast<const double2 *>(v) + 2 * q + 1);
+        x[0] = (AccT)a.x;
+        x[1] = (AccT)a.y;
+        x[2] = (AccT)b.x;
+        x[3] = (AccT)b.y;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// FP32 pair arithmetic (a value carried as an unevaluated sum hi + lo of two
+// floats): Knuth's two-sum and the FMA form of Dekker's two-product, exact for
+// finite operands without overflow.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+__device__ __forceinline__ float two_prod(float a, float b, float &e) {
+    const float p = a * b;
+    e = fmaf(a, b, -p);
+    return p;
+}
+__device__ __forceinline__ void split_f32(double x, float &hi, float &lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// A running sum in the accumulation type of a sparse pass.  For FP32 it is a
+// pair (hi + lo): every added term goes in through two-sum, so the sum of n
+// terms carries O(eps) error instead of O(n eps); partial sums leave the pass
+// as such pairs (float2) so that the consumer adds them without rounding.  For
+// FP64 it is a plain double.
+template <class AccT>
+struct CompSum;
+template <>
+struct CompSum<float> {
+    using Part = float2;
+    float h = 0.f, l = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float e;
+        h = two_sum(h, x, e);
+        l += e;
+    }
+    __device__ __forceinline__ void add(const CompSum &o) {
+        float e;
+        h = two_sum(h, o.h, e);
+        l += o.l + e;
+    }
+    __device__ __forceinline__ void xor_reduce(int o) {
+        CompSum t;
+        t.h = __shfl_xor_sync(0xffffffffu, h, o);
+        t.l = __shfl_xor_sync(0xffffffffu, l, o);
+        add(t);
+    }
+    __device__ __forceinline__ Part part() const {
+        float e;
+        const float s = two_sum(h, l, e);
+        return make_float2(s, e);
+    }
+    __device__ __forceinline__ double to_double() const { return (double)h + (double)l; }
+    static __device__ __forceinline__ Part from_double(double x) {
+        float a, b;
+        split_f32(x, a, b);
+        return make_float2(a, b);
+    }
+    static __device__ __forceinline__ void add_part(CompSum &s, const Part &p) {
+        CompSum t;
+        t.h = p.x;
+        t.l = p.y;
+        s.add(t);
+    }
+    __device__ __forceinline__ float value() const { return h + l; }
+};
+template <>
+struct CompSum<double> {
+    using Part = double;
+    double h = 0.0;
+    __device__ __forceinline__ void add(double x) { h += x; }
+    __device__ __forceinline__ void add(const CompSum &o) { h += o.h; }
+    __device__ __forceinline__ void xor_reduce(int o) { h += __shfl_xor_sync(0xffffffffu, h, o); }
+    __device__ __forceinline__ Part part() const { return h; }
+    __device__ __forceinline__ double to_double() const { return h; }
+    static __device__ __forceinline__ Part from_double(double x) { return x; }
+    static __device__ __forceinline__ void add_part(CompSum &s, const Part &p) { s.h += p; }
+    __device__ __forceinline__ double value() const { return h; }
 };
 
 // ---------------------------------------------------------------------------
@@ -194,6 +332,18 @@ __device__ __forceinline__ bool arrive_last(const double *mine, double *partials
     return last != 0;
 }
 
+// Threads of a block of the blocked column pass (kColBlkPerSm blocks per SM;
+// a block's shared memory holds one range's slice of the gathered vector).  Its tiles are
+// worked by single warps: at most kWarpTileNnz nonzeros and kWarpTileSegs
+// columns; columns longer than kWarpBigSeg take whole-warp tiles.
+constexpr int kColBlk = 1024;
+constexpr int kColBlkPerSm = 1;   // blocks of the blocked column pass resident per SM
+constexpr int kWarpTileNnz = 512;
+constexpr int kWarpTileSegs = 128;
+constexpr int kWarpBigSeg = 128;
+// Shared memory the blocked column pass keeps for itself besides the slice.
+constexpr int kColBlkReserve = 2048;
+
 // Shared-memory doubles a block reduction of up to four sums needs.
 constexpr int kRedDoubles = 4 * (kBlock / 32);
 
@@ -227,6 +377,72 @@ __device__ __forceinline__ void block_dots(AT (&v)[NDOT], double (&out)[NDOT], d
             for (int o = NW / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             out[k] = x;
         }
+    }
+}
+
+// Block sums of NDOT compensated per-thread sums (CompSum): pair shuffle trees
+// within each warp, then the first warp over the warp sums; no rounding to the
+// plain type on the way.  The result (parts) is valid in thread 0 only.  `red`
+// holds NDOT * kBlock/32 parts.  Contains __syncthreads().
+template <int NDOT, class AT>
+__device__ __forceinline__ void block_parts(CompSum<AT> (&v)[NDOT], typename CompSum<AT>::Part (&out)[NDOT],
+                                            typename CompSum<AT>::Part *red) {
+    constexpr int NW = kBlock / 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) v[k].xor_reduce(o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();   // `red` may still be read by an earlier reduction
+    if (l == 0) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) red[k * NW + w] = v[k].part();
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) {
+            CompSum<AT> x;
+            if (l < NW) CompSum<AT>::add_part(x, red[k * NW + l]);
+#pragma unroll
+            for (int o = NW / 2; o > 0; o >>= 1) x.xor_reduce(o);
+            out[k] = x.part();
+        }
+    }
+}
+
+// Grid-wide "last block" protocol on compensated parts: every block stores its
+// NDOT parts; returns true in the block that arrives last (for all its threads).
+template <int NDOT, class Part>
+__device__ __forceinline__ bool arrive_last_parts(const Part *mine, Part *partials, unsigned *counter) {
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) partials[(int64_t)blockIdx.x * NDOT + k] = mine[k];
+        last = (arrive(counter) == gridDim.x - 1);
+    }
+    __syncthreads();
+    return last != 0;
+}
+
+// Fixed-order compensated sum of the grid's parts (called by every thread of
+// the last block), converted to FP64 once; valid in thread 0 only.
+template <int NDOT, class AT>
+__device__ __forceinline__ void grid_parts(const typename CompSum<AT>::Part *partials, int nblocks,
+                                           double (&out)[NDOT], typename CompSum<AT>::Part *red) {
+    CompSum<AT> s[NDOT];
+    for (int b = threadIdx.x; b < nblocks; b += kBlock) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) CompSum<AT>::add_part(s[k], __ldcg(partials + (int64_t)b * NDOT + k));
+    }
+    typename CompSum<AT>::Part tot[NDOT];
+    block_parts<NDOT, AT>(s, tot, red);
+#pragma unroll
+    for (int k = 0; k < NDOT; ++k) {
+        CompSum<AT> t;
+        CompSum<AT>::add_part(t, tot[k]);
+        out[k] = t.to_double();
     }
 }
 

@@ -7,8 +7,8 @@
 //   phase 1  (rows of X):     ut = X p_k - <mu, p_k> 1   (p_k = r_k + alpha_k p_{k-1} formed at the gather)
 //   phase 2  (rows of S):     v = omega P_l ut + alpha (D ut - S ut);  <ut, v>, 1^T v
 //                             -> gamma_k, zeta^s_{k+1}, gamma^s_k
-//   phase 3a (columns of X):  s = X^T v
-//   phase 3b (stream over D): q = s - mu (1^T v) + sigma0 p_k;  r_{k+1} = r_k + gamma_k q;
+//   phase 3a (columns of X):  s_r = X_r^T v for each range r of rows
+//   phase 3b (stream over D): s = sum_r s_r;  q = s - mu (1^T v) + sigma0 p_k;  r_{k+1} = r_k + gamma_k q;
 //                             P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1};  W^s_{k+1} = W^s_k - gamma^s_k P^s_k;
 //                             <r,r>, <mu,r>, <r,p_k>  -> alpha_{k+1}, <mu,p_{k+1}>, <p_{k+1},p_{k+1}>, stop tests
 // <p, (B + sigma0) p> = <ut, v> + sigma0 <p, p> is known after phase 2, so q is
@@ -17,12 +17,15 @@
 // ever waits for another).
 //
 // The row passes (X, S) use k_rowpass: G lanes per row with unrolled,
-// independent loads and register sums.  The column pass (X^T, Zipf-skewed
-// column lengths, features ordered by decreasing frequency) uses k_colpass over
-// tiles of consecutive columns: register groups for short and medium columns,
-// whole-block tiles for long ones, split across blocks when longer than
-// kTileNnz.  k_segpass (shared-memory staged tiles) serves the allocation-free
-// operator apply.
+// independent loads and register sums.  The column pass of the iteration
+// (X^T, Zipf-skewed column lengths, features ordered by decreasing frequency)
+// uses k_colblk: X split into ranges of rows whose slice of v fits a block's
+// shared memory, tiles of consecutive columns within a range (register groups
+// for short and medium columns, whole-block tiles for long ones, split across
+// blocks when longer than kTileNnz), every gather served from shared memory.
+// k_colpass (the same tiles over the whole CSC, gathers from global memory)
+// serves the FP64 operator pieces; k_segpass (shared-memory staged tiles) the
+// allocation-free operator apply.
 #pragma once
 
 #include "sda_operator.cuh"
@@ -322,37 +325,39 @@ struct EpiP2 {
         int ok;
         unsigned ballot[kMaxShifts / 32];
     };
+    using Part = typename CompSum<FT>::Part;
     FT *v;
     const FT *ut, *deg;
     SolveState *st;
     double *partials;
     unsigned *counter;
     const int8_t *y;
-    FT omega, al, d0, d1;
+    FT omega, al;
+    CompSum<FT> d[2];   // <ut, v>, 1^T v (compensated: 1^T v vanishes in exact arithmetic)
     SDA_TILE_PER_SEGMENT
     __device__ __forceinline__ bool skip() const { return st->done != 0; }
     __device__ __forceinline__ void begin(Shared &) {
         y = st->labels;
         omega = (FT)st->omega;
         al = (FT)st->alpha_l;
-        d0 = d1 = (FT)0;
     }
     __device__ __forceinline__ void segment(int64_t i, FT s) {
         const FT u = ut[i];
         const FT lap = fma(deg[i], u, -s);
         const FT vf = fma(al, lap, y[i] != 0 ? omega * u : (FT)0);
         v[i] = vf;
-        d0 = fma(u, vf, d0);
-        d1 += vf;
+        d[0].add(u * vf);
+        d[1].add(vf);
     }
     __device__ __forceinline__ void segment_block(int64_t i, FT s) {
         if (threadIdx.x == 0) segment(i, s);
     }
     __device__ void end(Shared &sh) {
-        FT mine_t[2] = {d0, d1};
-        double mine[2];
-        block_dots<2>(mine_t, mine, sh.red);
-        if (!arrive_last<2>(mine, partials, counter)) return;
+        Part mine[2];
+        Part *red = reinterpret_cast<Part *>(sh.red);
+        Part *parts = reinterpret_cast<Part *>(partials);
+        block_parts<2, FT>(d, mine, red);
+        if (!arrive_last_parts<2>(mine, parts, counter)) return;
         // the shift state is read before the grid sum so that its loads overlap it
         const int ns = st->n_shifts;
         const int q = threadIdx.x;
@@ -368,7 +373,7 @@ struct EpiP2 {
         }
         const double gp = st->gamma_prev, al_k = st->alpha;
         double tot[2];
-        grid_dots<2>(partials, gridDim.x, tot, sh.red);
+        grid_parts<2, FT>(parts, gridDim.x, tot, red);
         if (threadIdx.x == 0) {
             const double pq = tot[0] + st->sigma0 * st->pp;
             sh.ok = (pq > 0.0) && isfinite(pq);
@@ -602,7 +607,218 @@ __global__ void __launch_bounds__(kBlock) k_colpass(const Tile *__restrict__ til
     epi.end(esh);
 }
 
-// phase 3b (stream over D), q_j = s_j - mu_j t + sigma0 p_k,j for every feature:
+// Row pass ut = X p_k - <mu, p_k> 1 (Sec. 3.2.3, first identity) with the
+// frequent head of p_k in shared memory.  Features are numbered by decreasing
+// frequency, so p_k[0, head) serves most gathers: every block forms it once
+// from the {r_k, p_{k-1}} pairs (p_k = r_k + alpha_k p_{k-1}); the other
+// features read their pair from global memory.  Rows come padded with zero
+// entries (column 0) to whole quads: one 16-byte load brings four column
+// indices.  G lanes per row, two quads per lane in flight (more flood the
+// shared-memory pipe with gathers); lane 0 of the row's group writes ut_i.
+template <class VT, class FT, int G>
+__global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_rowhead(int64_t n, int head, int64_t ldw,
+                                                                  const int64_t *__restrict__ rp,
+                                                                  const int32_t *__restrict__ col,
+                                                                  const VT *__restrict__ val,
+                                                                  const typename RPair<FT>::T *__restrict__ pairs,
+                                                                  FT *__restrict__ ut, const SolveState *st) {
+    using R = typename RPair<FT>::T;
+    extern __shared__ __align__(16) unsigned char rowhead_smem[];
+    FT *ps = reinterpret_cast<FT *>(rowhead_smem);
+    if (st->done) return;
+    const R *__restrict__ a = pairs + (st->k & 1) * ldw;
+    const FT al = (FT)st->alpha, c = (FT)st->c;
+    if constexpr (std::is_same<FT, float>::value) {
+        // two pairs per 16-byte load, four loads per thread in flight
+        const float4 *src = reinterpret_cast<const float4 *>(a);
+        float2 *dst = reinterpret_cast<float2 *>(ps);
+        const int nv = head / 2;
+        for (int i0 = threadIdx.x; i0 < nv; i0 += 4 * kColBlk) {
+            float4 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + u * kColBlk < nv) x[u] = src[i0 + u * kColBlk];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + u * kColBlk < nv)
+                    dst[i0 + u * kColBlk] = make_float2(fmaf(al, x[u].y, x[u].x), fmaf(al, x[u].w, x[u].z));
+        }
+    } else {
+        for (int i0 = threadIdx.x; i0 < head; i0 += 4 * kColBlk) {
+            R x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + u * kColBlk < head) x[u] = a[i0 + u * kColBlk];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i0 + u * kColBlk < head) ps[i0 + u * kColBlk] = form_p<FT>(x[u].x, x[u].y, al);
+        }
+    }
+    __syncthreads();
+    const int4 *__restrict__ colq = reinterpret_cast<const int4 *>(col);
+    auto gat = [&](int j) -> FT { return j < head ? ps[j] : form_p<FT>(a[j].x, a[j].y, al); };
+    auto quad = [&](int64_t q, bool ok) -> FT {
+        int4 ci = make_int4(0, 0, 0, 0);
+        FT x[4] = {(FT)0, (FT)0, (FT)0, (FT)0};
+        if (ok) {
+            ci = __ldcs(colq + q);
+            Quad<VT, FT>::load(val, q, x);
+        }
+        return x[0] * gat(ci.x) + x[1] * gat(ci.y) + x[2] * gat(ci.z) + x[3] * gat(ci.w);
+    };
+    constexpr int RPW = 32 / G;
+    const int lane = threadIdx.x % G;
+    const int64_t warp = ((int64_t)blockIdx.x * kColBlk + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kColBlk) >> 5;
+    for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
+        const int64_t i = base + (threadIdx.x & 31) / G;
+        FT acc = 0;
+        if (i < n) {
+            const int64_t q0 = rp[i] >> 2;
+            const int nq = (int)((rp[i + 1] >> 2) - q0);
+            for (int qb = lane; qb < nq; qb += 2 * G) {
+                const FT a0 = quad(q0 + qb, true);
+                const FT a1 = quad(q0 + qb + G, qb + G < nq);
+                acc += a0 + a1;
+            }
+        }
+#pragma unroll
+        for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (i < n && lane == 0) ut[i] = acc - c;
+    }
+}
+
+// Column pass s = X^T v over ranges of rows (Sec. 3.2.3, second identity, before
+// the rank-one term): block b serves range r = b / per_range.  It first copies
+// v's slice of rows [r * rb, (r + 1) * rb) into shared memory (cp.async, all
+// copies in flight at once); then its warps work the range's warp tiles
+// round-robin, with every gather served from that copy.  Entries come in quads
+// (segments padded with zero entries to multiples of four): one 8-byte load
+// brings four 16-bit local row indices.  Multi-column tiles give each column a
+// group of `lanes` lanes, two quads per lane in flight; whole-warp tiles take
+// one chunk of a long column, four quads per lane; the chunk of a split column
+// that arrives last adds the chunks' parts in a fixed order.  Sums are
+// compensated (CompSum): the frequent features' columns run over most rows and
+// cancel (1^T v vanishes), so plain FP32 sums would lose their digits.  The
+// sums of range r go to out[r * ldo + j] as CompSum parts; the consumer adds
+// the ranges in order.
+template <class VT, class AccT>
+__global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__restrict__ tiles, int per_range,
+                                                   int64_t n, int64_t rb, int64_t nseg, int64_t ldo,
+                                                   const int64_t *__restrict__ cp, const uint16_t *__restrict__ row,
+                                                   const VT *__restrict__ val, const AccT *__restrict__ v,
+                                                   typename CompSum<AccT>::Part *__restrict__ out,
+                                                   typename CompSum<AccT>::Part *slots,
+                                                   unsigned *lcount, const SplitSeg *__restrict__ splits,
+                                                   const int32_t *__restrict__ tile_off, const SolveState *st) {
+    using CS = CompSum<AccT>;
+    extern __shared__ __align__(16) unsigned char colblk_smem[];
+    AccT *vs = reinterpret_cast<AccT *>(colblk_smem);
+    if (st && st->done) return;
+    const int r = blockIdx.x / per_range, c = blockIdx.x - r * per_range;
+    const int64_t r0 = (int64_t)r * rb;
+    const int len = (int)min(rb, n - r0);
+    {
+        // v + r0 is 16-byte aligned (rb is a multiple of 256 and v is aligned)
+        constexpr int VW = 16 / (int)sizeof(AccT);
+        const int n16 = len / VW;
+        const char *src = reinterpret_cast<const char *>(v + r0);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(colblk_smem);
+        for (int i = threadIdx.x; i < n16; i += kColBlk)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16u * (unsigned)i),
+                         "l"(src + 16 * (int64_t)i)
+                         : "memory");
+        for (int i = n16 * VW + threadIdx.x; i < len; i += kColBlk) vs[i] = v[r0 + i];
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
+    __syncthreads();
+    const uint2 *__restrict__ rowq = reinterpret_cast<const uint2 *>(row);
+    const int64_t *__restrict__ cpr = cp + (int64_t)r * (nseg + 1);
+    typename CS::Part *__restrict__ outr = out + (int64_t)r * ldo;
+    // dot of quad q with the staged slice (four products, rounded sum)
+    auto quad = [&](int64_t q, bool ok) -> AccT {
+        uint2 ri = make_uint2(0u, 0u);
+        AccT x[4] = {(AccT)0, (AccT)0, (AccT)0, (AccT)0};
+        if (ok) {
+            ri = __ldcs(rowq + q);
+            Quad<VT, AccT>::load(val, q, x);
+        }
+        return x[0] * vs[ri.x & 0xffffu] + x[1] * vs[ri.x >> 16] + x[2] * vs[ri.y & 0xffffu] + x[3] * vs[ri.y >> 16];
+    };
+    const int lane32 = threadIdx.x & 31;
+    // one warp tile
+    auto work = [&](const Tile &tl) {
+        if (tl.lanes > 0) {
+            const int G = tl.lanes, per = 32 / G;
+            const int g = lane32 / G, lane = lane32 % G;
+            const int nsg = tl.seg1 - tl.seg0;
+            for (int base = 0; base < nsg; base += per) {
+                const int sgi = base + g;
+                CS acc;
+                if (sgi < nsg) {
+                    const int64_t j = tl.seg0 + sgi;
+                    const int64_t q0 = cpr[j] >> 2;
+                    const int nq = (int)((cpr[j + 1] >> 2) - q0);
+                    for (int qb = lane; qb < nq; qb += 2 * G) {
+                        const AccT a0 = quad(q0 + qb, true);
+                        const AccT a1 = quad(q0 + qb + G, qb + G < nq);
+                        acc.add(a0);
+                        acc.add(a1);
+                    }
+                }
+                for (int o = G >> 1; o > 0; o >>= 1) acc.xor_reduce(o);
+                if (sgi < nsg && lane == 0) outr[tl.seg0 + sgi] = acc.part();
+            }
+            return;
+        }
+        const int64_t q0 = tl.nz0 >> 2;
+        const int nq = (int)((tl.nz1 >> 2) - q0);
+        CS acc;
+        for (int qb = lane32; qb < nq; qb += 4 * 32) {
+            const AccT a0 = quad(q0 + qb, true);
+            const AccT a1 = quad(q0 + qb + 32, qb + 32 < nq);
+            const AccT a2 = quad(q0 + qb + 64, qb + 64 < nq);
+            const AccT a3 = quad(q0 + qb + 96, qb + 96 < nq);
+            acc.add(a0);
+            acc.add(a1);
+            acc.add(a2);
+            acc.add(a3);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc.xor_reduce(o);
+        if (tl.slot < 0) {
+            if (lane32 == 0) outr[tl.seg0] = acc.part();
+            return;
+        }
+        // a chunk of a split column: its part goes to a slot; the warp of the
+        // chunk that arrives last adds the column's parts (compensated, fixed
+        // shuffle tree)
+        int last = 0;
+        const SplitSeg sp = splits[tl.lseg];
+        if (lane32 == 0) {
+            slots[tl.slot] = acc.part();
+            last = arrive(&lcount[tl.lseg]) == (unsigned)sp.nchunks - 1u;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            __syncwarp();
+            CS tot;
+            for (int q = lane32; q < sp.nchunks; q += 32) CS::add_part(tot, __ldcg(slots + sp.slot0 + q));
+            for (int o = 16; o > 0; o >>= 1) tot.xor_reduce(o);
+            if (lane32 == 0) {
+                lcount[tl.lseg] = 0u;
+                outr[tl.seg0] = tot.part();
+            }
+        }
+    };
+    // the range's tiles round-robin over its warps (tiles come in column order:
+    // long columns first, so every warp gets a mix of long and short ones)
+    const int nw = per_range * (kColBlk / 32);
+    const int t1 = tile_off[r + 1];
+    for (int t = tile_off[r] + c * (kColBlk / 32) + (threadIdx.x >> 5); t < t1; t += nw) work(tiles[t]);
+}
+
+// phase 3b (stream over D), s_j = sum of the row-range partials of X^T v,
+// q_j = s_j - mu_j t + sigma0 p_k,j for every feature:
 //   r_{k+1} = r_k + gamma_k q;  RP[k+1] = {r_{k+1}, p_k}
 //   P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1};  W^s_{k+1} = W^s_k - gamma^s_k P^s_k  (active shifts)
 // The base vectors are one grid-stride pass; the shift state a second one over
@@ -618,7 +834,27 @@ struct StreamSmem {
     FT zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
     double red[kRedDoubles];
     double alpha_new, rnorm;
+    float gh, gl, sh, sl, tf;   // gamma_k, sigma0 as FP32 pairs, t in FP32 (mixed path)
 };
+
+
+// r_{k+1} = r_k + gamma_k (s - mu t + sigma0 p_k) in FP32 pairs (s given as the
+// pair sjh + sjl), rounded once at the end (the same value as an FP64
+// evaluation rounded to FP32 up to ties); the mu t term is kept at FP32
+// precision since t = 1^T v vanishes in exact arithmetic.
+__device__ __forceinline__ float base_step_f32(float r, float pk, float sjh, float sjl, float mj,
+                                               const StreamSmem<float> &sm) {
+    float e0, e1, e2, e3;
+    const float bh = two_prod(sm.sh, pk, e0);
+    const float bl = fmaf(sm.sl, pk, e0);
+    const float qh0 = two_sum(sjh, bh, e1);
+    const float ql0 = fmaf(-mj, sm.tf, (e1 + bl) + sjl);
+    const float qh = qh0 + ql0;
+    const float ql = ql0 - (qh - qh0);
+    const float ph = two_prod(sm.gh, qh, e2);
+    const float sh = two_sum(r, ph, e3);
+    return sh + ((e3 + e2) + fmaf(sm.gh, ql, sm.gl * qh));
+}
 
 __device__ __forceinline__ void load_r(const float2 *a, int64_t j0, float (&r)[4]) {
     const float4 u = *reinterpret_cast<const float4 *>(a + j0);
@@ -634,7 +870,8 @@ __device__ __forceinline__ void load_r(const double2 *a, int64_t j0, double (&r)
 }
 
 template <class FT>
-__global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, const FT *__restrict__ s,
+__global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw,
+                                                       const typename CompSum<FT>::Part *__restrict__ s, int nparts,
                                                        typename RPair<FT>::T *__restrict__ rp,
                                                        FT *__restrict__ W, FT *__restrict__ P, SolveState *st,
                                                        double *partials, unsigned *counter) {
@@ -653,6 +890,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
             sm.sigma0 = sp.sigma0;
             sm.nact = sp.nact;
         }
+        if (threadIdx.x == 32) {
+            split_f32(sp.gamma, sm.gh, sm.gl);
+            split_f32(sp.sigma0, sm.sh, sm.sl);
+            sm.tf = (float)sp.t;
+        }
         if (threadIdx.x < kMaxShifts) {
             sm.act[threadIdx.x] = sp.act[threadIdx.x];
             sm.zk[threadIdx.x] = (FT)sp.zk[threadIdx.x];
@@ -660,30 +902,53 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
             sm.gk[threadIdx.x] = (FT)sp.gk[threadIdx.x];
         }
     }
+    constexpr bool kF32 = std::is_same<FT, float>::value;
     __syncthreads();
     const int par = st->k & 1;
     const R *__restrict__ a = rp + par * ldw;
     R *__restrict__ an_ = rp + (par ^ 1) * ldw;
-    const double *__restrict__ mu = st->mu;
-    // the base recurrence r_{k+1} = r_k + gamma_k q is evaluated in FP64 and
-    // rounded once to the vector type (D elements per iteration)
+    // the base recurrence r_{k+1} = r_k + gamma_k q is rounded once to the vector
+    // type: FP64 arithmetic on the FP64 path, FP32 pairs on the mixed path (D
+    // elements per iteration); the dots are summed in the vector type per warp
     const FT al = (FT)sm.alpha;
-    const double t = sm.t, sigma0 = sm.sigma0, gam = sm.gamma;
     const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
-    double dd[3] = {0.0, 0.0, 0.0};
-    for (int64_t j = tid; j < d; j += nthr) {
-        const R x = a[j];
-        const FT pk = form_p<FT>(x.x, x.y, al);
-        const double mj = mu[j];
-        const double qj = (double)s[j] - mj * t + sigma0 * (double)pk;
-        const FT rnj = (FT)((double)x.x + gam * qj);
-        R y;
-        y.x = rnj;
-        y.y = pk;
-        an_[j] = y;
-        dd[0] += (double)rnj * (double)rnj;
-        dd[1] += mj * (double)rnj;
-        dd[2] += (double)rnj * (double)pk;
+    CompSum<FT> dd[3];   // compensated: <mu, r> and <r, p> may cancel
+    if constexpr (kF32) {
+        const float *__restrict__ mu = st->mu32;
+        for (int64_t j = tid; j < d; j += nthr) {
+            const R x = a[j];
+            const float pk = form_p<float>(x.x, x.y, al);
+            const float mj = mu[j];
+            CompSum<float> sj;
+            for (int q = 0; q < nparts; ++q) CompSum<float>::add_part(sj, s[(int64_t)q * ldw + j]);
+            const float rnj = base_step_f32(x.x, pk, sj.h, sj.l, mj, sm);
+            R y;
+            y.x = rnj;
+            y.y = pk;
+            an_[j] = y;
+            dd[0].add(rnj * rnj);
+            dd[1].add(mj * rnj);
+            dd[2].add(rnj * pk);
+        }
+    } else {
+        const double *__restrict__ mu = st->mu;
+        const double t = sm.t, sigma0 = sm.sigma0, gam = sm.gamma;
+        for (int64_t j = tid; j < d; j += nthr) {
+            const R x = a[j];
+            const FT pk = form_p<FT>(x.x, x.y, al);
+            const double mj = mu[j];
+            CompSum<FT> sj;
+            for (int q = 0; q < nparts; ++q) CompSum<FT>::add_part(sj, s[(int64_t)q * ldw + j]);
+            const double qj = (double)sj.value() - mj * t + sigma0 * (double)pk;
+            const FT rnj = (FT)((double)x.x + gam * qj);
+            R y;
+            y.x = rnj;
+            y.y = pk;
+            an_[j] = y;
+            dd[0].add(rnj * rnj);
+            dd[1].add((FT)mj * rnj);
+            dd[2].add(rnj * pk);
+        }
     }
     // shift items i = q * nch + c (shift slot q, 16-byte chunk c), thread stride
     // nthr; (q, c) advance by (nthr / nch, nthr % nch) without a division per item
@@ -726,9 +991,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
             *reinterpret_cast<V *>(W + off[u]) = wv[u];
         }
     }
-    double mine[3];
-    block_dots<3>(dd, mine, sm.red);
-    if (!arrive_last<3>(mine, partials, counter)) return;
+    using Part = typename CompSum<FT>::Part;
+    Part mine[3];
+    Part *red = reinterpret_cast<Part *>(sm.red);
+    Part *parts = reinterpret_cast<Part *>(partials);
+    block_parts<3, FT>(dd, mine, red);
+    if (!arrive_last_parts<3>(mine, parts, counter)) return;
     // the shift state is read before the grid sum so that its loads overlap it
     const int ns = st->n_shifts, sh_q = threadIdx.x;
     ShiftState *h = st->sh + sh_q;
@@ -743,7 +1011,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw, c
     const double tolb = st->tol * st->bnorm, inv_b = st->inv_bnorm;
     const int fixed = st->fixed;
     double tot[3];
-    grid_dots<3>(partials, gridDim.x, tot, sm.red);
+    grid_parts<3, FT>(parts, gridDim.x, tot, red);
     if (threadIdx.x == 0) {
         const double rr_new = tot[0];
         const double anw = rr_new / st->rr;

@@ -37,6 +37,7 @@ struct SolveState {
     int32_t pad0;
     const int8_t *labels;   // labels of the target being solved
     const double *mu;       // its mu_l (permuted feature order)
+    const float *mu32;      // mu_l rounded to FP32
     // iteration
     int32_t k;              // iterations completed
     int32_t done;
@@ -53,13 +54,38 @@ struct SolveState {
     ShiftState sh[kMaxShifts];
 };
 
+// A sparse matrix in column segments split into ranges of its row index, so
+// that a block can keep one range's slice of the gathered vector in shared
+// memory: range r holds rows [r * rb, (r + 1) * rb) with 16-bit indices local
+// to it; every (range, segment) is padded with zero entries (index 0) to whole
+// quads.  Warp tiles of all ranges, range after range: those of range r are
+// [tile_off[r], tile_off[r + 1]).
+struct RangeBlocks {
+    int nranges = 0;
+    int64_t rb = 0;
+    int64_t nseg = 0;                 // segments (columns) per range
+    int per_range = 1;                // blocks per range
+    DevBuf<int64_t> cp;               // [R][nseg + 1] absolute offsets into idx / val (multiples of 4)
+    DevBuf<uint16_t> idx;
+    DevBuf<char> val;                 // value type of the pass; FP8 E4M3 ones for a pattern
+    ColSchedule sched;
+    DevBuf<int32_t> tile_off;         // [R + 1]
+    int32_t slot0 = 0, lseg0 = 0;     // split chunks' slots / counters in the operator's arrays
+    size_t bytes() const { return cp.bytes() + idx.bytes() + val.bytes() + sched.tiles.bytes() +
+                                  sched.splits.bytes() + tile_off.bytes(); }
+};
+
 struct Workspace {
     int fp64 = -1;
     int64_t d = 0, n = 0, ldw = 0;   // ldw: D rounded up to 8 (leading dimension of D-vectors)
     int n_shifts = 0;
     int vt = -1;                     // compute dtype the grids below were sized for
     int grid1 = 0, grid2 = 0, grid3a = 0, grid3b = 0;
-    DevBuf<char> vec;        // RP[2][ldw] ({r, p} pairs), s[ldw], ut[N], v[N] in the vector type
+    int nparts = 0;                  // row ranges of the column pass (partial sums of X^T v)
+    size_t colblk_smem = 0;          // its dynamic shared memory
+    size_t rowhead_smem = 0;         // dynamic shared memory of the row pass (head of p_k)
+    DevBuf<char> vec;        // RP[2][ldw] ({r, p} pairs), s[nparts][ldw] (pairs), ut[N8], v[N8] in the
+                             // vector type (N8: N rounded up to 8)
     DevBuf<char> shift;      // W[S][ldw], P[S][ldw] in the vector type
     DevBuf<SolveState> st;
     DevBuf<double> part;     // [3][grid][4] block partials of init / phase 2 / phase 3
@@ -92,6 +118,18 @@ struct sda_operator {
     sda::DevBuf<int64_t> x_rp, x_cp;
     sda::DevBuf<int32_t> x_col, x_row;
     sda::DevBuf<char> x_val_r, x_val_c;   // compute dtype (empty for PATTERN)
+    // X in column-major order split into ranges of rows, for the column pass of the
+    // iteration (a block keeps its range's slice of v in shared memory)
+    sda::RangeBlocks xb;
+    // X in row-major order with rows padded by zero entries (column 0) to whole
+    // quads, for the row pass of the iteration; features [0, xr_head) (the most
+    // frequent) are gathered from shared memory there
+    sda::DevBuf<int64_t> xr_rp;          // [N + 1], multiples of 4
+    sda::DevBuf<int32_t> xr_col;
+    sda::DevBuf<char> xr_val;            // compute dtype; FP8 E4M3 ones for PATTERN
+    int xr_head = 0;
+    int xr_lanes = 8;                    // lanes per row of that pass
+
     // graph S (CSR) and degrees D_ii; FP32 copies for the mixed path
     sda::DevBuf<int64_t> s_rp;
     sda::DevBuf<int32_t> s_col;
@@ -100,6 +138,7 @@ struct sda_operator {
     // targets
     sda::DevBuf<int8_t> labels;          // [T][N]
     sda::DevBuf<double> mu;              // [T][D] mu_l, permuted order
+    sda::DevBuf<float> mu32;             // [T][D] mu_l rounded to FP32 (mixed-path stream kernel)
     sda::DevBuf<double> dvec;            // [T][D] mu_+ - mu_-, permuted order
     std::vector<double> counts;          // [T][3]: l, N+, N-
     // tile schedules of the sparse passes: columns of X, rows of X, rows of S;

@@ -229,28 +229,35 @@ static int lanes_for(int64_t maxlen) {
     return g;
 }
 
-int build_seg_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
-    const int64_t d = (int64_t)colptr.size() - 1;
-    std::vector<Tile> tiles;
-    std::vector<SplitSeg> splits;
-    int64_t slots = 0;
+// Appends the tiles of the segments [0, d) of `colptr` (absolute nonzero
+// offsets); split chunks take slots from `*slots` and split entries after the
+// ones already in `splits`.
+// Segments longer than big_seg become tiles of their own (split into chunks of
+// at most tile_nnz); the others are grouped into multi-segment tiles of at most
+// tile_nnz nonzeros and tile_segs segments.
+// Chunk boundaries are multiples of `align` nonzeros from the segment start.
+static void append_seg_tiles(const int64_t *colptr, int64_t d, int64_t tile_nnz, int64_t tile_segs,
+                             int64_t big_seg, int64_t align, std::vector<Tile> &tiles,
+                             std::vector<SplitSeg> &splits, int64_t *slots) {
     int64_t j = 0;
     while (j < d) {
         const int64_t len = colptr[j + 1] - colptr[j];
-        if (len > kBigSeg) {
-            const int64_t nch = (len + kTileNnz - 1) / kTileNnz;
+        if (len > big_seg) {
+            const int64_t nch0 = (len + tile_nnz - 1) / tile_nnz;
+            const int64_t chunk0 = ((len + nch0 - 1) / nch0 + align - 1) / align * align;
+            const int64_t nch = (len + chunk0 - 1) / chunk0;
             if (nch == 1) {
                 tiles.push_back(Tile{colptr[j], colptr[j + 1], (int32_t)j, (int32_t)(j + 1), 0, -1, -1, 0});
             } else {
-                const int64_t chunk = (len + nch - 1) / nch;
+                const int64_t chunk = chunk0;
                 const int32_t lseg = (int32_t)splits.size();
-                splits.push_back(SplitSeg{(int32_t)slots, (int32_t)nch});
+                splits.push_back(SplitSeg{(int32_t)*slots, (int32_t)nch});
                 for (int64_t c = 0; c < nch; ++c) {
                     const int64_t a = colptr[j] + c * chunk;
                     const int64_t b = std::min(colptr[j + 1], a + chunk);
-                    tiles.push_back(Tile{a, b, (int32_t)j, (int32_t)(j + 1), 0, (int32_t)(slots + c), lseg, 0});
+                    tiles.push_back(Tile{a, b, (int32_t)j, (int32_t)(j + 1), 0, (int32_t)(*slots + c), lseg, 0});
                 }
-                slots += nch;
+                *slots += nch;
             }
             ++j;
             continue;
@@ -259,13 +266,17 @@ int build_seg_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
         int64_t nz = 0, maxlen = 0;
         while (j < d) {
             const int64_t l = colptr[j + 1] - colptr[j];
-            if (l > kBigSeg || (j > start && (nz + l > kTileNnz || j - start >= kTileSegs))) break;
+            if (l > big_seg || (j > start && (nz + l > tile_nnz || j - start >= tile_segs))) break;
             nz += l;
             maxlen = std::max(maxlen, l);
             ++j;
         }
         tiles.push_back(Tile{colptr[start], colptr[j], (int32_t)start, (int32_t)j, lanes_for(maxlen), -1, -1, 0});
     }
+}
+
+static int upload_schedule(const std::vector<Tile> &tiles, const std::vector<SplitSeg> &splits, int64_t slots,
+                           ColSchedule &out) {
     if (slots > INT32_MAX || (int64_t)tiles.size() > INT32_MAX)
         return fail(SDA_ERR_UNSUPPORTED, "column schedule too large");
     out.ntiles = (int32_t)tiles.size();
@@ -279,6 +290,30 @@ int build_seg_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
         SDA_CUDA(cudaMemcpy(out.splits.p, splits.data(), splits.size() * sizeof(SplitSeg),
                             cudaMemcpyHostToDevice));
     return SDA_OK;
+}
+
+int build_seg_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
+    std::vector<Tile> tiles;
+    std::vector<SplitSeg> splits;
+    int64_t slots = 0;
+    append_seg_tiles(colptr.data(), (int64_t)colptr.size() - 1, kTileNnz, kTileSegs, kBigSeg, 1, tiles, splits,
+                     &slots);
+    return upload_schedule(tiles, splits, slots, out);
+}
+
+int build_range_schedule(const std::vector<int64_t> &ptr, int nranges, int64_t d, ColSchedule &out,
+                         std::vector<int32_t> &tile_off) {
+    std::vector<Tile> tiles;
+    std::vector<SplitSeg> splits;
+    int64_t slots = 0;
+    tile_off.assign((size_t)nranges + 1, 0);
+    for (int r = 0; r < nranges; ++r) {
+        append_seg_tiles(ptr.data() + (size_t)r * (size_t)(d + 1), d, kWarpTileNnz, kWarpTileSegs, kWarpBigSeg, 4,
+                         tiles, splits, &slots);
+        if ((int64_t)tiles.size() > INT32_MAX) return fail(SDA_ERR_UNSUPPORTED, "column schedule too large");
+        tile_off[(size_t)r + 1] = (int32_t)tiles.size();
+    }
+    return upload_schedule(tiles, splits, slots, out);
 }
 
 }  // namespace sda

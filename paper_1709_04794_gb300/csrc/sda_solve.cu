@@ -149,6 +149,17 @@ static int with_row_lanes(int g, F &&f) {
     }
 }
 
+template <class F>
+static int with_quad_lanes(int g, F &&f) {
+    switch (g) {
+    case 2: return f(std::integral_constant<int, 2>());
+    case 4: return f(std::integral_constant<int, 4>());
+    case 8: return f(std::integral_constant<int, 8>());
+    case 16: return f(std::integral_constant<int, 16>());
+    default: return f(std::integral_constant<int, 32>());
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 operator pieces (permuted feature order)
 // ---------------------------------------------------------------------------
@@ -281,12 +292,15 @@ static int ensure_workspace(sda_operator *op, int ns) {
     const int fp64 = op->compute == SDA_F64;
     const size_t fsz = fp64 ? sizeof(double) : sizeof(float);
     const int64_t ldw = (op->d + 7) / 8 * 8;
-    const bool realloc = w.fp64 != fp64 || w.d != op->d || w.n != op->n || w.n_shifts < ns;
+    const int64_t n8 = (op->n + 7) / 8 * 8;
+    const bool realloc = w.fp64 != fp64 || w.d != op->d || w.n != op->n || w.n_shifts < ns ||
+                         w.nparts != op->xb.nranges;
     if (!realloc) return SDA_OK;
     if (w.graph) cudaGraphExecDestroy(w.graph);
     w.graph = nullptr;
     w.graph_iters = 0;
-    SDA_TRY(w.vec.alloc((size_t)(5 * ldw + 2 * op->n) * fsz));
+    // range partials are CompSum parts: two vector-type words each
+    SDA_TRY(w.vec.alloc((size_t)((4 + 2 * op->xb.nranges) * ldw + 2 * n8) * fsz));
     SDA_TRY(w.shift.alloc((size_t)(2 * (int64_t)ns * ldw) * fsz));
     SDA_TRY(w.st.alloc(1));
     SDA_TRY(w.part.alloc((size_t)3 * kMaxBlocksPerSm * op->sm_count * 4));
@@ -299,6 +313,7 @@ static int ensure_workspace(sda_operator *op, int ns) {
     w.n = op->n;
     w.ldw = ldw;
     w.n_shifts = ns;
+    w.nparts = op->xb.nranges;
     w.vt = -1;
     return SDA_OK;
 }
@@ -306,7 +321,8 @@ static int ensure_workspace(sda_operator *op, int ns) {
 template <class FT>
 struct WsView {
     typename RPair<FT>::T *rp;
-    FT *s, *ut, *v, *W, *P;
+    typename CompSum<FT>::Part *s;     // [nparts][ldw] range partials of X^T v
+    FT *ut, *v, *W, *P;
 };
 
 template <class FT>
@@ -314,8 +330,10 @@ static WsView<FT> view(const sda_operator *op) {
     const Workspace &w = op->ws;
     FT *base = (FT *)w.vec.p;
     FT *sb = (FT *)w.shift.p;
-    const int64_t l = w.ldw;
-    return WsView<FT>{(typename RPair<FT>::T *)base, base + 4 * l, base + 5 * l, base + 5 * l + op->n, sb,
+    const int64_t l = w.ldw, n8 = (op->n + 7) / 8 * 8;
+    using Part = typename CompSum<FT>::Part;
+    FT *ut = base + (4 + 2 * w.nparts) * l;
+    return WsView<FT>{(typename RPair<FT>::T *)base, (Part *)(base + 4 * l), ut, ut + n8, sb,
                       sb + (int64_t)w.n_shifts * l};
 }
 
@@ -328,15 +346,39 @@ static int grid_of(const void *kernel, int sms) {
     return std::min(nb, kMaxBlocksPerSm) * sms;
 }
 
+// out[r * ldo + j] = sum over the entries of segment j in range r of value * v[row]
+template <class VT, class FT>
+static int range_pass(const sda_operator *op, const RangeBlocks &rb, int64_t n, int64_t nseg, int64_t ldo,
+                      const FT *v, typename CompSum<FT>::Part *out, int grid, size_t smem, cudaStream_t s) {
+    using Part = typename CompSum<FT>::Part;   // one slot (8 bytes) per part in either type
+    k_colblk<VT, FT><<<grid, kColBlk, smem, s>>>(rb.sched.tiles.p, rb.per_range, n, rb.rb, nseg, ldo, rb.cp.p,
+                                                 rb.idx.p, (const VT *)rb.val.p, v, out,
+                                                 reinterpret_cast<Part *>(op->slots.p) + rb.slot0,
+                                                 op->lcount.p + rb.lseg0, rb.sched.splits.p, rb.tile_off.p,
+                                                 op->ws.st.p);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
+// value type of the blocked column layout (a pattern X stores FP8 ones there)
+template <class VT>
+using BlkVT = std::conditional_t<std::is_same<VT, Pattern>::value, __nv_fp8_e4m3, VT>;
+
 // sizes the grids of the iteration kernels for this operator's dtypes
 template <class VT, class FT>
 static int size_grids(sda_operator *op) {
     Workspace &w = op->ws;
     if (w.vt == (int)op->compute) return SDA_OK;
     const int sms = op->sm_count;
-    SDA_TRY(with_row_lanes(op->x_lanes, [&](auto G, auto U) -> int {
-        w.grid1 = grid_of((const void *)k_rowpass<VT, FT, decltype(G)::value, decltype(U)::value, GatherP<FT>,
-                                                  EpiP1<FT>>, sms);
+    SDA_TRY(with_quad_lanes(op->xr_lanes, [&](auto G) -> int {
+        const void *k = (const void *)k_rowhead<BlkVT<VT>, FT, decltype(G)::value>;
+        const size_t smem = (size_t)op->xr_head * sizeof(FT);
+        SDA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int nb = 0;
+        SDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kColBlk, smem));
+        if (nb <= 0) return fail(SDA_ERR_UNSUPPORTED, "the row pass does not fit on an SM");
+        w.grid1 = nb * sms;
+        w.rowhead_smem = smem;
         return SDA_OK;
     }));
     SDA_TRY(with_row_lanes(op->s_lanes, [&](auto G, auto U) -> int {
@@ -344,7 +386,16 @@ static int size_grids(sda_operator *op) {
                                                   EpiP2<FT>>, sms);
         return SDA_OK;
     }));
-    w.grid3a = grid_of((const void *)k_colpass<VT, FT, 8, EpiStore<FT>>, sms);
+    {
+        const void *k = (const void *)k_colblk<BlkVT<VT>, FT>;
+        const size_t smem = (size_t)op->xb.rb * sizeof(FT);
+        SDA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int nb = 0;
+        SDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kColBlk, smem));
+        if (nb <= 0) return fail(SDA_ERR_UNSUPPORTED, "the column pass does not fit on an SM");
+        w.colblk_smem = smem;
+        w.grid3a = op->xb.per_range * op->xb.nranges;
+    }
     w.grid3b = grid_of((const void *)k_cg_phase3b<FT>, sms);
     w.vt = (int)op->compute;
     return SDA_OK;
@@ -356,25 +407,29 @@ template <class VT, class FT>
 static int launch_iteration(const sda_operator *op, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     const Workspace &w = op->ws;
     WsView<FT> b = view<FT>(op);
-    const FT *sv = std::is_same<FT, double>::value ? (const FT *)op->s_val64.p : (const FT *)op->s_val32.p;
     const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
     const size_t P = (size_t)kMaxBlocksPerSm * op->sm_count;
     if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
-    SDA_TRY((rowpass<VT, FT>(op->x_lanes, op->n, op->x_rp.p, op->x_col.p, op->x_val_r.p,
-                             GatherP<FT>{b.rp, w.ldw, w.st.p, nullptr, (FT)0}, EpiP1<FT>{b.ut, w.st.p, 0.0}, w.grid1,
-                             s)));
+    SDA_TRY(with_quad_lanes(op->xr_lanes, [&](auto G) -> int {
+        k_rowhead<BlkVT<VT>, FT, decltype(G)::value><<<w.grid1, kColBlk, w.rowhead_smem, s>>>(
+            op->n, op->xr_head, w.ldw, op->xr_rp.p, op->xr_col.p, (const BlkVT<VT> *)op->xr_val.p, b.rp, b.ut,
+            w.st.p);
+        SDA_LAUNCHED();
+        return SDA_OK;
+    }));
     if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[2], s));
+    const FT *sv = std::is_same<FT, double>::value ? (const FT *)op->s_val64.p : (const FT *)op->s_val32.p;
     SDA_TRY((rowpass<FT, FT>(op->s_lanes, op->n, op->s_rp.p, op->s_col.p, sv, GatherVec<FT, FT>{b.ut},
-                             EpiP2<FT>{b.v, b.ut, dg, w.st.p, w.part.p + P * 4, w.cnt.p + 1, nullptr, 0, 0, 0, 0},
+                             EpiP2<FT>{b.v, b.ut, dg, w.st.p, w.part.p + P * 4, w.cnt.p + 1, nullptr, 0, 0},
                              w.grid2, s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[3], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[4], s));
-    SDA_TRY((colpass<VT, FT>(op, b.v, EpiStore<FT>{b.s, nullptr, w.st.p, 0.0}, w.grid3a, s)));
+    SDA_TRY((range_pass<BlkVT<VT>, FT>(op, op->xb, op->n, op->d, w.ldw, b.v, b.s, w.grid3a, w.colblk_smem, s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
-    k_cg_phase3b<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b.s, b.rp, b.W, b.P, w.st.p, w.part.p + P * 8,
-                                                 w.cnt.p + 2);
+    k_cg_phase3b<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b.s, w.nparts, b.rp, b.W, b.P, w.st.p,
+                                                 w.part.p + P * 8, w.cnt.p + 2);
     SDA_LAUNCHED();
     if (ev) SDA_CUDA(cudaEventRecord(ev[7], s));
     return SDA_OK;
@@ -461,6 +516,7 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
     h.limit = o.fixed_iters > 0 ? o.fixed_iters : o.max_iter;
     h.labels = op->labels.p + (int64_t)t * op->n;
     h.mu = op->mu.p + (int64_t)t * op->d;
+    h.mu32 = op->mu32.p + (int64_t)t * op->d;
     for (int i = 0; i < ns; ++i) h.sh[i].delta = shifts[i] - sigma0;
     SDA_CUDA(cudaMemcpyAsync(w.st.p, &h, sizeof(SolveState), cudaMemcpyHostToDevice, s));
     k_cg_init<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b_perm, bv.rp, bv.W, bv.P, w.st.p, w.part.p,
@@ -806,6 +862,10 @@ extern "C" SDA_API int sda_get_operator_info(const sda_operator *op, sda_operato
     info->alpha = op->alpha;
     info->omega = op->omega;
     info->device_bytes = op->bytes;
+    info->col_ranges = op->xb.nranges;
+    info->row_head = op->xr_head;
+    info->col_entries = (int64_t)op->xb.idx.n;
+    info->row_entries = (int64_t)op->xr_col.n;
     return SDA_OK;
 }
 

@@ -69,7 +69,9 @@ class sda_solve_stats(ctypes.Structure):
 class sda_operator_info(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("graph_nnz", ctypes.c_int64), ("n_targets", ctypes.c_int32), ("compute", ctypes.c_int),
-                ("alpha", ctypes.c_double), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("alpha", ctypes.c_double), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("col_ranges", ctypes.c_int32), ("row_head", ctypes.c_int32), ("col_entries", ctypes.c_int64),
+                ("row_entries", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p

@@ -44,3 +44,4 @@ def test_struct_layouts_match_header():
     assert sda.sda_solve_opts.rhs.offset == 24
     assert ctypes.sizeof(sda.sda_solve_opts) == 80
     assert ctypes.sizeof(sda.sda_solve_stats) == 104
+    assert ctypes.sizeof(sda.sda_operator_info) == 88
