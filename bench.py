@@ -109,13 +109,16 @@ class ClockSampler:
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
 
+KERNEL_SOURCES = ("sda_common.cuh", "sda_operator.cuh", "sda_kernels.cuh")
+
+
 def sources_hash() -> str:
+    """Hash of the files that define the iteration kernels (their traffic
+    changes only when these do)."""
     csrc = os.path.join(ROOT, "paper_1709_04794_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "sda.h"), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -154,11 +154,17 @@ typedef struct {
     double alpha;           /* NaN: the operator's alpha; else this call's alpha in [0, 1] (eq. 7)  */
     double scatter_weight;  /* NaN: 1 - alpha if the operator was built with a NaN scatter weight,
                                else the operator's omega; else this call's omega >= 0              */
+    int32_t refine_rounds;  /* > 0: per-shift refinement (no paper counterpart): while a shift's FP64
+                               true residual exceeds refine_tol, solve (B + beta I) c = b - (B + beta I) w
+                               in the iteration's precision and add c in FP64, at most this many times;
+                               a shift still above refine_tol reports SDA_NOT_CONVERGED             */
+    int32_t reserved;
+    double refine_tol;      /* target FP64 true relative residual (NaN or <= 0: tol)                */
 } sda_solve_opts;
 
 /* Fills *opt with: tol 1e-6, max_iter 10000, fixed_iters 0, canonical RHS,
  * all targets, FP64 residual check on, device output, graphs on, auto batch,
- * the operator's alpha and omega. */
+ * the operator's alpha and omega, no refinement. */
 SDA_API void sda_default_opts(sda_solve_opts *opt);
 
 /* Per target and shift outcome of sda_solve_shifts. */

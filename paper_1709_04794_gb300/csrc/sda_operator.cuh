@@ -87,6 +87,7 @@ struct Workspace {
     DevBuf<char> vec;        // RP[2][ldw] ({r, p} pairs), s[nparts][ldw] (pairs), ut[N8], v[N8] in the
                              // vector type (N8: N rounded up to 8)
     DevBuf<char> shift;      // W[S][ldw], P[S][ldw] in the vector type
+    DevBuf<double> w64;      // the solutions in FP64 [S][D] and a residual vector [D] (permuted order)
     DevBuf<SolveState> st;
     DevBuf<double> part;     // [3][grid][4] block partials of init / phase 2 / phase 3
     DevBuf<unsigned> cnt;    // grid arrival counters of init / phase 2 / phase 3

@@ -72,19 +72,24 @@ __global__ void k_to_old(int64_t d, int64_t count, const int32_t *new_of_old, co
 }
 
 // out[s][old] = W[s][new(old)] as FP64
-template <class FT>
-__global__ void k_w_out(int64_t d, int64_t ldw, int ns, const int32_t *new_of_old, const FT *W, double *out) {
-    const int64_t m = d * ns;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = i / d, o = i - s * d;
-        out[i] = (double)W[s * ldw + new_of_old[o]];
-    }
-}
 
 template <class FT>
 __global__ void k_w_f64(int64_t d, const FT *W, double *out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (double)W[i];
+}
+
+// out = a x + b y
+__global__ void k_axpby_f64(int64_t n, double a, const double *x, double b, const double *y, double *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + b * y[i];
+}
+
+// w += W (one shift's solution in the vector type)
+template <class FT>
+__global__ void k_add_w(int64_t d, const FT *W, double *w) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] += (double)W[i];
 }
 
 __global__ void k_scale(int64_t d, const double *x, const double *coef, double mult, double *out) {
@@ -284,6 +289,7 @@ void release_workspace(sda_operator *op) {
     w.part.release();
     w.cnt.release();
     w.f64.release();
+    w.w64.release();
     w.dev_b.release();
 }
 
@@ -496,10 +502,13 @@ static int read_header(sda_operator *op, cudaStream_t s) {
     return SDA_OK;
 }
 
+// One shifted-CG run (Algorithm 3) on (B + beta I) w = b for the given shifts;
+// the solutions stay in the workspace's W in the vector type, the final header
+// and shift states in w.h_st.
 template <class VT, class FT>
-static int solve_target(sda_operator *op, int t, const double *b_perm, const double *shifts, int ns,
-                        const sda_solve_opts &o, double alpha, double omega, double *w_out_t,
-                        sda_shift_report *rep_t, cudaStream_t s, int *worst) {
+static int run_shifted(sda_operator *op, int t, const double *b_perm, const double *shifts, int ns, double tol,
+                       int limit, bool fixed, const sda_solve_opts &o, double alpha, double omega, cudaStream_t s,
+                       int *worst) {
     Workspace &w = op->ws;
     SDA_TRY((size_grids<VT, FT>(op)));
     WsView<FT> bv = view<FT>(op);
@@ -510,10 +519,10 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
     h.sigma0 = sigma0;
     h.omega = omega;
     h.alpha_l = alpha;
-    h.tol = o.tol;
+    h.tol = tol;
     h.n_shifts = ns;
-    h.fixed = o.fixed_iters > 0 ? 1 : 0;
-    h.limit = o.fixed_iters > 0 ? o.fixed_iters : o.max_iter;
+    h.fixed = fixed ? 1 : 0;
+    h.limit = limit;
     h.labels = op->labels.p + (int64_t)t * op->n;
     h.mu = op->mu.p + (int64_t)t * op->d;
     h.mu32 = op->mu32.p + (int64_t)t * op->d;
@@ -539,52 +548,113 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
     }
     SDA_CUDA(cudaMemcpyAsync(w.h_st, w.st.p, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
-    // solution out, in the caller's feature order
-    if (w_out_t) {
-        double *dst = w_out_t;
-        double *tmp = nullptr;
-        DevBuf<double> hostbuf;
-        if (!o.out_on_device) {
-            SDA_TRY(hostbuf.alloc((size_t)ns * op->d));
-            tmp = hostbuf.p;
-            dst = tmp;
-        }
-        k_w_out<FT><<<grid_elems((int64_t)ns * op->d, op->sm_count), kBlock, 0, s>>>(op->d, w.ldw, ns,
-                                                                                      op->new_of_old.p, bv.W, dst);
-        SDA_LAUNCHED();
-        if (!o.out_on_device) {
-            SDA_CUDA(cudaMemcpyAsync(w_out_t, tmp, (size_t)ns * op->d * sizeof(double), cudaMemcpyDeviceToHost, s));
-            SDA_CUDA(cudaStreamSynchronize(s));
+    op->stats.iterations += h.k;
+    for (int i = 0; i < ns; ++i) op->stats.shift_iterations += h.sh[i].iters;
+    return SDA_OK;
+}
+
+// ||b - (B + beta I) w|| squared into *out (FP64, permuted order)
+static int resid2(sda_operator *op, int t, double beta, const double *b_perm, const double *w64, double *out,
+                  double alpha, double omega, cudaStream_t s) {
+    double *q = op->ws.f64.p + op->d;
+    SDA_TRY(op_apply_f64(op, t, beta, w64, q, s, alpha, omega));
+    k_resid_f64<<<op->grid, kBlock, 0, s>>>(op->d, b_perm, q, out, op->part.p, op->cnt.p);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
+template <class VT, class FT>
+static int solve_target(sda_operator *op, int t, const double *b_perm, const double *shifts, int ns,
+                        const sda_solve_opts &o, double alpha, double omega, double *w_out_t,
+                        sda_shift_report *rep_t, cudaStream_t s, int *worst) {
+    Workspace &w = op->ws;
+    const int64_t d = op->d;
+    const bool fixed = o.fixed_iters > 0;
+    SDA_TRY((run_shifted<VT, FT>(op, t, b_perm, shifts, ns, o.tol, fixed ? o.fixed_iters : o.max_iter, fixed, o,
+                                 alpha, omega, s, worst)));
+    const SolveState outer = *w.h_st;
+    const int rounds = fixed ? 0 : std::max(0, o.refine_rounds);
+    const double rtol = std::isnan(o.refine_tol) || o.refine_tol <= 0.0 ? o.tol : o.refine_tol;
+    const bool check = o.check_residual != 0 || rounds > 0;
+    // the solutions in FP64 (refinement adds its corrections there)
+    if (w.w64.n < (size_t)ns * (size_t)d + d) SDA_TRY(w.w64.alloc((size_t)ns * (size_t)d + d));
+    double *W64 = w.w64.p, *rvec = w.w64.p + (int64_t)ns * d;
+    {
+        WsView<FT> bv = view<FT>(op);
+        for (int i = 0; i < ns; ++i) {
+            k_w_f64<FT><<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, bv.W + (int64_t)i * w.ldw,
+                                                                       W64 + (int64_t)i * d);
+            SDA_LAUNCHED();
         }
     }
-    // FP64 true residual of every shift
+    // FP64 true residual of every shift, and per-shift refinement (mixed
+    // precision: r = b - (B + beta) w in FP64, a single-shift solve of the
+    // correction in the iteration's precision, w += correction in FP64)
     std::vector<double> tres((size_t)ns, -1.0);
-    if (o.check_residual) {
-        double *w64 = w.f64.p, *q = w.f64.p + op->d;
+    std::vector<int> rstatus((size_t)ns, SDA_OK);
+    if (check) {
         DevBuf<double> rs;
         SDA_TRY(rs.alloc((size_t)ns + 1));
-        SDA_TRY(dot_f64(op, op->d, b_perm, b_perm, rs.p + ns, s));
-        for (int i = 0; i < ns; ++i) {
-            k_w_f64<FT><<<grid_elems(op->d, op->sm_count), kBlock, 0, s>>>(op->d, bv.W + (int64_t)i * w.ldw, w64);
-            SDA_LAUNCHED();
-            SDA_TRY(op_apply_f64(op, t, shifts[i], w64, q, s, alpha, omega));
-            k_resid_f64<<<op->grid, kBlock, 0, s>>>(op->d, b_perm, q, rs.p + i, op->part.p, op->cnt.p);
-            SDA_LAUNCHED();
-        }
+        SDA_TRY(dot_f64(op, d, b_perm, b_perm, rs.p + ns, s));
+        for (int i = 0; i < ns; ++i)
+            SDA_TRY(resid2(op, t, shifts[i], b_perm, W64 + (int64_t)i * d, rs.p + i, alpha, omega, s));
         std::vector<double> hr((size_t)ns + 1);
         SDA_CUDA(cudaMemcpyAsync(hr.data(), rs.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
         const double bn = sqrt(hr[ns]);
         for (int i = 0; i < ns; ++i) tres[i] = bn > 0 ? sqrt(hr[i]) / bn : sqrt(hr[i]);
+        for (int i = 0; i < ns; ++i) {
+            for (int rd = 0; rd < rounds && tres[i] > rtol && bn > 0; ++rd) {
+                double *wi = W64 + (int64_t)i * d;
+                double *q = op->ws.f64.p + d;
+                SDA_TRY(op_apply_f64(op, t, shifts[i], wi, q, s, alpha, omega));
+                k_axpby_f64<<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, 1.0, b_perm, -1.0, q, rvec);
+                SDA_LAUNCHED();
+                // relative reduction asked of the correction solve: to the target,
+                // but not below what the iteration's precision can reach
+                const double inner = std::min(0.5, std::max(rtol / tres[i], 1e-4));
+                int iw = SDA_OK;
+                SDA_TRY((run_shifted<VT, FT>(op, t, rvec, &shifts[i], 1, inner, o.max_iter, false, o, alpha, omega,
+                                             s, &iw)));
+                if (iw != SDA_OK) {
+                    rstatus[i] = iw;
+                    break;
+                }
+                WsView<FT> bv = view<FT>(op);
+                k_add_w<FT><<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, bv.W, wi);
+                SDA_LAUNCHED();
+                SDA_TRY(resid2(op, t, shifts[i], b_perm, wi, rs.p + i, alpha, omega, s));
+                double r2 = 0.0;
+                SDA_CUDA(cudaMemcpyAsync(&r2, rs.p + i, sizeof(double), cudaMemcpyDeviceToHost, s));
+                SDA_CUDA(cudaStreamSynchronize(s));
+                tres[i] = sqrt(r2) / bn;
+            }
+        }
+        if (!o.check_residual && rounds == 0) std::fill(tres.begin(), tres.end(), -1.0);
     }
-    op->stats.iterations += h.k;
-    for (int i = 0; i < ns; ++i) op->stats.shift_iterations += h.sh[i].iters;
+    // solution out, in the caller's feature order
+    if (w_out_t) {
+        double *dst = w_out_t;
+        DevBuf<double> hostbuf;
+        if (!o.out_on_device) {
+            SDA_TRY(hostbuf.alloc((size_t)ns * d));
+            dst = hostbuf.p;
+        }
+        SDA_TRY(permute_to_old(op, W64, dst, ns, s));
+        if (!o.out_on_device) {
+            SDA_CUDA(cudaMemcpyAsync(w_out_t, dst, (size_t)ns * d * sizeof(double), cudaMemcpyDeviceToHost, s));
+            SDA_CUDA(cudaStreamSynchronize(s));
+        }
+    }
     for (int i = 0; i < ns; ++i) {
-        const ShiftState &sh = h.sh[i];
+        const ShiftState &sh = outer.sh[i];
         int st = SDA_OK;
-        if (h.status != SDA_OK) st = h.status;
-        else if (!h.fixed && sh.active) st = SDA_NOT_CONVERGED;
+        if (outer.status != SDA_OK) st = outer.status;
+        else if (rstatus[i] != SDA_OK) st = rstatus[i];
+        else if (rounds > 0) st = tres[i] <= rtol ? SDA_OK : SDA_NOT_CONVERGED;
+        else if (!fixed && sh.active) st = SDA_NOT_CONVERGED;
         if (st == SDA_NOT_CONVERGED && *worst == SDA_OK) *worst = SDA_NOT_CONVERGED;
+        if (st < 0 && *worst >= 0) *worst = st;
         if (rep_t) {
             rep_t[i].iters = sh.iters;
             rep_t[i].status = st;
@@ -616,6 +686,8 @@ extern "C" SDA_API void sda_default_opts(sda_solve_opts *o) {
     o->profile = 0;
     o->alpha = NAN;
     o->scatter_weight = NAN;
+    o->refine_rounds = 0;
+    o->refine_tol = NAN;
 }
 
 // the (alpha, omega) of a call: overrides from the options, else the operator's
@@ -643,6 +715,7 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
     else sda_default_opts(&o);
     if (o.fixed_iters <= 0 && (!(o.tol >= 0.0) || o.max_iter < 0))
         return fail(SDA_ERR_INVALID_ARG, "tol must be >= 0 and max_iter >= 0");
+    if (o.refine_rounds < 0) return fail(SDA_ERR_INVALID_ARG, "refine_rounds must be >= 0");
     const int t0 = o.target_begin;
     const int tc = o.target_count < 0 ? op->n_targets - t0 : o.target_count;
     if (t0 < 0 || tc < 0 || t0 + tc > op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target range out of bounds");
@@ -776,20 +849,15 @@ extern "C" SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double
     int rc;
     if (op->compute == SDA_F64) {
         rc = solve_target<double, double>(op, target, c, &beta, 1, o, al, om, nullptr, &rep, s, &worst);
-        if (rc >= 0) {
-            k_w_f64<double><<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, (const double *)ws.shift.p, lam);
-            SDA_LAUNCHED();
-        }
     } else {
         rc = with_vt(op->compute, [&](auto tag) -> int {
             using VT = std::remove_pointer_t<decltype(tag)>;
-            SDA_TRY((solve_target<VT, float>(op, target, c, &beta, 1, o, al, om, nullptr, &rep, s, &worst)));
-            k_w_f64<float><<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, (const float *)ws.shift.p, lam);
-            SDA_LAUNCHED();
-            return SDA_OK;
+            return solve_target<VT, float>(op, target, c, &beta, 1, o, al, om, nullptr, &rep, s, &worst);
         });
     }
     if (rc < 0) return rc;
+    // lambda: the solve's FP64 solution (permuted order)
+    SDA_CUDA(cudaMemcpyAsync(lam, ws.w64.p, (size_t)d * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (worst < 0) return worst;
     // d/d beta = -lambda^T w;  d/d alpha = -[(X~ lambda)^T L (X~ w) - c (X~ lambda)^T P_l (X~ w)]
     SDA_TRY(dot_f64(op, d, lam, wp, sc.p + 1, s));
