@@ -158,7 +158,10 @@ typedef struct {
                                true residual exceeds refine_tol, solve (B + beta I) c = b - (B + beta I) w
                                in the iteration's precision and add c in FP64, at most this many times;
                                a shift still above refine_tol reports SDA_NOT_CONVERGED             */
-    int32_t reserved;
+    int32_t batch_targets;  /* 1: solve the call's targets in batches of 16 that share every pass over
+                               X and S (vectors stored target-contiguous; no paper counterpart);
+                               0: one target after another.  Not combined with refine_rounds > 0
+                               or profile (SDA_ERR_UNSUPPORTED)                                    */
     double refine_tol;      /* target FP64 true relative residual (NaN or <= 0: tol)                */
 } sda_solve_opts;
 

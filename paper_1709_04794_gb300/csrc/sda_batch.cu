@@ -1,0 +1,909 @@
+// Batched targets: many binary targets that share X and S are solved together,
+// kTB targets per batch, one shifted-CG run (Algorithm 3) per target advanced
+// in lockstep.  The operator passes become sparse-matrix x dense-block products:
+// every vector is stored target-contiguous ([index][kTB]), a group of kTB lanes
+// (one lane per target) serves one row or column, the index and value of a
+// nonzero are loaded once for the group and the gather of the kTB targets'
+// values is one contiguous access.  Per target: its own labels, mu_l, right-hand
+// side, CG scalars and shift states (a SolveState each); the shift list is the
+// call's.  X and S are streamed once per batch iteration instead of once per
+// target.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sda_kernels.cuh"
+
+namespace sda {
+
+constexpr int kTB = 16;              // targets per batch
+constexpr int kTG = kBlock / kTB;    // lane groups per block
+
+// Bounds of every array the batched kernels index with computed offsets: the
+// kernels check each such index and skip an access that falls outside,
+// recording the first one in BatchCtl::err (reported to the caller).
+struct BatchBounds {
+    int64_t n, d, ldw, n8, nnz_x, nnz_s, ntiles, nslots, nsplits, npart;
+};
+
+struct BatchCtl {
+    int32_t k;        // iterations completed
+    int32_t done;     // every target of the batch has stopped
+    int32_t status;
+    int32_t pad;
+    unsigned long long err;   // first index check that failed: (site << 40) | index; 0 if none
+    BatchBounds bb;
+};
+
+__device__ __forceinline__ bool in_bounds(BatchCtl *ctl, long long idx, long long bound, int site) {
+    if (idx >= 0 && idx < bound) return true;
+    atomicCAS(&ctl->err, 0ull, ((unsigned long long)site << 40) | ((unsigned long long)idx & 0xffffffffffull));
+    return false;
+}
+#define BOK(idx, bound, site) in_bounds(const_cast<BatchCtl *>(ctl), (long long)(idx), (long long)(bound), (site))
+
+// per (shift, target) coefficients of the stream, written by phase 2
+template <class FT>
+struct BatchCoef {
+    FT z, a, g;       // zeta_k, alpha^s_k, gamma^s_k
+    int32_t active;
+};
+
+struct BatchWs {
+    int fp64 = -1;
+    int64_t d = 0, n = 0, ldw = 0, n8 = 0;
+    int ns = 0;
+    DevBuf<char> vec;      // pairs [2][ldw][kTB], s parts [ldw][kTB], ut [n8][kTB], v [n8][kTB]
+    DevBuf<char> shift;    // W [ns][ldw][kTB], P [ns][ldw][kTB]
+    DevBuf<double> b, mu64;
+    DevBuf<float> mu32;
+    DevBuf<int8_t> ylab;
+    DevBuf<SolveState> st;
+    DevBuf<BatchCtl> ctl;
+    DevBuf<char> coef;
+    DevBuf<double> part, slots, w64;
+    DevBuf<unsigned> cnt, lcount;
+    SolveState *h_st = nullptr;
+    BatchCtl *h_ctl = nullptr;
+    int grid = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    cudaStream_t cap_stream = nullptr;
+    ~BatchWs() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (h_st) cudaFreeHost(h_st);
+        if (h_ctl) cudaFreeHost(h_ctl);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// per-target reductions (thread x holds target x % kTB)
+// ---------------------------------------------------------------------------
+// Block sums per target of NDOT compensated sums; the parts of target t land in
+// thread t (t < kTB).  `red` holds (kBlock / 32) * kTB * NDOT parts.
+template <int NDOT, class AT>
+__device__ __forceinline__ void block_tparts(CompSum<AT> (&v)[NDOT], typename CompSum<AT>::Part (&out)[NDOT],
+                                             typename CompSum<AT>::Part *red) {
+    constexpr int NW = kBlock / 32;
+#pragma unroll
+    for (int o = 16; o >= kTB; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) v[k].xor_reduce(o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l < kTB) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) red[(w * kTB + l) * NDOT + k] = v[k].part();
+    }
+    __syncthreads();
+    if (threadIdx.x < kTB) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) {
+            CompSum<AT> s;
+            for (int q = 0; q < NW; ++q) CompSum<AT>::add_part(s, red[(q * kTB + threadIdx.x) * NDOT + k]);
+            out[k] = s.part();
+        }
+    }
+}
+
+// The block's per-target parts go to partials[block][t][k]; returns true in the
+// block that arrives last (for all its threads).
+template <int NDOT, class Part>
+__device__ __forceinline__ bool arrive_last_t(const Part (&mine)[NDOT], Part *partials, unsigned *counter,
+                                              const BatchCtl *ctl) {
+    __shared__ int last;
+    if (threadIdx.x < kTB) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k)
+            if (BOK(((int64_t)blockIdx.x * kTB + threadIdx.x) * NDOT + k, ctl->bb.npart, 51))
+                partials[((int64_t)blockIdx.x * kTB + threadIdx.x) * NDOT + k] = mine[k];
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = (arrive(counter) == gridDim.x - 1);
+    __syncthreads();
+    return last != 0;
+}
+
+// Per-target fixed-order sums of the grid's parts (last block); target t's
+// FP64 totals land in thread t.  `red` holds kBlock * NDOT parts.
+template <int NDOT, class AT>
+__device__ __forceinline__ void grid_tparts(const typename CompSum<AT>::Part *partials, int nblocks,
+                                            double (&out)[NDOT], typename CompSum<AT>::Part *red) {
+    const int t = threadIdx.x % kTB, g = threadIdx.x / kTB;
+    CompSum<AT> s[NDOT];
+    for (int b = g; b < nblocks; b += kTG) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k)
+            CompSum<AT>::add_part(s[k], __ldcg(partials + ((int64_t)b * kTB + t) * NDOT + k));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NDOT; ++k) red[threadIdx.x * NDOT + k] = s[k].part();
+    __syncthreads();
+    if (threadIdx.x < kTB) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) {
+            CompSum<AT> tot;
+            for (int q = 0; q < kTG; ++q) CompSum<AT>::add_part(tot, red[(q * kTB + threadIdx.x) * NDOT + k]);
+            out[k] = tot.to_double();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+// RP[0] = {b, 0}, RP[1] = 0, W = P = 0; per target <r,r>, <mu,r>; start values
+template <class FT>
+__global__ void __launch_bounds__(kBlock) kb_init(int64_t ldw, int ns, const double *__restrict__ b,
+                                                 const double *__restrict__ mu, typename RPair<FT>::T *rp, FT *W,
+                                                 FT *P, SolveState *st, BatchCtl *ctl, double *partials,
+                                                 unsigned *counter) {
+    using R = typename RPair<FT>::T;
+    using Part = CompSum<double>::Part;
+    __shared__ Part red[kBlock * 2];
+    const int64_t m = ldw * kTB;
+    CompSum<double> dd[2];
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m; e += (int64_t)gridDim.x * kBlock) {
+        const FT rj = (FT)b[e];
+        R x;
+        x.x = rj;
+        x.y = (FT)0;
+        rp[e] = x;
+        x.x = (FT)0;
+        rp[m + e] = x;
+        for (int s = 0; s < ns; ++s) {
+            W[(int64_t)s * m + e] = (FT)0;
+            P[(int64_t)s * m + e] = (FT)0;
+        }
+        dd[0].add((double)rj * (double)rj);
+        dd[1].add(mu[e] * (double)rj);
+    }
+    Part mine[2];
+    block_tparts<2, double>(dd, mine, red);
+    if (!arrive_last_t<2>(mine, reinterpret_cast<Part *>(partials), counter, ctl)) return;
+    double tot[2];
+    grid_tparts<2, double>(reinterpret_cast<const Part *>(partials), gridDim.x, tot, red);
+    if (threadIdx.x < kTB) {
+        SolveState &S = st[threadIdx.x];
+        S.rr = tot[0];
+        S.bnorm = sqrt(tot[0]);
+        S.inv_bnorm = S.bnorm > 0.0 ? 1.0 / S.bnorm : 0.0;
+        S.c = tot[1];
+        S.pp = tot[0];
+        S.alpha = 0.0;
+        S.gamma = 0.0;
+        S.gamma_prev = 1.0;
+        S.t = 0.0;
+        S.k = 0;
+        S.status = SDA_OK;
+        const bool zero_rhs = !(S.bnorm > 0.0);
+        for (int s = 0; s < ns; ++s) {
+            ShiftState &h = S.sh[s];
+            h.z_prev = 1.0;
+            h.z = 1.0;
+            h.ratio = 1.0;
+            h.g = 0.0;
+            h.a = 0.0;
+            h.res = zero_rhs ? 0.0 : 1.0;
+            h.active = zero_rhs ? 0 : 1;
+            h.iters = 0;
+        }
+        S.nactive = zero_rhs ? 0 : ns;
+        S.done = (zero_rhs || S.limit <= 0) ? 1 : 0;
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int all = 1;
+        for (int t = 0; t < kTB; ++t) all &= st[t].done;
+        ctl->k = 0;
+        ctl->done = all;
+        ctl->status = SDA_OK;
+    }
+}
+
+// phase 1: ut[i][t] = (X p_k,t)_i - <mu_t, p_k,t>, p_k,t formed at the gather
+template <class VT, class FT>
+__global__ void __launch_bounds__(kBlock) kb_phase1(int64_t n, int64_t ldw, const int64_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                                   const typename RPair<FT>::T *__restrict__ pairs,
+                                                   FT *__restrict__ ut, const SolveState *st, const BatchCtl *ctl) {
+    using R = typename RPair<FT>::T;
+    if (ctl->done) return;
+    const int t = threadIdx.x % kTB;
+    const FT al = (FT)st[t].alpha, c = (FT)st[t].c;
+    const R *__restrict__ a = pairs + (ctl->k & 1) * ldw * kTB;
+    const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kTB;
+    const int64_t ng = (int64_t)gridDim.x * kTG;
+    for (int64_t i = g; i < n; i += ng) {
+        const int64_t e0 = rp[i], e1 = rp[i + 1];
+        FT acc = 0;
+        for (int64_t e = e0; e < e1; e += 4) {
+            int32_t jj[4];
+            FT vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = e + u < e1 && BOK(e + u, ctl->bb.nnz_x, 11);
+                jj[u] = ok ? col[e + u] : 0;
+                vv[u] = ok ? (FT)Val<VT>::get(val, e + u) : (FT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!BOK((int64_t)jj[u] * kTB + t, ctl->bb.ldw * kTB, 12)) continue;
+                const R x = a[(int64_t)jj[u] * kTB + t];
+                acc += vv[u] * form_p<FT>(x.x, x.y, al);
+            }
+        }
+        if (BOK(i * kTB + t, ctl->bb.n8 * kTB, 13)) ut[i * kTB + t] = acc - c;
+    }
+}
+
+// phase 2: v = omega P_l ut + alpha (D ut - S ut) per target; <ut, v>, 1^T v;
+// the last block forms gamma_k per target and the (shift, target) coefficients
+template <class FT>
+__global__ void __launch_bounds__(kBlock) kb_phase2(int64_t n, const int64_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ col, const FT *__restrict__ sval,
+                                                   const FT *__restrict__ ut, const FT *__restrict__ deg,
+                                                   const int8_t *__restrict__ ylab, FT *__restrict__ v,
+                                                   SolveState *st, BatchCtl *ctl, BatchCoef<FT> *coef, int ns,
+                                                   double *partials, unsigned *counter) {
+    using Part = typename CompSum<FT>::Part;
+    __shared__ Part red[kBlock * 2];
+    if (ctl->done) return;
+    const int t = threadIdx.x % kTB;
+    const FT om = (FT)st[t].omega, al = (FT)st[t].alpha_l;
+    const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kTB;
+    const int64_t ng = (int64_t)gridDim.x * kTG;
+    CompSum<FT> dd[2];
+    for (int64_t i = g; i < n; i += ng) {
+        const int64_t e0 = rp[i], e1 = rp[i + 1];
+        FT acc = 0;
+        for (int64_t e = e0; e < e1; e += 4) {
+            int32_t jj[4];
+            FT vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = e + u < e1 && BOK(e + u, ctl->bb.nnz_s, 21);
+                jj[u] = ok ? col[e + u] : 0;
+                vv[u] = ok ? sval[e + u] : (FT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (BOK((int64_t)jj[u] * kTB + t, ctl->bb.n8 * kTB, 22)) acc += vv[u] * ut[(int64_t)jj[u] * kTB + t];
+        }
+        if (!BOK(i * kTB + t, ctl->bb.n8 * kTB, 23)) continue;
+        const FT u = ut[i * kTB + t];
+        const FT lap = fma(deg[i], u, -acc);
+        const FT vf = fma(al, lap, ylab[i * kTB + t] != 0 ? om * u : (FT)0);
+        v[i * kTB + t] = vf;
+        dd[0].add(u * vf);
+        dd[1].add(vf);
+    }
+    Part mine[2];
+    block_tparts<2, FT>(dd, mine, red);
+    if (!arrive_last_t<2>(mine, reinterpret_cast<Part *>(partials), counter, ctl)) return;
+    double tot[2];
+    grid_tparts<2, FT>(reinterpret_cast<const Part *>(partials), gridDim.x, tot, red);
+    if (threadIdx.x < kTB) {
+        SolveState &S = st[threadIdx.x];
+        if (!S.done) {
+            const double pq = tot[0] + S.sigma0 * S.pp;
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                S.status = SDA_ERR_BREAKDOWN;
+                S.done = 1;
+                S.gamma = 0.0;
+                S.alpha = 0.0;
+            } else {
+                S.gamma = -S.rr / pq;
+                S.t = tot[1];
+            }
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+    __syncthreads();
+    // zeta_{k+1} / zeta_k and gamma^s_k of every (target, shift) still active
+    for (int q = threadIdx.x; q < kTB * ns; q += kBlock) {
+        const int tt = q / ns, s = q - tt * ns;
+        SolveState &S = st[tt];
+        ShiftState &h = S.sh[s];
+        BatchCoef<FT> cf;
+        cf.z = cf.a = cf.g = (FT)0;
+        cf.active = (!S.done && h.active) ? 1 : 0;
+        if (cf.active) {
+            const double den = S.gamma * S.alpha * (h.z_prev - h.z) + h.z_prev * S.gamma_prev * (1.0 - h.delta * S.gamma);
+            const double ratio = h.z_prev * S.gamma_prev / den;
+            h.ratio = ratio;
+            h.g = S.gamma * ratio;
+            cf.z = (FT)h.z;
+            cf.a = (FT)h.a;
+            cf.g = (FT)h.g;
+        }
+        if (BOK(s * kTB + tt, kMaxShifts * kTB, 24)) coef[s * kTB + tt] = cf;
+    }
+}
+
+// phase 3a: s[j][t] = (X^T v_t)_j over the column tiles of the operator's CSC
+// (a lane group per column in multi-column tiles; the block's groups share a
+// long column's chunk); compensated sums, written as parts
+template <class VT, class FT>
+__global__ void __launch_bounds__(kBlock) kb_phase3a(const Tile *__restrict__ tiles, int ntiles,
+                                                    const int64_t *__restrict__ cp, const int32_t *__restrict__ row,
+                                                    const VT *__restrict__ val, const FT *__restrict__ v,
+                                                    typename CompSum<FT>::Part *__restrict__ out,
+                                                    typename CompSum<FT>::Part *slots, unsigned *lcount,
+                                                    const SplitSeg *__restrict__ splits, const BatchCtl *ctl) {
+    using CS = CompSum<FT>;
+    using Part = typename CS::Part;
+    __shared__ Part red[kBlock];
+    __shared__ int last;
+    if (ctl->done) return;
+    const int t = threadIdx.x % kTB, g = threadIdx.x / kTB;
+    auto dot = [&](int64_t e0, int64_t e1, int64_t step, CS &acc) {
+        for (int64_t e = e0; e < e1; e += 4 * step) {
+            int32_t ii[4];
+            FT vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = e + u * step < e1 && BOK(e + u * step, ctl->bb.nnz_x, 31);
+                ii[u] = ok ? row[e + u * step] : 0;
+                vv[u] = ok ? (FT)Val<VT>::get(val, e + u * step) : (FT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (BOK((int64_t)ii[u] * kTB + t, ctl->bb.n8 * kTB, 32)) acc.add(vv[u] * v[(int64_t)ii[u] * kTB + t]);
+        }
+    };
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const Tile tl = tiles[tile];
+        if (tl.lanes > 0) {
+            const int nseg = tl.seg1 - tl.seg0;
+            for (int sgi = g; sgi < nseg; sgi += kTG) {
+                const int64_t j = tl.seg0 + sgi;
+                if (!BOK(j, ctl->bb.d, 33)) continue;
+                CS acc;
+                dot(cp[j], cp[j + 1], 1, acc);
+                out[j * kTB + t] = acc.part();
+            }
+            continue;
+        }
+        CS acc;
+        dot(tl.nz0 + g, tl.nz1, kTG, acc);
+        __syncthreads();
+        red[threadIdx.x] = acc.part();
+        __syncthreads();
+        Part part{};
+        if (threadIdx.x < kTB) {
+            CS tot;
+            for (int q = 0; q < kTG; ++q) CS::add_part(tot, red[q * kTB + threadIdx.x]);
+            part = tot.part();
+        }
+        if (tl.slot < 0) {
+            if (threadIdx.x < kTB && BOK(tl.seg0, ctl->bb.d, 34)) out[(int64_t)tl.seg0 * kTB + threadIdx.x] = part;
+            continue;
+        }
+        if (!BOK(tl.slot, ctl->bb.nslots, 35) || !BOK(tl.lseg, ctl->bb.nsplits, 36)) { __syncthreads(); continue; }
+        if (threadIdx.x < kTB) {
+            slots[(int64_t)tl.slot * kTB + threadIdx.x] = part;
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) last = (arrive(&lcount[tl.lseg]) == (unsigned)splits[tl.lseg].nchunks - 1u);
+        __syncthreads();
+        if (last && threadIdx.x < kTB) {
+            const SplitSeg sp = splits[tl.lseg];
+            CS tot;
+            for (int q = 0; q < sp.nchunks; ++q) CS::add_part(tot, __ldcg(slots + (int64_t)(sp.slot0 + q) * kTB + threadIdx.x));
+            out[(int64_t)tl.seg0 * kTB + threadIdx.x] = tot.part();
+            if (threadIdx.x == 0) lcount[tl.lseg] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// phase 3b: base recurrence per (feature, target), shift-state stream over the
+// shifts some target still updates, per-target dots; the last block forms
+// alpha_{k+1}, the shift coefficients and the stop tests of every target
+template <class FT>
+__global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int ns,
+                                                    const typename CompSum<FT>::Part *__restrict__ s,
+                                                    typename RPair<FT>::T *__restrict__ pairs, FT *__restrict__ W,
+                                                    FT *__restrict__ P, SolveState *st, BatchCtl *ctl,
+                                                    const BatchCoef<FT> *__restrict__ coef,
+                                                    const float *__restrict__ mu32, const double *__restrict__ mu64,
+                                                    double *partials, unsigned *counter) {
+    using R = typename RPair<FT>::T;
+    using Part = typename CompSum<FT>::Part;
+    __shared__ Part red[kBlock * 3];
+    __shared__ BatchCoef<FT> cf[kMaxShifts * kTB];
+    __shared__ int any[kMaxShifts];
+    __shared__ FT s_al[kTB];
+    __shared__ double s_gam[kTB], s_t[kTB];
+    __shared__ float s_gh[kTB], s_gl[kTB], s_tf[kTB];
+    __shared__ float s_sh, s_sl;
+    __shared__ double s_sigma0;
+    __shared__ double s_anw[kTB], s_rn[kTB];
+    if (ctl->done) return;
+    if (threadIdx.x < kTB) {
+        const SolveState &S = st[threadIdx.x];
+        s_al[threadIdx.x] = (FT)S.alpha;
+        s_gam[threadIdx.x] = S.gamma;
+        s_t[threadIdx.x] = S.t;
+        split_f32(S.gamma, s_gh[threadIdx.x], s_gl[threadIdx.x]);
+        s_tf[threadIdx.x] = (float)S.t;
+        if (threadIdx.x == 0) {
+            s_sigma0 = S.sigma0;
+            split_f32(S.sigma0, s_sh, s_sl);
+        }
+    }
+    for (int q = threadIdx.x; q < ns * kTB; q += kBlock) cf[q] = coef[q];
+    if (threadIdx.x < ns) any[threadIdx.x] = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < ns * kTB; q += kBlock)
+        if (cf[q].active) any[q / kTB] = 1;
+    __syncthreads();
+    const int64_t m = ldw * kTB;
+    const int par = ctl->k & 1;
+    const R *__restrict__ a = pairs + par * m;
+    R *__restrict__ an_ = pairs + (par ^ 1) * m;
+    const int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x, nthr = (int64_t)gridDim.x * kBlock;
+    const int t = threadIdx.x % kTB;
+    CompSum<FT> dd[3];
+    const int64_t md = d * kTB;
+    for (int64_t e = tid; e < md; e += nthr) {
+        if (!BOK(e, ctl->bb.ldw * kTB, 41)) continue;
+        const R x = a[e];
+        const FT pk = form_p<FT>(x.x, x.y, s_al[t]);
+        CompSum<FT> sj;
+        CompSum<FT>::add_part(sj, s[e]);
+        FT rnj, mj;
+        if constexpr (std::is_same<FT, float>::value) {
+            mj = mu32[e];
+            rnj = base_step_f32v(x.x, pk, sj.h, sj.l, mj, s_sh, s_sl, s_tf[t], s_gh[t], s_gl[t]);
+        } else {
+            const double m64 = mu64[e];
+            mj = (FT)m64;
+            const double qj = (double)sj.value() - m64 * s_t[t] + s_sigma0 * (double)pk;
+            rnj = (FT)((double)x.x + s_gam[t] * qj);
+        }
+        R y;
+        y.x = rnj;
+        y.y = pk;
+        an_[e] = y;
+        dd[0].add(rnj * rnj);
+        dd[1].add(mj * rnj);
+        dd[2].add(rnj * pk);
+    }
+    // shift state: P^s_k = zeta r_k + alpha^s P^s_{k-1}; W^s_{k+1} = W^s_k - gamma^s P^s_k
+    // (targets whose shift stopped keep their values); four consecutive targets per thread
+    const int64_t m4 = m / 4;
+    for (int sh = 0; sh < ns; ++sh) {
+        if (!any[sh]) continue;
+        FT *__restrict__ Ps = P + (int64_t)sh * m;
+        FT *__restrict__ Ws = W + (int64_t)sh * m;
+        const BatchCoef<FT> *c = cf + sh * kTB;
+        for (int64_t e4 = tid; e4 < m4; e4 += nthr) {
+            const int64_t e = 4 * e4;
+            const int t0 = (int)(e % kTB);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!BOK(e + u, ctl->bb.ldw * kTB, 42) || !BOK(sh * kTB + t0 + u, kMaxShifts * kTB, 43)) continue;
+                const BatchCoef<FT> cu = c[t0 + u];
+                if (!cu.active) continue;
+                const FT r = a[e + u].x;
+                const FT pn = cu.z * r + cu.a * Ps[e + u];
+                Ps[e + u] = pn;
+                Ws[e + u] = Ws[e + u] - cu.g * pn;
+            }
+        }
+    }
+    Part mine[3];
+    block_tparts<3, FT>(dd, mine, red);
+    if (!arrive_last_t<3>(mine, reinterpret_cast<Part *>(partials), counter, ctl)) return;
+    double tot[3];
+    grid_tparts<3, FT>(reinterpret_cast<const Part *>(partials), gridDim.x, tot, red);
+    if (threadIdx.x < kTB) {
+        SolveState &S = st[threadIdx.x];
+        s_anw[threadIdx.x] = 0.0;
+        s_rn[threadIdx.x] = 0.0;
+        if (!S.done) {
+            const double rr_new = tot[0];
+            const double anw = rr_new / S.rr;
+            const double c_new = tot[1] + anw * S.c;
+            const double pp_new = rr_new + 2.0 * anw * tot[2] + anw * anw * S.pp;
+            if (!isfinite(rr_new) || !isfinite(anw)) S.status = SDA_ERR_BREAKDOWN;
+            S.gamma_prev = S.gamma;
+            S.alpha = anw;
+            S.c = c_new;
+            S.pp = pp_new;
+            S.rr = rr_new;
+            S.k = S.k + 1;
+            s_anw[threadIdx.x] = anw;
+            s_rn[threadIdx.x] = sqrt(rr_new);
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kTB * ns; q += kBlock) {
+        const int tt = q / ns, sh = q - tt * ns;
+        SolveState &S = st[tt];
+        ShiftState &h = S.sh[sh];
+        if (S.done || !h.active) continue;
+        const double ratio = h.ratio, zn = h.z * ratio;
+        h.a = s_anw[tt] * ratio * ratio;
+        h.z_prev = h.z;
+        h.z = zn;
+        h.iters = S.k;
+        const double rz = fabs(zn) * s_rn[tt];
+        h.res = rz * S.inv_bnorm;
+        if (!S.fixed && (rz < S.tol * S.bnorm || !(fabs(zn) > 0.0))) h.active = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < kTB) {
+        SolveState &S = st[threadIdx.x];
+        if (!S.done) {
+            int na = 0;
+            for (int sh = 0; sh < ns; ++sh) na += S.sh[sh].active;
+            S.nactive = na;
+            if (na == 0 || S.k >= S.limit || S.status != SDA_OK) {
+                S.done = 1;
+                S.alpha = 0.0;   // a stopped target's vectors stay put (gamma 0, p = r)
+                S.gamma = 0.0;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int all = 1;
+        for (int q = 0; q < kTB; ++q) all &= st[q].done;
+        ctl->k = ctl->k + 1;
+        ctl->done = all;
+    }
+}
+
+// column t of a [len][kTB] block from / to a plain vector
+template <class T>
+__global__ void kb_put(int64_t len, const T *__restrict__ src, T *__restrict__ dst, int t) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i * kTB + t] = src ? src[i] : (T)0;
+}
+__global__ void kb_put_mu32(int64_t len, const double *__restrict__ src, float *__restrict__ dst, int t) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i * kTB + t] = src ? (float)src[i] : 0.f;
+}
+// w[s][j] (FP64, permuted order) of target t from W[s][j][t]
+template <class FT>
+__global__ void kb_take_w(int64_t d, int64_t ldw, int ns, const FT *__restrict__ W, int t, double *__restrict__ out) {
+    const int64_t m = (int64_t)ns * d;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sh = i / d, j = i - sh * d;
+        out[i] = (double)W[(sh * ldw + j) * kTB + t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+static int grid_for(const void *kernel, int sms) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, 0) != cudaSuccess || nb <= 0) {
+        (void)cudaGetLastError();
+        nb = 1;
+    }
+    return std::min(nb, kMaxBlocksPerSm) * sms;
+}
+static int grid_elems_b(int64_t m, int sms) {
+    const int64_t g = (m + kBlock - 1) / kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
+}
+
+template <class FT>
+struct BView {
+    typename RPair<FT>::T *pairs;
+    typename CompSum<FT>::Part *s;
+    FT *ut, *v, *W, *P;
+    BatchCoef<FT> *coef;
+};
+
+template <class FT>
+static BView<FT> bview(BatchWs &b) {
+    using Part = typename CompSum<FT>::Part;
+    char *base = b.vec.p;
+    auto *pairs = (typename RPair<FT>::T *)base;
+    base += 2 * b.ldw * kTB * sizeof(typename RPair<FT>::T);
+    auto *s = (Part *)base;
+    base += b.ldw * kTB * sizeof(Part);
+    FT *ut = (FT *)base, *v = ut + b.n8 * kTB;
+    FT *W = (FT *)b.shift.p, *P = W + (int64_t)b.ns * b.ldw * kTB;
+    return BView<FT>{pairs, s, ut, v, W, P, (BatchCoef<FT> *)b.coef.p};
+}
+
+template <class FT>
+static int ensure_batch(sda_operator *op, int ns) {
+    if (!op->bws) op->bws = new BatchWs();
+    BatchWs &b = *op->bws;
+    using Part = typename CompSum<FT>::Part;
+    const int fp64 = std::is_same<FT, double>::value;
+    const int64_t ldw = (op->d + 7) / 8 * 8, n8 = (op->n + 7) / 8 * 8;
+    if (b.fp64 == fp64 && b.d == op->d && b.n == op->n && b.ns >= ns) return SDA_OK;
+    if (b.graph) cudaGraphExecDestroy(b.graph);
+    b.graph = nullptr;
+    b.graph_iters = 0;
+    SDA_TRY(b.vec.alloc((size_t)(2 * ldw * kTB * sizeof(typename RPair<FT>::T) + ldw * kTB * sizeof(Part) +
+                                 2 * n8 * kTB * sizeof(FT))));
+    SDA_TRY(b.shift.alloc((size_t)(2 * (int64_t)ns * ldw * kTB * sizeof(FT))));
+    SDA_TRY(b.b.alloc((size_t)(ldw * kTB)));
+    SDA_TRY(b.mu64.alloc((size_t)(ldw * kTB)));
+    SDA_TRY(b.mu32.alloc((size_t)(ldw * kTB)));
+    SDA_TRY(b.ylab.alloc((size_t)(n8 * kTB)));
+    SDA_TRY(b.st.alloc(kTB));
+    SDA_TRY(b.ctl.alloc(1));
+    SDA_TRY(b.coef.alloc((size_t)kMaxShifts * kTB * sizeof(BatchCoef<FT>)));
+    SDA_TRY(b.part.alloc((size_t)kMaxBlocksPerSm * op->sm_count * kTB * 5));   // phase 2: 2 per target, 3b: 3
+    SDA_TRY(b.cnt.alloc(4));
+    SDA_CUDA(cudaMemset(b.cnt.p, 0, b.cnt.bytes()));
+    SDA_TRY(b.slots.alloc((size_t)std::max(op->col.nslots, 1) * kTB * 2));
+    SDA_TRY(b.lcount.alloc((size_t)std::max(op->col.nsplits, 1)));
+    SDA_CUDA(cudaMemset(b.lcount.p, 0, b.lcount.bytes()));
+    SDA_TRY(b.w64.alloc((size_t)ns * op->d + op->d));
+    if (!b.h_st) SDA_CUDA(cudaMallocHost(&b.h_st, sizeof(SolveState) * kTB));
+    if (!b.h_ctl) SDA_CUDA(cudaMallocHost(&b.h_ctl, sizeof(BatchCtl)));
+    b.fp64 = fp64;
+    b.d = op->d;
+    b.n = op->n;
+    b.ldw = ldw;
+    b.n8 = n8;
+    b.ns = ns;
+    b.grid = 0;
+    return SDA_OK;
+}
+
+template <class VT, class FT>
+static int batch_iteration(sda_operator *op, int ns, cudaStream_t s) {
+    BatchWs &b = *op->bws;
+    BView<FT> bv = bview<FT>(b);
+    const FT *sv = std::is_same<FT, double>::value ? (const FT *)op->s_val64.p : (const FT *)op->s_val32.p;
+    const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
+    const int P = kMaxBlocksPerSm * op->sm_count;
+    kb_phase1<VT, FT><<<b.grid, kBlock, 0, s>>>(op->n, b.ldw, op->x_rp.p, op->x_col.p, (const VT *)op->x_val_r.p,
+                                               bv.pairs, bv.ut, b.st.p, b.ctl.p);
+    SDA_LAUNCHED();
+
+    kb_phase2<FT><<<b.grid, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, sv, bv.ut, dg, b.ylab.p, bv.v, b.st.p,
+                                           b.ctl.p, bv.coef, ns, b.part.p, b.cnt.p + 0);
+    SDA_LAUNCHED();
+
+    using Part = typename CompSum<FT>::Part;
+    kb_phase3a<VT, FT><<<b.grid, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
+                                                (const VT *)op->x_val_c.p, bv.v, bv.s, (Part *)b.slots.p,
+                                                b.lcount.p, op->col.splits.p, b.ctl.p);
+    SDA_LAUNCHED();
+
+    kb_phase3b<FT><<<b.grid, kBlock, 0, s>>>(op->d, b.ldw, ns, bv.s, bv.pairs, bv.W, bv.P, b.st.p, b.ctl.p, bv.coef,
+                                            b.mu32.p, b.mu64.p, b.part.p + (int64_t)P * kTB * 2, b.cnt.p + 1);
+    SDA_LAUNCHED();
+
+    return SDA_OK;
+}
+
+template <class VT, class FT>
+static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, cudaStream_t s) {
+    BatchWs &b = *op->bws;
+    if (!use_graph) {
+        for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, s)));
+        return SDA_OK;
+    }
+    if (!b.graph || b.graph_iters != nb_iters) {
+        if (b.graph) cudaGraphExecDestroy(b.graph);
+        b.graph = nullptr;
+        if (!b.cap_stream) SDA_CUDA(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
+        SDA_CUDA(cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal));
+        set_capturing(true);
+        int rc = SDA_OK;
+        for (int i = 0; i < nb_iters && rc == SDA_OK; ++i) rc = batch_iteration<VT, FT>(op, ns, b.cap_stream);
+        set_capturing(false);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b.cap_stream, &g);
+        if (rc != SDA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        e = cudaGraphInstantiate(&b.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+        b.graph_iters = nb_iters;
+    }
+    SDA_CUDA(cudaGraphLaunch(b.graph, s));
+    note_launch(4 * (int64_t)nb_iters);
+    return SDA_OK;
+}
+
+// One batch: targets t0 .. t0 + nt - 1 (nt <= kTB).
+template <class VT, class FT>
+static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_perm, const double *shifts, int ns,
+                       const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
+                       cudaStream_t s, int *worst) {
+    SDA_TRY(ensure_batch<FT>(op, ns));
+    BatchWs &b = *op->bws;
+    if (!b.grid) {
+        b.grid = std::min(std::min(grid_for((const void *)kb_phase1<VT, FT>, op->sm_count),
+                                   grid_for((const void *)kb_phase2<FT>, op->sm_count)),
+                          std::min(grid_for((const void *)kb_phase3a<VT, FT>, op->sm_count),
+                                   grid_for((const void *)kb_phase3b<FT>, op->sm_count)));
+    }
+    const int64_t d = op->d, n = op->n;
+    const int ge = grid_elems_b(std::max(b.ldw, b.n8), op->sm_count);
+    SDA_CUDA(cudaMemsetAsync(b.b.p, 0, b.b.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(b.mu64.p, 0, b.mu64.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(b.mu32.p, 0, b.mu32.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(b.ylab.p, 0, b.ylab.bytes(), s));
+    for (int i = 0; i < nt; ++i) {
+        const int t = t0 + i;
+        kb_put<double><<<ge, kBlock, 0, s>>>(d, b_perm[i], b.b.p, i);
+        kb_put<double><<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)t * d, b.mu64.p, i);
+        kb_put_mu32<<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)t * d, b.mu32.p, i);
+        kb_put<int8_t><<<ge, kBlock, 0, s>>>(n, op->labels.p + (int64_t)t * n, b.ylab.p, i);
+        SDA_LAUNCHED();
+    }
+    // per-target fixed scalars; targets past nt have a zero right-hand side and stop at once
+    SolveState *h = b.h_st;
+    memset(h, 0, sizeof(SolveState) * kTB);
+    double sigma0 = shifts[0];
+    for (int i = 1; i < ns; ++i) sigma0 = std::min(sigma0, shifts[i]);
+    const bool fixed = o.fixed_iters > 0;
+    for (int t = 0; t < kTB; ++t) {
+        h[t].sigma0 = sigma0;
+        h[t].omega = omega;
+        h[t].alpha_l = alpha;
+        h[t].tol = o.tol;
+        h[t].n_shifts = ns;
+        h[t].fixed = fixed ? 1 : 0;
+        h[t].limit = fixed ? o.fixed_iters : o.max_iter;
+        for (int i = 0; i < ns; ++i) h[t].sh[i].delta = shifts[i] - sigma0;
+    }
+    SDA_CUDA(cudaMemcpyAsync(b.st.p, h, sizeof(SolveState) * kTB, cudaMemcpyHostToDevice, s));
+    BView<FT> bv = bview<FT>(b);
+    {
+        BatchCtl hc{};
+        hc.bb = BatchBounds{op->n, op->d, b.ldw, b.n8, op->nnz, op->s_nnz, op->col.ntiles, op->col.nslots,
+                            op->col.nsplits, (int64_t)b.part.n};
+        *b.h_ctl = hc;
+        SDA_CUDA(cudaMemcpyAsync(b.ctl.p, b.h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
+    }
+    kb_init<FT><<<b.grid, kBlock, 0, s>>>(b.ldw, ns, b.b.p, b.mu64.p, bv.pairs, bv.W, bv.P, b.st.p, b.ctl.p, b.part.p,
+                                          b.cnt.p + 2);
+    SDA_LAUNCHED();
+    SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    const int limit = fixed ? o.fixed_iters : o.max_iter;
+    const int nbi = o.iter_batch > 0 ? o.iter_batch : 32;
+    int launched = 0;
+    while (!b.h_ctl->done && launched <= limit) {
+        SDA_TRY((batch_run<VT, FT>(op, ns, nbi, o.use_graph != 0, s)));
+        launched += nbi;
+        SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+        SDA_CUDA(cudaStreamSynchronize(s));
+        if (b.h_ctl->err)
+            return fail(SDA_ERR_INDEX, "batched solve: index check %llu failed at %llu",
+                        (unsigned long long)(b.h_ctl->err >> 40), (unsigned long long)(b.h_ctl->err & 0xffffffffffull));
+    }
+    SDA_CUDA(cudaMemcpyAsync(h, b.st.p, sizeof(SolveState) * kTB, cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    DevBuf<double> rs;
+    if (o.check_residual) SDA_TRY(rs.alloc((size_t)ns + 1));
+    for (int i = 0; i < nt; ++i) {
+        const int t = t0 + i;
+        const SolveState &S = h[i];
+        op->stats.iterations = std::max<int64_t>(op->stats.iterations, S.k);
+        for (int sh = 0; sh < ns; ++sh) op->stats.shift_iterations += S.sh[sh].iters;
+        kb_take_w<FT><<<grid_elems_b((int64_t)ns * d, op->sm_count), kBlock, 0, s>>>(d, b.ldw, ns, bv.W, i, b.w64.p);
+        SDA_LAUNCHED();
+        if (w_out) {
+            double *dst = w_out + (int64_t)i * ns * d;
+            DevBuf<double> hostbuf;
+            if (!o.out_on_device) {
+                SDA_TRY(hostbuf.alloc((size_t)ns * d));
+                SDA_TRY(permute_to_old(op, b.w64.p, hostbuf.p, ns, s));
+                SDA_CUDA(cudaMemcpyAsync(dst, hostbuf.p, (size_t)ns * d * sizeof(double), cudaMemcpyDeviceToHost, s));
+                SDA_CUDA(cudaStreamSynchronize(s));
+            } else {
+                SDA_TRY(permute_to_old(op, b.w64.p, dst, ns, s));
+            }
+        }
+        std::vector<double> tres((size_t)ns, -1.0);
+        if (o.check_residual) {
+            SDA_TRY(dot_f64(op, d, b_perm[i], b_perm[i], rs.p + ns, s));
+            for (int sh = 0; sh < ns; ++sh)
+                SDA_TRY(resid2(op, t, shifts[sh], b_perm[i], b.w64.p + (int64_t)sh * d, rs.p + sh, alpha, omega, s));
+            std::vector<double> hr((size_t)ns + 1);
+            SDA_CUDA(cudaMemcpyAsync(hr.data(), rs.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            SDA_CUDA(cudaStreamSynchronize(s));
+            const double bn = sqrt(hr[ns]);
+            for (int sh = 0; sh < ns; ++sh) tres[sh] = bn > 0 ? sqrt(hr[sh]) / bn : sqrt(hr[sh]);
+        }
+        if (S.status != SDA_OK) {
+            *worst = S.status;
+            fail(S.status, "breakdown in the batched shifted CG of target %d at iteration %d", t, S.k);
+        }
+        for (int sh = 0; sh < ns; ++sh) {
+            const ShiftState &hs = S.sh[sh];
+            int st = SDA_OK;
+            if (S.status != SDA_OK) st = S.status;
+            else if (!fixed && hs.active) st = SDA_NOT_CONVERGED;
+            if (st == SDA_NOT_CONVERGED && *worst == SDA_OK) *worst = SDA_NOT_CONVERGED;
+            if (rep) {
+                sda_shift_report &r = rep[(int64_t)i * ns + sh];
+                r.iters = hs.iters;
+                r.status = st;
+                r.est_residual = hs.res;
+                r.true_residual = tres[sh];
+            }
+        }
+    }
+    return SDA_OK;
+}
+
+template <class F>
+static int with_vt_b(int compute, F &&f) {
+    switch (compute) {
+    case SDA_F64: return f((double *)nullptr);
+    case SDA_F32: return f((float *)nullptr);
+    case SDA_F16: return f((__half *)nullptr);
+    case SDA_F8E4M3: return f((__nv_fp8_e4m3 *)nullptr);
+    default: return f((Pattern *)nullptr);
+    }
+}
+
+int solve_batched(sda_operator *op, int t0, int nt, const double *const *b_perm, const double *shifts, int ns,
+                  const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
+                  cudaStream_t s, int *worst) {
+    for (int i0 = 0; i0 < nt; i0 += kTB) {
+        const int nb = std::min(kTB, nt - i0);
+        double *wo = w_out ? w_out + (int64_t)i0 * ns * op->d : nullptr;
+        sda_shift_report *rp = rep ? rep + (int64_t)i0 * ns : nullptr;
+        int rc;
+        if (op->compute == SDA_F64) {
+            rc = solve_batch<double, double>(op, t0 + i0, nb, b_perm + i0, shifts, ns, o, alpha, omega, wo, rp, s,
+                                             worst);
+        } else {
+            rc = with_vt_b(op->compute, [&](auto tag) -> int {
+                using VT = std::remove_pointer_t<decltype(tag)>;
+                return solve_batch<VT, float>(op, t0 + i0, nb, b_perm + i0, shifts, ns, o, alpha, omega, wo, rp, s,
+                                              worst);
+            });
+        }
+        if (rc < 0) return rc;
+    }
+    return SDA_OK;
+}
+
+void release_batch(sda_operator *op) {
+    delete op->bws;
+    op->bws = nullptr;
+}
+
+}  // namespace sda

@@ -842,18 +842,22 @@ struct StreamSmem {
 // pair sjh + sjl), rounded once at the end (the same value as an FP64
 // evaluation rounded to FP32 up to ties); the mu t term is kept at FP32
 // precision since t = 1^T v vanishes in exact arithmetic.
-__device__ __forceinline__ float base_step_f32(float r, float pk, float sjh, float sjl, float mj,
-                                               const StreamSmem<float> &sm) {
+__device__ __forceinline__ float base_step_f32v(float r, float pk, float sjh, float sjl, float mj, float sh,
+                                                float sl, float tf, float gh, float gl) {
     float e0, e1, e2, e3;
-    const float bh = two_prod(sm.sh, pk, e0);
-    const float bl = fmaf(sm.sl, pk, e0);
+    const float bh = two_prod(sh, pk, e0);
+    const float bl = fmaf(sl, pk, e0);
     const float qh0 = two_sum(sjh, bh, e1);
-    const float ql0 = fmaf(-mj, sm.tf, (e1 + bl) + sjl);
+    const float ql0 = fmaf(-mj, tf, (e1 + bl) + sjl);
     const float qh = qh0 + ql0;
     const float ql = ql0 - (qh - qh0);
-    const float ph = two_prod(sm.gh, qh, e2);
-    const float sh = two_sum(r, ph, e3);
-    return sh + ((e3 + e2) + fmaf(sm.gh, ql, sm.gl * qh));
+    const float ph = two_prod(gh, qh, e2);
+    const float s = two_sum(r, ph, e3);
+    return s + ((e3 + e2) + fmaf(gh, ql, gl * qh));
+}
+__device__ __forceinline__ float base_step_f32(float r, float pk, float sjh, float sjl, float mj,
+                                               const StreamSmem<float> &sm) {
+    return base_step_f32v(r, pk, sjh, sjl, mj, sm.sh, sm.sl, sm.tf, sm.gh, sm.gl);
 }
 
 __device__ __forceinline__ void load_r(const float2 *a, int64_t j0, float (&r)[4]) {

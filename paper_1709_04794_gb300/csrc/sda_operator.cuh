@@ -102,6 +102,8 @@ struct Workspace {
     cudaStream_t cap_stream = nullptr;
 };
 
+struct BatchWs;   // workspace of the batched-target solve (sda_batch.cu)
+
 }  // namespace sda
 
 struct sda_operator {
@@ -157,6 +159,7 @@ struct sda_operator {
     sda::DevBuf<double> scal;             // device scalars of the FP64 operator apply
 
     sda::Workspace ws;
+    sda::BatchWs *bws = nullptr;
     sda_solve_stats stats{};
 };
 
@@ -171,5 +174,15 @@ int permute_to_new(const sda_operator *op, const double *old_order, double *new_
 int permute_to_old(const sda_operator *op, const double *new_order, double *old_order, int64_t count,
                    cudaStream_t s);
 void release_workspace(sda_operator *op);
+int dot_f64(const sda_operator *op, int64_t n, const double *a, const double *b, double *out, cudaStream_t s);
+// ||b - (B + beta I) w||^2 of target t into *out (device), FP64, permuted order
+int resid2(sda_operator *op, int t, double beta, const double *b_perm, const double *w64, double *out,
+           double alpha, double omega, cudaStream_t s);
+// batched targets (sda_batch.cu): targets [t0, t0 + nt) in batches sharing X and S;
+// b_perm[i]: target t0 + i's right-hand side (device, permuted order)
+int solve_batched(sda_operator *op, int t0, int nt, const double *const *b_perm, const double *shifts, int ns,
+                  const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
+                  cudaStream_t s, int *worst);
+void release_batch(sda_operator *op);
 int64_t launch_count();
 }  // namespace sda

@@ -219,7 +219,7 @@ int op_xmul_f64(const sda_operator *op, const double *w, double *u, const double
     });
 }
 
-static int dot_f64(const sda_operator *op, int64_t n, const double *a, const double *b, double *out, cudaStream_t s) {
+int dot_f64(const sda_operator *op, int64_t n, const double *a, const double *b, double *out, cudaStream_t s) {
     k_dot_f64<<<op->grid, kBlock, 0, s>>>(n, a, b, out, op->part.p, op->cnt.p);
     SDA_LAUNCHED();
     return SDA_OK;
@@ -554,8 +554,8 @@ static int run_shifted(sda_operator *op, int t, const double *b_perm, const doub
 }
 
 // ||b - (B + beta I) w|| squared into *out (FP64, permuted order)
-static int resid2(sda_operator *op, int t, double beta, const double *b_perm, const double *w64, double *out,
-                  double alpha, double omega, cudaStream_t s) {
+int resid2(sda_operator *op, int t, double beta, const double *b_perm, const double *w64, double *out,
+           double alpha, double omega, cudaStream_t s) {
     double *q = op->ws.f64.p + op->d;
     SDA_TRY(op_apply_f64(op, t, beta, w64, q, s, alpha, omega));
     k_resid_f64<<<op->grid, kBlock, 0, s>>>(op->d, b_perm, q, out, op->part.p, op->cnt.p);
@@ -687,6 +687,7 @@ extern "C" SDA_API void sda_default_opts(sda_solve_opts *o) {
     o->alpha = NAN;
     o->scatter_weight = NAN;
     o->refine_rounds = 0;
+    o->batch_targets = 0;
     o->refine_tol = NAN;
 }
 
@@ -749,8 +750,31 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
     }
     int worst = SDA_OK;
     DevBuf<double> bt;
-    if (o.rhs_mode == SDA_RHS_FROM_R) SDA_TRY(bt.alloc((size_t)d + 1));
-    for (int i = 0; i < tc; ++i) {
+    if (o.batch_targets) {
+        if (o.refine_rounds > 0 || o.profile)
+            return fail(SDA_ERR_UNSUPPORTED, "batched targets do not combine with refinement or profile mode");
+        // right-hand side of every target of the call, then the batches
+        std::vector<const double *> bl((size_t)tc);
+        if (o.rhs_mode == SDA_RHS_FROM_R) SDA_TRY(bt.alloc((size_t)tc * d + 1));
+        for (int i = 0; i < tc; ++i) {
+            const int t = t0 + i;
+            bl[(size_t)i] = op->dvec.p + (int64_t)t * d;
+            if (o.rhs_mode == SDA_RHS_GIVEN) {
+                bl[(size_t)i] = w.dev_b.p + (int64_t)i * d;
+            } else if (o.rhs_mode == SDA_RHS_FROM_R) {
+                const double *cnt = &op->counts[(size_t)t * 3];
+                SDA_TRY(dot_f64(op, d, op->dvec.p + (int64_t)t * d, w.dev_b.p, bt.p + (int64_t)tc * d, s));
+                k_scale<<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, op->dvec.p + (int64_t)t * d,
+                                                                      bt.p + (int64_t)tc * d, cnt[1] * cnt[2] / cnt[0],
+                                                                      bt.p + (int64_t)i * d);
+                SDA_LAUNCHED();
+                bl[(size_t)i] = bt.p + (int64_t)i * d;
+            }
+        }
+        SDA_TRY(solve_batched(op, t0, tc, bl.data(), shifts, n_shifts, o, alpha, omega, w_out, report, s, &worst));
+    }
+    if (o.rhs_mode == SDA_RHS_FROM_R && !o.batch_targets) SDA_TRY(bt.alloc((size_t)d + 1));
+    for (int i = 0; i < (o.batch_targets ? 0 : tc); ++i) {
         const int t = t0 + i;
         const double *b = op->dvec.p + (int64_t)t * d;
         if (o.rhs_mode == SDA_RHS_GIVEN) {
@@ -947,6 +971,7 @@ extern "C" SDA_API void sda_destroy_operator(sda_operator *op) {
     if (!op) return;
     cudaDeviceSynchronize();
     release_workspace(op);
+    release_batch(op);
     delete op;
 }
 

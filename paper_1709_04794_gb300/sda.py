@@ -54,7 +54,7 @@ class sda_solve_opts(ctypes.Structure):
                 ("check_residual", ctypes.c_int32), ("out_on_device", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("iter_batch", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("alpha", ctypes.c_double), ("scatter_weight", ctypes.c_double),
-                ("refine_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32), ("refine_tol", ctypes.c_double)]
+                ("refine_rounds", ctypes.c_int32), ("batch_targets", ctypes.c_int32), ("refine_tol", ctypes.c_double)]
 
 
 class sda_shift_report(ctypes.Structure):

@@ -1,0 +1,102 @@
+"""Batched targets (opts.batch_targets): many targets sharing X and S solved in
+batches of 16 with target-contiguous vectors, against the FP64 oracle per
+target and against the one-target-at-a-time path.
+
+19 targets (one full batch and a ragged one of 3) with uneven labelled subsets
+(each target keeps a different share of its labels).  Bars as for one target:
+FP64 after a fixed number of iterations 1e-9 relative per (target, shift);
+FP64 converged to tol 1e-10, batched and sequential solutions within 1e-6 of
+each other and FP64 true residuals below 1e-9; the mixed path's true residual
+within 20 x tol.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_04794_gb300 import sda, synth
+
+pytestmark = pytest.mark.gpu
+
+T = 19
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def multi():
+    p = synth.custom_problem(3000, 2048, 30, seed=21, values="counts", n_targets=T, n_labelled=300, k=5,
+                             shifts=(1e-3, 1e2, 6))
+    rng = np.random.default_rng(3)
+    for i in range(T):
+        lab = np.nonzero(p.labels[i])[0]
+        keep = max(40, int(len(lab) * (0.2 + 0.8 * i / (T - 1))))
+        p.labels[i][rng.permutation(lab)[keep:]] = 0
+        assert (p.labels[i] > 0).any() and (p.labels[i] < 0).any()
+    return p
+
+
+def _solve(prob, compute, batch, tol=1e-10, fixed=0, check=1, begin=0, count=-1):
+    op = sda.Operator(prob, compute=compute)
+    nt = op.info["n_targets"] - begin if count < 0 else count
+    ns, d = len(prob.shifts), prob.d
+    w = torch.empty((nt, ns, d), dtype=torch.float64, device="cuda")
+    o = sda.sda_default_opts()
+    o.tol, o.fixed_iters, o.max_iter = tol, fixed, 20000
+    o.batch_targets, o.check_residual = batch, check
+    o.target_begin, o.target_count = begin, count
+    code, rep = sda.sda_solve_shifts(op.handle, prob.shifts, o, w_out=w, n_report=nt)
+    return code, rep, w.cpu().numpy()
+
+
+def test_batched_fixed_iterations_match_oracle(multi):
+    k = 8
+    code, rep, w = _solve(multi, "f64", 1, fixed=k, check=0)
+    for t in range(T):
+        o = oracle.from_problem(multi, target=t)
+        ref = o.shifted_cg(o.rhs_canonical(), multi.shifts, fixed_iters=k)
+        for s in range(len(multi.shifts)):
+            assert _rel(w[t, s], ref.W[s]) < 1e-9, (t, s, _rel(w[t, s], ref.W[s]))
+
+
+def test_batched_equals_sequential_converged(multi):
+    code_b, rep_b, wb = _solve(multi, "f64", 1)
+    code_s, rep_s, ws = _solve(multi, "f64", 0)
+    assert code_b == sda.SDA_OK and code_s == sda.SDA_OK
+    for t in range(T):
+        for s in range(len(multi.shifts)):
+            assert _rel(wb[t, s], ws[t, s]) < 1e-6, (t, s)
+            assert rep_b[t][s]["true_residual"] < 1e-9, (t, s, rep_b[t][s])
+            ib, i_s = rep_b[t][s]["iters"], rep_s[t][s]["iters"]
+            assert abs(ib - i_s) <= max(2, 0.02 * i_s), (t, s, ib, i_s)
+
+
+def test_batched_mixed_true_residuals(multi):
+    tol = 1e-6
+    code, rep, w = _solve(multi, "f16", 1, tol=tol)
+    assert code == sda.SDA_OK
+    for t in range(T):
+        for r in rep[t]:
+            assert r["status"] == sda.SDA_OK and r["true_residual"] < 20 * tol, (t, r)
+
+
+def test_batched_target_range(multi):
+    """A sub-range of targets (one ragged batch) equals the same targets solved alone."""
+    k = 6
+    _, _, wb = _solve(multi, "f64", 1, fixed=k, check=0, begin=3, count=5)
+    _, _, ws = _solve(multi, "f64", 0, fixed=k, check=0, begin=3, count=5)
+    for t in range(5):
+        for s in range(len(multi.shifts)):
+            assert _rel(wb[t, s], ws[t, s]) < 1e-12
+
+
+def test_batched_rejects_refinement(multi):
+    op = sda.Operator(multi, compute="f16")
+    o = sda.sda_default_opts()
+    o.batch_targets, o.refine_rounds = 1, 2
+    w = torch.empty((T, len(multi.shifts), multi.d), dtype=torch.float64, device="cuda")
+    with pytest.raises(sda.SDAError) as e:
+        sda.sda_solve_shifts(op.handle, multi.shifts, o, w_out=w, n_report=T)
+    assert e.value.code == sda.SDA_ERR_UNSUPPORTED
