@@ -161,7 +161,7 @@ typedef struct {
     int32_t batch_targets;  /* 1: solve the call's targets in batches of 16 that share every pass over
                                X and S (vectors stored target-contiguous; no paper counterpart);
                                0: one target after another.  Not combined with refine_rounds > 0
-                               or profile (SDA_ERR_UNSUPPORTED)                                    */
+                               (SDA_ERR_UNSUPPORTED)                                                */
     double refine_tol;      /* target FP64 true relative residual (NaN or <= 0: tol)                */
 } sda_solve_opts;
 
@@ -277,7 +277,8 @@ SDA_API int sda_operator_apply_static(const sda_operator *op, int32_t target, do
 
 /* Counters of the last sda_solve_shifts call on an operator. */
 typedef struct {
-    int64_t iterations;        /* Krylov iterations summed over the call's targets                  */
+    int64_t iterations;        /* Krylov iterations summed over the call's targets (batched mode:
+                                  over its batches, each counting its slowest target)               */
     int64_t shift_iterations;  /* sum over targets and shifts of the iterations each shift ran      */
     int64_t launches[5];       /* kernel launches: [0] start, [1] X rows (X p), [2] S rows (L u),
                                   [3] X columns (X^T v), [4] vector and shift-state update          */

@@ -226,22 +226,81 @@ __global__ void __launch_bounds__(kBlock) kb_init(int64_t ldw, int ns, const dou
     }
 }
 
+// Lanes hold several consecutive targets: one 16-byte access per lane brings
+// TPL values of the vector type (4 FP32 / 2 FP64) or PPL {r, p} pairs (2 FP32 /
+// 1 FP64); a row or column is served by a group of kTB / TPL (or kTB / PPL)
+// lanes, several groups per warp.
+template <class FT>
+struct BLanes {
+    using V = typename Vec16<FT>::T;
+    using R = typename RPair<FT>::T;
+    static constexpr int TPL = Vec16<FT>::n;                 // targets per lane (vector values)
+    static constexpr int LG = kTB / TPL;                     // lanes per group
+    static constexpr int PPL = 16 / (int)sizeof(R);          // targets per lane (pairs)
+    static constexpr int LGP = kTB / PPL;                    // lanes per group (pairs)
+};
+
+// Block sums per target of NDOT compensated sums held TPL targets per thread
+// (thread x: targets TPL * (x % (kTB / TPL)) + q); the parts of target t land in
+// thread t.  `red` holds (kBlock / 32) * kTB * NDOT parts.
+template <int NDOT, int TPL, class AT>
+__device__ __forceinline__ void block_tparts_v(CompSum<AT> (&v)[NDOT][TPL], typename CompSum<AT>::Part (&out)[NDOT],
+                                               typename CompSum<AT>::Part *red) {
+    constexpr int NW = kBlock / 32, LG = kTB / TPL;
+#pragma unroll
+    for (int o = 16; o >= LG; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) {
+#pragma unroll
+            for (int q = 0; q < TPL; ++q) v[k][q].xor_reduce(o);
+        }
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l < LG) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) {
+#pragma unroll
+            for (int q = 0; q < TPL; ++q) red[(w * kTB + l * TPL + q) * NDOT + k] = v[k][q].part();
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kTB) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) {
+            CompSum<AT> s;
+            for (int q = 0; q < NW; ++q) CompSum<AT>::add_part(s, red[(q * kTB + threadIdx.x) * NDOT + k]);
+            out[k] = s.part();
+        }
+    }
+}
+
 // phase 1: ut[i][t] = (X p_k,t)_i - <mu_t, p_k,t>, p_k,t formed at the gather
 template <class VT, class FT>
 __global__ void __launch_bounds__(kBlock) kb_phase1(int64_t n, int64_t ldw, const int64_t *__restrict__ rp,
                                                    const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                    const typename RPair<FT>::T *__restrict__ pairs,
                                                    FT *__restrict__ ut, const SolveState *st, const BatchCtl *ctl) {
-    using R = typename RPair<FT>::T;
+    using L = BLanes<FT>;
+    using R = typename L::R;
+    constexpr int PPL = L::PPL, LG = L::LGP;
     if (ctl->done) return;
-    const int t = threadIdx.x % kTB;
-    const FT al = (FT)st[t].alpha, c = (FT)st[t].c;
+    const int lg = threadIdx.x % LG;
+    FT al[PPL], c[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        al[q] = (FT)st[lg * PPL + q].alpha;
+        c[q] = (FT)st[lg * PPL + q].c;
+    }
     const R *__restrict__ a = pairs + (ctl->k & 1) * ldw * kTB;
-    const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kTB;
-    const int64_t ng = (int64_t)gridDim.x * kTG;
+    const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LG;
+    const int64_t ng = (int64_t)gridDim.x * (kBlock / LG);
+    const int64_t lim = ctl->bb.ldw * kTB;
     for (int64_t i = g; i < n; i += ng) {
         const int64_t e0 = rp[i], e1 = rp[i + 1];
-        FT acc = 0;
+        FT acc[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) acc[q] = (FT)0;
         for (int64_t e = e0; e < e1; e += 4) {
             int32_t jj[4];
             FT vv[4];
@@ -253,12 +312,18 @@ __global__ void __launch_bounds__(kBlock) kb_phase1(int64_t n, int64_t ldw, cons
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                if (!BOK((int64_t)jj[u] * kTB + t, ctl->bb.ldw * kTB, 12)) continue;
-                const R x = a[(int64_t)jj[u] * kTB + t];
-                acc += vv[u] * form_p<FT>(x.x, x.y, al);
+                const int64_t off = (int64_t)jj[u] * kTB + lg * PPL;
+                if (!BOK(off + PPL - 1, lim, 12)) continue;
+                R x[PPL];
+                *reinterpret_cast<typename L::V *>(x) = *reinterpret_cast<const typename L::V *>(a + off);
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) acc[q] += vv[u] * form_p<FT>(x[q].x, x[q].y, al[q]);
             }
         }
-        if (BOK(i * kTB + t, ctl->bb.n8 * kTB, 13)) ut[i * kTB + t] = acc - c;
+        if (BOK(i * kTB + lg * PPL + PPL - 1, ctl->bb.n8 * kTB, 13)) {
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) ut[i * kTB + lg * PPL + q] = acc[q] - c[q];
+        }
     }
 }
 
@@ -271,17 +336,23 @@ __global__ void __launch_bounds__(kBlock) kb_phase2(int64_t n, const int64_t *__
                                                    const int8_t *__restrict__ ylab, FT *__restrict__ v,
                                                    SolveState *st, BatchCtl *ctl, BatchCoef<FT> *coef, int ns,
                                                    double *partials, unsigned *counter) {
+    using L = BLanes<FT>;
+    using V = typename L::V;
     using Part = typename CompSum<FT>::Part;
+    constexpr int TPL = L::TPL, LG = L::LG;
     __shared__ Part red[kBlock * 2];
     if (ctl->done) return;
-    const int t = threadIdx.x % kTB;
-    const FT om = (FT)st[t].omega, al = (FT)st[t].alpha_l;
-    const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / kTB;
-    const int64_t ng = (int64_t)gridDim.x * kTG;
-    CompSum<FT> dd[2];
+    const int lg = threadIdx.x % LG, t0 = lg * TPL;
+    const FT om = (FT)st[0].omega, al = (FT)st[0].alpha_l;
+    const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LG;
+    const int64_t ng = (int64_t)gridDim.x * (kBlock / LG);
+    const int64_t lim = ctl->bb.n8 * kTB;
+    CompSum<FT> dd[2][TPL];
     for (int64_t i = g; i < n; i += ng) {
         const int64_t e0 = rp[i], e1 = rp[i + 1];
-        FT acc = 0;
+        FT acc[TPL];
+#pragma unroll
+        for (int q = 0; q < TPL; ++q) acc[q] = (FT)0;
         for (int64_t e = e0; e < e1; e += 4) {
             int32_t jj[4];
             FT vv[4];
@@ -292,19 +363,31 @@ __global__ void __launch_bounds__(kBlock) kb_phase2(int64_t n, const int64_t *__
                 vv[u] = ok ? sval[e + u] : (FT)0;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (BOK((int64_t)jj[u] * kTB + t, ctl->bb.n8 * kTB, 22)) acc += vv[u] * ut[(int64_t)jj[u] * kTB + t];
+            for (int u = 0; u < 4; ++u) {
+                const int64_t off = (int64_t)jj[u] * kTB + t0;
+                if (!BOK(off + TPL - 1, lim, 22)) continue;
+                FT x[TPL];
+                *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(ut + off);
+#pragma unroll
+                for (int q = 0; q < TPL; ++q) acc[q] += vv[u] * x[q];
+            }
         }
-        if (!BOK(i * kTB + t, ctl->bb.n8 * kTB, 23)) continue;
-        const FT u = ut[i * kTB + t];
-        const FT lap = fma(deg[i], u, -acc);
-        const FT vf = fma(al, lap, ylab[i * kTB + t] != 0 ? om * u : (FT)0);
-        v[i * kTB + t] = vf;
-        dd[0].add(u * vf);
-        dd[1].add(vf);
+        const int64_t io = i * kTB + t0;
+        if (!BOK(io + TPL - 1, lim, 23)) continue;
+        FT u[TPL], vo[TPL];
+        *reinterpret_cast<V *>(u) = *reinterpret_cast<const V *>(ut + io);
+        const FT dg = deg[i];
+#pragma unroll
+        for (int q = 0; q < TPL; ++q) {
+            const FT lap = fma(dg, u[q], -acc[q]);
+            vo[q] = fma(al, lap, ylab[io + q] != 0 ? om * u[q] : (FT)0);
+            dd[0][q].add(u[q] * vo[q]);
+            dd[1][q].add(vo[q]);
+        }
+        *reinterpret_cast<V *>(v + io) = *reinterpret_cast<const V *>(vo);
     }
     Part mine[2];
-    block_tparts<2, FT>(dd, mine, red);
+    block_tparts_v<2, TPL, FT>(dd, mine, red);
     if (!arrive_last_t<2>(mine, reinterpret_cast<Part *>(partials), counter, ctl)) return;
     double tot[2];
     grid_tparts<2, FT>(reinterpret_cast<const Part *>(partials), gridDim.x, tot, red);
@@ -348,7 +431,8 @@ __global__ void __launch_bounds__(kBlock) kb_phase2(int64_t n, const int64_t *__
 
 // phase 3a: s[j][t] = (X^T v_t)_j over the column tiles of the operator's CSC
 // (a lane group per column in multi-column tiles; the block's groups share a
-// long column's chunk); compensated sums, written as parts
+// long column's chunk); the four products of a step summed plainly, the steps
+// compensated; written as parts
 template <class VT, class FT>
 __global__ void __launch_bounds__(kBlock) kb_phase3a(const Tile *__restrict__ tiles, int ntiles,
                                                     const int64_t *__restrict__ cp, const int32_t *__restrict__ row,
@@ -356,13 +440,17 @@ __global__ void __launch_bounds__(kBlock) kb_phase3a(const Tile *__restrict__ ti
                                                     typename CompSum<FT>::Part *__restrict__ out,
                                                     typename CompSum<FT>::Part *slots, unsigned *lcount,
                                                     const SplitSeg *__restrict__ splits, const BatchCtl *ctl) {
+    using L = BLanes<FT>;
+    using V = typename L::V;
     using CS = CompSum<FT>;
     using Part = typename CS::Part;
-    __shared__ Part red[kBlock];
+    constexpr int TPL = L::TPL, LG = L::LG, GPB = kBlock / LG;
+    __shared__ Part red[GPB * kTB];
     __shared__ int last;
     if (ctl->done) return;
-    const int t = threadIdx.x % kTB, g = threadIdx.x / kTB;
-    auto dot = [&](int64_t e0, int64_t e1, int64_t step, CS &acc) {
+    const int lg = threadIdx.x % LG, g = threadIdx.x / LG, t0 = lg * TPL;
+    const int64_t lim = ctl->bb.n8 * kTB;
+    auto dot = [&](int64_t e0, int64_t e1, int64_t step, CS (&acc)[TPL]) {
         for (int64_t e = e0; e < e1; e += 4 * step) {
             int32_t ii[4];
             FT vv[4];
@@ -372,40 +460,56 @@ __global__ void __launch_bounds__(kBlock) kb_phase3a(const Tile *__restrict__ ti
                 ii[u] = ok ? row[e + u * step] : 0;
                 vv[u] = ok ? (FT)Val<VT>::get(val, e + u * step) : (FT)0;
             }
+            FT sum[TPL];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (BOK((int64_t)ii[u] * kTB + t, ctl->bb.n8 * kTB, 32)) acc.add(vv[u] * v[(int64_t)ii[u] * kTB + t]);
+            for (int q = 0; q < TPL; ++q) sum[q] = (FT)0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t off = (int64_t)ii[u] * kTB + t0;
+                if (!BOK(off + TPL - 1, lim, 32)) continue;
+                FT x[TPL];
+                *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(v + off);
+#pragma unroll
+                for (int q = 0; q < TPL; ++q) sum[q] += vv[u] * x[q];
+            }
+#pragma unroll
+            for (int q = 0; q < TPL; ++q) acc[q].add(sum[q]);
         }
     };
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const Tile tl = tiles[tile];
         if (tl.lanes > 0) {
             const int nseg = tl.seg1 - tl.seg0;
-            for (int sgi = g; sgi < nseg; sgi += kTG) {
+            for (int sgi = g; sgi < nseg; sgi += GPB) {
                 const int64_t j = tl.seg0 + sgi;
                 if (!BOK(j, ctl->bb.d, 33)) continue;
-                CS acc;
+                CS acc[TPL];
                 dot(cp[j], cp[j + 1], 1, acc);
-                out[j * kTB + t] = acc.part();
+#pragma unroll
+                for (int q = 0; q < TPL; ++q) out[j * kTB + t0 + q] = acc[q].part();
             }
             continue;
         }
-        CS acc;
-        dot(tl.nz0 + g, tl.nz1, kTG, acc);
+        CS acc[TPL];
+        dot(tl.nz0 + g, tl.nz1, GPB, acc);
         __syncthreads();
-        red[threadIdx.x] = acc.part();
+#pragma unroll
+        for (int q = 0; q < TPL; ++q) red[g * kTB + t0 + q] = acc[q].part();
         __syncthreads();
         Part part{};
         if (threadIdx.x < kTB) {
             CS tot;
-            for (int q = 0; q < kTG; ++q) CS::add_part(tot, red[q * kTB + threadIdx.x]);
+            for (int q = 0; q < GPB; ++q) CS::add_part(tot, red[q * kTB + threadIdx.x]);
             part = tot.part();
         }
         if (tl.slot < 0) {
             if (threadIdx.x < kTB && BOK(tl.seg0, ctl->bb.d, 34)) out[(int64_t)tl.seg0 * kTB + threadIdx.x] = part;
             continue;
         }
-        if (!BOK(tl.slot, ctl->bb.nslots, 35) || !BOK(tl.lseg, ctl->bb.nsplits, 36)) { __syncthreads(); continue; }
+        if (!BOK(tl.slot, ctl->bb.nslots, 35) || !BOK(tl.lseg, ctl->bb.nsplits, 36)) {
+            __syncthreads();
+            continue;
+        }
         if (threadIdx.x < kTB) {
             slots[(int64_t)tl.slot * kTB + threadIdx.x] = part;
             __threadfence();
@@ -681,39 +785,67 @@ static int ensure_batch(sda_operator *op, int ns) {
     return SDA_OK;
 }
 
+// `ev` (profile mode): a start and an end event around each of the four kernels
 template <class VT, class FT>
-static int batch_iteration(sda_operator *op, int ns, cudaStream_t s) {
+static int batch_iteration(sda_operator *op, int ns, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     BatchWs &b = *op->bws;
     BView<FT> bv = bview<FT>(b);
     const FT *sv = std::is_same<FT, double>::value ? (const FT *)op->s_val64.p : (const FT *)op->s_val32.p;
     const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
     const int P = kMaxBlocksPerSm * op->sm_count;
+    if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
     kb_phase1<VT, FT><<<b.grid, kBlock, 0, s>>>(op->n, b.ldw, op->x_rp.p, op->x_col.p, (const VT *)op->x_val_r.p,
                                                bv.pairs, bv.ut, b.st.p, b.ctl.p);
     SDA_LAUNCHED();
 
+    if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
+    if (ev) SDA_CUDA(cudaEventRecord(ev[2], s));
     kb_phase2<FT><<<b.grid, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, sv, bv.ut, dg, b.ylab.p, bv.v, b.st.p,
                                            b.ctl.p, bv.coef, ns, b.part.p, b.cnt.p + 0);
     SDA_LAUNCHED();
 
     using Part = typename CompSum<FT>::Part;
+    if (ev) SDA_CUDA(cudaEventRecord(ev[3], s));
+    if (ev) SDA_CUDA(cudaEventRecord(ev[4], s));
     kb_phase3a<VT, FT><<<b.grid, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
                                                 (const VT *)op->x_val_c.p, bv.v, bv.s, (Part *)b.slots.p,
                                                 b.lcount.p, op->col.splits.p, b.ctl.p);
     SDA_LAUNCHED();
 
+    if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
+    if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
     kb_phase3b<FT><<<b.grid, kBlock, 0, s>>>(op->d, b.ldw, ns, bv.s, bv.pairs, bv.W, bv.P, b.st.p, b.ctl.p, bv.coef,
                                             b.mu32.p, b.mu64.p, b.part.p + (int64_t)P * kTB * 2, b.cnt.p + 1);
     SDA_LAUNCHED();
+    if (ev) SDA_CUDA(cudaEventRecord(ev[7], s));
 
     return SDA_OK;
 }
 
 template <class VT, class FT>
-static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, cudaStream_t s) {
+static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, bool profile, cudaStream_t s) {
     BatchWs &b = *op->bws;
+    if (profile) {
+        std::vector<cudaEvent_t> &pe = op->ws.prof_ev;
+        while (pe.size() < (size_t)nb_iters * 8) {
+            cudaEvent_t e;
+            SDA_CUDA(cudaEventCreate(&e));
+            pe.push_back(e);
+        }
+        for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, s, pe.data() + 8 * i)));
+        SDA_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nb_iters; ++i)
+            for (int ph = 0; ph < 4; ++ph) {
+                float ms = 0.f;
+                SDA_CUDA(cudaEventElapsedTime(&ms, pe[8 * i + 2 * ph], pe[8 * i + 2 * ph + 1]));
+                op->stats.ms[1 + ph] += ms;
+            }
+        for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
+        return SDA_OK;
+    }
     if (!use_graph) {
         for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, s)));
+        for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
         return SDA_OK;
     }
     if (!b.graph || b.graph_iters != nb_iters) {
@@ -739,6 +871,7 @@ static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, cud
     }
     SDA_CUDA(cudaGraphLaunch(b.graph, s));
     note_launch(4 * (int64_t)nb_iters);
+    for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
     return SDA_OK;
 }
 
@@ -803,7 +936,7 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     const int nbi = o.iter_batch > 0 ? o.iter_batch : 32;
     int launched = 0;
     while (!b.h_ctl->done && launched <= limit) {
-        SDA_TRY((batch_run<VT, FT>(op, ns, nbi, o.use_graph != 0, s)));
+        SDA_TRY((batch_run<VT, FT>(op, ns, nbi, o.use_graph != 0, o.profile != 0, s)));
         launched += nbi;
         SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
@@ -815,10 +948,11 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     SDA_CUDA(cudaStreamSynchronize(s));
     DevBuf<double> rs;
     if (o.check_residual) SDA_TRY(rs.alloc((size_t)ns + 1));
+    int batch_k = 0;
     for (int i = 0; i < nt; ++i) {
         const int t = t0 + i;
         const SolveState &S = h[i];
-        op->stats.iterations = std::max<int64_t>(op->stats.iterations, S.k);
+        batch_k = std::max(batch_k, S.k);
         for (int sh = 0; sh < ns; ++sh) op->stats.shift_iterations += S.sh[sh].iters;
         kb_take_w<FT><<<grid_elems_b((int64_t)ns * d, op->sm_count), kBlock, 0, s>>>(d, b.ldw, ns, bv.W, i, b.w64.p);
         SDA_LAUNCHED();
@@ -864,6 +998,7 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
             }
         }
     }
+    op->stats.iterations += batch_k;   // iterations of the batch (its slowest target)
     return SDA_OK;
 }
 

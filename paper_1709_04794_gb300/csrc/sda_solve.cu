@@ -751,8 +751,8 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
     int worst = SDA_OK;
     DevBuf<double> bt;
     if (o.batch_targets) {
-        if (o.refine_rounds > 0 || o.profile)
-            return fail(SDA_ERR_UNSUPPORTED, "batched targets do not combine with refinement or profile mode");
+        if (o.refine_rounds > 0)
+            return fail(SDA_ERR_UNSUPPORTED, "batched targets do not combine with refinement");
         // right-hand side of every target of the call, then the batches
         std::vector<const double *> bl((size_t)tc);
         if (o.rhs_mode == SDA_RHS_FROM_R) SDA_TRY(bt.alloc((size_t)tc * d + 1));
