@@ -53,7 +53,7 @@ struct BatchWs {
     int fp64 = -1;
     int64_t d = 0, n = 0, ldw = 0, n8 = 0;
     int ns = 0;
-    DevBuf<char> vec;      // pairs [2][ldw][kTB], s parts [ldw][kTB], ut [n8][kTB], v [n8][kTB]
+    DevBuf<char> vec;      // pairs [2][ldw][kTB], s parts [ldw][kTB], ut [n8][kTB], v [n8][kTB], p [ldw][kTB]
     DevBuf<char> shift;    // W [ns][ldw][kTB], P [ns][ldw][kTB]
     DevBuf<double> b, mu64;
     DevBuf<float> mu32;
@@ -275,32 +275,44 @@ __device__ __forceinline__ void block_tparts_v(CompSum<AT> (&v)[NDOT][TPL], type
     }
 }
 
-// phase 1: ut[i][t] = (X p_k,t)_i - <mu_t, p_k,t>, p_k,t formed at the gather
+// p_k = r_k + alpha_k p_{k-1} of every target, formed once per iteration (the
+// row pass then gathers 4 bytes per target and nonzero instead of the pair)
+template <class FT>
+__global__ void __launch_bounds__(kBlock) kb_formp(int64_t d, int64_t ldw, const typename RPair<FT>::T *__restrict__ pairs,
+                                                  FT *__restrict__ p, const SolveState *st, const BatchCtl *ctl) {
+    using R = typename RPair<FT>::T;
+    if (ctl->done) return;
+    const R *__restrict__ a = pairs + (ctl->k & 1) * ldw * kTB;
+    const FT al = (FT)st[threadIdx.x % kTB].alpha;
+    const int64_t md = d * kTB;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < md; e += (int64_t)gridDim.x * kBlock) {
+        const R x = a[e];
+        p[e] = form_p<FT>(x.x, x.y, al);
+    }
+}
+
+// phase 1: ut[i][t] = (X p_k,t)_i - <mu_t, p_k,t>
 template <class VT, class FT>
 __global__ void __launch_bounds__(kBlock) kb_phase1(int64_t n, int64_t ldw, const int64_t *__restrict__ rp,
                                                    const int32_t *__restrict__ col, const VT *__restrict__ val,
-                                                   const typename RPair<FT>::T *__restrict__ pairs,
-                                                   FT *__restrict__ ut, const SolveState *st, const BatchCtl *ctl) {
+                                                   const FT *__restrict__ p, FT *__restrict__ ut,
+                                                   const SolveState *st, const BatchCtl *ctl) {
     using L = BLanes<FT>;
-    using R = typename L::R;
-    constexpr int PPL = L::PPL, LG = L::LGP;
+    using V = typename L::V;
+    constexpr int TPL = L::TPL, LG = L::LG;
     if (ctl->done) return;
-    const int lg = threadIdx.x % LG;
-    FT al[PPL], c[PPL];
+    const int lg = threadIdx.x % LG, t0 = lg * TPL;
+    FT c[TPL];
 #pragma unroll
-    for (int q = 0; q < PPL; ++q) {
-        al[q] = (FT)st[lg * PPL + q].alpha;
-        c[q] = (FT)st[lg * PPL + q].c;
-    }
-    const R *__restrict__ a = pairs + (ctl->k & 1) * ldw * kTB;
+    for (int q = 0; q < TPL; ++q) c[q] = (FT)st[t0 + q].c;
     const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LG;
     const int64_t ng = (int64_t)gridDim.x * (kBlock / LG);
     const int64_t lim = ctl->bb.ldw * kTB;
     for (int64_t i = g; i < n; i += ng) {
         const int64_t e0 = rp[i], e1 = rp[i + 1];
-        FT acc[PPL];
+        FT acc[TPL];
 #pragma unroll
-        for (int q = 0; q < PPL; ++q) acc[q] = (FT)0;
+        for (int q = 0; q < TPL; ++q) acc[q] = (FT)0;
         for (int64_t e = e0; e < e1; e += 4) {
             int32_t jj[4];
             FT vv[4];
@@ -312,17 +324,20 @@ __global__ void __launch_bounds__(kBlock) kb_phase1(int64_t n, int64_t ldw, cons
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int64_t off = (int64_t)jj[u] * kTB + lg * PPL;
-                if (!BOK(off + PPL - 1, lim, 12)) continue;
-                R x[PPL];
-                *reinterpret_cast<typename L::V *>(x) = *reinterpret_cast<const typename L::V *>(a + off);
+                const int64_t off = (int64_t)jj[u] * kTB + t0;
+                if (!BOK(off + TPL - 1, lim, 12)) continue;
+                FT x[TPL];
+                *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(p + off);
 #pragma unroll
-                for (int q = 0; q < PPL; ++q) acc[q] += vv[u] * form_p<FT>(x[q].x, x[q].y, al[q]);
+                for (int q = 0; q < TPL; ++q) acc[q] += vv[u] * x[q];
             }
         }
-        if (BOK(i * kTB + lg * PPL + PPL - 1, ctl->bb.n8 * kTB, 13)) {
+        const int64_t io = i * kTB + t0;
+        if (BOK(io + TPL - 1, ctl->bb.n8 * kTB, 13)) {
+            FT o[TPL];
 #pragma unroll
-            for (int q = 0; q < PPL; ++q) ut[i * kTB + lg * PPL + q] = acc[q] - c[q];
+            for (int q = 0; q < TPL; ++q) o[q] = acc[q] - c[q];
+            *reinterpret_cast<V *>(ut + io) = *reinterpret_cast<const V *>(o);
         }
     }
 }
@@ -730,6 +745,7 @@ struct BView {
     typename CompSum<FT>::Part *s;
     FT *ut, *v, *W, *P;
     BatchCoef<FT> *coef;
+    FT *p;   // p_k [ldw][kTB]
 };
 
 template <class FT>
@@ -742,7 +758,7 @@ static BView<FT> bview(BatchWs &b) {
     base += b.ldw * kTB * sizeof(Part);
     FT *ut = (FT *)base, *v = ut + b.n8 * kTB;
     FT *W = (FT *)b.shift.p, *P = W + (int64_t)b.ns * b.ldw * kTB;
-    return BView<FT>{pairs, s, ut, v, W, P, (BatchCoef<FT> *)b.coef.p};
+    return BView<FT>{pairs, s, ut, v, W, P, (BatchCoef<FT> *)b.coef.p, v + b.n8 * kTB};
 }
 
 template <class FT>
@@ -757,7 +773,7 @@ static int ensure_batch(sda_operator *op, int ns) {
     b.graph = nullptr;
     b.graph_iters = 0;
     SDA_TRY(b.vec.alloc((size_t)(2 * ldw * kTB * sizeof(typename RPair<FT>::T) + ldw * kTB * sizeof(Part) +
-                                 2 * n8 * kTB * sizeof(FT))));
+                                 2 * n8 * kTB * sizeof(FT) + ldw * kTB * sizeof(FT))));
     SDA_TRY(b.shift.alloc((size_t)(2 * (int64_t)ns * ldw * kTB * sizeof(FT))));
     SDA_TRY(b.b.alloc((size_t)(ldw * kTB)));
     SDA_TRY(b.mu64.alloc((size_t)(ldw * kTB)));
@@ -794,8 +810,10 @@ static int batch_iteration(sda_operator *op, int ns, cudaStream_t s, cudaEvent_t
     const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
     const int P = kMaxBlocksPerSm * op->sm_count;
     if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
+    kb_formp<FT><<<b.grid, kBlock, 0, s>>>(op->d, b.ldw, bv.pairs, bv.p, b.st.p, b.ctl.p);
+    SDA_LAUNCHED();
     kb_phase1<VT, FT><<<b.grid, kBlock, 0, s>>>(op->n, b.ldw, op->x_rp.p, op->x_col.p, (const VT *)op->x_val_r.p,
-                                               bv.pairs, bv.ut, b.st.p, b.ctl.p);
+                                               bv.p, bv.ut, b.st.p, b.ctl.p);
     SDA_LAUNCHED();
 
     if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
@@ -870,7 +888,7 @@ static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, boo
         b.graph_iters = nb_iters;
     }
     SDA_CUDA(cudaGraphLaunch(b.graph, s));
-    note_launch(4 * (int64_t)nb_iters);
+    note_launch(5 * (int64_t)nb_iters);
     for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
     return SDA_OK;
 }
