@@ -762,9 +762,9 @@ static BView<FT> bview(BatchWs &b) {
 }
 
 template <class FT>
-static int ensure_batch(sda_operator *op, int ns) {
-    if (!op->bws) op->bws = new BatchWs();
-    BatchWs &b = *op->bws;
+static int ensure_batch_ws(sda_operator *op, BatchWs *&slot, int ns) {
+    if (!slot) slot = new BatchWs();
+    BatchWs &b = *slot;
     using Part = typename CompSum<FT>::Part;
     const int fp64 = std::is_same<FT, double>::value;
     const int64_t ldw = (op->d + 7) / 8 * 8, n8 = (op->n + 7) / 8 * 8;
@@ -799,6 +799,11 @@ static int ensure_batch(sda_operator *op, int ns) {
     b.ns = ns;
     b.grid = 0;
     return SDA_OK;
+}
+
+template <class FT>
+static int ensure_batch(sda_operator *op, int ns) {
+    return ensure_batch_ws<FT>(op, op->bws, ns);
 }
 
 // `ev` (profile mode): a start and an end event around each of the four kernels
@@ -989,8 +994,7 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
         std::vector<double> tres((size_t)ns, -1.0);
         if (o.check_residual) {
             SDA_TRY(dot_f64(op, d, b_perm[i], b_perm[i], rs.p + ns, s));
-            for (int sh = 0; sh < ns; ++sh)
-                SDA_TRY(resid2(op, t, shifts[sh], b_perm[i], b.w64.p + (int64_t)sh * d, rs.p + sh, alpha, omega, s));
+            SDA_TRY(resid_block(op, t, shifts, ns, b_perm[i], b.w64.p, rs.p, alpha, omega, s));
             std::vector<double> hr((size_t)ns + 1);
             SDA_CUDA(cudaMemcpyAsync(hr.data(), rs.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
             SDA_CUDA(cudaStreamSynchronize(s));
@@ -1031,6 +1035,201 @@ static int with_vt_b(int compute, F &&f) {
     }
 }
 
+template <class VT>
+using BlockVT = VT;
+
+// ---------------------------------------------------------------------------
+// FP64 utilities on blocks of 16 vectors: the batched kernels with FP64
+// vectors, the 16 "targets" being 16 vectors of one target (its labels in every
+// lane).  X and S are read once per 16 vectors.
+// ---------------------------------------------------------------------------
+// P[j][v] = W[v][j] for v < nv (zero for the other lanes)
+__global__ void kb_pack(int64_t d, int64_t ldw, int nv, const double *__restrict__ W, double *__restrict__ P) {
+    const int64_t m = ldw * kTB;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / kTB;
+        const int v = (int)(e - j * kTB);
+        P[e] = (v < nv && j < d) ? W[(int64_t)v * d + j] : 0.0;
+    }
+}
+// out[v][i] = U[i][v] for v < nv
+__global__ void kb_unpack(int64_t n, int nv, const double *__restrict__ U, double *__restrict__ out) {
+    const int64_t m = n * nv;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = e / n, i = e - v * n;
+        out[e] = U[i * kTB + v];
+    }
+}
+// ylab[i][v] = y[i] for every lane
+__global__ void kb_replab(int64_t n, const int8_t *__restrict__ y, int8_t *__restrict__ ylab) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * kTB; e += (int64_t)gridDim.x * blockDim.x)
+        ylab[e] = y[e / kTB];
+}
+// st[v].c = <mu, P_v>
+__global__ void __launch_bounds__(kBlock) kb_dot_mu(int64_t d, const double *__restrict__ mu,
+                                                   const double *__restrict__ P, SolveState *st, BatchCtl *ctl,
+                                                   double *partials, unsigned *counter) {
+    using Part = CompSum<double>::Part;
+    __shared__ Part red[kBlock];
+    CompSum<double> acc[1];
+    const int64_t m = d * kTB;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m; e += (int64_t)gridDim.x * kBlock)
+        acc[0].add(mu[e / kTB] * P[e]);
+    Part mine[1];
+    block_tparts<1, double>(acc, mine, red);
+    if (!arrive_last_t<1>(mine, reinterpret_cast<Part *>(partials), counter, ctl)) return;
+    double tot[1];
+    grid_tparts<1, double>(reinterpret_cast<const Part *>(partials), gridDim.x, tot, red);
+    if (threadIdx.x < kTB) {
+        st[threadIdx.x].c = tot[0];
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+// out[v] = || b - ((X~^T M X~) P_v + sig_v P_v) ||^2 from S = X^T V, t_v = 1^T V_v
+__global__ void __launch_bounds__(kBlock) kb_resid(int64_t d, int nv, const double *__restrict__ b,
+                                                  const double *__restrict__ mu, const double *__restrict__ S,
+                                                  const double *__restrict__ P, const double *__restrict__ sig,
+                                                  const SolveState *st, BatchCtl *ctl, double *out, double *partials,
+                                                  unsigned *counter) {
+    using Part = CompSum<double>::Part;
+    __shared__ Part red[kBlock];
+    const int t = threadIdx.x % kTB;
+    const double tv = st[t].t, sg = sig[t];
+    CompSum<double> acc[1];
+    const int64_t m = d * kTB;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m; e += (int64_t)gridDim.x * kBlock) {
+        const int64_t j = e / kTB;
+        const double q = S[e] - mu[j] * tv + sg * P[e];
+        const double r = b[j] - q;
+        acc[0].add(r * r);
+    }
+    Part mine[1];
+    block_tparts<1, double>(acc, mine, red);
+    if (!arrive_last_t<1>(mine, reinterpret_cast<Part *>(partials), counter, ctl)) return;
+    double tot[1];
+    grid_tparts<1, double>(reinterpret_cast<const Part *>(partials), gridDim.x, tot, red);
+    if (threadIdx.x < kTB) {
+        if (threadIdx.x < nv) out[threadIdx.x] = tot[0];
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
+template <class VT>
+static int block64_setup(sda_operator *op, BatchWs *&B, double alpha, double omega, cudaStream_t s) {
+    SDA_TRY(ensure_batch_ws<double>(op, op->bws64, 1));
+    B = op->bws64;
+    if (!B->grid) {
+        B->grid = std::min(std::min(grid_for((const void *)kb_phase1<VT, double>, op->sm_count),
+                                    grid_for((const void *)kb_phase2<double>, op->sm_count)),
+                           std::min(grid_for((const void *)kb_phase3a<VT, double>, op->sm_count),
+                                    grid_for((const void *)kb_resid, op->sm_count)));
+    }
+    SolveState *h = B->h_st;
+    memset(h, 0, sizeof(SolveState) * kTB);
+    for (int v = 0; v < kTB; ++v) {
+        h[v].omega = omega;
+        h[v].alpha_l = alpha;
+        h[v].sigma0 = 1.0;   // keeps the phase-2 step's <p, (B + sigma0) p> positive; its gamma is unused
+        h[v].pp = 1.0;
+    }
+    SDA_CUDA(cudaMemcpyAsync(B->st.p, h, sizeof(SolveState) * kTB, cudaMemcpyHostToDevice, s));
+    BatchCtl hc{};
+    hc.bb = BatchBounds{op->n, op->d, B->ldw, B->n8, op->nnz, op->s_nnz, op->col.ntiles, op->col.nslots,
+                        op->col.nsplits, (int64_t)B->part.n};
+    *B->h_ctl = hc;
+    SDA_CUDA(cudaMemcpyAsync(B->ctl.p, B->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    return SDA_OK;
+}
+
+template <class VT>
+static int resid_block_t(sda_operator *op, int t, const double *shifts, int ns, const double *b_perm,
+                         const double *W64, double *out_r2, double alpha, double omega, cudaStream_t s) {
+    BatchWs *B = nullptr;
+    SDA_TRY(block64_setup<VT>(op, B, alpha, omega, s));
+    BView<double> bv = bview<double>(*B);
+    const int ge = grid_elems_b(std::max(B->ldw, B->n8) * kTB, op->sm_count);
+    const double *mu = op->mu.p + (int64_t)t * op->d;
+    kb_replab<<<ge, kBlock, 0, s>>>(op->n, op->labels.p + (int64_t)t * op->n, B->ylab.p);
+    SDA_LAUNCHED();
+    for (int c0 = 0; c0 < ns; c0 += kTB) {
+        const int nv = std::min(kTB, ns - c0);
+        double sig[kTB] = {0};
+        for (int v = 0; v < nv; ++v) sig[v] = shifts[c0 + v];
+        SDA_CUDA(cudaMemcpyAsync(B->b.p, sig, sizeof(sig), cudaMemcpyHostToDevice, s));
+        kb_pack<<<ge, kBlock, 0, s>>>(op->d, B->ldw, nv, W64 + (int64_t)c0 * op->d, bv.p);
+        SDA_LAUNCHED();
+        kb_dot_mu<<<B->grid, kBlock, 0, s>>>(op->d, mu, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
+        SDA_LAUNCHED();
+        kb_phase1<VT, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->x_rp.p, op->x_col.p,
+                                                        (const VT *)op->x_val_r.p, bv.p, bv.ut, B->st.p, B->ctl.p);
+        SDA_LAUNCHED();
+        kb_phase2<double><<<B->grid, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, op->s_val64.p, bv.ut,
+                                                    op->deg64.p, B->ylab.p, bv.v, B->st.p, B->ctl.p, bv.coef, 0,
+                                                    B->part.p, B->cnt.p + 1);
+        SDA_LAUNCHED();
+        kb_phase3a<VT, double><<<B->grid, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
+                                                         (const VT *)op->x_val_c.p, bv.v, bv.s, B->slots.p,
+                                                         B->lcount.p, op->col.splits.p, B->ctl.p);
+        SDA_LAUNCHED();
+        kb_resid<<<B->grid, kBlock, 0, s>>>(op->d, nv, b_perm, mu, bv.s, bv.p, B->b.p, B->st.p, B->ctl.p,
+                                           out_r2 + c0, B->part.p, B->cnt.p + 2);
+        SDA_LAUNCHED();
+    }
+    SDA_CUDA(cudaMemcpyAsync(B->h_ctl, B->ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    if (B->h_ctl->err)
+        return fail(SDA_ERR_INDEX, "block residual: index check %llu failed at %llu",
+                    (unsigned long long)(B->h_ctl->err >> 40), (unsigned long long)(B->h_ctl->err & 0xffffffffffull));
+    return SDA_OK;
+}
+
+template <class VT>
+static int project_block_t(sda_operator *op, const double *Wn, int64_t nvec, double *scores, int centred, int t,
+                           cudaStream_t s) {
+    BatchWs *B = nullptr;
+    SDA_TRY(block64_setup<VT>(op, B, 0.0, 1.0, s));
+    BView<double> bv = bview<double>(*B);
+    const int ge = grid_elems_b(std::max(B->ldw, B->n8) * kTB, op->sm_count);
+    for (int64_t c0 = 0; c0 < nvec; c0 += kTB) {
+        const int nv = (int)std::min<int64_t>(kTB, nvec - c0);
+        kb_pack<<<ge, kBlock, 0, s>>>(op->d, B->ldw, nv, Wn + c0 * op->d, bv.p);
+        SDA_LAUNCHED();
+        if (centred) {
+            kb_dot_mu<<<B->grid, kBlock, 0, s>>>(op->d, op->mu.p + (int64_t)t * op->d, bv.p, B->st.p, B->ctl.p,
+                                                 B->part.p, B->cnt.p + 0);
+            SDA_LAUNCHED();
+        }
+        kb_phase1<VT, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->x_rp.p, op->x_col.p,
+                                                        (const VT *)op->x_val_r.p, bv.p, bv.ut, B->st.p, B->ctl.p);
+        SDA_LAUNCHED();
+        kb_unpack<<<ge, kBlock, 0, s>>>(op->n, nv, bv.ut, scores + c0 * op->n);
+        SDA_LAUNCHED();
+    }
+    SDA_CUDA(cudaMemcpyAsync(B->h_ctl, B->ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    if (B->h_ctl->err)
+        return fail(SDA_ERR_INDEX, "block projection: index check %llu failed at %llu",
+                    (unsigned long long)(B->h_ctl->err >> 40), (unsigned long long)(B->h_ctl->err & 0xffffffffffull));
+    return SDA_OK;
+}
+
+int resid_block(sda_operator *op, int t, const double *shifts, int ns, const double *b_perm, const double *W64,
+                double *out_r2, double alpha, double omega, cudaStream_t s) {
+    return with_vt_b(op->compute, [&](auto tag) -> int {
+        using VT = std::remove_pointer_t<decltype(tag)>;
+        return resid_block_t<BlockVT<VT>>(op, t, shifts, ns, b_perm, W64, out_r2, alpha, omega, s);
+    });
+}
+
+int project_block(sda_operator *op, const double *Wn, int64_t nvec, double *scores, int centred, int t,
+                  cudaStream_t s) {
+    return with_vt_b(op->compute, [&](auto tag) -> int {
+        using VT = std::remove_pointer_t<decltype(tag)>;
+        return project_block_t<BlockVT<VT>>(op, Wn, nvec, scores, centred, t, s);
+    });
+}
+
 int solve_batched(sda_operator *op, int t0, int nt, const double *const *b_perm, const double *shifts, int ns,
                   const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
                   cudaStream_t s, int *worst) {
@@ -1057,6 +1256,8 @@ int solve_batched(sda_operator *op, int t0, int nt, const double *const *b_perm,
 void release_batch(sda_operator *op) {
     delete op->bws;
     op->bws = nullptr;
+    delete op->bws64;
+    op->bws64 = nullptr;
 }
 
 }  // namespace sda

@@ -449,14 +449,22 @@ static int build_row_quads(sda_operator *op, bool fp64, size_t vsz, int sms, cud
     int g = 2;
     while (g < 32 && 8 * g < med) g <<= 1;
     op->xr_lanes = g;
-    // head of p kept in shared memory: as many features as a block's share allows
+    // head of p kept in shared memory: the fewest leading (most frequent) features
+    // that hold kRowHeadCover of the nonzeros, at most kRowHeadMax and what a
+    // block's shared memory allows (every block forms the head once per
+    // iteration, so a larger head costs more than its extra gathers save)
     int optin = 0, per_sm = 0;
     SDA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, op->device));
     SDA_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, op->device));
     const int64_t fsz = fp64 ? 8 : 4;
     const int64_t budget = std::min<int64_t>(optin, per_sm / kColBlkPerSm) - kColBlkReserve;
-    const int64_t hmax = std::max<int64_t>(0, budget / fsz / 256 * 256);
-    op->xr_head = (int)std::min<int64_t>(hmax, d / 8 * 8);   // within the pair buffer, whole 16-byte vectors
+    const int64_t hmax = std::min<int64_t>(kRowHeadMax, std::max<int64_t>(0, budget / fsz / 256 * 256));
+    std::vector<int64_t> cp((size_t)d + 1);
+    SDA_CUDA(cudaMemcpy(cp.data(), op->x_cp.p, cp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    const int64_t goal = (int64_t)std::ceil(kRowHeadCover * (double)nnz);
+    const int64_t cover = std::lower_bound(cp.begin(), cp.end(), goal) - cp.begin();
+    const int64_t head = (cover + 255) / 256 * 256;
+    op->xr_head = (int)std::min(std::min<int64_t>(hmax, head), d / 8 * 8);   // whole 16-byte vectors of pairs
     return SDA_OK;
 }
 

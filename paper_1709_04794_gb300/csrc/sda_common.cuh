@@ -339,6 +339,10 @@ __device__ __forceinline__ bool arrive_last(const double *mine, double *partials
 constexpr int kColBlk = 1024;
 constexpr int kColBlkPerSm = 1;   // blocks of the blocked column pass resident per SM
 constexpr int kWarpTileNnz = 512;
+// Row pass: leading features kept in shared memory (share of the nonzeros they
+// should cover, and a cap measured on the 200k workload: 16k-32k features best)
+constexpr double kRowHeadCover = 0.85;
+constexpr int64_t kRowHeadMax = 32768;
 constexpr int kWarpTileSegs = 128;
 constexpr int kWarpBigSeg = 128;
 // Shared memory the blocked column pass keeps for itself besides the slice.

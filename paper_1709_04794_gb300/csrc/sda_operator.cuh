@@ -160,6 +160,7 @@ struct sda_operator {
 
     sda::Workspace ws;
     sda::BatchWs *bws = nullptr;
+    sda::BatchWs *bws64 = nullptr;   // FP64 block utilities (residual check, projection)
     sda_solve_stats stats{};
 };
 
@@ -184,5 +185,11 @@ int solve_batched(sda_operator *op, int t0, int nt, const double *const *b_perm,
                   const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
                   cudaStream_t s, int *worst);
 void release_batch(sda_operator *op);
+// FP64 blocks of 16 vectors (sda_batch.cu): out_r2[v] = ||b - (B + shifts[v] I) W64[v]||^2 of
+// target t for v < ns (all device, permuted order); scores[v] = X Wn[v] (- <mu_t, Wn[v]> if centred)
+int resid_block(sda_operator *op, int t, const double *shifts, int ns, const double *b_perm, const double *W64,
+                double *out_r2, double alpha, double omega, cudaStream_t s);
+int project_block(sda_operator *op, const double *Wn, int64_t nvec, double *scores, int centred, int t,
+                  cudaStream_t s);
 int64_t launch_count();
 }  // namespace sda

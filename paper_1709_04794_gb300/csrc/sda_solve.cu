@@ -596,8 +596,7 @@ static int solve_target(sda_operator *op, int t, const double *b_perm, const dou
         DevBuf<double> rs;
         SDA_TRY(rs.alloc((size_t)ns + 1));
         SDA_TRY(dot_f64(op, d, b_perm, b_perm, rs.p + ns, s));
-        for (int i = 0; i < ns; ++i)
-            SDA_TRY(resid2(op, t, shifts[i], b_perm, W64 + (int64_t)i * d, rs.p + i, alpha, omega, s));
+        SDA_TRY(resid_block(op, t, shifts, ns, b_perm, W64, rs.p, alpha, omega, s));
         std::vector<double> hr((size_t)ns + 1);
         SDA_CUDA(cudaMemcpyAsync(hr.data(), rs.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
@@ -928,17 +927,12 @@ extern "C" SDA_API int sda_project(const sda_operator *op, const double *w, int6
     if (centred && (target < 0 || target >= op->n_targets)) return fail(SDA_ERR_INVALID_ARG, "target out of range");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     sda_operator *mop = const_cast<sda_operator *>(op);
-    SDA_TRY(ensure_apply_scratch(mop));
-    double *wn = op->ws.f64.p;
-    for (int64_t v = 0; v < n_vec; ++v) {
-        SDA_TRY(permute_to_new(op, w + v * op->d, wn, 1, s));
-        const double *csub = nullptr;
-        if (centred) {
-            SDA_TRY(dot_f64(op, op->d, op->mu.p + (int64_t)target * op->d, wn, op->scal.p + 2, s));
-            csub = op->scal.p + 2;
-        }
-        SDA_TRY(op_xmul_f64(op, wn, scores + v * op->n, csub, s));
-    }
+    if (n_vec == 0) return SDA_OK;
+    // the vectors in the permuted feature order, then X (or X~) on blocks of 16
+    DevBuf<double> wn;
+    SDA_TRY(wn.alloc((size_t)(n_vec * op->d)));
+    SDA_TRY(permute_to_new(op, w, wn.p, n_vec, s));
+    SDA_TRY(project_block(mop, wn.p, n_vec, scores, centred, target, s));
     SDA_CUDA(cudaStreamSynchronize(s));
     return SDA_OK;
 }
