@@ -382,7 +382,8 @@ static int build_range_blocks(sda_operator *op, RangeBlocks &out, const int64_t 
     int optin = 0, per_sm = 0;
     SDA_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, op->device));
     SDA_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, op->device));
-    const int64_t budget = std::min<int64_t>(optin, per_sm / kColBlkPerSm) - kColBlkReserve;
+    const int64_t budget =
+        std::min<int64_t>(optin, per_sm / kColBlkPerSm) - kColBlkReserve - colblk_scratch((int64_t)fsz);
     const int64_t rb_max = std::min<int64_t>(65280, budget / (int64_t)fsz / 256 * 256);
     if (rb_max < 256) return fail(SDA_ERR_UNSUPPORTED, "not enough shared memory per block for the range passes");
     const int64_t nr = std::max<int64_t>(1, (nidx + rb_max - 1) / rb_max);

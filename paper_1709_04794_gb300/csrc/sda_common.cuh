@@ -347,6 +347,14 @@ constexpr int kWarpTileSegs = 128;
 constexpr int kWarpBigSeg = 128;
 // Shared memory the blocked column pass keeps for itself besides the slice.
 constexpr int kColBlkReserve = 2048;
+// Per-warp scratch of the blocked column pass after the slice: the quad sums of
+// one multi-column tile (kWarpTileNnz / 4 values of the iteration type) and its
+// column starts (kWarpTileSegs + 1 16-bit quad offsets, padded to 16 bytes).
+constexpr int kWarpTileQuads = kWarpTileNnz / 4;
+constexpr int kWarpTilePosBytes = ((kWarpTileSegs + 1) * 2 + 15) / 16 * 16;
+constexpr int64_t colblk_scratch(int64_t fsz) {
+    return (int64_t)(kColBlk / 32) * ((int64_t)kWarpTileQuads * fsz + kWarpTilePosBytes);
+}
 
 // Shared-memory doubles a block reduction of up to four sums needs.
 constexpr int kRedDoubles = 4 * (kBlock / 32);

@@ -694,10 +694,11 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_rowhead(int64_t n, in
 // copies in flight at once); then its warps work the range's warp tiles
 // round-robin, with every gather served from that copy.  Entries come in quads
 // (segments padded with zero entries to multiples of four): one 8-byte load
-// brings four 16-bit local row indices.  Multi-column tiles give each column a
-// group of `lanes` lanes, two quads per lane in flight; whole-warp tiles take
-// one chunk of a long column, four quads per lane; the chunk of a split column
-// that arrives last adds the chunks' parts in a fixed order.  Sums are
+// brings four 16-bit local row indices.  A multi-column tile loads all its
+// quads and column starts at once, parks the quad sums in the warp's scratch
+// and gives each column a group of `lanes` lanes to add them; whole-warp tiles
+// take one chunk of a long column, four quads per lane; the chunk of a split
+// column that arrives last adds the chunks' parts in a fixed order.  Sums are
 // compensated (CompSum): the frequent features' columns run over most rows and
 // cancel (1^T v vanishes), so plain FP32 sums would lose their digits.  The
 // sums of range r go to out[r * ldo + j] as CompSum parts; the consumer adds
@@ -735,40 +736,81 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
     const uint2 *__restrict__ rowq = reinterpret_cast<const uint2 *>(row);
     const int64_t *__restrict__ cpr = cp + (int64_t)r * (nseg + 1);
     typename CS::Part *__restrict__ outr = out + (int64_t)r * ldo;
-    // dot of quad q with the staged slice (four products, rounded sum)
+    const int lane32 = threadIdx.x & 31;
+    // this warp's scratch: quad sums of a multi-column tile, then its column starts
+    AccT *qs = reinterpret_cast<AccT *>(colblk_smem + (rb * (int64_t)sizeof(AccT) + 15) / 16 * 16 +
+                                        (int64_t)(threadIdx.x >> 5) *
+                                            ((int64_t)kWarpTileQuads * (int64_t)sizeof(AccT) + kWarpTilePosBytes));
+    int16_t *qpos = reinterpret_cast<int16_t *>(qs + kWarpTileQuads);
+    using QL = Quad<VT, AccT>;
+    // dot of a quad with the staged slice (four products, rounded sum)
+    auto dot4 = [&](uint2 ri, const AccT (&x)[4]) -> AccT {
+        return x[0] * vs[ri.x & 0xffffu] + x[1] * vs[ri.x >> 16] + x[2] * vs[ri.y & 0xffffu] + x[3] * vs[ri.y >> 16];
+    };
     auto quad = [&](int64_t q, bool ok) -> AccT {
         uint2 ri = make_uint2(0u, 0u);
         AccT x[4] = {(AccT)0, (AccT)0, (AccT)0, (AccT)0};
         if (ok) {
             ri = __ldcs(rowq + q);
-            Quad<VT, AccT>::load(val, q, x);
+            QL::load(val, q, x);
         }
-        return x[0] * vs[ri.x & 0xffffu] + x[1] * vs[ri.x >> 16] + x[2] * vs[ri.y & 0xffffu] + x[3] * vs[ri.y >> 16];
+        return dot4(ri, x);
     };
-    const int lane32 = threadIdx.x & 31;
     // one warp tile
     auto work = [&](const Tile &tl) {
         if (tl.lanes > 0) {
+            // multi-column tile: at most kWarpTileQuads quads and kWarpTileSegs
+            // columns.  All its quads and column starts load at once (coalesced);
+            // the quad sums go to the warp's scratch, then `lanes` lanes per
+            // column add them (compensated, lane-strided as the quads lie).
+            const int64_t q0 = tl.nz0 >> 2;
+            const int nq = (int)((tl.nz1 >> 2) - q0);
+            const int nsg = tl.seg1 - tl.seg0;
+            constexpr int QPL = kWarpTileQuads / 32;
+            constexpr int SPL = (kWarpTileSegs + 32) / 32;
+            uint2 ri[QPL];
+            AccT x[QPL][4];
+            int64_t cv[SPL];
+#pragma unroll
+            for (int u = 0; u < QPL; ++u) {
+                const int q = lane32 + 32 * u;
+                ri[u] = make_uint2(0u, 0u);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[u][e] = (AccT)0;
+                if (q < nq) {
+                    ri[u] = __ldcs(rowq + q0 + q);
+                    QL::load(val, q0 + q, x[u]);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < SPL; ++m) {
+                const int sg = lane32 + 32 * m;
+                cv[m] = sg <= nsg ? __ldg(cpr + tl.seg0 + sg) : 0;
+            }
+#pragma unroll
+            for (int m = 0; m < SPL; ++m) {
+                const int sg = lane32 + 32 * m;
+                if (sg <= nsg) qpos[sg] = (int16_t)((cv[m] >> 2) - q0);
+            }
+#pragma unroll
+            for (int u = 0; u < QPL; ++u) {
+                const int q = lane32 + 32 * u;
+                if (q < nq) qs[q] = dot4(ri[u], x[u]);
+            }
+            __syncwarp();
             const int G = tl.lanes, per = 32 / G;
             const int g = lane32 / G, lane = lane32 % G;
-            const int nsg = tl.seg1 - tl.seg0;
             for (int base = 0; base < nsg; base += per) {
                 const int sgi = base + g;
                 CS acc;
                 if (sgi < nsg) {
-                    const int64_t j = tl.seg0 + sgi;
-                    const int64_t q0 = cpr[j] >> 2;
-                    const int nq = (int)((cpr[j + 1] >> 2) - q0);
-                    for (int qb = lane; qb < nq; qb += 2 * G) {
-                        const AccT a0 = quad(q0 + qb, true);
-                        const AccT a1 = quad(q0 + qb + G, qb + G < nq);
-                        acc.add(a0);
-                        acc.add(a1);
-                    }
+                    const int e1 = qpos[sgi + 1];
+                    for (int e = qpos[sgi] + lane; e < e1; e += G) acc.add(qs[e]);
                 }
                 for (int o = G >> 1; o > 0; o >>= 1) acc.xor_reduce(o);
                 if (sgi < nsg && lane == 0) outr[tl.seg0 + sgi] = acc.part();
             }
+            __syncwarp();
             return;
         }
         const int64_t q0 = tl.nz0 >> 2;
@@ -811,10 +853,23 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
         }
     };
     // the range's tiles round-robin over its warps (tiles come in column order:
-    // long columns first, so every warp gets a mix of long and short ones)
+    // long columns first, so every warp gets a mix of long and short ones); the
+    // next tile's descriptor loads while a tile is worked
     const int nw = per_range * (kColBlk / 32);
     const int t1 = tile_off[r + 1];
-    for (int t = tile_off[r] + c * (kColBlk / 32) + (threadIdx.x >> 5); t < t1; t += nw) work(tiles[t]);
+    int t = tile_off[r] + c * (kColBlk / 32) + (threadIdx.x >> 5);
+    if (t < t1) {
+        Tile cur = tiles[t];
+        for (;;) {
+            const int tn = t + nw;
+            Tile nxt = cur;
+            if (tn < t1) nxt = tiles[tn];
+            work(cur);
+            if (tn >= t1) break;
+            cur = nxt;
+            t = tn;
+        }
+    }
 }
 
 // phase 3b (stream over D), s_j = sum of the row-range partials of X^T v,

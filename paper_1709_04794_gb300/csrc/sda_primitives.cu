@@ -236,7 +236,9 @@ static int lanes_for(int64_t maxlen) {
 // at most tile_nnz); the others are grouped into multi-segment tiles of at most
 // tile_nnz nonzeros and tile_segs segments.
 // Chunk boundaries are multiples of `align` nonzeros from the segment start.
-static void append_seg_tiles(const int64_t *colptr, int64_t d, int64_t tile_nnz, int64_t tile_segs,
+// returns false if a multi-column tile would exceed the limits (the blocked
+// column pass keeps such a tile in a fixed per-warp scratch)
+static bool append_seg_tiles(const int64_t *colptr, int64_t d, int64_t tile_nnz, int64_t tile_segs,
                              int64_t big_seg, int64_t align, std::vector<Tile> &tiles,
                              std::vector<SplitSeg> &splits, int64_t *slots) {
     int64_t j = 0;
@@ -272,7 +274,9 @@ static void append_seg_tiles(const int64_t *colptr, int64_t d, int64_t tile_nnz,
             ++j;
         }
         tiles.push_back(Tile{colptr[start], colptr[j], (int32_t)start, (int32_t)j, lanes_for(maxlen), -1, -1, 0});
+        if (nz > std::max(tile_nnz, big_seg) || j - start > tile_segs) return false;
     }
+    return true;
 }
 
 static int upload_schedule(const std::vector<Tile> &tiles, const std::vector<SplitSeg> &splits, int64_t slots,
@@ -296,8 +300,9 @@ int build_seg_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
     std::vector<Tile> tiles;
     std::vector<SplitSeg> splits;
     int64_t slots = 0;
-    append_seg_tiles(colptr.data(), (int64_t)colptr.size() - 1, kTileNnz, kTileSegs, kBigSeg, 1, tiles, splits,
-                     &slots);
+    if (!append_seg_tiles(colptr.data(), (int64_t)colptr.size() - 1, kTileNnz, kTileSegs, kBigSeg, 1, tiles, splits,
+                          &slots))
+        return fail(SDA_ERR_UNSUPPORTED, "segment tile over its limits");
     return upload_schedule(tiles, splits, slots, out);
 }
 
@@ -308,8 +313,9 @@ int build_range_schedule(const std::vector<int64_t> &ptr, int nranges, int64_t d
     int64_t slots = 0;
     tile_off.assign((size_t)nranges + 1, 0);
     for (int r = 0; r < nranges; ++r) {
-        append_seg_tiles(ptr.data() + (size_t)r * (size_t)(d + 1), d, kWarpTileNnz, kWarpTileSegs, kWarpBigSeg, 4,
-                         tiles, splits, &slots);
+        if (!append_seg_tiles(ptr.data() + (size_t)r * (size_t)(d + 1), d, kWarpTileNnz, kWarpTileSegs,
+                              kWarpBigSeg, 4, tiles, splits, &slots))
+            return fail(SDA_ERR_UNSUPPORTED, "warp tile over its limits");
         if ((int64_t)tiles.size() > INT32_MAX) return fail(SDA_ERR_UNSUPPORTED, "column schedule too large");
         tile_off[(size_t)r + 1] = (int32_t)tiles.size();
     }

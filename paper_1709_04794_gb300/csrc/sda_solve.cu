@@ -394,7 +394,7 @@ static int size_grids(sda_operator *op) {
     }));
     {
         const void *k = (const void *)k_colblk<BlkVT<VT>, FT>;
-        const size_t smem = (size_t)op->xb.rb * sizeof(FT);
+        const size_t smem = ((size_t)op->xb.rb * sizeof(FT) + 15) / 16 * 16 + (size_t)colblk_scratch(sizeof(FT));
         SDA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int nb = 0;
         SDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kColBlk, smem));
