@@ -150,10 +150,11 @@ def algorithmic_bytes(prob, compute: str, iters: int, shift_iters: int, info: di
                            read once, degrees, labels, v written.
     phase3a (columns of X, k_colblk): 16-bit indices + values + the R ranges'
                            column pointers, v read once, the R ranges' partial
-                           sums (pairs of the vector type) written.
+                           sums (pairs of the vector type) written; its stream
+                           warps read r_k once and, per active shift, read and
+                           write P and W.
     phase3b (stream):      the R partial sums, {r_k, p_{k-1}} and mu_l read,
-                           {r_{k+1}, p_k} written, and per active shift P and W
-                           read and written."""
+                           {r_{k+1}, p_k} written."""
     n, d = prob.n, prob.d
     nnz = int(prob.x_ptr[-1])
     snz = int(prob.s_ptr[-1])
@@ -165,8 +166,9 @@ def algorithmic_bytes(prob, compute: str, iters: int, shift_iters: int, info: di
     return {
         "phase1": nnz * (4 + vsz) + (n + 1) * 8 + 2 * d * fsz + n * fsz,
         "phase2": snz * (4 + fsz) + (n + 1) * 8 + 3 * n * fsz + n,
-        "phase3a": nnz * (2 + vsz) + R * (d + 1) * 8 + n * fsz + R * d * psz,
-        "phase3b": d * (R * psz + 4 * fsz + mus) + (shift_iters / max(iters, 1)) * d * 4 * fsz,
+        "phase3a": (nnz * (2 + vsz) + R * (d + 1) * 8 + n * fsz + R * d * psz + d * fsz
+                    + (shift_iters / max(iters, 1)) * d * 4 * fsz),
+        "phase3b": d * (R * psz + 4 * fsz + mus),
     }
 
 
@@ -421,7 +423,7 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = per_launch[dominant] / (durs[dominant] * 1e-3) / 1e9
     kernel_names = {"phase1": "k_rowhead (rows of X)", "phase2": "k_rowpass<EpiP2> (rows of S)",
-                    "phase3a": "k_colblk (columns of X)", "phase3b": "k_cg_phase3b (vector and shift stream)"}
+                    "phase3a": "k_colblk (columns of X, shift stream)", "phase3b": "k_cg_phase3b (vector stream)"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(dominant),
                 "kernel": kernel_names[dominant], "peak_kind": peak_kind,

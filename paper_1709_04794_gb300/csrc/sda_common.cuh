@@ -350,10 +350,15 @@ constexpr int kColBlkReserve = 2048;
 // Per-warp scratch of the blocked column pass after the slice: the quad sums of
 // one multi-column tile (kWarpTileNnz / 4 values of the iteration type) and its
 // column starts (kWarpTileSegs + 1 16-bit quad offsets, padded to 16 bytes).
+// The last kColBlkStreamWarps warps of a block stream the shift state instead,
+// with a table of the shift scalars (kShiftTabBytes) at the end of the scratch.
+constexpr int kColBlkStreamWarps = 4;
 constexpr int kWarpTileQuads = kWarpTileNnz / 4;
 constexpr int kWarpTilePosBytes = ((kWarpTileSegs + 1) * 2 + 15) / 16 * 16;
+constexpr int kShiftTabBytes = 2048;
 constexpr int64_t colblk_scratch(int64_t fsz) {
-    return (int64_t)(kColBlk / 32) * ((int64_t)kWarpTileQuads * fsz + kWarpTilePosBytes);
+    return (int64_t)(kColBlk / 32 - kColBlkStreamWarps) * ((int64_t)kWarpTileQuads * fsz + kWarpTilePosBytes) +
+           kShiftTabBytes;
 }
 
 // Shared-memory doubles a block reduction of up to four sums needs.

@@ -688,6 +688,96 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_rowhead(int64_t n, in
     }
 }
 
+// r_k values of four (FP32) or two (FP64) consecutive features from the
+// interleaved {r, p} pairs
+__device__ __forceinline__ void load_r(const float2 *a, int64_t j0, float (&r)[4]) {
+    const float4 u = *reinterpret_cast<const float4 *>(a + j0);
+    const float4 w = *reinterpret_cast<const float4 *>(a + j0 + 2);
+    r[0] = u.x;
+    r[1] = u.z;
+    r[2] = w.x;
+    r[3] = w.z;
+}
+__device__ __forceinline__ void load_r(const double2 *a, int64_t j0, double (&r)[2]) {
+    r[0] = a[j0].x;
+    r[1] = a[j0 + 1].x;
+}
+
+// Compact scalars of one iteration's shift-state stream (shared memory): the
+// active shifts in order and their zeta^s_k, alpha^s_k, gamma^s_k.
+template <class FT>
+struct ShiftTab {
+    int act[kMaxShifts];
+    FT zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
+    int nact;
+};
+static_assert(sizeof(ShiftTab<double>) <= kShiftTabBytes, "shift table outgrows its shared-memory slot");
+
+// threads [0, kMaxShifts) of a block copy the compact parameters of phase 2
+template <class FT>
+__device__ __forceinline__ void load_shift_tab(const StreamParams &sp, ShiftTab<FT> &tab) {
+    if (threadIdx.x == 0) tab.nact = sp.nact;
+    if (threadIdx.x < kMaxShifts) {
+        tab.act[threadIdx.x] = sp.act[threadIdx.x];
+        tab.zk[threadIdx.x] = (FT)sp.zk[threadIdx.x];
+        tab.ak[threadIdx.x] = (FT)sp.ak[threadIdx.x];
+        tab.gk[threadIdx.x] = (FT)sp.gk[threadIdx.x];
+    }
+}
+
+// The shift-state stream of iteration k (Algorithm 3, every active shift s):
+//   P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1};  W^s_{k+1} = W^s_k - gamma^s_k P^s_k
+// over items i = q * nch + c (active slot q, 16-byte chunk c), item i to thread
+// i mod nthr; (q, c) advance by (nthr / nch, nthr % nch) without a division per
+// item, two items per thread in flight.  a: the {r_k, p_{k-1}} pairs.
+template <class FT>
+__device__ __forceinline__ void shift_stream(int64_t tid, int64_t nthr, int64_t ldw,
+                                             const typename RPair<FT>::T *__restrict__ a, FT *__restrict__ W,
+                                             FT *__restrict__ P, const ShiftTab<FT> &tab) {
+    using V = typename Vec16<FT>::T;
+    constexpr int VW = Vec16<FT>::n;
+    constexpr int UNROLL = 2;
+    const int nch = (int)(ldw / VW), nact = tab.nact;
+    int q = (int)(tid / nch), c = (int)(tid - (int64_t)q * nch);
+    const int sq = (int)(nthr / nch), sc = (int)(nthr - (int64_t)sq * nch);
+    while (q < nact) {
+        FT r[UNROLL][VW];
+        V pv[UNROLL], wv[UNROLL];
+        int64_t off[UNROLL];
+        int qq[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            qq[u] = q;
+            if (q < nact) {
+                const int64_t j0 = (int64_t)c * VW;
+                off[u] = (int64_t)tab.act[q] * ldw + j0;
+                load_r(a, j0, r[u]);
+                pv[u] = *reinterpret_cast<const V *>(P + off[u]);
+                wv[u] = *reinterpret_cast<const V *>(W + off[u]);
+            }
+            q += sq;
+            c += sc;
+            if (c >= nch) {
+                c -= nch;
+                ++q;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            if (qq[u] >= nact) continue;
+            const FT z = tab.zk[qq[u]], aa = tab.ak[qq[u]], g = tab.gk[qq[u]];
+#pragma unroll
+            for (int e = 0; e < VW; ++e) {
+                const FT pn = z * r[u][e] + aa * v16_get(pv[u], e);
+                v16_set(pv[u], e, pn);
+                v16_set(wv[u], e, v16_get(wv[u], e) - g * pn);
+            }
+            *reinterpret_cast<V *>(P + off[u]) = pv[u];
+            *reinterpret_cast<V *>(W + off[u]) = wv[u];
+        }
+    }
+}
+
 // Column pass s = X^T v over ranges of rows (Sec. 3.2.3, second identity, before
 // the rank-one term): block b serves range r = b / per_range.  It first copies
 // v's slice of rows [r * rb, (r + 1) * rb) into shared memory (cp.async, all
@@ -698,7 +788,11 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_rowhead(int64_t n, in
 // quads and column starts at once, parks the quad sums in the warp's scratch
 // and gives each column a group of `lanes` lanes to add them; whole-warp tiles
 // take one chunk of a long column, four quads per lane; the chunk of a split
-// column that arrives last adds the chunks' parts in a fixed order.  Sums are
+// column that arrives last adds the chunks' parts in a fixed order.  The last
+// kColBlkStreamWarps warps of each block run the iteration's shift-state
+// stream instead (W, P of the active shifts; none when W is null): it needs
+// only phase 2's scalars and r_k, and uses the bandwidth the latency-bound
+// tiles leave.  Sums are
 // compensated (CompSum): the frequent features' columns run over most rows and
 // cancel (1^T v vanishes), so plain FP32 sums would lose their digits.  The
 // sums of range r go to out[r * ldo + j] as CompSum parts; the consumer adds
@@ -711,11 +805,17 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
                                                    typename CompSum<AccT>::Part *__restrict__ out,
                                                    typename CompSum<AccT>::Part *slots,
                                                    unsigned *lcount, const SplitSeg *__restrict__ splits,
-                                                   const int32_t *__restrict__ tile_off, const SolveState *st) {
+                                                   const int32_t *__restrict__ tile_off, const SolveState *st,
+                                                   int64_t ldw, const typename RPair<AccT>::T *__restrict__ rp,
+                                                   AccT *__restrict__ W, AccT *__restrict__ P) {
     using CS = CompSum<AccT>;
     extern __shared__ __align__(16) unsigned char colblk_smem[];
     AccT *vs = reinterpret_cast<AccT *>(colblk_smem);
+    ShiftTab<AccT> &tab = *reinterpret_cast<ShiftTab<AccT> *>(
+        colblk_smem + (rb * (int64_t)sizeof(AccT) + 15) / 16 * 16 + colblk_scratch((int64_t)sizeof(AccT)) -
+        kShiftTabBytes);
     if (st && st->done) return;
+    if (W) load_shift_tab<AccT>(st->sp, tab);
     const int r = blockIdx.x / per_range, c = blockIdx.x - r * per_range;
     const int64_t r0 = (int64_t)r * rb;
     const int len = (int)min(rb, n - r0);
@@ -852,12 +952,23 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
             }
         }
     };
-    // the range's tiles round-robin over its warps (tiles come in column order:
-    // long columns first, so every warp gets a mix of long and short ones); the
-    // next tile's descriptor loads while a tile is worked
-    const int nw = per_range * (kColBlk / 32);
+    // the last kColBlkStreamWarps warps of every block run the shift-state
+    // stream of this iteration (bandwidth-bound; the tile warps are bound by
+    // latency), the others the range's tiles
+    constexpr int TW = kColBlk / 32 - kColBlkStreamWarps;
+    const int wib = threadIdx.x >> 5;
+    if (wib >= TW) {
+        if (W)
+            shift_stream<AccT>((int64_t)(blockIdx.x * kColBlkStreamWarps + (wib - TW)) * 32 + lane32,
+                               (int64_t)gridDim.x * kColBlkStreamWarps * 32, ldw, rp + (st->k & 1) * ldw, W, P, tab);
+        return;
+    }
+    // the range's tiles round-robin over its tile warps (tiles come in column
+    // order: long columns first, so every warp gets a mix of long and short
+    // ones); the next tile's descriptor loads while a tile is worked
+    const int nw = per_range * TW;
     const int t1 = tile_off[r + 1];
-    int t = tile_off[r] + c * (kColBlk / 32) + (threadIdx.x >> 5);
+    int t = tile_off[r] + c * TW + wib;
     if (t < t1) {
         Tile cur = tiles[t];
         for (;;) {
@@ -875,18 +986,14 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
 // phase 3b (stream over D), s_j = sum of the row-range partials of X^T v,
 // q_j = s_j - mu_j t + sigma0 p_k,j for every feature:
 //   r_{k+1} = r_k + gamma_k q;  RP[k+1] = {r_{k+1}, p_k}
-//   P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1};  W^s_{k+1} = W^s_k - gamma^s_k P^s_k  (active shifts)
-// The base vectors are one grid-stride pass; the shift state a second one over
-// (active shift, 16-byte chunk) pairs, four pairs per thread in flight.  The
-// scalars arrive in the compact block st->sp written by phase 2.  Dots
-// <r_{k+1}, r_{k+1}>, <mu, r_{k+1}>, <r_{k+1}, p_k>; the last block forms
-// alpha_{k+1}, <mu, p_{k+1}>, ||p_{k+1}||^2 and the stop tests.
+// one grid-stride pass (the shift state of the iteration is streamed by the
+// column pass, which runs before).  The scalars arrive in the compact block
+// st->sp written by phase 2.  Dots <r_{k+1}, r_{k+1}>, <mu, r_{k+1}>,
+// <r_{k+1}, p_k>; the last block forms alpha_{k+1}, <mu, p_{k+1}>,
+// ||p_{k+1}||^2 and the stop tests.
 template <class FT>
 struct StreamSmem {
     double alpha, gamma, t, sigma0;
-    int nact;
-    int act[kMaxShifts];
-    FT zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
     double red[kRedDoubles];
     double alpha_new, rnorm;
     float gh, gl, sh, sl, tf;   // gamma_k, sigma0 as FP32 pairs, t in FP32 (mixed path)
@@ -915,18 +1022,6 @@ __device__ __forceinline__ float base_step_f32(float r, float pk, float sjh, flo
     return base_step_f32v(r, pk, sjh, sjl, mj, sm.sh, sm.sl, sm.tf, sm.gh, sm.gl);
 }
 
-__device__ __forceinline__ void load_r(const float2 *a, int64_t j0, float (&r)[4]) {
-    const float4 u = *reinterpret_cast<const float4 *>(a + j0);
-    const float4 w = *reinterpret_cast<const float4 *>(a + j0 + 2);
-    r[0] = u.x;
-    r[1] = u.z;
-    r[2] = w.x;
-    r[3] = w.z;
-}
-__device__ __forceinline__ void load_r(const double2 *a, int64_t j0, double (&r)[2]) {
-    r[0] = a[j0].x;
-    r[1] = a[j0 + 1].x;
-}
 
 template <class FT>
 __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw,
@@ -934,10 +1029,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw,
                                                        typename RPair<FT>::T *__restrict__ rp,
                                                        FT *__restrict__ W, FT *__restrict__ P, SolveState *st,
                                                        double *partials, unsigned *counter) {
-    using V = typename Vec16<FT>::T;
     using R = typename RPair<FT>::T;
-    constexpr int VW = Vec16<FT>::n;
-    constexpr int UNROLL = 2;
     __shared__ StreamSmem<FT> sm;
     if (st->done) return;
     {
@@ -947,18 +1039,11 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw,
             sm.gamma = sp.gamma;
             sm.t = sp.t;
             sm.sigma0 = sp.sigma0;
-            sm.nact = sp.nact;
         }
         if (threadIdx.x == 32) {
             split_f32(sp.gamma, sm.gh, sm.gl);
             split_f32(sp.sigma0, sm.sh, sm.sl);
             sm.tf = (float)sp.t;
-        }
-        if (threadIdx.x < kMaxShifts) {
-            sm.act[threadIdx.x] = sp.act[threadIdx.x];
-            sm.zk[threadIdx.x] = (FT)sp.zk[threadIdx.x];
-            sm.ak[threadIdx.x] = (FT)sp.ak[threadIdx.x];
-            sm.gk[threadIdx.x] = (FT)sp.gk[threadIdx.x];
         }
     }
     constexpr bool kF32 = std::is_same<FT, float>::value;
@@ -1007,47 +1092,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw,
             dd[0].add(rnj * rnj);
             dd[1].add((FT)mj * rnj);
             dd[2].add(rnj * pk);
-        }
-    }
-    // shift items i = q * nch + c (shift slot q, 16-byte chunk c), thread stride
-    // nthr; (q, c) advance by (nthr / nch, nthr % nch) without a division per item
-    const int nch = (int)(ldw / VW), nact = sm.nact;
-    int q = (int)(tid / nch), c = (int)(tid - (int64_t)q * nch);
-    const int sq = (int)(nthr / nch), sc = (int)(nthr - (int64_t)sq * nch);
-    while (q < nact) {
-        FT r[UNROLL][VW];
-        V pv[UNROLL], wv[UNROLL];
-        int64_t off[UNROLL];
-        int qq[UNROLL];
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            qq[u] = q;
-            if (q < nact) {
-                const int64_t j0 = (int64_t)c * VW;
-                off[u] = (int64_t)sm.act[q] * ldw + j0;
-                load_r(a, j0, r[u]);
-                pv[u] = *reinterpret_cast<const V *>(P + off[u]);
-                wv[u] = *reinterpret_cast<const V *>(W + off[u]);
-            }
-            q += sq;
-            c += sc;
-            if (c >= nch) {
-                c -= nch;
-                ++q;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < UNROLL; ++u) {
-            if (qq[u] >= nact) continue;
-            const FT z = sm.zk[qq[u]], aa = sm.ak[qq[u]], g = sm.gk[qq[u]];
-#pragma unroll
-            for (int e = 0; e < VW; ++e) {
-                const FT pn = z * r[u][e] + aa * v16_get(pv[u], e);
-                v16_set(pv[u], e, pn);
-                v16_set(wv[u], e, v16_get(wv[u], e) - g * pn);
-            }
-            *reinterpret_cast<V *>(P + off[u]) = pv[u];
-            *reinterpret_cast<V *>(W + off[u]) = wv[u];
         }
     }
     using Part = typename CompSum<FT>::Part;
