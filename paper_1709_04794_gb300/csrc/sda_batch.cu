@@ -24,7 +24,12 @@ constexpr int kTG = kBlock / kTB;    // lane groups per block
 // recording the first one in BatchCtl::err (reported to the caller).
 struct BatchBounds {
     int64_t n, d, ldw, n8, nnz_x, nnz_s, ntiles, nslots, nsplits, npart;
+    int64_t nqx;   // quads of the padded row layout of X
 };
+
+// value type of the padded row layout (a pattern X stores FP8 ones there)
+template <class VT>
+using BVT = std::conditional_t<std::is_same<VT, Pattern>::value, __nv_fp8_e4m3, VT>;
 
 struct BatchCtl {
     int32_t k;        // iterations completed
@@ -308,28 +313,39 @@ __global__ void __launch_bounds__(kBlock) kb_phase1(int64_t n, int64_t ldw, cons
     const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LG;
     const int64_t ng = (int64_t)gridDim.x * (kBlock / LG);
     const int64_t lim = ctl->bb.ldw * kTB;
+    const int4 *__restrict__ colq = reinterpret_cast<const int4 *>(col);
     for (int64_t i = g; i < n; i += ng) {
-        const int64_t e0 = rp[i], e1 = rp[i + 1];
+        const int64_t q0 = rp[i] >> 2, q1 = rp[i + 1] >> 2;
         FT acc[TPL];
 #pragma unroll
         for (int q = 0; q < TPL; ++q) acc[q] = (FT)0;
-        for (int64_t e = e0; e < e1; e += 4) {
-            int32_t jj[4];
-            FT vv[4];
+        // two quads (eight entries) per step: their indices and values load
+        // first, then the eight gathers go out together
+        for (int64_t q = q0; q < q1; q += 2) {
+            int4 ci[2];
+            FT xv[2][4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool ok = e + u < e1 && BOK(e + u, ctl->bb.nnz_x, 11);
-                jj[u] = ok ? col[e + u] : 0;
-                vv[u] = ok ? (FT)Val<VT>::get(val, e + u) : (FT)0;
+            for (int u = 0; u < 2; ++u) {
+                ci[u] = make_int4(0, 0, 0, 0);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) xv[u][e] = (FT)0;
+                if (q + u < q1 && BOK(q + u, ctl->bb.nqx, 11)) {
+                    ci[u] = colq[q + u];
+                    Quad<VT, FT>::load(val, q + u, xv[u]);
+                }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t off = (int64_t)jj[u] * kTB + t0;
-                if (!BOK(off + TPL - 1, lim, 12)) continue;
-                FT x[TPL];
-                *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(p + off);
+            for (int u = 0; u < 2; ++u) {
 #pragma unroll
-                for (int q = 0; q < TPL; ++q) acc[q] += vv[u] * x[q];
+                for (int e = 0; e < 4; ++e) {
+                    const int32_t j = e == 0 ? ci[u].x : e == 1 ? ci[u].y : e == 2 ? ci[u].z : ci[u].w;
+                    const int64_t off = (int64_t)j * kTB + t0;
+                    if (!BOK(off + TPL - 1, lim, 12)) continue;
+                    FT x[TPL];
+                    *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(p + off);
+#pragma unroll
+                    for (int t = 0; t < TPL; ++t) acc[t] += xv[u][e] * x[t];
+                }
             }
         }
         const int64_t io = i * kTB + t0;
@@ -465,37 +481,49 @@ __global__ void __launch_bounds__(kBlock) kb_phase3a(const Tile *__restrict__ ti
     if (ctl->done) return;
     const int lg = threadIdx.x % LG, g = threadIdx.x / LG, t0 = lg * TPL;
     const int64_t lim = ctl->bb.n8 * kTB;
+    // eight entries (stride `step`) per round: their indices and values load
+    // first, then the gathers go out together; each group of four entries is
+    // summed, then added to the compensated sums
     auto dot = [&](int64_t e0, int64_t e1, int64_t step, CS (&acc)[TPL]) {
-        for (int64_t e = e0; e < e1; e += 4 * step) {
-            int32_t ii[4];
-            FT vv[4];
+        for (int64_t e = e0; e < e1; e += 8 * step) {
+            int32_t ii[8];
+            FT vv[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const bool ok = e + u * step < e1 && BOK(e + u * step, ctl->bb.nnz_x, 31);
                 ii[u] = ok ? row[e + u * step] : 0;
                 vv[u] = ok ? (FT)Val<VT>::get(val, e + u * step) : (FT)0;
             }
-            FT sum[TPL];
 #pragma unroll
-            for (int q = 0; q < TPL; ++q) sum[q] = (FT)0;
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && e + 4 * step >= e1) break;
+                FT sum[TPL];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t off = (int64_t)ii[u] * kTB + t0;
-                if (!BOK(off + TPL - 1, lim, 32)) continue;
-                FT x[TPL];
-                *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(v + off);
+                for (int q = 0; q < TPL; ++q) sum[q] = (FT)0;
 #pragma unroll
-                for (int q = 0; q < TPL; ++q) sum[q] += vv[u] * x[q];
+                for (int u = 4 * h; u < 4 * h + 4; ++u) {
+                    const int64_t off = (int64_t)ii[u] * kTB + t0;
+                    if (!BOK(off + TPL - 1, lim, 32)) continue;
+                    FT x[TPL];
+                    *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(v + off);
+#pragma unroll
+                    for (int q = 0; q < TPL; ++q) sum[q] += vv[u] * x[q];
+                }
+#pragma unroll
+                for (int q = 0; q < TPL; ++q) acc[q].add(sum[q]);
             }
-#pragma unroll
-            for (int q = 0; q < TPL; ++q) acc[q].add(sum[q]);
         }
     };
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const Tile tl = tiles[tile];
         if (tl.lanes > 0) {
+            // columns go to lane groups from a starting group that moves from
+            // tile to tile (23 is odd: every residue in turn), so that tiles of
+            // few columns do not always load the same groups
             const int nseg = tl.seg1 - tl.seg0;
-            for (int sgi = g; sgi < nseg; sgi += GPB) {
+            const int rot = (it * 23 + blockIdx.x) % GPB;
+            for (int sgi = (g - rot + GPB) % GPB; sgi < nseg; sgi += GPB) {
                 const int64_t j = tl.seg0 + sgi;
                 if (!BOK(j, ctl->bb.d, 33)) continue;
                 CS acc[TPL];
@@ -817,8 +845,8 @@ static int batch_iteration(sda_operator *op, int ns, cudaStream_t s, cudaEvent_t
     if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
     kb_formp<FT><<<b.grid, kBlock, 0, s>>>(op->d, b.ldw, bv.pairs, bv.p, b.st.p, b.ctl.p);
     SDA_LAUNCHED();
-    kb_phase1<VT, FT><<<b.grid, kBlock, 0, s>>>(op->n, b.ldw, op->x_rp.p, op->x_col.p, (const VT *)op->x_val_r.p,
-                                               bv.p, bv.ut, b.st.p, b.ctl.p);
+    kb_phase1<BVT<VT>, FT><<<b.grid, kBlock, 0, s>>>(op->n, b.ldw, op->xr_rp.p, op->xr_col.p,
+                                                    (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, b.st.p, b.ctl.p);
     SDA_LAUNCHED();
 
     if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
@@ -906,7 +934,7 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     SDA_TRY(ensure_batch<FT>(op, ns));
     BatchWs &b = *op->bws;
     if (!b.grid) {
-        b.grid = std::min(std::min(grid_for((const void *)kb_phase1<VT, FT>, op->sm_count),
+        b.grid = std::min(std::min(grid_for((const void *)kb_phase1<BVT<VT>, FT>, op->sm_count),
                                    grid_for((const void *)kb_phase2<FT>, op->sm_count)),
                           std::min(grid_for((const void *)kb_phase3a<VT, FT>, op->sm_count),
                                    grid_for((const void *)kb_phase3b<FT>, op->sm_count)));
@@ -946,7 +974,7 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     {
         BatchCtl hc{};
         hc.bb = BatchBounds{op->n, op->d, b.ldw, b.n8, op->nnz, op->s_nnz, op->col.ntiles, op->col.nslots,
-                            op->col.nsplits, (int64_t)b.part.n};
+                            op->col.nsplits, (int64_t)b.part.n, (int64_t)(op->xr_col.n / 4)};
         *b.h_ctl = hc;
         SDA_CUDA(cudaMemcpyAsync(b.ctl.p, b.h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
     }
@@ -1119,7 +1147,7 @@ static int block64_setup(sda_operator *op, BatchWs *&B, double alpha, double ome
     SDA_TRY(ensure_batch_ws<double>(op, op->bws64, 1));
     B = op->bws64;
     if (!B->grid) {
-        B->grid = std::min(std::min(grid_for((const void *)kb_phase1<VT, double>, op->sm_count),
+        B->grid = std::min(std::min(grid_for((const void *)kb_phase1<BVT<VT>, double>, op->sm_count),
                                     grid_for((const void *)kb_phase2<double>, op->sm_count)),
                            std::min(grid_for((const void *)kb_phase3a<VT, double>, op->sm_count),
                                     grid_for((const void *)kb_resid, op->sm_count)));
@@ -1135,7 +1163,7 @@ static int block64_setup(sda_operator *op, BatchWs *&B, double alpha, double ome
     SDA_CUDA(cudaMemcpyAsync(B->st.p, h, sizeof(SolveState) * kTB, cudaMemcpyHostToDevice, s));
     BatchCtl hc{};
     hc.bb = BatchBounds{op->n, op->d, B->ldw, B->n8, op->nnz, op->s_nnz, op->col.ntiles, op->col.nslots,
-                        op->col.nsplits, (int64_t)B->part.n};
+                        op->col.nsplits, (int64_t)B->part.n, (int64_t)(op->xr_col.n / 4)};
     *B->h_ctl = hc;
     SDA_CUDA(cudaMemcpyAsync(B->ctl.p, B->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
     SDA_CUDA(cudaStreamSynchronize(s));
@@ -1161,8 +1189,9 @@ static int resid_block_t(sda_operator *op, int t, const double *shifts, int ns, 
         SDA_LAUNCHED();
         kb_dot_mu<<<B->grid, kBlock, 0, s>>>(op->d, mu, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
         SDA_LAUNCHED();
-        kb_phase1<VT, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->x_rp.p, op->x_col.p,
-                                                        (const VT *)op->x_val_r.p, bv.p, bv.ut, B->st.p, B->ctl.p);
+        kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->xr_rp.p, op->xr_col.p,
+                                                             (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, B->st.p,
+                                                             B->ctl.p);
         SDA_LAUNCHED();
         kb_phase2<double><<<B->grid, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, op->s_val64.p, bv.ut,
                                                     op->deg64.p, B->ylab.p, bv.v, B->st.p, B->ctl.p, bv.coef, 0,
@@ -1200,8 +1229,9 @@ static int project_block_t(sda_operator *op, const double *Wn, int64_t nvec, dou
                                                  B->part.p, B->cnt.p + 0);
             SDA_LAUNCHED();
         }
-        kb_phase1<VT, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->x_rp.p, op->x_col.p,
-                                                        (const VT *)op->x_val_r.p, bv.p, bv.ut, B->st.p, B->ctl.p);
+        kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->xr_rp.p, op->xr_col.p,
+                                                             (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, B->st.p,
+                                                             B->ctl.p);
         SDA_LAUNCHED();
         kb_unpack<<<ge, kBlock, 0, s>>>(op->n, nv, bv.ut, scores + c0 * op->n);
         SDA_LAUNCHED();
