@@ -149,11 +149,20 @@ __global__ void __launch_bounds__(kBlock) k_segpass(const Tile *__restrict__ til
     epi.end(esh);
 }
 
+struct EpiNoPre {
+    struct Pre {};
+};
+
 // Row pass for segments of similar, moderate length (rows of X, rows of S):
 // G lanes per row, each lane loads up to U (index, value) pairs of its row at
 // once (predicated, evict-first) and then issues their U gathers together; the
 // row sum is an xor tree over the G lanes; no shared memory.  Rows longer than
 // G * U take several rounds.  Epi::segment(i, sum) runs on the row's first lane.
+template <class E, class = void>
+struct EpiHasPre : std::false_type {};
+template <class E>
+struct EpiHasPre<E, std::void_t<typename E::Pre>> : std::true_type {};
+
 template <class VT, class AccT, int G, int U, class Gather, class Epi>
 __global__ void __launch_bounds__(kBlock) k_rowpass(int64_t n, const int64_t *__restrict__ rp,
                                                     const int32_t *__restrict__ idx, const VT *__restrict__ val,
@@ -166,12 +175,32 @@ __global__ void __launch_bounds__(kBlock) k_rowpass(int64_t n, const int64_t *__
     const int lane = threadIdx.x % G;
     const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
+    // the row pointers of a warp's next round load during the current one
+    int64_t p0 = 0, p1 = 0;
+    {
+        const int64_t i = warp * RPW + (threadIdx.x & 31) / G;
+        if (i < n) {
+            p0 = rp[i];
+            p1 = rp[i + 1];
+        }
+    }
     for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
         const int64_t i = base + (threadIdx.x & 31) / G;
+        const int64_t e0 = p0;
+        const int len = (int)(p1 - p0);
+        {
+            const int64_t in = i + nwarps * RPW;
+            if (in < n) {
+                p0 = rp[in];
+                p1 = rp[in + 1];
+            }
+        }
+        // an epilogue with a Pre type reads its per-row inputs before the row sum
+        typename std::conditional<EpiHasPre<Epi>::value, Epi, EpiNoPre>::type::Pre pre{};
+        if constexpr (EpiHasPre<Epi>::value)
+            if (i < n && lane == 0) pre = epi.pre(i);
         AccT acc = 0;
         if (i < n) {
-            const int64_t e0 = rp[i];
-            const int len = (int)(rp[i + 1] - e0);
             const int32_t *__restrict__ ip = idx + e0;
             const VT *__restrict__ vp = val + (val ? e0 : 0);
             for (int eb = lane; eb < len; eb += G * U) {
@@ -192,7 +221,12 @@ __global__ void __launch_bounds__(kBlock) k_rowpass(int64_t n, const int64_t *__
         }
 #pragma unroll
         for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (i < n && lane == 0) epi.segment(i, acc);
+        if (i < n && lane == 0) {
+            if constexpr (EpiHasPre<Epi>::value)
+                epi.segment(i, acc, pre);
+            else
+                epi.segment(i, acc);
+        }
     }
     epi.end(esh);
 }
@@ -341,14 +375,21 @@ struct EpiP2 {
         omega = (FT)st->omega;
         al = (FT)st->alpha_l;
     }
-    __device__ __forceinline__ void segment(int64_t i, FT s) {
-        const FT u = ut[i];
-        const FT lap = fma(deg[i], u, -s);
-        const FT vf = fma(al, lap, y[i] != 0 ? omega * u : (FT)0);
+    // the row's own inputs, read before its sum
+    struct Pre {
+        FT u, dg;
+        int y;
+    };
+    __device__ __forceinline__ Pre pre(int64_t i) const { return Pre{ut[i], deg[i], (int)y[i]}; }
+    __device__ __forceinline__ void segment(int64_t i, FT s, const Pre &pr) {
+        const FT u = pr.u;
+        const FT lap = fma(pr.dg, u, -s);
+        const FT vf = fma(al, lap, pr.y != 0 ? omega * u : (FT)0);
         v[i] = vf;
         d[0].add(u * vf);
         d[1].add(vf);
     }
+    __device__ __forceinline__ void segment(int64_t i, FT s) { segment(i, s, pre(i)); }
     __device__ __forceinline__ void segment_block(int64_t i, FT s) {
         if (threadIdx.x == 0) segment(i, s);
     }
@@ -670,12 +711,28 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_rowhead(int64_t n, in
     const int lane = threadIdx.x % G;
     const int64_t warp = ((int64_t)blockIdx.x * kColBlk + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kColBlk) >> 5;
+    // the row pointers of a warp's next round load during the current one
+    int64_t p0 = 0, p1 = 0;
+    {
+        const int64_t i = warp * RPW + (threadIdx.x & 31) / G;
+        if (i < n) {
+            p0 = rp[i];
+            p1 = rp[i + 1];
+        }
+    }
     for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
         const int64_t i = base + (threadIdx.x & 31) / G;
+        const int64_t q0 = p0 >> 2;
+        const int nq = (int)((p1 >> 2) - q0);
+        {
+            const int64_t in = i + nwarps * RPW;
+            if (in < n) {
+                p0 = rp[in];
+                p1 = rp[in + 1];
+            }
+        }
         FT acc = 0;
         if (i < n) {
-            const int64_t q0 = rp[i] >> 2;
-            const int nq = (int)((rp[i + 1] >> 2) - q0);
             for (int qb = lane; qb < nq; qb += 2 * G) {
                 const FT a0 = quad(q0 + qb, true);
                 const FT a1 = quad(q0 + qb + G, qb + G < nq);
