@@ -355,16 +355,12 @@ template <class FT>
 struct EpiP2 {
     struct Shared {
         double red[kRedDoubles];
-        double gamma;
-        int ok;
-        unsigned ballot[kMaxShifts / 32];
     };
     using Part = typename CompSum<FT>::Part;
     FT *v;
     const FT *ut, *deg;
     SolveState *st;
     double *partials;
-    unsigned *counter;
     const int8_t *y;
     FT omega, al;
     CompSum<FT> d[2];   // <ut, v>, 1^T v (compensated: 1^T v vanishes in exact arithmetic)
@@ -393,76 +389,16 @@ struct EpiP2 {
     __device__ __forceinline__ void segment_block(int64_t i, FT s) {
         if (threadIdx.x == 0) segment(i, s);
     }
+    // the block's parts go to partials[block]; the scalar step that closes the
+    // phase (gamma_k, the shift ratios) runs in the column pass (stream_scalars)
     __device__ void end(Shared &sh) {
         Part mine[2];
         Part *red = reinterpret_cast<Part *>(sh.red);
-        Part *parts = reinterpret_cast<Part *>(partials);
         block_parts<2, FT>(d, mine, red);
-        if (!arrive_last_parts<2>(mine, parts, counter)) return;
-        // the shift state is read before the grid sum so that its loads overlap it
-        const int ns = st->n_shifts;
-        const int q = threadIdx.x;
-        ShiftState *h = st->sh + q;
-        int act = 0;
-        double zp = 0.0, zk = 0.0, ak = 0.0, dl = 0.0;
-        if (q < ns) {
-            act = h->active;
-            zp = h->z_prev;
-            zk = h->z;
-            ak = h->a;
-            dl = h->delta;
-        }
-        const double gp = st->gamma_prev, al_k = st->alpha;
-        double tot[2];
-        grid_parts<2, FT>(parts, gridDim.x, tot, red);
         if (threadIdx.x == 0) {
-            const double pq = tot[0] + st->sigma0 * st->pp;
-            sh.ok = (pq > 0.0) && isfinite(pq);
-            if (!sh.ok) {
-                st->status = SDA_ERR_BREAKDOWN;
-                st->done = 1;
-            } else {
-                const double gam = -st->rr / pq;
-                st->gamma = gam;
-                st->t = tot[1];
-                sh.gamma = gam;
-                StreamParams &sp = st->sp;
-                sp.alpha = al_k;
-                sp.gamma = gam;
-                sp.t = tot[1];
-                sp.sigma0 = st->sigma0;
-            }
-            *counter = 0u;
-        }
-        __syncthreads();
-        if (!sh.ok) return;
-        // zeta_{k+1} / zeta_k = zeta_{k-1} gamma_{k-1} / den (one division per shift)
-        const double gam = sh.gamma;
-        double gk = 0.0;
-        if (act) {
-            const double den = gam * al_k * (zp - zk) + zp * gp * (1.0 - dl * gam);
-            const double ratio = zp * gp / den;
-            h->ratio = ratio;
-            gk = gam * ratio;
-            h->g = gk;
-        }
-        // compact the active shifts for the stream kernel (slot = active shifts before it)
-        const unsigned bal = __ballot_sync(0xffffffffu, act);
-        if (q < kMaxShifts && (q & 31) == 0) sh.ballot[q >> 5] = bal;
-        __syncthreads();
-        if (act) {
-            int pos = __popc(bal & ((1u << (q & 31)) - 1u));
-            for (int w = 0; w < (q >> 5); ++w) pos += __popc(sh.ballot[w]);
-            StreamParams &sp = st->sp;
-            sp.act[pos] = q;
-            sp.zk[pos] = zk;
-            sp.ak[pos] = ak;
-            sp.gk[pos] = gk;
-        }
-        if (threadIdx.x == 0) {
-            int na = 0;
-            for (int w = 0; w < kMaxShifts / 32; ++w) na += __popc(sh.ballot[w]);
-            st->sp.nact = na;
+            Part *parts = reinterpret_cast<Part *>(partials);
+            parts[(int64_t)blockIdx.x * 2 + 0] = mine[0];
+            parts[(int64_t)blockIdx.x * 2 + 1] = mine[1];
         }
     }
 };
@@ -767,19 +703,113 @@ struct ShiftTab {
     int act[kMaxShifts];
     FT zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
     int nact;
+    typename CompSum<FT>::Part wsum[kColBlkStreamWarps][2];   // per-warp parts of phase 2's sums
+    int wcount[kMaxShifts / 32];                               // active shifts per 32
 };
-static_assert(sizeof(ShiftTab<double>) <= kShiftTabBytes, "shift table outgrows its shared-memory slot");
+static_assert(sizeof(ShiftTab<double>) <= kShiftTabBytes && sizeof(ShiftTab<float>) <= kShiftTabBytes,
+              "shift table outgrows its shared-memory slot");
 
-// threads [0, kMaxShifts) of a block copy the compact parameters of phase 2
+// The scalar step that closes phase 2 (Algorithm 3): from the phase's block
+// parts of <ut, v> and 1^T v, <p, (B + sigma0) p> = <ut, v> + sigma0 ||p||^2,
+// gamma_k = -<r, r> / <p, (B + sigma0) p>, and per active shift
+//   zeta_{k+1} / zeta_k = zeta_{k-1} gamma_{k-1} / (gamma_k alpha_k (zeta_{k-1} - zeta_k)
+//                          + zeta_{k-1} gamma_{k-1} (1 - (beta - sigma0) gamma_k)),
+//   gamma^s_k = gamma_k zeta_{k+1} / zeta_k.
+// Run by the NT = kColBlkStreamWarps * 32 stream threads (index sl) of every
+// column-pass block on the same parts in a fixed order, so every block gets
+// the same values; it fills `tab` (the active shifts' zeta^s_k, alpha^s_k,
+// gamma^s_k in shift order) and, in the writer block, the solve state.
+// Returns false on breakdown (<p, (B + sigma0) p> <= 0 or not finite).
 template <class FT>
-__device__ __forceinline__ void load_shift_tab(const StreamParams &sp, ShiftTab<FT> &tab) {
-    if (threadIdx.x == 0) tab.nact = sp.nact;
-    if (threadIdx.x < kMaxShifts) {
-        tab.act[threadIdx.x] = sp.act[threadIdx.x];
-        tab.zk[threadIdx.x] = (FT)sp.zk[threadIdx.x];
-        tab.ak[threadIdx.x] = (FT)sp.ak[threadIdx.x];
-        tab.gk[threadIdx.x] = (FT)sp.gk[threadIdx.x];
+__device__ bool stream_scalars(SolveState *st, const typename CompSum<FT>::Part *__restrict__ parts, int nb,
+                               ShiftTab<FT> &tab, int sl, bool writer) {
+    constexpr int NT = kColBlkStreamWarps * 32;
+    using CS = CompSum<FT>;
+    const int w = sl >> 5, l = sl & 31;
+    // the shift state is read first so that its loads overlap the sum
+    const int ns = st->n_shifts;
+    ShiftState *h = st->sh + sl;
+    int act = 0;
+    double zp = 0.0, zk = 0.0, ak = 0.0, dl = 0.0;
+    if (sl < ns) {
+        act = h->active;
+        zp = h->z_prev;
+        zk = h->z;
+        ak = h->a;
+        dl = h->delta;
     }
+    const double gp = st->gamma_prev, al_k = st->alpha, rr = st->rr, sigma0 = st->sigma0, pp = st->pp;
+    CS a[2];
+    for (int b = sl; b < nb; b += NT) {
+        CS::add_part(a[0], __ldcg(parts + 2 * (int64_t)b));
+        CS::add_part(a[1], __ldcg(parts + 2 * (int64_t)b + 1));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a[0].xor_reduce(o);
+        a[1].xor_reduce(o);
+    }
+    if (l == 0) {
+        tab.wsum[w][0] = a[0].part();
+        tab.wsum[w][1] = a[1].part();
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+    double tot[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        CS t;
+#pragma unroll
+        for (int q = 0; q < kColBlkStreamWarps; ++q) CS::add_part(t, tab.wsum[q][k]);
+        tot[k] = t.to_double();
+    }
+    const double pq = tot[0] + sigma0 * pp;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        if (writer && sl == 0) {
+            st->status = SDA_ERR_BREAKDOWN;
+            st->done = 1;
+        }
+        return false;
+    }
+    const double gam = -rr / pq;
+    double gk = 0.0;
+    if (act) {
+        const double den = gam * al_k * (zp - zk) + zp * gp * (1.0 - dl * gam);
+        const double ratio = zp * gp / den;
+        gk = gam * ratio;
+        if (writer) {
+            h->ratio = ratio;
+            h->g = gk;
+        }
+    }
+    // compact the active shifts (slot = active shifts before it)
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    if (l == 0 && w < kMaxShifts / 32) tab.wcount[w] = __popc(bal);
+    asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+    if (act) {
+        int pos = __popc(bal & ((1u << l) - 1u));
+        for (int q = 0; q < w; ++q) pos += tab.wcount[q];
+        tab.act[pos] = sl;
+        tab.zk[pos] = (FT)zk;
+        tab.ak[pos] = (FT)ak;
+        tab.gk[pos] = (FT)gk;
+    }
+    if (sl == 0) {
+        int na = 0;
+        for (int q = 0; q < kMaxShifts / 32; ++q) na += tab.wcount[q];
+        tab.nact = na;
+        if (writer) {
+            st->gamma = gam;
+            st->t = tot[1];
+            StreamParams &sp = st->sp;
+            sp.alpha = al_k;
+            sp.gamma = gam;
+            sp.t = tot[1];
+            sp.sigma0 = sigma0;
+            sp.nact = na;
+        }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(NT) : "memory");
+    return true;
 }
 
 // The shift-state stream of iteration k (Algorithm 3, every active shift s):
@@ -847,9 +877,10 @@ __device__ __forceinline__ void shift_stream(int64_t tid, int64_t nthr, int64_t 
 // take one chunk of a long column, four quads per lane; the chunk of a split
 // column that arrives last adds the chunks' parts in a fixed order.  The last
 // kColBlkStreamWarps warps of each block run the iteration's shift-state
-// stream instead (W, P of the active shifts; none when W is null): it needs
-// only phase 2's scalars and r_k, and uses the bandwidth the latency-bound
-// tiles leave.  Sums are
+// stream instead (W, P of the active shifts; none when W is null): they first
+// close phase 2 (gamma_k and the shift coefficients, from phase 2's block
+// parts, identically in every block; block 0 stores them), then stream, using
+// the bandwidth the latency-bound tiles leave.  Sums are
 // compensated (CompSum): the frequent features' columns run over most rows and
 // cancel (1^T v vanishes), so plain FP32 sums would lose their digits.  The
 // sums of range r go to out[r * ldo + j] as CompSum parts; the consumer adds
@@ -862,9 +893,11 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
                                                    typename CompSum<AccT>::Part *__restrict__ out,
                                                    typename CompSum<AccT>::Part *slots,
                                                    unsigned *lcount, const SplitSeg *__restrict__ splits,
-                                                   const int32_t *__restrict__ tile_off, const SolveState *st,
+                                                   const int32_t *__restrict__ tile_off, SolveState *st,
                                                    int64_t ldw, const typename RPair<AccT>::T *__restrict__ rp,
-                                                   AccT *__restrict__ W, AccT *__restrict__ P) {
+                                                   AccT *__restrict__ W, AccT *__restrict__ P,
+                                                   const typename CompSum<AccT>::Part *__restrict__ p2parts,
+                                                   int p2blocks) {
     using CS = CompSum<AccT>;
     extern __shared__ __align__(16) unsigned char colblk_smem[];
     AccT *vs = reinterpret_cast<AccT *>(colblk_smem);
@@ -872,7 +905,6 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
         colblk_smem + (rb * (int64_t)sizeof(AccT) + 15) / 16 * 16 + colblk_scratch((int64_t)sizeof(AccT)) -
         kShiftTabBytes);
     if (st && st->done) return;
-    if (W) load_shift_tab<AccT>(st->sp, tab);
     const int r = blockIdx.x / per_range, c = blockIdx.x - r * per_range;
     const int64_t r0 = (int64_t)r * rb;
     const int len = (int)min(rb, n - r0);
@@ -1015,7 +1047,7 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
     constexpr int TW = kColBlk / 32 - kColBlkStreamWarps;
     const int wib = threadIdx.x >> 5;
     if (wib >= TW) {
-        if (W)
+        if (W && stream_scalars<AccT>(st, p2parts, p2blocks, tab, threadIdx.x - TW * 32, blockIdx.x == 0))
             shift_stream<AccT>((int64_t)(blockIdx.x * kColBlkStreamWarps + (wib - TW)) * 32 + lane32,
                                (int64_t)gridDim.x * kColBlkStreamWarps * 32, ldw, rp + (st->k & 1) * ldw, W, P, tab);
         return;

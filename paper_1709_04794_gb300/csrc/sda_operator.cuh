@@ -19,17 +19,16 @@ struct ShiftState {
     int32_t iters;   // iteration count when it stopped (or so far)
 };
 
-// Compact scalars of the vector / shift-state stream of one iteration, written
-// by the last block of phase 2 (active shifts first, in shift order).
+// Scalars of the base-vector stream of one iteration, written by block 0 of
+// the column pass once it has closed phase 2 (nact: shifts still active).
 struct StreamParams {
     double alpha, gamma, t, sigma0;
     int32_t nact, pad;
-    int32_t act[kMaxShifts];
-    double zk[kMaxShifts], ak[kMaxShifts], gk[kMaxShifts];
 };
 
 // Scalars of one shifted-CG run, read by every phase kernel, written by the
-// last block of the phase that completes them.
+// block that completes them (the last block of a phase, or block 0 of the
+// column pass for phase 2's step).
 struct SolveState {
     // fixed for the run
     double sigma0, omega, alpha_l, tol, bnorm, inv_bnorm;

@@ -356,13 +356,14 @@ static int grid_of(const void *kernel, int sms) {
 template <class VT, class FT>
 static int range_pass(const sda_operator *op, const RangeBlocks &rb, int64_t n, int64_t nseg, int64_t ldo,
                       const FT *v, typename CompSum<FT>::Part *out, int grid, size_t smem, cudaStream_t s,
-                      const typename RPair<FT>::T *rp, FT *W, FT *P) {
+                      const typename RPair<FT>::T *rp, FT *W, FT *P, const void *p2parts, int p2blocks) {
     using Part = typename CompSum<FT>::Part;   // one slot (8 bytes) per part in either type
     k_colblk<VT, FT><<<grid, kColBlk, smem, s>>>(rb.sched.tiles.p, rb.per_range, n, rb.rb, nseg, ldo, rb.cp.p,
                                                  rb.idx.p, (const VT *)rb.val.p, v, out,
                                                  reinterpret_cast<Part *>(op->slots.p) + rb.slot0,
                                                  op->lcount.p + rb.lseg0, rb.sched.splits.p, rb.tile_off.p,
-                                                 op->ws.st.p, ldo, rp, W, P);
+                                                 op->ws.st.p, ldo, rp, W, P,
+                                                 (const typename CompSum<FT>::Part *)p2parts, p2blocks);
     SDA_LAUNCHED();
     return SDA_OK;
 }
@@ -428,12 +429,12 @@ static int launch_iteration(const sda_operator *op, cudaStream_t s, cudaEvent_t 
     if (ev) SDA_CUDA(cudaEventRecord(ev[2], s));
     const FT *sv = std::is_same<FT, double>::value ? (const FT *)op->s_val64.p : (const FT *)op->s_val32.p;
     SDA_TRY((rowpass<FT, FT>(op->s_lanes, op->n, op->s_rp.p, op->s_col.p, sv, GatherVec<FT, FT>{b.ut},
-                             EpiP2<FT>{b.v, b.ut, dg, w.st.p, w.part.p + P * 4, w.cnt.p + 1, nullptr, 0, 0},
+                             EpiP2<FT>{b.v, b.ut, dg, w.st.p, w.part.p + P * 4, nullptr, 0, 0},
                              w.grid2, s)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[3], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[4], s));
     SDA_TRY((range_pass<BlkVT<VT>, FT>(op, op->xb, op->n, op->d, w.ldw, b.v, b.s, w.grid3a, w.colblk_smem, s, b.rp,
-                                       b.W, b.P)));
+                                       b.W, b.P, w.part.p + P * 4, w.grid2)));
     if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
     k_cg_phase3b<FT><<<w.grid3b, kBlock, 0, s>>>(op->d, w.ldw, b.s, w.nparts, b.rp, b.W, b.P, w.st.p,
