@@ -27,6 +27,15 @@ struct BatchBounds {
     int64_t nqx;   // quads of the padded row layout of X
 };
 
+// Resident blocks per SM asked of the batched sparse passes: they are bound by
+// gather latency, so the FP32 ones are held to 40 registers for six blocks
+// (measured: 646 against 742 us per batch iteration at four blocks); the FP64
+// ones (block utilities) keep their registers.
+template <class FT>
+struct KbMinBlocks {
+    static constexpr int value = std::is_same<FT, float>::value ? 6 : 1;
+};
+
 // value type of the padded row layout (a pattern X stores FP8 ones there)
 template <class VT>
 using BVT = std::conditional_t<std::is_same<VT, Pattern>::value, __nv_fp8_e4m3, VT>;
@@ -70,7 +79,8 @@ struct BatchWs {
     DevBuf<unsigned> cnt, lcount;
     SolveState *h_st = nullptr;
     BatchCtl *h_ctl = nullptr;
-    int grid = 0;
+    int grid = 0;                          // every kernel but the sparse passes of the batched solve
+    int grid1 = 0, grid2 = 0, grid3a = 0;  // their own grids (occupancy of each)
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
     cudaStream_t cap_stream = nullptr;
@@ -298,7 +308,7 @@ __global__ void __launch_bounds__(kBlock) kb_formp(int64_t d, int64_t ldw, const
 
 // phase 1: ut[i][t] = (X p_k,t)_i - <mu_t, p_k,t>
 template <class VT, class FT>
-__global__ void __launch_bounds__(kBlock) kb_phase1(int64_t n, int64_t ldw, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase1(int64_t n, int64_t ldw, const int64_t *__restrict__ rp,
                                                    const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                    const FT *__restrict__ p, FT *__restrict__ ut,
                                                    const SolveState *st, const BatchCtl *ctl) {
@@ -361,7 +371,7 @@ __global__ void __launch_bounds__(kBlock) kb_phase1(int64_t n, int64_t ldw, cons
 // phase 2: v = omega P_l ut + alpha (D ut - S ut) per target; <ut, v>, 1^T v;
 // the last block forms gamma_k per target and the (shift, target) coefficients
 template <class FT>
-__global__ void __launch_bounds__(kBlock) kb_phase2(int64_t n, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase2(int64_t n, const int64_t *__restrict__ rp,
                                                    const int32_t *__restrict__ col, const FT *__restrict__ sval,
                                                    const FT *__restrict__ ut, const FT *__restrict__ deg,
                                                    const int8_t *__restrict__ ylab, FT *__restrict__ v,
@@ -465,7 +475,7 @@ __global__ void __launch_bounds__(kBlock) kb_phase2(int64_t n, const int64_t *__
 // long column's chunk); the four products of a step summed plainly, the steps
 // compensated; written as parts
 template <class VT, class FT>
-__global__ void __launch_bounds__(kBlock) kb_phase3a(const Tile *__restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase3a(const Tile *__restrict__ tiles, int ntiles,
                                                     const int64_t *__restrict__ cp, const int32_t *__restrict__ row,
                                                     const VT *__restrict__ val, const FT *__restrict__ v,
                                                     typename CompSum<FT>::Part *__restrict__ out,
@@ -845,20 +855,20 @@ static int batch_iteration(sda_operator *op, int ns, cudaStream_t s, cudaEvent_t
     if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
     kb_formp<FT><<<b.grid, kBlock, 0, s>>>(op->d, b.ldw, bv.pairs, bv.p, b.st.p, b.ctl.p);
     SDA_LAUNCHED();
-    kb_phase1<BVT<VT>, FT><<<b.grid, kBlock, 0, s>>>(op->n, b.ldw, op->xr_rp.p, op->xr_col.p,
-                                                    (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, b.st.p, b.ctl.p);
+    kb_phase1<BVT<VT>, FT><<<b.grid1, kBlock, 0, s>>>(op->n, b.ldw, op->xr_rp.p, op->xr_col.p,
+                                                     (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, b.st.p, b.ctl.p);
     SDA_LAUNCHED();
 
     if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[2], s));
-    kb_phase2<FT><<<b.grid, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, sv, bv.ut, dg, b.ylab.p, bv.v, b.st.p,
-                                           b.ctl.p, bv.coef, ns, b.part.p, b.cnt.p + 0);
+    kb_phase2<FT><<<b.grid2, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, sv, bv.ut, dg, b.ylab.p, bv.v, b.st.p,
+                                            b.ctl.p, bv.coef, ns, b.part.p, b.cnt.p + 0);
     SDA_LAUNCHED();
 
     using Part = typename CompSum<FT>::Part;
     if (ev) SDA_CUDA(cudaEventRecord(ev[3], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[4], s));
-    kb_phase3a<VT, FT><<<b.grid, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
+    kb_phase3a<VT, FT><<<b.grid3a, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
                                                 (const VT *)op->x_val_c.p, bv.v, bv.s, (Part *)b.slots.p,
                                                 b.lcount.p, op->col.splits.p, b.ctl.p);
     SDA_LAUNCHED();
@@ -934,10 +944,11 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     SDA_TRY(ensure_batch<FT>(op, ns));
     BatchWs &b = *op->bws;
     if (!b.grid) {
-        b.grid = std::min(std::min(grid_for((const void *)kb_phase1<BVT<VT>, FT>, op->sm_count),
-                                   grid_for((const void *)kb_phase2<FT>, op->sm_count)),
-                          std::min(grid_for((const void *)kb_phase3a<VT, FT>, op->sm_count),
-                                   grid_for((const void *)kb_phase3b<FT>, op->sm_count)));
+        b.grid1 = grid_for((const void *)kb_phase1<BVT<VT>, FT>, op->sm_count);
+        b.grid2 = grid_for((const void *)kb_phase2<FT>, op->sm_count);
+        b.grid3a = grid_for((const void *)kb_phase3a<VT, FT>, op->sm_count);
+        b.grid = std::min(std::min(b.grid1, b.grid2), std::min(b.grid3a, grid_for((const void *)kb_phase3b<FT>,
+                                                                                    op->sm_count)));
     }
     const int64_t d = op->d, n = op->n;
     const int ge = grid_elems_b(std::max(b.ldw, b.n8), op->sm_count);
