@@ -597,6 +597,8 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
     __shared__ Part red[kBlock * 3];
     __shared__ BatchCoef<FT> cf[kMaxShifts * kTB];
     __shared__ int any[kMaxShifts];
+    __shared__ int s_act[kMaxShifts];
+    __shared__ int s_nact;
     __shared__ FT s_al[kTB];
     __shared__ double s_gam[kTB], s_t[kTB];
     __shared__ float s_gh[kTB], s_gl[kTB], s_tf[kTB];
@@ -655,25 +657,63 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
         dd[2].add(rnj * pk);
     }
     // shift state: P^s_k = zeta r_k + alpha^s P^s_{k-1}; W^s_{k+1} = W^s_k - gamma^s P^s_k
-    // (targets whose shift stopped keep their values); four consecutive targets per thread
-    const int64_t m4 = m / 4;
-    for (int sh = 0; sh < ns; ++sh) {
-        if (!any[sh]) continue;
-        FT *__restrict__ Ps = P + (int64_t)sh * m;
-        FT *__restrict__ Ws = W + (int64_t)sh * m;
-        const BatchCoef<FT> *c = cf + sh * kTB;
-        for (int64_t e4 = tid; e4 < m4; e4 += nthr) {
-            const int64_t e = 4 * e4;
-            const int t0 = (int)(e % kTB);
+    // (targets whose shift stopped keep their values).  Items i = q * nch + c over
+    // the shifts some target still updates (slot q) and 16-byte chunks c of VW
+    // consecutive targets of one feature; (q, c) advance by (nthr / nch, nthr %
+    // nch), two items per thread in flight.
+    {
+        using V = typename Vec16<FT>::T;
+        constexpr int VW = Vec16<FT>::n;
+        constexpr int UNROLL = 2;
+        if (threadIdx.x == 0) {
+            int na = 0;
+            for (int sh = 0; sh < ns; ++sh)
+                if (any[sh]) s_act[na++] = sh;
+            s_nact = na;
+        }
+        __syncthreads();
+        const int nch = (int)(m / VW), nact = s_nact;
+        int q = (int)(tid / nch), c = (int)(tid - (int64_t)q * nch);
+        const int sq = (int)(nthr / nch), sc = (int)(nthr - (int64_t)sq * nch);
+        while (q < nact) {
+            FT r[UNROLL][VW];
+            V pv[UNROLL], wv[UNROLL];
+            int64_t off[UNROLL], e0[UNROLL];
+            int sh_[UNROLL];
+            bool ok[UNROLL];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (!BOK(e + u, ctl->bb.ldw * kTB, 42) || !BOK(sh * kTB + t0 + u, kMaxShifts * kTB, 43)) continue;
-                const BatchCoef<FT> cu = c[t0 + u];
-                if (!cu.active) continue;
-                const FT r = a[e + u].x;
-                const FT pn = cu.z * r + cu.a * Ps[e + u];
-                Ps[e + u] = pn;
-                Ws[e + u] = Ws[e + u] - cu.g * pn;
+            for (int u = 0; u < UNROLL; ++u) {
+                ok[u] = q < nact;
+                sh_[u] = ok[u] ? s_act[q] : 0;
+                e0[u] = (int64_t)c * VW;
+                off[u] = (int64_t)sh_[u] * m + e0[u];
+                ok[u] = ok[u] && BOK(e0[u] + VW - 1, ctl->bb.ldw * kTB, 42);
+                if (ok[u]) {
+                    load_r(a, e0[u], r[u]);
+                    pv[u] = *reinterpret_cast<const V *>(P + off[u]);
+                    wv[u] = *reinterpret_cast<const V *>(W + off[u]);
+                }
+                q += sq;
+                c += sc;
+                if (c >= nch) {
+                    c -= nch;
+                    ++q;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if (!ok[u]) continue;
+                const BatchCoef<FT> *cb = cf + sh_[u] * kTB + (int)(e0[u] % kTB);
+#pragma unroll
+                for (int v = 0; v < VW; ++v) {
+                    const BatchCoef<FT> cu = cb[v];
+                    if (!cu.active) continue;
+                    const FT pn = cu.z * r[u][v] + cu.a * v16_get(pv[u], v);
+                    v16_set(pv[u], v, pn);
+                    v16_set(wv[u], v, v16_get(wv[u], v) - cu.g * pn);
+                }
+                *reinterpret_cast<V *>(P + off[u]) = pv[u];
+                *reinterpret_cast<V *>(W + off[u]) = wv[u];
             }
         }
     }
