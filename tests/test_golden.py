@@ -1,0 +1,101 @@
+"""Stored expected values (tests/golden/small_300x96_fp64.json, written by
+tests/golden/make_golden.py from the FP64 oracle): a 300 x 96 count problem,
+one target, four shifts 1e-1..1e2.
+
+CPU: the oracle still reproduces the stored solutions (bit for bit up to
+1e-12) and they solve the dense definition (B + beta I) w = d of eq. 7 /
+Sec. 3.2.3 to 1e-9.  GPU: the CUDA FP64 path matches the stored solutions to
+1e-9 relative (kappa <= 1e3 on these shifts, both sides converged to 1e-12)
+and the stored AUCs to 4 decimals; the mixed FP16 path reaches 20 x tol in FP64
+true residual.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_04794_gb300 import synth
+
+PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "small_300x96_fp64.json")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    g = json.load(open(PATH))
+    wl = synth.Workload(name="golden", n=g["n"], d=g["d"], nnz_mean=10, values="counts", n_targets=1,
+                        labelled=("fixed", 80), pos_frac=("fixed", 0.3), knn_k=5, alpha=g["alpha"],
+                        shifts=(1e-1, 1e2, 4), seed=1709, value_dtype="f64")
+    p = synth.Problem(wl, np.asarray(g["x_ptr"], np.int64), np.asarray(g["x_col"], np.int32),
+                      np.asarray(g["x_val"], np.float64), np.asarray(g["s_ptr"], np.int64),
+                      np.asarray(g["s_col"], np.int32), np.asarray(g["s_val"], np.float64),
+                      np.asarray([g["labels"]], np.int8), np.asarray([g["truth"]], np.int8),
+                      [np.asarray(g["heldout"], np.int64)], np.asarray(g["shifts"]), g["alpha"])
+    return p, g
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_golden_oracle_reproduces(golden):
+    p, g = golden
+    o = oracle.from_problem(p)
+    b = o.rhs_canonical()
+    assert np.array_equal(b, np.asarray(g["rhs"]))
+    res = o.shifted_cg(b, p.shifts, tol=1e-13, max_iter=50000)
+    W = np.asarray(g["w"])
+    for s in range(len(p.shifts)):
+        assert _rel(res.W[s], W[s]) < 1e-12, s
+    assert res.iters.tolist() == g["iters"]
+
+
+def test_golden_solves_dense_definition(golden):
+    p, g = golden
+    X = oracle.dense_x(p.x_ptr, p.x_col, p.x_val, p.d)
+    B = oracle.dense_operator(X, p.s_ptr, p.s_col, p.s_val, p.labels[0], p.alpha)
+    b = np.asarray(g["rhs"])
+    for s, beta in enumerate(p.shifts):
+        w = np.linalg.solve(B + beta * np.eye(p.d), b)
+        assert _rel(np.asarray(g["w"][s]), w) < 1e-9, s
+
+
+@pytest.mark.gpu
+def test_golden_gpu_fp64(golden):
+    import torch
+    from paper_1709_04794_gb300 import sda
+    p, g = golden
+    op = sda.Operator(p, compute="f64")
+    ns = len(p.shifts)
+    w = torch.empty((1, ns, p.d), dtype=torch.float64, device="cuda")
+    o = sda.sda_default_opts()
+    o.tol, o.max_iter = 1e-12, 20000
+    code, rep = sda.sda_solve_shifts(op.handle, p.shifts, o, w_out=w, n_report=1)
+    assert code == sda.SDA_OK
+    W = w[0].cpu().numpy()
+    X = oracle.dense_x(p.x_ptr, p.x_col, p.x_val, p.d)
+    rows = np.asarray(g["heldout"])
+    for s in range(ns):
+        assert _rel(W[s], np.asarray(g["w"][s])) < 1e-9, s
+        assert abs(oracle.auc(X[rows] @ W[s], p.truth[0][rows]) - g["auc"][s]) < 5e-5
+
+
+@pytest.mark.gpu
+def test_golden_gpu_mixed(golden):
+    import torch
+    from paper_1709_04794_gb300 import sda
+    p, g = golden
+    op = sda.Operator(p, compute="f16")
+    ns = len(p.shifts)
+    w = torch.empty((1, ns, p.d), dtype=torch.float64, device="cuda")
+    o = sda.sda_default_opts()
+    tol = 1e-6
+    o.tol, o.max_iter = tol, 20000
+    code, rep = sda.sda_solve_shifts(op.handle, p.shifts, o, w_out=w, n_report=1)
+    assert code == sda.SDA_OK
+    ob = oracle.from_problem(p)
+    b = ob.rhs_canonical()
+    W = w[0].cpu().numpy()
+    for s, beta in enumerate(p.shifts):
+        assert ob.true_residual(b, beta, W[s]) < 20 * tol, s
