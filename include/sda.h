@@ -127,6 +127,24 @@ SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, const sda_lab
                                double alpha, double scatter_weight, sda_dtype compute,
                                void *cuda_stream, sda_operator **out);
 
+/*
+ * sda_build_regression - the operator of the regression step of CSR-SDA
+ * (Algorithm 5, line 5: shifted CG on (X^T X + beta I) w = X^T z), B = X^T X:
+ * the same device layouts of X as sda_build_operator, with no graph, every
+ * row weighted one and no centring.  One target (index 0).
+ * sda_solve_shifts on it takes rhs_mode SDA_RHS_GIVEN (b = X^T z, computed by
+ * the caller) and the operator's weights (opts alpha and scatter_weight NaN);
+ * other modes return INVALID_ARG.  sda_project gives X w; sda_adjoint_grad
+ * returns UNSUPPORTED.
+ *
+ *   X, compute, cuda_stream, out   as for sda_build_operator
+ *
+ * Errors: INVALID_ARG, SHAPE, INDEX, VALUE_NOT_EXACT, CUDA, OOM.  *out is
+ * NULL on error.
+ */
+SDA_API int sda_build_regression(const sda_csr *X, sda_dtype compute_values, void *cuda_stream,
+                                 sda_operator **out);
+
 /* Right-hand side of the solve (Alg. 7 step 4). */
 enum {
     SDA_RHS_CANONICAL = 0,  /* b = d = mu_+ - mu_- (positives score high)                          */

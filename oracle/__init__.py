@@ -9,7 +9,9 @@ Functions and what they follow:
 
 * :class:`Oracle`            - the C oracle: mu_l (Alg. 7 step 3), the
   operator in the paper's form (Alg. 7 step 4, Sec. 3.2.3), the RHS of
-  Alg. 7 step 4, CG (Alg. 2), shifted CG (Alg. 3), s = X w (Sec. 4).
+  Alg. 7 step 4, CG (Alg. 2), shifted CG (Alg. 3), s = X w (Sec. 4);
+  ``Oracle.regression``: B = X^T X of CSR-SDA's regression step (Alg. 5,
+  line 5).
 * :func:`dense_scatter_labelled` - S_t^l = sum_{i in l} (x_i - mu_l)(x_i - mu_l)^T
   (total labelled scatter, eq. 7 with centring of Sec. 2.5.2).
 * :func:`dense_manifold`     - X^T L X from the regulariser
@@ -67,6 +69,8 @@ def _load(path: str):
     vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     lib.oracle_create.restype = vp
     lib.oracle_create.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, vp, f64, f64]
+    lib.oracle_create_regression.restype = vp
+    lib.oracle_create_regression.argtypes = [i64, i64, vp, vp, vp, vp, vp]
     lib.oracle_destroy.argtypes = [vp]
     lib.oracle_destroy.restype = None
     lib.oracle_set_threads.argtypes = [i32]
@@ -130,6 +134,21 @@ class Oracle:
                                           self.alpha, self.omega)
         if not self._h:
             raise ValueError("oracle_create failed (allocation or column index out of range)")
+
+    @classmethod
+    def regression(cls, x_ptr, x_col, x_val, d, so_path: str | None = None):
+        """B = X^T X, the operator of CSR-SDA's regression step (Algorithm 5, line 5)."""
+        self = cls.__new__(cls)
+        self._lib = lib(so_path)
+        self.n = int(np.asarray(x_ptr).size - 1)
+        self.d = int(d)
+        self._keep = [_c(x_ptr, np.int64), _c(x_col, np.int32), _c(x_val, np.float64),
+                      np.zeros(self.n + 1, np.int64), np.ones(self.n, np.int8)]
+        self.alpha, self.omega = 0.0, 1.0
+        self._h = self._lib.oracle_create_regression(self.n, self.d, *(a.ctypes.data for a in self._keep))
+        if not self._h:
+            raise ValueError("oracle_create_regression failed (allocation or column index out of range)")
+        return self
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -160,6 +160,19 @@ oracle_problem *oracle_create(int64_t n, int64_t d,
     return P;
 }
 
+/* The operator of CSR-SDA's regression step (Algorithm 5, line 5: shifted CG
+ * on (X^T X + beta I) w = X^T z): B = X^T X, i.e. the operator above with no
+ * graph, every row labelled (P_l = I), alpha = 0, omega = 1 and no centring
+ * (mu_l = 0).  sp_zero: n + 1 zero row pointers, y_ones: n labels +1, kept
+ * alive by the caller.  NULL on error. */
+oracle_problem *oracle_create_regression(int64_t n, int64_t d, const int64_t *xp, const int32_t *xc,
+                                         const double *xv, const int64_t *sp_zero, const int8_t *y_ones)
+{
+    oracle_problem *P = oracle_create(n, d, xp, xc, xv, sp_zero, NULL, NULL, y_ones, 0.0, 1.0);
+    if (P) memset(P->mu, 0, (size_t)(d > 0 ? d : 1) * sizeof(double));
+    return P;
+}
+
 /* Class counts and means: mu_l, mu_+ = X^T 1_+ / N_+, mu_- = X^T 1_- / N_-. */
 void oracle_class_means(const oracle_problem *P, double *mu_l, double *mu_pos, double *mu_neg,
                         double *counts /* [ell, N+, N-] */)

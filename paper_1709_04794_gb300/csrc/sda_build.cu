@@ -674,6 +674,15 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
     SDA_TRY(op->mu32.alloc((size_t)(T * d)));
     SDA_TRY(op->dvec.alloc((size_t)(T * d)));
     op->counts.assign((size_t)T * 3, 0.0);
+    if (op->regression) {
+        // X^T X of the regression phase: every row counts, nothing is centred
+        SDA_CUDA(cudaMemsetAsync(op->mu.p, 0, op->mu.bytes(), s));
+        SDA_CUDA(cudaMemsetAsync(op->mu32.p, 0, op->mu32.bytes(), s));
+        SDA_CUDA(cudaMemsetAsync(op->dvec.p, 0, op->dvec.bytes(), s));
+        op->counts[0] = op->counts[1] = (double)n;
+        SDA_CUDA(cudaStreamSynchronize(s));
+        return SDA_OK;
+    }
     {
         DevBuf<double> ip, in_, sp, sn;
         DevBuf<unsigned long long> c2;
@@ -709,10 +718,9 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
 
 using namespace sda;
 
-extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, const sda_labels *y, double alpha,
-                                          double scatter_weight, sda_dtype compute, void *cuda_stream,
-                                          sda_operator **out) {
-    clear_error();
+static int build_entry(const sda_csr *X, const sda_csr *S, const sda_labels *y, double alpha,
+                       double scatter_weight, sda_dtype compute, void *cuda_stream, sda_operator **out,
+                       bool regression) {
     if (!out) return fail(SDA_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!X || !S || !y) return fail(SDA_ERR_INVALID_ARG, "X, S and y must not be NULL");
@@ -744,6 +752,7 @@ extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, co
     op->alpha = alpha;
     op->omega = omega;
     op->omega_follows_alpha = isnan(scatter_weight);
+    op->regression = regression;
     op->sm_count = device_sm_count();
     if (op->sm_count <= 0) {
         delete op;
@@ -766,4 +775,27 @@ extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, co
                           op->srow.splits.bytes());
     *out = op;
     return SDA_OK;
+}
+
+extern "C" SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, const sda_labels *y, double alpha,
+                                          double scatter_weight, sda_dtype compute, void *cuda_stream,
+                                          sda_operator **out) {
+    clear_error();
+    return build_entry(X, S, y, alpha, scatter_weight, compute, cuda_stream, out, false);
+}
+
+extern "C" SDA_API int sda_build_regression(const sda_csr *X, sda_dtype compute, void *cuda_stream,
+                                            sda_operator **out) {
+    clear_error();
+    if (!out) return fail(SDA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!X) return fail(SDA_ERR_INVALID_ARG, "X must not be NULL");
+    if (X->n_rows <= 0 || X->n_rows > INT32_MAX) return fail(SDA_ERR_SHAPE, "X must have 1 .. 2^31 - 1 rows");
+    // the SDA operator with an empty graph, every row labelled (P_l = I),
+    // alpha = 0, omega = 1; the build then drops the centring (mu = 0)
+    std::vector<int64_t> sp((size_t)X->n_rows + 1, 0);
+    std::vector<int8_t> lab((size_t)X->n_rows, 1);
+    const sda_csr S{X->n_rows, X->n_rows, 0, sp.data(), nullptr, nullptr, SDA_F64, 0};
+    const sda_labels y{1, lab.data(), 0};
+    return build_entry(X, &S, &y, 0.0, 1.0, compute, cuda_stream, out, true);
 }

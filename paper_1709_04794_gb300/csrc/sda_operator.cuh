@@ -112,6 +112,7 @@ struct sda_operator {
     sda_dtype compute = SDA_F64;
     double alpha = 0.0, omega = 1.0;
     bool omega_follows_alpha = true;     // built with a NaN scatter weight: omega = 1 - alpha
+    bool regression = false;             // B = X^T X (sda_build_regression): no centring, alpha and omega fixed
     int sm_count = 0;
 
     // feature order: columns sorted by descending count (new index = rank)

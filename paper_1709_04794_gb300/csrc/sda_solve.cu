@@ -724,6 +724,8 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
     if (t0 < 0 || tc < 0 || t0 + tc > op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target range out of bounds");
     if (o.rhs_mode != SDA_RHS_CANONICAL && !o.rhs) return fail(SDA_ERR_INVALID_ARG, "rhs is NULL");
     if (o.rhs_mode < 0 || o.rhs_mode > SDA_RHS_GIVEN) return fail(SDA_ERR_INVALID_ARG, "bad rhs_mode");
+    if (op->regression && (o.rhs_mode != SDA_RHS_GIVEN || !isnan(o.alpha) || !isnan(o.scatter_weight)))
+        return fail(SDA_ERR_INVALID_ARG, "a regression operator takes a given right-hand side and no weights");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     double alpha = 0.0, omega = 0.0;
     SDA_TRY(call_weights(op, o, &alpha, &omega));
@@ -828,6 +830,7 @@ extern "C" SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double
     if (n_rows < 0 || (n_rows > 0 && (!rows || !dloss_ds))) return fail(SDA_ERR_INVALID_ARG, "bad held-out rows");
     if (target < 0 || target >= op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target out of range");
     if (!(beta > 0.0) || !isfinite(beta)) return fail(SDA_ERR_INVALID_ARG, "beta must be finite and > 0");
+    if (op->regression) return fail(SDA_ERR_UNSUPPORTED, "the adjoint is defined for SDA operators only");
     sda_solve_opts o;
     if (opt) {
         o = *opt;

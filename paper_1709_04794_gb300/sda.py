@@ -80,6 +80,7 @@ _SIGS = {
     "sda_build_operator": (ctypes.c_int, [ctypes.POINTER(sda_csr), ctypes.POINTER(sda_csr),
                                           ctypes.POINTER(sda_labels), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "sda_build_regression": (ctypes.c_int, [ctypes.POINTER(sda_csr), ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "sda_default_opts": (None, [ctypes.POINTER(sda_solve_opts)]),
     "sda_solve_shifts": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(sda_solve_opts), _vp,
                                         ctypes.POINTER(sda_shift_report), _vp]),
@@ -198,6 +199,19 @@ def sda_build_operator(x_ptr, x_col, x_val, n_cols, s_ptr, s_col, s_val, labels,
     return out.value
 
 
+def sda_build_regression(x_ptr, x_col, x_val, n_cols, compute="f64", stream=None):
+    """Calls sda_build_regression (B = X^T X); returns the opaque operator handle (int)."""
+    lib = load()
+    keep = []
+    n = int(x_ptr.shape[0]) - 1
+    X = _csr(x_ptr, x_col, x_val, n, n_cols, keep)
+    out = _vp()
+    comp = DTYPES[compute] if isinstance(compute, str) else int(compute)
+    _check(lib.sda_build_regression(ctypes.byref(X), comp, _stream(stream), ctypes.byref(out)),
+           "sda_build_regression")
+    return out.value
+
+
 def sda_default_opts() -> sda_solve_opts:
     o = sda_solve_opts()
     load().sda_default_opts(ctypes.byref(o))
@@ -310,6 +324,14 @@ def exported_symbols() -> list:
 
 class Operator:
     """Owns one sda_operator handle (released on close / garbage collection)."""
+
+    @classmethod
+    def regression(cls, x_ptr, x_col, x_val, n_cols, compute="f64", stream=None):
+        """The X^T X operator of CSR-SDA's regression step (sda_build_regression)."""
+        self = cls.__new__(cls)
+        self.handle = sda_build_regression(x_ptr, x_col, x_val, n_cols, compute, stream)
+        self.info = sda_get_operator_info(self.handle)
+        return self
 
     def __init__(self, prob=None, compute="f64", alpha=None, scatter_weight=float("nan"), stream=None,
                  device_inputs=False, targets=None, **arrays):

@@ -373,3 +373,20 @@ def test_dense_adjoint_gradient_equals_finite_differences(tiny):
     lm = oracle.adjoint_grad_dense(*args, alpha, beta * np.exp(-h), rows, yr)[0]
     # d/d(log beta) = beta d/d beta
     assert abs((lp - lm) / (2 * h) - beta * db) <= 1e-6 * max(1.0, abs(beta * db))
+
+
+def test_regression_operator_is_xtx():
+    """CSR-SDA's regression step (Algorithm 5, line 5): the oracle's regression
+    operator is X^T X + sigma I, and its shifted CG reaches the dense solutions
+    of (X^T X + beta I) w = X^T z."""
+    p = synth.custom_problem(150, 40, 7, seed=13, values="counts", shifts=(1e-1, 1e1, 3))
+    o = oracle.Oracle.regression(p.x_ptr, p.x_col, p.x_val, p.d)
+    X = oracle.dense_x(p.x_ptr, p.x_col, p.x_val, p.d)
+    x = np.random.default_rng(2).standard_normal(p.d)
+    assert np.linalg.norm(o.apply(x, 0.3) - (X.T @ (X @ x) + 0.3 * x)) < 1e-10 * np.linalg.norm(x) * np.linalg.norm(X) ** 2
+    z = np.random.default_rng(4).uniform(-1.0, 1.0, p.n)
+    b = X.T @ z
+    res = o.shifted_cg(b, p.shifts, tol=1e-13, max_iter=5000)
+    for s, beta in enumerate(p.shifts):
+        w = np.linalg.solve(X.T @ X + beta * np.eye(p.d), b)
+        assert np.linalg.norm(res.W[s] - w) < 1e-9 * np.linalg.norm(w)
