@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="single_mixed_200k (default); batched_256t_200k: 256 targets solved in batches of "
                          "16 that share every pass over X and S; regression_200k: CSR-SDA's regression step "
-                         "(X^T X + beta I) w = X^T z on the same X")
+                         "(X^T X + beta I) w = X^T z on the same X; sa_200k: SA-SDA, the SDA operator with X = I_N on the "
+                         "same graph and labels")
     ap.add_argument("--targets", type=int, default=0, help="batched workload: solve only the first T targets")
     return ap.parse_args()
 
@@ -447,8 +448,90 @@ def run_regression(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_sa(args, rank, world, local):
+    """SA-SDA (Algorithm 6) on the graph and labels of the default workload: the
+    SDA operator with X = I_N (N = 200,000 unknowns), its 32 shifts, tol 1e-3;
+    a step = build + solve + FP64 residual check; the rating is the solution."""
+    import dataclasses
+    import torch
+    from paper_1709_04794_gb300 import sda, synth
+    prob = synth.make_problem(WORKLOAD)
+    compute = args.compute or prob.workload.value_dtype
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    n, ns = prob.n, len(prob.shifts)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k))).cuda()
+           for k in ("s_ptr", "s_col", "s_val", "labels")}
+    z = torch.empty((1, ns, n), dtype=torch.float64, device="cuda")
+
+    def opts(profile=0):
+        o = sda.sda_default_opts()
+        o.tol, o.max_iter, o.check_residual, o.profile = args.tol, args.max_iter, 1, profile
+        return o
+
+    def step(profile=0):
+        h = sda.sda_build_sa(dev["s_ptr"], dev["s_col"], dev["s_val"], dev["labels"], prob.alpha, float("nan"),
+                             compute, stream)
+        try:
+            code, rep = sda.sda_solve_shifts(h, prob.shifts, opts(profile), w_out=z, n_report=1, stream=stream)
+            stats = sda.sda_get_solve_stats(h)
+            stats["info"] = sda.sda_get_operator_info(h)
+        finally:
+            sda.sda_destroy_operator(h)
+        return code, rep, stats
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sda.sda_kernel_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        code, rep, stats = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = sda.sda_kernel_launch_count() - l0
+    clk = clocks.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    pcode, prep, pst = step(profile=1)
+    iters = max(1, pst["iterations"])
+    ident = synth.Problem(dataclasses.replace(prob.workload, d=n), np.arange(n + 1, dtype=np.int64),
+                          np.arange(n, dtype=np.int32), np.ones(n), prob.s_ptr, prob.s_col, prob.s_val,
+                          prob.labels, prob.truth, prob.heldout, prob.shifts, prob.alpha)
+    per = algorithmic_bytes(ident, compute, pst["iterations"], pst["shift_iterations"], pst["info"])
+    durs = {k: pst["ms"][i + 1] / iters for i, k in enumerate(("phase1", "phase2", "phase3a", "phase3b"))}
+    dominant = max(durs, key=durs.get)
+    peak, peak_kind = load_peaks()
+    names = {"phase1": "k_rowhead (rows of I)", "phase2": "k_rowpass<EpiP2> (rows of S)",
+             "phase3a": "k_colblk (columns of I, shift stream)", "phase3b": "k_cg_phase3b (vector stream)"}
+    achieved = per[dominant] / (durs[dominant] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": names[dominant], "peak_kind": peak_kind,
+                "bytes_per_launch": per[dominant], "ms_per_launch": durs[dominant],
+                "all_kernels": {names[k]: {"ms_per_launch": durs[k], "GB/s": per[k] / (durs[k] * 1e-3) / 1e9}
+                                for k in durs}}
+    line = {"metric": "SA-SDA solves/s (all shifts)", "value": args.steps / t, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if compute != "f64" else "f64", "data": "synthetic",
+            "config": {"workload": "sa_200k", "n": n, "graph_nnz": int(prob.s_ptr[-1]), "shifts": ns,
+                       "tol": args.tol, "alpha": prob.alpha, "iterations": stats["iterations"],
+                       "shift_iterations": stats["shift_iterations"], "status": code,
+                       "max_true_residual": max(r["true_residual"] for r in rep[0])},
+            "roofline": roofline, "cpu_baseline": None, "e2e": None, "clocks": clk, "gpu_launches": int(launches)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "sa_200k" and args.impl == "ours":
+        run_sa(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+               int(os.environ.get("LOCAL_RANK", "0")))
+        return
     if args.workload == "regression_200k" and args.impl == "ours":
         run_regression(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
                        int(os.environ.get("LOCAL_RANK", "0")))

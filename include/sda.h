@@ -145,6 +145,22 @@ SDA_API int sda_build_operator(const sda_csr *X, const sda_csr *S, const sda_lab
 SDA_API int sda_build_regression(const sda_csr *X, sda_dtype compute_values, void *cuda_stream,
                                  sda_operator **out);
 
+/*
+ * sda_build_sa - the operator of SA-SDA (Algorithm 6): the SDA operator with
+ * the identity I_N as the data matrix, B = (I - 1 1_l^T / l)^T M, M = omega P_l
+ * + alpha L, over N-vectors (= M - omega 1_l 1_l^T / l, symmetric, since
+ * M 1 = omega 1_l).  The canonical right-hand side d = 1_+ / N+ - 1_- / N- is
+ * the direction of Algorithm 6's [W 0; 0 0] r for any r orthogonal to 1_l; the
+ * solution z is the rating itself (s = z).  Every solve option applies.
+ *
+ *   S, y, alpha, scatter_weight, compute, cuda_stream, out
+ *                  as for sda_build_operator (X is I_N, built internally)
+ *
+ * Errors: as for sda_build_operator.
+ */
+SDA_API int sda_build_sa(const sda_csr *S, const sda_labels *y, double alpha, double scatter_weight,
+                         sda_dtype compute_values, void *cuda_stream, sda_operator **out);
+
 /* Right-hand side of the solve (Alg. 7 step 4). */
 enum {
     SDA_RHS_CANONICAL = 0,  /* b = d = mu_+ - mu_- (positives score high)                          */

@@ -799,3 +799,20 @@ extern "C" SDA_API int sda_build_regression(const sda_csr *X, sda_dtype compute,
     const sda_labels y{1, lab.data(), 0};
     return build_entry(X, &S, &y, 0.0, 1.0, compute, cuda_stream, out, true);
 }
+
+extern "C" SDA_API int sda_build_sa(const sda_csr *S, const sda_labels *y, double alpha, double scatter_weight,
+                                    sda_dtype compute, void *cuda_stream, sda_operator **out) {
+    clear_error();
+    if (!out) return fail(SDA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!S) return fail(SDA_ERR_INVALID_ARG, "S must not be NULL");
+    if (S->n_rows <= 0 || S->n_rows > INT32_MAX) return fail(SDA_ERR_SHAPE, "S must have 1 .. 2^31 - 1 rows");
+    // the SDA operator with the identity as the data matrix (Algorithm 6): X = I_N
+    const int64_t n = S->n_rows;
+    std::vector<int64_t> xp((size_t)n + 1);
+    std::vector<int32_t> xc((size_t)n);
+    for (int64_t i = 0; i <= n; ++i) xp[(size_t)i] = i;
+    for (int64_t i = 0; i < n; ++i) xc[(size_t)i] = (int32_t)i;
+    const sda_csr X{n, n, n, xp.data(), xc.data(), nullptr, SDA_PATTERN, 0};
+    return build_entry(&X, S, y, alpha, scatter_weight, compute, cuda_stream, out, false);
+}

@@ -81,6 +81,8 @@ _SIGS = {
                                           ctypes.POINTER(sda_labels), ctypes.c_double, ctypes.c_double,
                                           ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "sda_build_regression": (ctypes.c_int, [ctypes.POINTER(sda_csr), ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "sda_build_sa": (ctypes.c_int, [ctypes.POINTER(sda_csr), ctypes.POINTER(sda_labels), ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
     "sda_default_opts": (None, [ctypes.POINTER(sda_solve_opts)]),
     "sda_solve_shifts": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(sda_solve_opts), _vp,
                                         ctypes.POINTER(sda_shift_report), _vp]),
@@ -212,6 +214,23 @@ def sda_build_regression(x_ptr, x_col, x_val, n_cols, compute="f64", stream=None
     return out.value
 
 
+def sda_build_sa(s_ptr, s_col, s_val, labels, alpha, scatter_weight=float("nan"), compute="f64", stream=None):
+    """Calls sda_build_sa (SA-SDA: the SDA operator with X = I_N); returns the operator handle (int)."""
+    lib = load()
+    keep = []
+    n = int(s_ptr.shape[0]) - 1
+    S = _csr(s_ptr, s_col, s_val, n, n, keep)
+    lp, ldev, lk = _ptr(labels)
+    keep.append(lk)
+    nt = int(labels.shape[0]) if len(labels.shape) == 2 else 1
+    Y = sda_labels(nt, lp, ldev)
+    out = _vp()
+    comp = DTYPES[compute] if isinstance(compute, str) else int(compute)
+    _check(lib.sda_build_sa(ctypes.byref(S), ctypes.byref(Y), float(alpha), float(scatter_weight), comp,
+                            _stream(stream), ctypes.byref(out)), "sda_build_sa")
+    return out.value
+
+
 def sda_default_opts() -> sda_solve_opts:
     o = sda_solve_opts()
     load().sda_default_opts(ctypes.byref(o))
@@ -330,6 +349,14 @@ class Operator:
         """The X^T X operator of CSR-SDA's regression step (sda_build_regression)."""
         self = cls.__new__(cls)
         self.handle = sda_build_regression(x_ptr, x_col, x_val, n_cols, compute, stream)
+        self.info = sda_get_operator_info(self.handle)
+        return self
+
+    @classmethod
+    def sa(cls, s_ptr, s_col, s_val, labels, alpha, scatter_weight=float("nan"), compute="f64", stream=None):
+        """The SA-SDA operator (sda_build_sa): the SDA operator with X = I_N."""
+        self = cls.__new__(cls)
+        self.handle = sda_build_sa(s_ptr, s_col, s_val, labels, alpha, scatter_weight, compute, stream)
         self.info = sda_get_operator_info(self.handle)
         return self
 

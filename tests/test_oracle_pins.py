@@ -390,3 +390,38 @@ def test_regression_operator_is_xtx():
     for s, beta in enumerate(p.shifts):
         w = np.linalg.solve(X.T @ X + beta * np.eye(p.d), b)
         assert np.linalg.norm(res.W[s] - w) < 1e-9 * np.linalg.norm(w)
+
+
+def _identity_x(n):
+    return np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n)
+
+
+def test_sa_sda_operator_with_identity_data():
+    """SA-SDA (Algorithm 6) is the SDA operator with X = I_N: the oracle's
+    paper form (I - 1_l 1^T / l) M equals the symmetric M - omega 1_l 1_l^T / l
+    (M 1 = omega 1_l), and its canonical direction d = 1_+/N+ - 1_-/N- is
+    parallel to Algorithm 6's [W 0; 0 0] r for r orthogonal to 1_l."""
+    p = synth.custom_problem(180, 30, 6, seed=17, values="binary", n_labelled=60, k=5)
+    n, y, a = p.n, p.labels[0], p.alpha
+    om = 1.0 - a
+    xp, xc, xv = _identity_x(n)
+    o = oracle.Oracle(xp, xc, xv, p.s_ptr, p.s_col, p.s_val, y, n, a)
+    Sd = np.zeros((n, n))
+    for i in range(n):
+        Sd[i, p.s_col[p.s_ptr[i]:p.s_ptr[i + 1]]] = p.s_val[p.s_ptr[i]:p.s_ptr[i + 1]]
+    L = np.diag(Sd.sum(1)) - Sd
+    one_l = (y != 0).astype(float)
+    ell = one_l.sum()
+    Mt = om * np.diag(one_l) + a * L - om * np.outer(one_l, one_l) / ell
+    x = np.random.default_rng(5).standard_normal(n)
+    assert np.linalg.norm(o.apply(x, 0.2) - (Mt @ x + 0.2 * x)) < 1e-12 * np.linalg.norm(x) * max(1.0, np.abs(Mt).max())
+    pos, neg = (y > 0).astype(float), (y < 0).astype(float)
+    r = np.random.default_rng(6).uniform(-1.0, 1.0, n)
+    r = r - (one_l @ r) / ell                  # Algorithm 6, orthogonalisation: r - 1 <1_l, r> / l
+    Wr = pos * (pos @ r) / pos.sum() + neg * (neg @ r) / neg.sum()
+    d = o.rhs_canonical()
+    assert np.linalg.norm(Wr - (pos @ r) * d) < 1e-12 * np.linalg.norm(Wr)
+    res = o.shifted_cg(d, p.shifts, tol=1e-13, max_iter=5000)
+    for s, beta in enumerate(p.shifts):
+        z = np.linalg.solve(Mt + beta * np.eye(n), d)
+        assert np.linalg.norm(res.W[s] - z) < 1e-9 * np.linalg.norm(z)
