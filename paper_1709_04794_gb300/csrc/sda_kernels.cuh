@@ -4,28 +4,27 @@
 //   (B + sigma0 I) p = (X - 1 mu^T)^T M (X - 1 mu^T) p + sigma0 p,
 //   M = omega P_l + alpha L,  L = D - S                        (eq. 7, Alg. 7, Sec. 3.2.3)
 // runs as four kernels:
-//   phase 1  (rows of X):     ut = X p_k - <mu, p_k> 1   (p_k = r_k + alpha_k p_{k-1} formed at the gather)
-//   phase 2  (rows of S):     v = omega P_l ut + alpha (D ut - S ut);  <ut, v>, 1^T v
-//                             -> gamma_k, zeta^s_{k+1}, gamma^s_k
-//   phase 3a (columns of X):  s_r = X_r^T v for each range r of rows
-//   phase 3b (stream over D): s = sum_r s_r;  q = s - mu (1^T v) + sigma0 p_k;  r_{k+1} = r_k + gamma_k q;
-//                             P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1};  W^s_{k+1} = W^s_k - gamma^s_k P^s_k;
-//                             <r,r>, <mu,r>, <r,p_k>  -> alpha_{k+1}, <mu,p_{k+1}>, <p_{k+1},p_{k+1}>, stop tests
+//   phase 1  (rows of X, k_rowhead):  ut = X p_k - <mu, p_k> 1   (p_k = r_k + alpha_k p_{k-1};
+//                             its frequent head formed once per block in shared memory)
+//   phase 2  (rows of S, k_rowpass<EpiP2>):  v = omega P_l ut + alpha (D ut - S ut);
+//                             block parts of <ut, v> and 1^T v
+//   phase 3a (columns of X, k_colblk):  s_r = X_r^T v for each range r of rows; its stream
+//                             warps close phase 2 (gamma_k, zeta^s_{k+1} / zeta^s_k, gamma^s_k)
+//                             and update P^s_k = zeta^s_k r_k + alpha^s_k P^s_{k-1},
+//                             W^s_{k+1} = W^s_k - gamma^s_k P^s_k for the active shifts
+//   phase 3b (stream over D, k_cg_phase3b):  s = sum_r s_r;  q = s - mu (1^T v) + sigma0 p_k;
+//                             r_{k+1} = r_k + gamma_k q;  <r,r>, <mu,r>, <r,p_k>
+//                             -> alpha_{k+1}, <mu,p_{k+1}>, <p_{k+1},p_{k+1}>, stop tests
 // <p, (B + sigma0) p> = <ut, v> + sigma0 <p, p> is known after phase 2, so q is
 // never stored; <mu, p> and <p, p> follow from recurrences on the phase-3b dots.
-// The scalar work of a phase runs in the block that finishes last (no block
-// ever waits for another).
+// The scalar work of phase 3b runs in the block that finishes last, that of
+// phase 2 in every block of phase 3a from phase 2's block parts (no block ever
+// waits for another).
 //
-// The row passes (X, S) use k_rowpass: G lanes per row with unrolled,
-// independent loads and register sums.  The column pass of the iteration
-// (X^T, Zipf-skewed column lengths, features ordered by decreasing frequency)
-// uses k_colblk: X split into ranges of rows whose slice of v fits a block's
-// shared memory, tiles of consecutive columns within a range (register groups
-// for short and medium columns, whole-block tiles for long ones, split across
-// blocks when longer than kTileNnz), every gather served from shared memory.
-// k_colpass (the same tiles over the whole CSC, gathers from global memory)
-// serves the FP64 operator pieces; k_segpass (shared-memory staged tiles) the
-// allocation-free operator apply.
+// k_rowpass (G lanes per row, unrolled independent loads, register sums) serves
+// the rows of S and the FP64 operator pieces; k_colpass (column tiles over the
+// whole CSC, gathers from global memory) the FP64 operator pieces; k_segpass
+// (shared-memory staged tiles) the allocation-free operator apply.
 #pragma once
 
 #include "sda_operator.cuh"
@@ -241,24 +240,6 @@ struct GatherVec {
     __device__ __forceinline__ AccT operator()(int32_t j) const { return (AccT)v[j]; }
 };
 
-// p_k,j = r_k,j + alpha_k p_{k-1,j} from the interleaved buffer of iteration k
-template <class FT>
-struct GatherP {
-    const typename RPair<FT>::T *base;   // [2][ldw]
-    int64_t ldw;
-    const SolveState *st;
-    const typename RPair<FT>::T *a;
-    FT alpha;
-    __device__ __forceinline__ void begin() {
-        a = base + (st->k & 1) * ldw;
-        alpha = (FT)st->alpha;
-    }
-    __device__ __forceinline__ FT operator()(int32_t j) const {
-        const typename RPair<FT>::T x = a[j];
-        return form_p<FT>(x.x, x.y, alpha);
-    }
-};
-
 // ---------------------------------------------------------------------------
 // epilogues
 // ---------------------------------------------------------------------------
@@ -325,23 +306,6 @@ struct EpiApply {
     __device__ __forceinline__ void segment(int64_t j, double s) { q[j] = s - mu[j] * tv + sigma * p[j]; }
     __device__ __forceinline__ void segment_block(int64_t j, double s) {
         if (threadIdx.x == 0) segment(j, s);
-    }
-    __device__ __forceinline__ void end(Shared &) {}
-};
-
-// phase 1: ut_i = sum - <mu, p_k>
-template <class FT>
-struct EpiP1 {
-    using Shared = NoShared;
-    FT *ut;
-    const SolveState *st;
-    FT c;
-    SDA_TILE_PER_SEGMENT
-    __device__ __forceinline__ bool skip() const { return st->done != 0; }
-    __device__ __forceinline__ void begin(Shared &) { c = (FT)st->c; }
-    __device__ __forceinline__ void segment(int64_t i, FT s) { ut[i] = s - c; }
-    __device__ __forceinline__ void segment_block(int64_t i, FT s) {
-        if (threadIdx.x == 0) segment(i, s);
     }
     __device__ __forceinline__ void end(Shared &) {}
 };
