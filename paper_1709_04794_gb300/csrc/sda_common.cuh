@@ -345,6 +345,10 @@ constexpr double kRowHeadCover = 0.85;
 constexpr int64_t kRowHeadMax = 32768;
 constexpr int kWarpTileSegs = 128;
 constexpr int kWarpBigSeg = 128;
+// Chunk of a long column in one whole-warp tile, and the quads a lane loads at
+// once there (kWarpChunkNnz / 128).
+constexpr int kWarpChunkNnz = 1024;
+constexpr int kWarpChunkQpl = kWarpChunkNnz / 128;
 // Shared memory the blocked column pass keeps for itself besides the slice.
 constexpr int kColBlkReserve = 2048;
 // Per-warp scratch of the blocked column pass after the slice: the quad sums of

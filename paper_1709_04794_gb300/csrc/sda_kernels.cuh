@@ -969,15 +969,12 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
         const int64_t q0 = tl.nz0 >> 2;
         const int nq = (int)((tl.nz1 >> 2) - q0);
         CS acc;
-        for (int qb = lane32; qb < nq; qb += 4 * 32) {
-            const AccT a0 = quad(q0 + qb, true);
-            const AccT a1 = quad(q0 + qb + 32, qb + 32 < nq);
-            const AccT a2 = quad(q0 + qb + 64, qb + 64 < nq);
-            const AccT a3 = quad(q0 + qb + 96, qb + 96 < nq);
-            acc.add(a0);
-            acc.add(a1);
-            acc.add(a2);
-            acc.add(a3);
+        for (int qb = lane32; qb < nq; qb += kWarpChunkQpl * 32) {
+            AccT a[kWarpChunkQpl];
+#pragma unroll
+            for (int u = 0; u < kWarpChunkQpl; ++u) a[u] = quad(q0 + qb + 32 * u, qb + 32 * u < nq);
+#pragma unroll
+            for (int u = 0; u < kWarpChunkQpl; ++u) acc.add(a[u]);
         }
         for (int o = 16; o > 0; o >>= 1) acc.xor_reduce(o);
         if (tl.slot < 0) {

@@ -240,12 +240,13 @@ static int lanes_for(int64_t maxlen) {
 // column pass keeps such a tile in a fixed per-warp scratch)
 static bool append_seg_tiles(const int64_t *colptr, int64_t d, int64_t tile_nnz, int64_t tile_segs,
                              int64_t big_seg, int64_t align, std::vector<Tile> &tiles,
-                             std::vector<SplitSeg> &splits, int64_t *slots) {
+                             std::vector<SplitSeg> &splits, int64_t *slots, int64_t chunk_nnz = 0) {
+    if (chunk_nnz <= 0) chunk_nnz = tile_nnz;
     int64_t j = 0;
     while (j < d) {
         const int64_t len = colptr[j + 1] - colptr[j];
         if (len > big_seg) {
-            const int64_t nch0 = (len + tile_nnz - 1) / tile_nnz;
+            const int64_t nch0 = (len + chunk_nnz - 1) / chunk_nnz;
             const int64_t chunk0 = ((len + nch0 - 1) / nch0 + align - 1) / align * align;
             const int64_t nch = (len + chunk0 - 1) / chunk0;
             if (nch == 1) {
@@ -314,7 +315,7 @@ int build_range_schedule(const std::vector<int64_t> &ptr, int nranges, int64_t d
     tile_off.assign((size_t)nranges + 1, 0);
     for (int r = 0; r < nranges; ++r) {
         if (!append_seg_tiles(ptr.data() + (size_t)r * (size_t)(d + 1), d, kWarpTileNnz, kWarpTileSegs,
-                              kWarpBigSeg, 4, tiles, splits, &slots))
+                              kWarpBigSeg, 4, tiles, splits, &slots, kWarpChunkNnz))
             return fail(SDA_ERR_UNSUPPORTED, "warp tile over its limits");
         if ((int64_t)tiles.size() > INT32_MAX) return fail(SDA_ERR_UNSUPPORTED, "column schedule too large");
         tile_off[(size_t)r + 1] = (int32_t)tiles.size();
