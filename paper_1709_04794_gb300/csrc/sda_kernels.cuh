@@ -872,6 +872,14 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
     const int r = blockIdx.x / per_range, c = blockIdx.x - r * per_range;
     const int64_t r0 = (int64_t)r * rb;
     const int len = (int)min(rb, n - r0);
+    // a tile warp's first tile: its descriptor loads now, its quads are
+    // prefetched to L2 while the slice of v is staged
+    constexpr int TW = kColBlk / 32 - kColBlkStreamWarps;
+    const int wib = threadIdx.x >> 5;
+    const int t_first = tile_off[r] + c * TW + wib;
+    const bool has_first = wib < TW && t_first < tile_off[r + 1];
+    Tile first{};
+    if (has_first) first = tiles[t_first];
     {
         // v + r0 is 16-byte aligned (rb is a multiple of 256 and v is aligned)
         constexpr int VW = 16 / (int)sizeof(AccT);
@@ -883,6 +891,17 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
                          "l"(src + 16 * (int64_t)i)
                          : "memory");
         for (int i = n16 * VW + threadIdx.x; i < len; i += kColBlk) vs[i] = v[r0 + i];
+        if (has_first) {
+            // one 128-byte line of the tile's 16-bit indices and of its values per lane and round
+            const int64_t e0 = first.nz0, e1 = first.nz1;
+            const char *ib = reinterpret_cast<const char *>(row);
+            const char *vb = reinterpret_cast<const char *>(val);
+            for (int64_t b = (e0 * 2) / 128 + (threadIdx.x & 31); b * 128 < e1 * 2; b += 32)
+                asm volatile("prefetch.global.L2 [%0];\n" ::"l"(ib + b * 128));
+            for (int64_t b = (e0 * (int64_t)sizeof(VT)) / 128 + (threadIdx.x & 31); b * 128 < e1 * (int64_t)sizeof(VT);
+                 b += 32)
+                asm volatile("prefetch.global.L2 [%0];\n" ::"l"(vb + b * 128));
+        }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
     __syncthreads();
@@ -1005,8 +1024,6 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
     // the last kColBlkStreamWarps warps of every block run the shift-state
     // stream of this iteration (bandwidth-bound; the tile warps are bound by
     // latency), the others the range's tiles
-    constexpr int TW = kColBlk / 32 - kColBlkStreamWarps;
-    const int wib = threadIdx.x >> 5;
     if (wib >= TW) {
         if (W && stream_scalars<AccT>(st, p2parts, p2blocks, tab, threadIdx.x - TW * 32, blockIdx.x == 0))
             shift_stream<AccT>((int64_t)(blockIdx.x * kColBlkStreamWarps + (wib - TW)) * 32 + lane32,
@@ -1018,9 +1035,9 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
     // ones); the next tile's descriptor loads while a tile is worked
     const int nw = per_range * TW;
     const int t1 = tile_off[r + 1];
-    int t = tile_off[r] + c * TW + wib;
-    if (t < t1) {
-        Tile cur = tiles[t];
+    int t = t_first;
+    if (has_first) {
+        Tile cur = first;
         for (;;) {
             const int tn = t + nw;
             Tile nxt = cur;
