@@ -86,3 +86,48 @@ def test_planted_mistake_is_caught(name, tiny, cfg1):
                             "-lm"], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
         assert not _pins_pass(so, tiny, cfg1), "pins did not catch " + name
+
+
+# A mistake in the regression operator built on the same code (CSR-SDA,
+# Algorithm 5, line 5): keeping the centring must fail the X^T X pin.  (SA-SDA
+# runs the unchanged operator with X = I, covered by the mutations above.)
+MODE_MUTATIONS = {
+    "regression_keeps_centring": ("if (P) memset(P->mu, 0, (size_t)(d > 0 ? d : 1) * sizeof(double));",
+                                  "(void)P;"),
+}
+
+
+def _regression_pin_passes(so):
+    from paper_1709_04794_gb300 import synth
+    p = synth.custom_problem(120, 30, 6, seed=19, values="counts")
+    o = oracle.Oracle.regression(p.x_ptr, p.x_col, p.x_val, p.d, so_path=so)
+    X = oracle.dense_x(p.x_ptr, p.x_col, p.x_val, p.d)
+    x = np.random.default_rng(3).standard_normal(p.d)
+    ref = X.T @ (X @ x) + 0.7 * x
+    return bool(np.linalg.norm(o.apply(x, 0.7) - ref) <= 1e-12 * np.linalg.norm(ref))
+
+
+def _compile_mutant(tmp, old, new):
+    import subprocess
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor not found"
+    path = os.path.join(tmp, "mut.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    so = os.path.join(tmp, "mut.so")
+    r = subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", path, "-o", so, "-lm"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return so
+
+
+def test_unmutated_regression_pin_passes():
+    assert _regression_pin_passes(oracle.build())
+
+
+@pytest.mark.parametrize("name", sorted(MODE_MUTATIONS))
+def test_planted_mode_mistake_is_caught(name):
+    old, new = MODE_MUTATIONS[name]
+    with tempfile.TemporaryDirectory() as tmp:
+        so = _compile_mutant(tmp, old, new)
+        assert not _regression_pin_passes(so), "pin did not catch " + name
