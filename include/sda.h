@@ -224,6 +224,10 @@ typedef struct {
  *   w_out      [target_count][n_shifts][D] doubles in the caller's feature order, or NULL
  *   report     host array [target_count][n_shifts], or NULL
  *
+ * D is the operator's number of features (N for an operator from
+ * sda_build_sa).  An operator from sda_build_regression takes rhs_mode
+ * SDA_RHS_GIVEN and opts alpha / scatter_weight NaN, else INVALID_ARG.
+ *
  * Returns SDA_OK, SDA_NOT_CONVERGED (some shift hit max_iter; its report
  * says which), or an error: INVALID_ARG, SHAPE, BREAKDOWN, TIMEOUT, CUDA,
  * OOM.  Synchronises the stream.
