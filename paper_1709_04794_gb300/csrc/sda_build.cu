@@ -412,7 +412,7 @@ static int build_range_blocks(sda_operator *op, RangeBlocks &out, const int64_t 
     SDA_LAUNCHED();
     std::vector<int32_t> off;
     out.per_range = std::max(1, sms * kColBlkPerSm / (int)nr);
-    SDA_TRY(build_range_schedule(hp, (int)nr, nseg, out.sched, off));
+    SDA_TRY(build_range_schedule(hp, (int)nr, nseg, out.sched, off, warp_chunk_nnz((int64_t)fsz)));
     SDA_TRY(out.tile_off.alloc(off.size()));
     SDA_CUDA(cudaMemcpy(out.tile_off.p, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     return SDA_OK;

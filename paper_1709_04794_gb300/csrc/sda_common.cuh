@@ -111,7 +111,7 @@ int build_seg_schedule(const std::vector<int64_t> &ptr, ColSchedule &out);
 // of `nranges` pointer arrays of d + 1 entries each, stored one after the other
 // in `ptr`; the tiles of range r are [tile_off[r], tile_off[r + 1])
 int build_range_schedule(const std::vector<int64_t> &ptr, int nranges, int64_t d, ColSchedule &out,
-                         std::vector<int32_t> &tile_off);
+                         std::vector<int32_t> &tile_off, int64_t chunk_nnz);
 
 // ---------------------------------------------------------------------------
 // value storage types
@@ -344,11 +344,12 @@ constexpr int kWarpTileNnz = 512;
 constexpr double kRowHeadCover = 0.85;
 constexpr int64_t kRowHeadMax = 32768;
 constexpr int kWarpTileSegs = 128;
-constexpr int kWarpBigSeg = 128;
-// Chunk of a long column in one whole-warp tile, and the quads a lane loads at
-// once there (kWarpChunkNnz / 128).
+constexpr int kWarpBigSeg = 256;
+// Chunk of a long column in one whole-warp tile (FP32 and FP64 vectors), and
+// the quads a lane loads at once there (chunk / 128).
 constexpr int kWarpChunkNnz = 1024;
-constexpr int kWarpChunkQpl = kWarpChunkNnz / 128;
+constexpr int kWarpChunkNnz64 = 512;
+constexpr int warp_chunk_nnz(int64_t fsz) { return fsz == 8 ? kWarpChunkNnz64 : kWarpChunkNnz; }
 // Shared memory the blocked column pass keeps for itself besides the slice.
 constexpr int kColBlkReserve = 2048;
 // Per-warp scratch of the blocked column pass after the slice: the quad sums of

@@ -988,12 +988,13 @@ __global__ void __launch_bounds__(kColBlk, kColBlkPerSm) k_colblk(const Tile *__
         const int64_t q0 = tl.nz0 >> 2;
         const int nq = (int)((tl.nz1 >> 2) - q0);
         CS acc;
-        for (int qb = lane32; qb < nq; qb += kWarpChunkQpl * 32) {
-            AccT a[kWarpChunkQpl];
+        constexpr int QPL = warp_chunk_nnz((int64_t)sizeof(AccT)) / 128;
+        for (int qb = lane32; qb < nq; qb += QPL * 32) {
+            AccT a[QPL];
 #pragma unroll
-            for (int u = 0; u < kWarpChunkQpl; ++u) a[u] = quad(q0 + qb + 32 * u, qb + 32 * u < nq);
+            for (int u = 0; u < QPL; ++u) a[u] = quad(q0 + qb + 32 * u, qb + 32 * u < nq);
 #pragma unroll
-            for (int u = 0; u < kWarpChunkQpl; ++u) acc.add(a[u]);
+            for (int u = 0; u < QPL; ++u) acc.add(a[u]);
         }
         for (int o = 16; o > 0; o >>= 1) acc.xor_reduce(o);
         if (tl.slot < 0) {

@@ -308,14 +308,14 @@ int build_seg_schedule(const std::vector<int64_t> &colptr, ColSchedule &out) {
 }
 
 int build_range_schedule(const std::vector<int64_t> &ptr, int nranges, int64_t d, ColSchedule &out,
-                         std::vector<int32_t> &tile_off) {
+                         std::vector<int32_t> &tile_off, int64_t chunk_nnz) {
     std::vector<Tile> tiles;
     std::vector<SplitSeg> splits;
     int64_t slots = 0;
     tile_off.assign((size_t)nranges + 1, 0);
     for (int r = 0; r < nranges; ++r) {
         if (!append_seg_tiles(ptr.data() + (size_t)r * (size_t)(d + 1), d, kWarpTileNnz, kWarpTileSegs,
-                              kWarpBigSeg, 4, tiles, splits, &slots, kWarpChunkNnz))
+                              kWarpBigSeg, 4, tiles, splits, &slots, chunk_nnz))
             return fail(SDA_ERR_UNSUPPORTED, "warp tile over its limits");
         if ((int64_t)tiles.size() > INT32_MAX) return fail(SDA_ERR_UNSUPPORTED, "column schedule too large");
         tile_off[(size_t)r + 1] = (int32_t)tiles.size();
