@@ -1,11 +1,11 @@
 """CUDA path against the FP64 CPU oracle, through the C ABI.
 
-Tolerances (derivation in DESIGN.md, "Parity bar"):
+Tolerances:
 * FP64 path, same iterations: the two sides differ only in summation order,
   ~1e-16 per operation, amplified along the Krylov recurrence on the
   ill-conditioned shifts: 1e-9 relative after <= 40 iterations.
-* FP64 path, converged to tol 1e-10: 1e-6 relative on w per shift (the
-  spec bar), AUC equal to 4 decimals.
+* FP64 path, converged to tol 1e-10: 1e-6 relative on w per shift, AUC equal
+  to 4 decimals.
 * Mixed path (FP32 vectors, FP64 scalars): converged to tol, its FP64 true
   residual stays within a small factor of tol; w within kappa_s x residual of
   the oracle's.
