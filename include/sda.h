@@ -14,7 +14,10 @@
  * with one shifted conjugate-gradient run per target (Algorithm 3) and the
  * centring applied implicitly as a rank-1 correction (Sec. 3.2.3), so X is
  * never densified.  mu_l is the mean labelled sample (Alg. 7 step 3), P_l
- * the diagonal 0/1 matrix of the labelled rows.
+ * the diagonal 0/1 matrix of the labelled rows.  The same solver also serves
+ * two operators of the paper's comparison methods: X^T X of CSR-SDA's
+ * regression step (Algorithm 5; sda_build_regression) and the SDA operator
+ * with X = I_N of SA-SDA (Algorithm 6; sda_build_sa).
  *
  * Conventions for every call:
  *  - Return value 0 (SDA_OK) on success, a positive warning code, or a
