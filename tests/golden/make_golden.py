@@ -6,7 +6,9 @@ shifts 1e-1..1e2, alpha 0.1, scatter weight 1 - alpha as in eq. 7), stored
 with the results so that they do not depend on the generator's host library.
 Outputs: the FP64 oracle's shifted-CG solutions (Algorithm 3, base shift the
 smallest, relative tolerance 1e-13), its iteration counts, and the AUC of the
-scores X w on the held-out rows (Sec. 5.1).  Only oracle/ computes them.
+scores X w on the held-out rows (Sec. 5.1); and, in a second file, the
+solutions of the same sweep for CSR-SDA's regression operator X^T X (b = X^T z,
+z seeded) and for SA-SDA's operator (X = I_N).  Only oracle/ computes them.
 
     python tests/golden/make_golden.py
 """
@@ -23,6 +25,7 @@ import oracle  # noqa: E402
 from paper_1709_04794_gb300 import synth  # noqa: E402
 
 OUT = os.path.join(HERE, "small_300x96_fp64.json")
+OUT_MODES = os.path.join(HERE, "small_300x96_modes_fp64.json")
 
 
 def main():
@@ -48,6 +51,29 @@ def main():
     with open(OUT, "w") as f:
         json.dump(doc, f)
     print("wrote", OUT)
+    # the same X and graph under the two other operators: CSR-SDA's regression
+    # step (Algorithm 5, line 5: X^T X, b = X^T z) and SA-SDA (Algorithm 6: X = I_N)
+    z = np.random.default_rng(17090).uniform(-1.0, 1.0, p.n)
+    rows_all = np.repeat(np.arange(p.n), np.diff(p.x_ptr))
+    breg = np.bincount(p.x_col, weights=p.x_val * z[rows_all], minlength=p.d)
+    oreg = oracle.Oracle.regression(p.x_ptr, p.x_col, p.x_val, p.d)
+    rreg = oreg.shifted_cg(breg, p.shifts, tol=1e-13, max_iter=50000)
+    assert rreg.status == 0
+    n = p.n
+    osa = oracle.Oracle(np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n),
+                        p.s_ptr, p.s_col, p.s_val, p.labels[0], n, p.alpha)
+    bsa = osa.rhs_canonical()
+    rsa = osa.shifted_cg(bsa, p.shifts, tol=1e-13, max_iter=50000)
+    assert rsa.status == 0
+    modes = {
+        "source": "tests/golden/make_golden.py (FP64 oracle, Algorithm 3, tol 1e-13)",
+        "inputs": os.path.basename(OUT),
+        "regression": {"z": z.tolist(), "rhs": breg.tolist(), "w": rreg.W.tolist(), "iters": rreg.iters.tolist()},
+        "sa": {"rhs": bsa.tolist(), "z": rsa.W.tolist(), "iters": rsa.iters.tolist()},
+    }
+    with open(OUT_MODES, "w") as f:
+        json.dump(modes, f)
+    print("wrote", OUT_MODES)
 
 
 if __name__ == "__main__":

@@ -1,6 +1,7 @@
-"""Stored expected values (tests/golden/small_300x96_fp64.json, written by
-tests/golden/make_golden.py from the FP64 oracle): a 300 x 96 count problem,
-one target, four shifts 1e-1..1e2.
+"""Stored expected values (tests/golden/small_300x96_fp64.json and
+small_300x96_modes_fp64.json, written by tests/golden/make_golden.py from the
+FP64 oracle): a 300 x 96 count problem, one target, four shifts 1e-1..1e2,
+under the SDA operator, CSR-SDA's regression operator and SA-SDA's operator.
 
 CPU: the oracle still reproduces the stored solutions (bit for bit up to
 1e-12) and they solve the dense definition (B + beta I) w = d of eq. 7 /
@@ -99,3 +100,53 @@ def test_golden_gpu_mixed(golden):
     W = w[0].cpu().numpy()
     for s, beta in enumerate(p.shifts):
         assert ob.true_residual(b, beta, W[s]) < 20 * tol, s
+
+
+MODES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "small_300x96_modes_fp64.json")
+
+
+@pytest.fixture(scope="module")
+def modes():
+    return json.load(open(MODES))
+
+
+def test_golden_regression_mode(golden, modes):
+    """CSR-SDA's regression step (Algorithm 5, line 5) on the stored X: the
+    oracle reproduces the stored solutions, which solve (X^T X + beta I) w = X^T z."""
+    p, g = golden
+    m = modes["regression"]
+    X = oracle.dense_x(p.x_ptr, p.x_col, p.x_val, p.d)
+    b = np.asarray(m["rhs"])
+    assert np.allclose(b, X.T @ np.asarray(m["z"]), rtol=1e-13, atol=1e-12)
+    o = oracle.Oracle.regression(p.x_ptr, p.x_col, p.x_val, p.d)
+    res = o.shifted_cg(b, p.shifts, tol=1e-13, max_iter=50000)
+    assert res.iters.tolist() == m["iters"]
+    for s, beta in enumerate(p.shifts):
+        w = np.asarray(m["w"][s])
+        assert _rel(res.W[s], w) < 1e-12, s
+        assert _rel(w, np.linalg.solve(X.T @ X + beta * np.eye(p.d), b)) < 1e-9, s
+
+
+def test_golden_sa_mode(golden, modes):
+    """SA-SDA (Algorithm 6) on the stored graph and labels: the oracle with
+    X = I_N reproduces the stored ratings, which solve (M - omega 1_l 1_l^T / l
+    + beta I) z = d."""
+    p, g = golden
+    m = modes["sa"]
+    n, y, a = p.n, p.labels[0], p.alpha
+    o = oracle.Oracle(np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), np.ones(n),
+                      p.s_ptr, p.s_col, p.s_val, y, n, a)
+    d = o.rhs_canonical()
+    assert np.array_equal(d, np.asarray(m["rhs"]))
+    res = o.shifted_cg(d, p.shifts, tol=1e-13, max_iter=50000)
+    assert res.iters.tolist() == m["iters"]
+    Sd = np.zeros((n, n))
+    for i in range(n):
+        Sd[i, p.s_col[p.s_ptr[i]:p.s_ptr[i + 1]]] = p.s_val[p.s_ptr[i]:p.s_ptr[i + 1]]
+    one_l = (y != 0).astype(float)
+    om = 1.0 - a
+    Mt = om * np.diag(one_l) + a * (np.diag(Sd.sum(1)) - Sd) - om * np.outer(one_l, one_l) / one_l.sum()
+    for s, beta in enumerate(p.shifts):
+        z = np.asarray(m["z"][s])
+        assert _rel(res.W[s], z) < 1e-12, s
+        assert _rel(z, np.linalg.solve(Mt + beta * np.eye(n), d)) < 1e-9, s
