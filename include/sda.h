@@ -27,7 +27,10 @@
  *  - Inputs are borrowed for the duration of the call only; an operator
  *    keeps its own device copies.  Outputs are allocated by the caller.
  *  - Pointers are host or device pointers as the accompanying flag says;
- *    device pointers belong to the current CUDA device.
+ *    device pointers belong to the current CUDA device.  An operator lives
+ *    on the device that was current when it was built: every call that
+ *    launches work on it returns SDA_ERR_INVALID_ARG (naming both device
+ *    ordinals) when another device is current, before any launch.
  *  - Device work is ordered on the caller's stream (cudaStream_t passed as
  *    void*, NULL = legacy default stream); calls that return host results
  *    synchronise that stream before returning.
@@ -60,7 +63,7 @@ enum {
     SDA_ERR_NO_NEGATIVE = -6,     /* a target has no labelled negative sample: mu_- undefined        */
     SDA_ERR_NOT_SYMMETRIC = -7,   /* S differs from S^T, or holds a negative or non-finite weight    */
     SDA_ERR_BREAKDOWN = -8,       /* <p, (B + sigma0 I) p> <= 0 or not finite during the solve       */
-    SDA_ERR_TIMEOUT = -9,         /* a bounded device-side wait ran out                              */
+    SDA_ERR_TIMEOUT = -9,         /* reserved: a bounded device-side wait ran out                    */
     SDA_ERR_CUDA = -10,           /* a CUDA runtime call failed (detail in sda_last_error_detail)    */
     SDA_ERR_OOM = -11,            /* device allocation failed                                        */
     SDA_ERR_UNSUPPORTED = -12     /* a combination of options this build does not provide            */
@@ -197,8 +200,8 @@ typedef struct {
                                a shift still above refine_tol reports SDA_NOT_CONVERGED             */
     int32_t batch_targets;  /* 1: solve the call's targets in batches of 16 that share every pass over
                                X and S (vectors stored target-contiguous; no paper counterpart);
-                               0: one target after another.  Not combined with refine_rounds > 0
-                               (SDA_ERR_UNSUPPORTED)                                                */
+                               0: one target after another.  With refine_rounds > 0 the correction
+                               solves of up to 16 (target, shift) pairs of a batch share one run too */
     double refine_tol;      /* target FP64 true relative residual (NaN or <= 0: tol)                */
 } sda_solve_opts;
 
@@ -232,8 +235,8 @@ typedef struct {
  * SDA_RHS_GIVEN and opts alpha / scatter_weight NaN, else INVALID_ARG.
  *
  * Returns SDA_OK, SDA_NOT_CONVERGED (some shift hit max_iter; its report
- * says which), or an error: INVALID_ARG, SHAPE, BREAKDOWN, TIMEOUT, CUDA,
- * OOM.  Synchronises the stream.
+ * says which), or an error: INVALID_ARG, SHAPE, BREAKDOWN, CUDA, OOM.
+ * Synchronises the stream.
  */
 SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, int32_t n_shifts,
                              const sda_solve_opts *opt, double *w_out, sda_shift_report *report,
@@ -291,12 +294,12 @@ SDA_API int sda_operator_apply(const sda_operator *op, int32_t target, double si
 
 /*
  * sda_operator_apply_static - the same q = (B + sigma I) p as
- * sda_operator_apply, for callers that cannot allocate device memory: code
- * that runs while a CUDA stream is being captured into a graph (cudaMalloc
- * and cudaFree are not allowed there), code whose device memory is entirely
- * owned by its own pool allocator, and latency-critical loops where the
- * implicit device synchronisation of cudaMalloc / cudaFree is not acceptable.
- * The paper has no counterpart; this is an interface convenience.
+ * sda_operator_apply, for callers that cannot allocate device memory: a
+ * host application whose device memory is entirely owned by its own pool
+ * allocator (a cudaMalloc from the library would compete with it for the
+ * same memory), and latency-critical loops where the implicit device
+ * synchronisation of cudaMalloc / cudaFree is not acceptable.  The paper has
+ * no counterpart; this is an interface convenience.
  *
  * Every per-call buffer lives in one file-scope device array of
  * SDA_STATIC_SCRATCH_DOUBLES doubles (8 MiB) that every GPU loading the
@@ -304,12 +307,14 @@ SDA_API int sda_operator_apply(const sda_operator *op, int32_t target, double si
  * does not synchronise the stream.  The operator must satisfy
  *     2 D + 2 N + (reduction and split-segment slots) <= SDA_STATIC_SCRATCH_DOUBLES,
  * otherwise the call returns SDA_ERR_SHAPE and names the size it needed.
- * All calls share the array, so calls that overlap on the GPU (different
- * streams, or different host threads) race and must be serialised by the
- * caller.  The first call on a device looks the array's address up (which
- * loads the library's device code on that device): make that first call
- * before any stream capture.  p and q are device arrays of D doubles in the
- * caller's feature order; errors as sda_operator_apply.
+ * All calls share the array and it keeps the last call's contents (the call
+ * clears the counters that must start at zero itself), so calls that overlap
+ * on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  The first call on a device looks the array's
+ * address up with that device current (which loads the library's device code
+ * on that device); make that first call before any stream capture.  p and q
+ * are device arrays of D doubles in the caller's feature order; errors as
+ * sda_operator_apply.
  */
 #define SDA_STATIC_SCRATCH_DOUBLES (1 << 20)
 

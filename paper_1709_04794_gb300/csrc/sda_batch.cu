@@ -8,6 +8,7 @@
 // side, CG scalars and shift states (a SolveState each); the shift list is the
 // call's.  X and S are streamed once per batch iteration instead of once per
 // target.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -75,14 +76,17 @@ struct BatchWs {
     DevBuf<SolveState> st;
     DevBuf<BatchCtl> ctl;
     DevBuf<char> coef;
-    DevBuf<double> part, slots, w64;
+    DevBuf<double> part, slots;
+    DevBuf<double> sig, r2;    // per-lane shifts and squared residual norms of the FP64 block utilities
+    DevBuf<double> wall;       // FP64 solutions of a batch's (target, shift) pairs [target][shift][D]
+    DevBuf<double> rbuf;       // residual vectors of up to kTB pairs [lane][D] (refinement right-hand sides)
     DevBuf<unsigned> cnt, lcount;
     SolveState *h_st = nullptr;
     BatchCtl *h_ctl = nullptr;
     int grid = 0;                          // every kernel but the sparse passes of the batched solve
     int grid1 = 0, grid2 = 0, grid3a = 0;  // their own grids (occupancy of each)
     cudaGraphExec_t graph = nullptr;
-    int graph_iters = 0;
+    int graph_iters = 0, graph_ns = 0;
     cudaStream_t cap_stream = nullptr;
     ~BatchWs() {
         if (graph) cudaGraphExecDestroy(graph);
@@ -214,7 +218,8 @@ __global__ void __launch_bounds__(kBlock) kb_init(int64_t ldw, int ns, const dou
         S.gamma_prev = 1.0;
         S.t = 0.0;
         S.k = 0;
-        S.status = SDA_OK;
+        // a non-finite right-hand side stops its target at once, as a breakdown
+        S.status = (isfinite(tot[0]) && isfinite(tot[1])) ? SDA_OK : SDA_ERR_BREAKDOWN;
         const bool zero_rhs = !(S.bnorm > 0.0);
         for (int s = 0; s < ns; ++s) {
             ShiftState &h = S.sh[s];
@@ -602,8 +607,8 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
     __shared__ FT s_al[kTB];
     __shared__ double s_gam[kTB], s_t[kTB];
     __shared__ float s_gh[kTB], s_gl[kTB], s_tf[kTB];
-    __shared__ float s_sh, s_sl;
-    __shared__ double s_sigma0;
+    __shared__ float s_sh[kTB], s_sl[kTB];   // each lane's base shift sigma0 as an FP32 pair
+    __shared__ double s_sigma0[kTB];
     __shared__ double s_anw[kTB], s_rn[kTB];
     if (ctl->done) return;
     if (threadIdx.x < kTB) {
@@ -613,10 +618,8 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
         s_t[threadIdx.x] = S.t;
         split_f32(S.gamma, s_gh[threadIdx.x], s_gl[threadIdx.x]);
         s_tf[threadIdx.x] = (float)S.t;
-        if (threadIdx.x == 0) {
-            s_sigma0 = S.sigma0;
-            split_f32(S.sigma0, s_sh, s_sl);
-        }
+        s_sigma0[threadIdx.x] = S.sigma0;
+        split_f32(S.sigma0, s_sh[threadIdx.x], s_sl[threadIdx.x]);
     }
     for (int q = threadIdx.x; q < ns * kTB; q += kBlock) cf[q] = coef[q];
     if (threadIdx.x < ns) any[threadIdx.x] = 0;
@@ -641,11 +644,11 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
         FT rnj, mj;
         if constexpr (std::is_same<FT, float>::value) {
             mj = mu32[e];
-            rnj = base_step_f32v(x.x, pk, sj.h, sj.l, mj, s_sh, s_sl, s_tf[t], s_gh[t], s_gl[t]);
+            rnj = base_step_f32v(x.x, pk, sj.h, sj.l, mj, s_sh[t], s_sl[t], s_tf[t], s_gh[t], s_gl[t]);
         } else {
             const double m64 = mu64[e];
             mj = (FT)m64;
-            const double qj = (double)sj.value() - m64 * s_t[t] + s_sigma0 * (double)pk;
+            const double qj = (double)sj.value() - m64 * s_t[t] + s_sigma0[t] * (double)pk;
             rnj = (FT)((double)x.x + s_gam[t] * qj);
         }
         R y;
@@ -791,6 +794,12 @@ __global__ void kb_put_mu32(int64_t len, const double *__restrict__ src, float *
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
         dst[i * kTB + t] = src ? (float)src[i] : 0.f;
 }
+// every lane of a [len][kTB] block from one plain vector
+template <class T>
+__global__ void kb_rep(int64_t len, const T *__restrict__ src, T *__restrict__ dst) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len * kTB; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = src[e / kTB];
+}
 // w[s][j] (FP64, permuted order) of target t from W[s][j][t]
 template <class FT>
 __global__ void kb_take_w(int64_t d, int64_t ldw, int ns, const FT *__restrict__ W, int t, double *__restrict__ out) {
@@ -799,6 +808,12 @@ __global__ void kb_take_w(int64_t d, int64_t ldw, int ns, const FT *__restrict__
         const int64_t sh = i / d, j = i - sh * d;
         out[i] = (double)W[(sh * ldw + j) * kTB + t];
     }
+}
+// w[j] += W[0][j][t] in FP64 (a refinement correction added to its solution)
+template <class FT>
+__global__ void kb_add_lane(int64_t d, const FT *__restrict__ W, int t, double *__restrict__ w) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < d; j += (int64_t)gridDim.x * blockDim.x)
+        w[j] += (double)W[j * kTB + t];
 }
 
 // ---------------------------------------------------------------------------
@@ -866,7 +881,8 @@ static int ensure_batch_ws(sda_operator *op, BatchWs *&slot, int ns) {
     SDA_TRY(b.slots.alloc((size_t)std::max(op->col.nslots, 1) * kTB * 2));
     SDA_TRY(b.lcount.alloc((size_t)std::max(op->col.nsplits, 1)));
     SDA_CUDA(cudaMemset(b.lcount.p, 0, b.lcount.bytes()));
-    SDA_TRY(b.w64.alloc((size_t)ns * op->d + op->d));
+    SDA_TRY(b.sig.alloc(kTB));
+    SDA_TRY(b.r2.alloc(kTB));
     if (!b.h_st) SDA_CUDA(cudaMallocHost(&b.h_st, sizeof(SolveState) * kTB));
     if (!b.h_ctl) SDA_CUDA(cudaMallocHost(&b.h_ctl, sizeof(BatchCtl)));
     b.fp64 = fp64;
@@ -949,7 +965,7 @@ static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, boo
         for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
         return SDA_OK;
     }
-    if (!b.graph || b.graph_iters != nb_iters) {
+    if (!b.graph || b.graph_iters != nb_iters || b.graph_ns != ns) {
         if (b.graph) cudaGraphExecDestroy(b.graph);
         b.graph = nullptr;
         if (!b.cap_stream) SDA_CUDA(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
@@ -969,6 +985,7 @@ static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, boo
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
         b.graph_iters = nb_iters;
+        b.graph_ns = ns;
     }
     SDA_CUDA(cudaGraphLaunch(b.graph, s));
     note_launch(5 * (int64_t)nb_iters);
@@ -976,11 +993,24 @@ static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, boo
     return SDA_OK;
 }
 
-// One batch: targets t0 .. t0 + nt - 1 (nt <= kTB).
+// One lane of a batched shifted-CG run: the operator target whose labels and
+// mu_l it uses, its right-hand side (device, permuted order), the base shift
+// sigma0 of its Krylov run and its relative stop tolerance.
+struct BatchLane {
+    int t;
+    const double *b;
+    double sigma0;
+    double tol;
+};
+
+// Shifted CG (Algorithm 3) on nl <= kTB lanes in lockstep: lane l solves
+// (B_{t_l} + (sigma0_l + delta_s) I) w = b_l for the ns relative shifts
+// delta_s (shared by the lanes).  Lanes past nl hold a zero right-hand side
+// and stop at once.  Leaves every lane's W^s in the workspace ([s][j][lane])
+// and the final solve states in the workspace's h_st.
 template <class VT, class FT>
-static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_perm, const double *shifts, int ns,
-                       const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
-                       cudaStream_t s, int *worst) {
+static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const double *deltas, int ns, bool fixed,
+                     int limit, const sda_solve_opts &o, double alpha, double omega, cudaStream_t s) {
     SDA_TRY(ensure_batch<FT>(op, ns));
     BatchWs &b = *op->bws;
     if (!b.grid) {
@@ -996,29 +1026,26 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     SDA_CUDA(cudaMemsetAsync(b.mu64.p, 0, b.mu64.bytes(), s));
     SDA_CUDA(cudaMemsetAsync(b.mu32.p, 0, b.mu32.bytes(), s));
     SDA_CUDA(cudaMemsetAsync(b.ylab.p, 0, b.ylab.bytes(), s));
-    for (int i = 0; i < nt; ++i) {
-        const int t = t0 + i;
-        kb_put<double><<<ge, kBlock, 0, s>>>(d, b_perm[i], b.b.p, i);
+    for (int i = 0; i < nl; ++i) {
+        const int t = lanes[i].t;
+        kb_put<double><<<ge, kBlock, 0, s>>>(d, lanes[i].b, b.b.p, i);
         kb_put<double><<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)t * d, b.mu64.p, i);
         kb_put_mu32<<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)t * d, b.mu32.p, i);
         kb_put<int8_t><<<ge, kBlock, 0, s>>>(n, op->labels.p + (int64_t)t * n, b.ylab.p, i);
         SDA_LAUNCHED();
     }
-    // per-target fixed scalars; targets past nt have a zero right-hand side and stop at once
     SolveState *h = b.h_st;
     memset(h, 0, sizeof(SolveState) * kTB);
-    double sigma0 = shifts[0];
-    for (int i = 1; i < ns; ++i) sigma0 = std::min(sigma0, shifts[i]);
-    const bool fixed = o.fixed_iters > 0;
-    for (int t = 0; t < kTB; ++t) {
-        h[t].sigma0 = sigma0;
-        h[t].omega = omega;
-        h[t].alpha_l = alpha;
-        h[t].tol = o.tol;
-        h[t].n_shifts = ns;
-        h[t].fixed = fixed ? 1 : 0;
-        h[t].limit = fixed ? o.fixed_iters : o.max_iter;
-        for (int i = 0; i < ns; ++i) h[t].sh[i].delta = shifts[i] - sigma0;
+    for (int l = 0; l < kTB; ++l) {
+        const BatchLane &ln = lanes[l < nl ? l : 0];
+        h[l].sigma0 = ln.sigma0;
+        h[l].omega = omega;
+        h[l].alpha_l = alpha;
+        h[l].tol = ln.tol;
+        h[l].n_shifts = ns;
+        h[l].fixed = fixed ? 1 : 0;
+        h[l].limit = limit;
+        for (int i = 0; i < ns; ++i) h[l].sh[i].delta = deltas[i];
     }
     SDA_CUDA(cudaMemcpyAsync(b.st.p, h, sizeof(SolveState) * kTB, cudaMemcpyHostToDevice, s));
     BView<FT> bv = bview<FT>(b);
@@ -1034,7 +1061,6 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     SDA_LAUNCHED();
     SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
-    const int limit = fixed ? o.fixed_iters : o.max_iter;
     const int nbi = o.iter_batch > 0 ? o.iter_batch : 32;
     int launched = 0;
     while (!b.h_ctl->done && launched <= limit) {
@@ -1048,58 +1074,172 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     }
     SDA_CUDA(cudaMemcpyAsync(h, b.st.p, sizeof(SolveState) * kTB, cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
-    DevBuf<double> rs;
-    if (o.check_residual) SDA_TRY(rs.alloc((size_t)ns + 1));
-    int batch_k = 0;
-    for (int i = 0; i < nt; ++i) {
-        const int t = t0 + i;
-        const SolveState &S = h[i];
-        batch_k = std::max(batch_k, S.k);
-        for (int sh = 0; sh < ns; ++sh) op->stats.shift_iterations += S.sh[sh].iters;
-        kb_take_w<FT><<<grid_elems_b((int64_t)ns * d, op->sm_count), kBlock, 0, s>>>(d, b.ldw, ns, bv.W, i, b.w64.p);
-        SDA_LAUNCHED();
-        if (w_out) {
-            double *dst = w_out + (int64_t)i * ns * d;
-            DevBuf<double> hostbuf;
-            if (!o.out_on_device) {
-                SDA_TRY(hostbuf.alloc((size_t)ns * d));
-                SDA_TRY(permute_to_old(op, b.w64.p, hostbuf.p, ns, s));
-                SDA_CUDA(cudaMemcpyAsync(dst, hostbuf.p, (size_t)ns * d * sizeof(double), cudaMemcpyDeviceToHost, s));
-                SDA_CUDA(cudaStreamSynchronize(s));
-            } else {
-                SDA_TRY(permute_to_old(op, b.w64.p, dst, ns, s));
+    int bk = 0;
+    for (int l = 0; l < nl; ++l) bk = std::max(bk, h[l].k);
+    op->stats.iterations += bk;   // iterations of the run (its slowest lane)
+    return SDA_OK;
+}
+
+// One batch: targets t0 .. t0 + nt - 1 (nt <= kTB) share one run; then the
+// FP64 true residual of every (target, shift) and, with refine_rounds > 0,
+// per-pair refinement: while a pair's FP64 true residual exceeds refine_tol,
+// its correction (B_t + beta_s I) c = b_t - (B_t + beta_s I) w_ts is solved in
+// the iteration's precision and added in FP64; the corrections of up to kTB
+// pairs (of any targets and shifts) run as the lanes of one batched run.
+template <class VT, class FT>
+static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_perm, const double *shifts, int ns,
+                       const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
+                       cudaStream_t s, int *worst) {
+    const int64_t d = op->d;
+    const bool fixed = o.fixed_iters > 0;
+    double sigma0 = shifts[0];
+    for (int i = 1; i < ns; ++i) sigma0 = std::min(sigma0, shifts[i]);
+    std::vector<double> deltas((size_t)ns);
+    for (int i = 0; i < ns; ++i) deltas[(size_t)i] = shifts[i] - sigma0;
+    BatchLane lanes[kTB];
+    for (int i = 0; i < nt; ++i) lanes[i] = BatchLane{t0 + i, b_perm[i], sigma0, o.tol};
+    SDA_TRY((run_lanes<VT, FT>(op, lanes, nt, deltas.data(), ns, fixed, fixed ? o.fixed_iters : o.max_iter, o, alpha,
+                               omega, s)));
+    BatchWs &b = *op->bws;
+    const std::vector<SolveState> fin(b.h_st, b.h_st + kTB);   // later runs reuse h_st
+    for (int i = 0; i < nt; ++i)
+        for (int sh = 0; sh < ns; ++sh) op->stats.shift_iterations += fin[(size_t)i].sh[sh].iters;
+    // the FP64 solutions of every (target, shift) of the batch, [i][s][j], permuted order
+    const size_t wall_n = (size_t)nt * ns * d;
+    if (b.wall.n < wall_n) SDA_TRY(b.wall.alloc(wall_n));
+    {
+        BView<FT> bv = bview<FT>(b);
+        for (int i = 0; i < nt; ++i) {
+            kb_take_w<FT><<<grid_elems_b((int64_t)ns * d, op->sm_count), kBlock, 0, s>>>(
+                d, b.ldw, ns, bv.W, i, b.wall.p + (int64_t)i * ns * d);
+            SDA_LAUNCHED();
+        }
+    }
+    const int rounds = fixed ? 0 : std::max(0, o.refine_rounds);
+    const double rtol = std::isnan(o.refine_tol) || o.refine_tol <= 0.0 ? o.tol : o.refine_tol;
+    const bool check = o.check_residual != 0 || rounds > 0;
+    std::vector<double> tres((size_t)nt * ns, -1.0), bn((size_t)nt, 0.0);
+    std::vector<int> pst((size_t)nt * ns, SDA_OK);
+    if (check) {
+        // ||b_t|| of every target
+        DevBuf<double> bb;
+        SDA_TRY(bb.alloc((size_t)nt));
+        for (int i = 0; i < nt; ++i) SDA_TRY(dot_f64(op, d, b_perm[i], b_perm[i], bb.p + i, s));
+        std::vector<double> hb((size_t)nt);
+        SDA_CUDA(cudaMemcpyAsync(hb.data(), bb.p, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SDA_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nt; ++i) bn[(size_t)i] = sqrt(hb[(size_t)i]);
+        auto lane_of = [&](int q) {
+            const int i = q / ns, sh = q - i * ns;
+            return ResidLane{t0 + i, shifts[sh], b_perm[i], b.wall.p + (int64_t)q * d};
+        };
+        auto rel = [&](int q, double r2) {
+            const double bq = bn[(size_t)(q / ns)];
+            return bq > 0 ? sqrt(r2) / bq : sqrt(r2);
+        };
+        // FP64 true residual of every pair, kTB pairs per FP64 block pass
+        std::vector<int> all((size_t)nt * ns);
+        for (int q = 0; q < nt * ns; ++q) all[(size_t)q] = q;
+        for (size_t g0 = 0; g0 < all.size(); g0 += kTB) {
+            const int ng = (int)std::min<size_t>(kTB, all.size() - g0);
+            ResidLane rl[kTB];
+            double r2[kTB];
+            for (int g = 0; g < ng; ++g) rl[g] = lane_of(all[g0 + g]);
+            SDA_TRY(resid_lanes(op, rl, ng, r2, nullptr, alpha, omega, s));
+            for (int g = 0; g < ng; ++g) tres[(size_t)all[g0 + g]] = rel(all[g0 + g], r2[g]);
+        }
+        // refinement rounds
+        if (rounds > 0 && b.rbuf.n < (size_t)kTB * d) SDA_TRY(b.rbuf.alloc((size_t)kTB * d));
+        for (int rd = 0; rd < rounds; ++rd) {
+            // pairs still above the target, shift by shift: a group's run lasts as long
+            // as its smallest shift needs, so groups of equal shifts waste the least
+            std::vector<int> sorder((size_t)ns);
+            for (int sh = 0; sh < ns; ++sh) sorder[(size_t)sh] = sh;
+            std::stable_sort(sorder.begin(), sorder.end(), [&](int a, int c) { return shifts[a] < shifts[c]; });
+            std::vector<int> act;
+            for (int sh : sorder)
+                for (int i = 0; i < nt; ++i) {
+                    const int q = i * ns + sh;
+                    if (tres[(size_t)q] > rtol && bn[(size_t)i] > 0 && fin[(size_t)i].status == SDA_OK &&
+                        pst[(size_t)q] == SDA_OK)
+                        act.push_back(q);
+                }
+            if (act.empty()) break;
+            for (size_t g0 = 0; g0 < act.size(); g0 += kTB) {
+                const int ng = (int)std::min<size_t>(kTB, act.size() - g0);
+                ResidLane rl[kTB];
+                double r2[kTB];
+                BatchLane cl[kTB];
+                for (int g = 0; g < ng; ++g) {
+                    const int q = act[g0 + g];
+                    rl[g] = lane_of(q);
+                    // relative reduction asked of the correction: to the target, but
+                    // not below what the iteration's precision can reach
+                    const double inner = std::min(0.5, std::max(rtol / tres[(size_t)q], 1e-4));
+                    cl[g] = BatchLane{rl[g].t, b.rbuf.p + (int64_t)g * d, rl[g].sigma, inner};
+                }
+                // residual vectors b - (B + beta) w in FP64, then the corrections
+                SDA_TRY(resid_lanes(op, rl, ng, r2, b.rbuf.p, alpha, omega, s));
+                const double zero = 0.0;
+                SDA_TRY((run_lanes<VT, FT>(op, cl, ng, &zero, 1, false, o.max_iter, o, alpha, omega, s)));
+                BView<FT> bv = bview<FT>(*op->bws);
+                for (int g = 0; g < ng; ++g) {
+                    const int q = act[g0 + g];
+                    const SolveState &cs = op->bws->h_st[g];
+                    if (cs.status != SDA_OK) {
+                        pst[(size_t)q] = cs.status;
+                        continue;
+                    }
+                    kb_add_lane<FT><<<grid_elems_b(d, op->sm_count), kBlock, 0, s>>>(d, bv.W, g,
+                                                                                    b.wall.p + (int64_t)q * d);
+                    SDA_LAUNCHED();
+                }
+                SDA_TRY(resid_lanes(op, rl, ng, r2, nullptr, alpha, omega, s));
+                for (int g = 0; g < ng; ++g) tres[(size_t)act[g0 + g]] = rel(act[g0 + g], r2[g]);
             }
         }
-        std::vector<double> tres((size_t)ns, -1.0);
-        if (o.check_residual) {
-            SDA_TRY(dot_f64(op, d, b_perm[i], b_perm[i], rs.p + ns, s));
-            SDA_TRY(resid_block(op, t, shifts, ns, b_perm[i], b.w64.p, rs.p, alpha, omega, s));
-            std::vector<double> hr((size_t)ns + 1);
-            SDA_CUDA(cudaMemcpyAsync(hr.data(), rs.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (!o.check_residual && rounds == 0) std::fill(tres.begin(), tres.end(), -1.0);
+    }
+    // solutions out, in the caller's feature order
+    for (int i = 0; i < nt && w_out; ++i) {
+        double *dst = w_out + (int64_t)i * ns * d;
+        const double *src = b.wall.p + (int64_t)i * ns * d;
+        if (!o.out_on_device) {
+            DevBuf<double> hostbuf;
+            SDA_TRY(hostbuf.alloc((size_t)ns * d));
+            SDA_TRY(permute_to_old(op, src, hostbuf.p, ns, s));
+            SDA_CUDA(cudaMemcpyAsync(dst, hostbuf.p, (size_t)ns * d * sizeof(double), cudaMemcpyDeviceToHost, s));
             SDA_CUDA(cudaStreamSynchronize(s));
-            const double bn = sqrt(hr[ns]);
-            for (int sh = 0; sh < ns; ++sh) tres[sh] = bn > 0 ? sqrt(hr[sh]) / bn : sqrt(hr[sh]);
+        } else {
+            SDA_TRY(permute_to_old(op, src, dst, ns, s));
         }
+    }
+    for (int i = 0; i < nt; ++i) {
+        const int t = t0 + i;
+        const SolveState &S = fin[(size_t)i];
         if (S.status != SDA_OK) {
             *worst = S.status;
             fail(S.status, "breakdown in the batched shifted CG of target %d at iteration %d", t, S.k);
         }
         for (int sh = 0; sh < ns; ++sh) {
+            const int q = i * ns + sh;
             const ShiftState &hs = S.sh[sh];
             int st = SDA_OK;
             if (S.status != SDA_OK) st = S.status;
+            else if (pst[(size_t)q] != SDA_OK) st = pst[(size_t)q];
+            else if (rounds > 0) st = tres[(size_t)q] <= rtol ? SDA_OK : SDA_NOT_CONVERGED;
             else if (!fixed && hs.active) st = SDA_NOT_CONVERGED;
             if (st == SDA_NOT_CONVERGED && *worst == SDA_OK) *worst = SDA_NOT_CONVERGED;
+            if (st < 0 && *worst >= 0) *worst = st;
             if (rep) {
-                sda_shift_report &r = rep[(int64_t)i * ns + sh];
+                sda_shift_report &r = rep[(int64_t)q];
                 r.iters = hs.iters;
                 r.status = st;
                 r.est_residual = hs.res;
-                r.true_residual = tres[sh];
+                r.true_residual = tres[(size_t)q];
             }
         }
     }
-    op->stats.iterations += batch_k;   // iterations of the batch (its slowest target)
     return SDA_OK;
 }
 
@@ -1114,23 +1254,11 @@ static int with_vt_b(int compute, F &&f) {
     }
 }
 
-template <class VT>
-using BlockVT = VT;
-
 // ---------------------------------------------------------------------------
 // FP64 utilities on blocks of 16 vectors: the batched kernels with FP64
-// vectors, the 16 "targets" being 16 vectors of one target (its labels in every
-// lane).  X and S are read once per 16 vectors.
+// vectors, each lane one vector with the labels and mu_l of its own target.
+// X and S are read once per 16 vectors.
 // ---------------------------------------------------------------------------
-// P[j][v] = W[v][j] for v < nv (zero for the other lanes)
-__global__ void kb_pack(int64_t d, int64_t ldw, int nv, const double *__restrict__ W, double *__restrict__ P) {
-    const int64_t m = ldw * kTB;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = e / kTB;
-        const int v = (int)(e - j * kTB);
-        P[e] = (v < nv && j < d) ? W[(int64_t)v * d + j] : 0.0;
-    }
-}
 // out[v][i] = U[i][v] for v < nv
 __global__ void kb_unpack(int64_t n, int nv, const double *__restrict__ U, double *__restrict__ out) {
     const int64_t m = n * nv;
@@ -1139,12 +1267,7 @@ __global__ void kb_unpack(int64_t n, int nv, const double *__restrict__ U, doubl
         out[e] = U[i * kTB + v];
     }
 }
-// ylab[i][v] = y[i] for every lane
-__global__ void kb_replab(int64_t n, const int8_t *__restrict__ y, int8_t *__restrict__ ylab) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * kTB; e += (int64_t)gridDim.x * blockDim.x)
-        ylab[e] = y[e / kTB];
-}
-// st[v].c = <mu, P_v>
+// st[v].c = <mu_v, P_v> (mu and P as [d][kTB] blocks)
 __global__ void __launch_bounds__(kBlock) kb_dot_mu(int64_t d, const double *__restrict__ mu,
                                                    const double *__restrict__ P, SolveState *st, BatchCtl *ctl,
                                                    double *partials, unsigned *counter) {
@@ -1153,7 +1276,7 @@ __global__ void __launch_bounds__(kBlock) kb_dot_mu(int64_t d, const double *__r
     CompSum<double> acc[1];
     const int64_t m = d * kTB;
     for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m; e += (int64_t)gridDim.x * kBlock)
-        acc[0].add(mu[e / kTB] * P[e]);
+        acc[0].add(mu[e] * P[e]);
     Part mine[1];
     block_tparts<1, double>(acc, mine, red);
     if (!arrive_last_t<1>(mine, reinterpret_cast<Part *>(partials), counter, ctl)) return;
@@ -1164,12 +1287,13 @@ __global__ void __launch_bounds__(kBlock) kb_dot_mu(int64_t d, const double *__r
         if (threadIdx.x == 0) *counter = 0u;
     }
 }
-// out[v] = || b - ((X~^T M X~) P_v + sig_v P_v) ||^2 from S = X^T V, t_v = 1^T V_v
+// lane v: r = b_v - ((X~^T M_v X~) P_v + sig_v P_v) from S = X^T V and t_v = 1^T V_v;
+// out[v] = ||r||^2; rvec[v][j] = r_j (v < nv) when rvec is not NULL
 __global__ void __launch_bounds__(kBlock) kb_resid(int64_t d, int nv, const double *__restrict__ b,
                                                   const double *__restrict__ mu, const double *__restrict__ S,
                                                   const double *__restrict__ P, const double *__restrict__ sig,
-                                                  const SolveState *st, BatchCtl *ctl, double *out, double *partials,
-                                                  unsigned *counter) {
+                                                  const SolveState *st, BatchCtl *ctl, double *out,
+                                                  double *__restrict__ rvec, double *partials, unsigned *counter) {
     using Part = CompSum<double>::Part;
     __shared__ Part red[kBlock];
     const int t = threadIdx.x % kTB;
@@ -1178,9 +1302,10 @@ __global__ void __launch_bounds__(kBlock) kb_resid(int64_t d, int nv, const doub
     const int64_t m = d * kTB;
     for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m; e += (int64_t)gridDim.x * kBlock) {
         const int64_t j = e / kTB;
-        const double q = S[e] - mu[j] * tv + sg * P[e];
-        const double r = b[j] - q;
+        const double q = S[e] - mu[e] * tv + sg * P[e];
+        const double r = b[e] - q;
         acc[0].add(r * r);
+        if (rvec && t < nv) rvec[(int64_t)t * d + j] = r;
     }
     Part mine[1];
     block_tparts<1, double>(acc, mine, red);
@@ -1217,51 +1342,60 @@ static int block64_setup(sda_operator *op, BatchWs *&B, double alpha, double ome
                         op->col.nsplits, (int64_t)B->part.n, (int64_t)(op->xr_col.n / 4)};
     *B->h_ctl = hc;
     SDA_CUDA(cudaMemcpyAsync(B->ctl.p, B->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
+    return SDA_OK;
+}
+
+static int block64_check(BatchWs *B, const char *what, cudaStream_t s) {
+    SDA_CUDA(cudaMemcpyAsync(B->h_ctl, B->ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
+    if (B->h_ctl->err)
+        return fail(SDA_ERR_INDEX, "%s: index check %llu failed at %llu", what,
+                    (unsigned long long)(B->h_ctl->err >> 40), (unsigned long long)(B->h_ctl->err & 0xffffffffffull));
     return SDA_OK;
 }
 
 template <class VT>
-static int resid_block_t(sda_operator *op, int t, const double *shifts, int ns, const double *b_perm,
-                         const double *W64, double *out_r2, double alpha, double omega, cudaStream_t s) {
+static int resid_lanes_t(sda_operator *op, const ResidLane *lanes, int nl, double *r2_host, double *rvec,
+                         double alpha, double omega, cudaStream_t s) {
     BatchWs *B = nullptr;
     SDA_TRY(block64_setup<VT>(op, B, alpha, omega, s));
     BView<double> bv = bview<double>(*B);
-    const int ge = grid_elems_b(std::max(B->ldw, B->n8) * kTB, op->sm_count);
-    const double *mu = op->mu.p + (int64_t)t * op->d;
-    kb_replab<<<ge, kBlock, 0, s>>>(op->n, op->labels.p + (int64_t)t * op->n, B->ylab.p);
-    SDA_LAUNCHED();
-    for (int c0 = 0; c0 < ns; c0 += kTB) {
-        const int nv = std::min(kTB, ns - c0);
-        double sig[kTB] = {0};
-        for (int v = 0; v < nv; ++v) sig[v] = shifts[c0 + v];
-        SDA_CUDA(cudaMemcpyAsync(B->b.p, sig, sizeof(sig), cudaMemcpyHostToDevice, s));
-        kb_pack<<<ge, kBlock, 0, s>>>(op->d, B->ldw, nv, W64 + (int64_t)c0 * op->d, bv.p);
-        SDA_LAUNCHED();
-        kb_dot_mu<<<B->grid, kBlock, 0, s>>>(op->d, mu, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
-        SDA_LAUNCHED();
-        kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->xr_rp.p, op->xr_col.p,
-                                                             (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, B->st.p,
-                                                             B->ctl.p);
-        SDA_LAUNCHED();
-        kb_phase2<double><<<B->grid, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, op->s_val64.p, bv.ut,
-                                                    op->deg64.p, B->ylab.p, bv.v, B->st.p, B->ctl.p, bv.coef, 0,
-                                                    B->part.p, B->cnt.p + 1);
-        SDA_LAUNCHED();
-        kb_phase3a<VT, double><<<B->grid, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
-                                                         (const VT *)op->x_val_c.p, bv.v, bv.s, B->slots.p,
-                                                         B->lcount.p, op->col.splits.p, B->ctl.p);
-        SDA_LAUNCHED();
-        kb_resid<<<B->grid, kBlock, 0, s>>>(op->d, nv, b_perm, mu, bv.s, bv.p, B->b.p, B->st.p, B->ctl.p,
-                                           out_r2 + c0, B->part.p, B->cnt.p + 2);
+    const int64_t d = op->d, n = op->n;
+    const int ge = grid_elems_b(std::max(B->ldw, B->n8), op->sm_count);
+    SDA_CUDA(cudaMemsetAsync(B->b.p, 0, B->b.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(B->mu64.p, 0, B->mu64.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(B->ylab.p, 0, B->ylab.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(bv.p, 0, (size_t)B->ldw * kTB * sizeof(double), s));
+    double sig[kTB] = {0};
+    for (int l = 0; l < nl; ++l) {
+        const int t = lanes[l].t;
+        sig[l] = lanes[l].sigma;
+        kb_put<double><<<ge, kBlock, 0, s>>>(d, lanes[l].w, bv.p, l);
+        kb_put<double><<<ge, kBlock, 0, s>>>(d, lanes[l].b, B->b.p, l);
+        kb_put<double><<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)t * d, B->mu64.p, l);
+        kb_put<int8_t><<<ge, kBlock, 0, s>>>(n, op->labels.p + (int64_t)t * n, B->ylab.p, l);
         SDA_LAUNCHED();
     }
-    SDA_CUDA(cudaMemcpyAsync(B->h_ctl, B->ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
-    SDA_CUDA(cudaStreamSynchronize(s));
-    if (B->h_ctl->err)
-        return fail(SDA_ERR_INDEX, "block residual: index check %llu failed at %llu",
-                    (unsigned long long)(B->h_ctl->err >> 40), (unsigned long long)(B->h_ctl->err & 0xffffffffffull));
-    return SDA_OK;
+    SDA_CUDA(cudaMemcpyAsync(B->sig.p, sig, sizeof(sig), cudaMemcpyHostToDevice, s));
+    kb_dot_mu<<<B->grid, kBlock, 0, s>>>(d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
+    SDA_LAUNCHED();
+    kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(n, B->ldw, op->xr_rp.p, op->xr_col.p,
+                                                         (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, B->st.p,
+                                                         B->ctl.p);
+    SDA_LAUNCHED();
+    kb_phase2<double><<<B->grid, kBlock, 0, s>>>(n, op->s_rp.p, op->s_col.p, op->s_val64.p, bv.ut, op->deg64.p,
+                                                B->ylab.p, bv.v, B->st.p, B->ctl.p, bv.coef, 0, B->part.p,
+                                                B->cnt.p + 1);
+    SDA_LAUNCHED();
+    kb_phase3a<VT, double><<<B->grid, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
+                                                     (const VT *)op->x_val_c.p, bv.v, bv.s, B->slots.p, B->lcount.p,
+                                                     op->col.splits.p, B->ctl.p);
+    SDA_LAUNCHED();
+    kb_resid<<<B->grid, kBlock, 0, s>>>(d, nl, B->b.p, B->mu64.p, bv.s, bv.p, B->sig.p, B->st.p, B->ctl.p, B->r2.p,
+                                       rvec, B->part.p, B->cnt.p + 2);
+    SDA_LAUNCHED();
+    SDA_CUDA(cudaMemcpyAsync(r2_host, B->r2.p, (size_t)nl * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return block64_check(B, "block residual", s);
 }
 
 template <class VT>
@@ -1271,13 +1405,19 @@ static int project_block_t(sda_operator *op, const double *Wn, int64_t nvec, dou
     SDA_TRY(block64_setup<VT>(op, B, 0.0, 1.0, s));
     BView<double> bv = bview<double>(*B);
     const int ge = grid_elems_b(std::max(B->ldw, B->n8) * kTB, op->sm_count);
+    if (centred) {
+        kb_rep<double><<<ge, kBlock, 0, s>>>(op->d, op->mu.p + (int64_t)t * op->d, B->mu64.p);
+        SDA_LAUNCHED();
+    }
     for (int64_t c0 = 0; c0 < nvec; c0 += kTB) {
         const int nv = (int)std::min<int64_t>(kTB, nvec - c0);
-        kb_pack<<<ge, kBlock, 0, s>>>(op->d, B->ldw, nv, Wn + c0 * op->d, bv.p);
-        SDA_LAUNCHED();
+        SDA_CUDA(cudaMemsetAsync(bv.p, 0, (size_t)B->ldw * kTB * sizeof(double), s));
+        for (int v = 0; v < nv; ++v) {
+            kb_put<double><<<ge, kBlock, 0, s>>>(op->d, Wn + (c0 + v) * op->d, bv.p, v);
+            SDA_LAUNCHED();
+        }
         if (centred) {
-            kb_dot_mu<<<B->grid, kBlock, 0, s>>>(op->d, op->mu.p + (int64_t)t * op->d, bv.p, B->st.p, B->ctl.p,
-                                                 B->part.p, B->cnt.p + 0);
+            kb_dot_mu<<<B->grid, kBlock, 0, s>>>(op->d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
             SDA_LAUNCHED();
         }
         kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->xr_rp.p, op->xr_col.p,
@@ -1287,27 +1427,37 @@ static int project_block_t(sda_operator *op, const double *Wn, int64_t nvec, dou
         kb_unpack<<<ge, kBlock, 0, s>>>(op->n, nv, bv.ut, scores + c0 * op->n);
         SDA_LAUNCHED();
     }
-    SDA_CUDA(cudaMemcpyAsync(B->h_ctl, B->ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
-    SDA_CUDA(cudaStreamSynchronize(s));
-    if (B->h_ctl->err)
-        return fail(SDA_ERR_INDEX, "block projection: index check %llu failed at %llu",
-                    (unsigned long long)(B->h_ctl->err >> 40), (unsigned long long)(B->h_ctl->err & 0xffffffffffull));
-    return SDA_OK;
+    return block64_check(B, "block projection", s);
+}
+
+int resid_lanes(sda_operator *op, const ResidLane *lanes, int nl, double *r2_host, double *rvec, double alpha,
+                double omega, cudaStream_t s) {
+    if (nl < 1 || nl > kTB) return fail(SDA_ERR_INVALID_ARG, "resid_lanes: %d lanes", nl);
+    return with_vt_b(op->compute, [&](auto tag) -> int {
+        using VT = std::remove_pointer_t<decltype(tag)>;
+        return resid_lanes_t<VT>(op, lanes, nl, r2_host, rvec, alpha, omega, s);
+    });
 }
 
 int resid_block(sda_operator *op, int t, const double *shifts, int ns, const double *b_perm, const double *W64,
                 double *out_r2, double alpha, double omega, cudaStream_t s) {
-    return with_vt_b(op->compute, [&](auto tag) -> int {
-        using VT = std::remove_pointer_t<decltype(tag)>;
-        return resid_block_t<BlockVT<VT>>(op, t, shifts, ns, b_perm, W64, out_r2, alpha, omega, s);
-    });
+    for (int c0 = 0; c0 < ns; c0 += kTB) {
+        const int nv = std::min(kTB, ns - c0);
+        ResidLane rl[kTB];
+        double r2[kTB];
+        for (int v = 0; v < nv; ++v) rl[v] = ResidLane{t, shifts[c0 + v], b_perm, W64 + (int64_t)(c0 + v) * op->d};
+        SDA_TRY(resid_lanes(op, rl, nv, r2, nullptr, alpha, omega, s));
+        SDA_CUDA(cudaMemcpyAsync(out_r2 + c0, r2, (size_t)nv * sizeof(double), cudaMemcpyHostToDevice, s));
+        SDA_CUDA(cudaStreamSynchronize(s));
+    }
+    return SDA_OK;
 }
 
 int project_block(sda_operator *op, const double *Wn, int64_t nvec, double *scores, int centred, int t,
                   cudaStream_t s) {
     return with_vt_b(op->compute, [&](auto tag) -> int {
         using VT = std::remove_pointer_t<decltype(tag)>;
-        return project_block_t<BlockVT<VT>>(op, Wn, nvec, scores, centred, t, s);
+        return project_block_t<VT>(op, Wn, nvec, scores, centred, t, s);
     });
 }
 

@@ -493,5 +493,7 @@ int radix_sort_pairs(uint32_t *keys, uint32_t *vals, int64_t n, int key_bits, cu
 int scan_exclusive_i64(int64_t *data, int64_t n, cudaStream_t s);
 
 int device_sm_count();
+// SDA_OK if `op_device` is the current device, else SDA_ERR_INVALID_ARG naming both
+int check_device(int op_device);
 
 }  // namespace sda

@@ -444,7 +444,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t d, int64_t ldw, cons
         st->gamma_prev = 1.0;
         st->t = 0.0;
         st->k = 0;
-        st->status = SDA_OK;
+        // a right-hand side with a non-finite entry stops the run before its
+        // first iteration (reported as a breakdown, not as a zero right-hand side)
+        st->status = (isfinite(tot[0]) && isfinite(tot[1])) ? SDA_OK : SDA_ERR_BREAKDOWN;
         *counter = 0u;
     }
     __syncthreads();

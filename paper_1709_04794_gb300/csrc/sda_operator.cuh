@@ -185,6 +185,18 @@ int solve_batched(sda_operator *op, int t0, int nt, const double *const *b_perm,
                   const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
                   cudaStream_t s, int *worst);
 void release_batch(sda_operator *op);
+// One vector of an FP64 block residual: w (device, permuted order) of target t,
+// against the right-hand side b, shifted by sigma.
+struct ResidLane {
+    int t;
+    double sigma;
+    const double *b;
+    const double *w;
+};
+// FP64 block of nl <= 16 lanes (sda_batch.cu): r2_host[l] = ||b_l - (B_{t_l} + sigma_l I) w_l||^2
+// (host array, written before return); rvec (device, optional): the residual vectors [nl][D]
+int resid_lanes(sda_operator *op, const ResidLane *lanes, int nl, double *r2_host, double *rvec, double alpha,
+                double omega, cudaStream_t s);
 // FP64 blocks of 16 vectors (sda_batch.cu): out_r2[v] = ||b - (B + shifts[v] I) W64[v]||^2 of
 // target t for v < ns (all device, permuted order); scores[v] = X Wn[v] (- <mu_t, Wn[v]> if centred)
 int resid_block(sda_operator *op, int t, const double *shifts, int ns, const double *b_perm, const double *W64,

@@ -52,6 +52,17 @@ void note_launch(int64_t n) {
 void set_capturing(bool on) { g_capturing = on; }
 int64_t launch_count() { return (int64_t)g_launches.load(); }
 
+// An operator's arrays live on the device that was current when it was built;
+// a call that would launch on another device is refused before any launch.
+int check_device(int op_device) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice", __FILE__, __LINE__);
+    if (dev != op_device)
+        return fail(SDA_ERR_INVALID_ARG, "the operator lives on device %d but device %d is current", op_device, dev);
+    return SDA_OK;
+}
+
 int device_sm_count() {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;

@@ -710,6 +710,7 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
                                         void *cuda_stream) {
     clear_error();
     if (!op || !shifts) return fail(SDA_ERR_INVALID_ARG, "operator and shifts must not be NULL");
+    SDA_TRY(check_device(op->device));
     if (n_shifts < 1 || n_shifts > kMaxShifts) return fail(SDA_ERR_INVALID_ARG, "n_shifts must be in [1, %d]", kMaxShifts);
     for (int i = 0; i < n_shifts; ++i)
         if (!(shifts[i] > 0.0) || !isfinite(shifts[i])) return fail(SDA_ERR_INVALID_ARG, "shifts must be finite and > 0");
@@ -755,8 +756,6 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
     int worst = SDA_OK;
     DevBuf<double> bt;
     if (o.batch_targets) {
-        if (o.refine_rounds > 0)
-            return fail(SDA_ERR_UNSUPPORTED, "batched targets do not combine with refinement");
         // right-hand side of every target of the call, then the batches
         std::vector<const double *> bl((size_t)tc);
         if (o.rhs_mode == SDA_RHS_FROM_R) SDA_TRY(bt.alloc((size_t)tc * d + 1));
@@ -827,6 +826,7 @@ extern "C" SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double
                                         double *lambda_out, void *cuda_stream) {
     clear_error();
     if (!op || !w || !d_alpha || !d_beta) return fail(SDA_ERR_INVALID_ARG, "NULL argument");
+    SDA_TRY(check_device(op->device));
     if (n_rows < 0 || (n_rows > 0 && (!rows || !dloss_ds))) return fail(SDA_ERR_INVALID_ARG, "bad held-out rows");
     if (target < 0 || target >= op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target out of range");
     if (!(beta > 0.0) || !isfinite(beta)) return fail(SDA_ERR_INVALID_ARG, "beta must be finite and > 0");
@@ -914,6 +914,7 @@ extern "C" SDA_API int sda_operator_apply(const sda_operator *op, int32_t target
                                           double *q, void *cuda_stream) {
     clear_error();
     if (!op || !p || !q) return fail(SDA_ERR_INVALID_ARG, "NULL argument");
+    SDA_TRY(check_device(op->device));
     if (target < 0 || target >= op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target out of range");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     sda_operator *mop = const_cast<sda_operator *>(op);
@@ -930,6 +931,7 @@ extern "C" SDA_API int sda_project(const sda_operator *op, const double *w, int6
                                    int32_t centred, int32_t target, void *cuda_stream) {
     clear_error();
     if (!op || !w || !scores || n_vec < 0) return fail(SDA_ERR_INVALID_ARG, "bad argument");
+    SDA_TRY(check_device(op->device));
     if (centred && (target < 0 || target >= op->n_targets)) return fail(SDA_ERR_INVALID_ARG, "target out of range");
     cudaStream_t s = (cudaStream_t)cuda_stream;
     sda_operator *mop = const_cast<sda_operator *>(op);
@@ -969,10 +971,16 @@ extern "C" SDA_API int sda_get_target_counts(const sda_operator *op, double *cou
 
 extern "C" SDA_API void sda_destroy_operator(sda_operator *op) {
     if (!op) return;
+    // free on the operator's own device, then give the caller back theirs
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    const int dev = op->device;
+    if (prev != dev) cudaSetDevice(dev);
     cudaDeviceSynchronize();
     release_workspace(op);
     release_batch(op);
     delete op;
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
 }
 
 extern "C" SDA_API const char *sda_status_string(int code) {

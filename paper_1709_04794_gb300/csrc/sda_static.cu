@@ -103,6 +103,7 @@ extern "C" SDA_API int sda_operator_apply_static(const sda_operator *op, int32_t
                                                  const double *p, double *q, void *cuda_stream) {
     clear_error();
     if (!op || !p || !q) return fail(SDA_ERR_INVALID_ARG, "NULL argument");
+    SDA_TRY(check_device(op->device));
     if (target < 0 || target >= op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target out of range");
     const int64_t nslots = (int64_t)op->col.nslots + op->xrow.nslots + op->srow.nslots;
     const int64_t nsplits = (int64_t)op->col.nsplits + op->xrow.nsplits + op->srow.nsplits;

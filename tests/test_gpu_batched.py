@@ -7,13 +7,16 @@ target and against the one-target-at-a-time path.
 FP64 after a fixed number of iterations 1e-9 relative per (target, shift);
 FP64 converged to tol 1e-10, batched and sequential solutions within 1e-6 of
 each other, FP64 true residuals below 1e-9 and iteration counts within 3 %;
-the mixed path's true residual within 20 x tol.
+the mixed path's true residual within 20 x tol; the mixed path refined per
+(target, shift) to FP64 residuals of 1e-11, against the oracle at the
+spec bar (see parity.py).
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
+import parity
 from paper_1709_04794_gb300 import sda, synth
 
 pytestmark = pytest.mark.gpu
@@ -94,14 +97,48 @@ def test_batched_target_range(multi):
             assert _rel(wb[t, s], ws[t, s]) < 1e-12
 
 
-def test_batched_rejects_refinement(multi):
+def test_batched_refined_matches_oracle(multi):
+    """Batched mixed path (FP16 X, FP32 vectors) with per-pair FP64 refinement
+    against the FP64 oracle at tol 1e-13, per (target, shift): FP64 true
+    residual <= refine_tol; w within 1e-6 (norm-wise and element-wise) where
+    the residual bound allows it, else within that bound; AUC of the held-out
+    rows equal to 4 decimals on every shift."""
+    rtol = 1e-11
     op = sda.Operator(multi, compute="f16")
+    ns, d = len(multi.shifts), multi.d
+    w = torch.empty((T, ns, d), dtype=torch.float64, device="cuda")
     o = sda.sda_default_opts()
-    o.batch_targets, o.refine_rounds = 1, 2
-    w = torch.empty((T, len(multi.shifts), multi.d), dtype=torch.float64, device="cuda")
-    with pytest.raises(sda.SDAError) as e:
-        sda.sda_solve_shifts(op.handle, multi.shifts, o, w_out=w, n_report=T)
-    assert e.value.code == sda.SDA_ERR_UNSUPPORTED
+    o.tol, o.max_iter, o.batch_targets = 1e-4, 20000, 1
+    o.refine_rounds, o.refine_tol = 12, rtol
+    code, rep = sda.sda_solve_shifts(op.handle, multi.shifts, o, w_out=w, n_report=T)
+    assert code == sda.SDA_OK
+    wg = w.cpu().numpy()
+    for t in range(T):
+        for r in rep[t]:
+            assert r["status"] == sda.SDA_OK and r["true_residual"] <= rtol, (t, r)
+        ob = oracle.from_problem(multi, target=t)
+        b = ob.rhs_canonical()
+        ref = ob.shifted_cg(b, multi.shifts, tol=1e-13, max_iter=50000)
+        lam = parity.lambda_max(ob)
+        rows = multi.heldout[t]
+        for s, beta in enumerate(multi.shifts):
+            rho = ob.true_residual(b, beta, wg[t, s])
+            rho_ref = ob.true_residual(b, beta, ref.W[s])
+            assert rho <= 1.5 * rtol, (t, s, rho)      # the oracle's own FP64 apply agrees
+            parity.check(parity.compare(wg[t, s], ref.W[s], beta, lam, rho, rho_ref), (t, s))
+            a_gpu = oracle.auc(ob.project(wg[t, s])[rows], multi.truth[t][rows])
+            a_ref = oracle.auc(ob.project(ref.W[s])[rows], multi.truth[t][rows])
+            assert abs(a_gpu - a_ref) < parity.AUC_BAR, (t, s, a_gpu, a_ref)
+
+
+def test_batched_refinement_off_by_default(multi):
+    code, rep, w = _solve(multi, "f16", 1, tol=1e-4)
+    op = sda.Operator(multi, compute="f16")
+    w2 = torch.empty((T, len(multi.shifts), multi.d), dtype=torch.float64, device="cuda")
+    o = sda.sda_default_opts()
+    o.tol, o.max_iter, o.batch_targets, o.refine_tol = 1e-4, 20000, 1, 1e-12
+    code2, rep2 = sda.sda_solve_shifts(op.handle, multi.shifts, o, w_out=w2, n_report=T)
+    assert np.array_equal(w, w2.cpu().numpy())
 
 
 def test_batched_full_size_first_batch():

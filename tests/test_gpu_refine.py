@@ -4,16 +4,17 @@ FP64 true residual exceeds refine_tol gets corrections c solved from
 FP64.  Refined, the FP16/FP32 solve reaches FP64-level residuals; its solution
 is then compared with the FP64 oracle's at the same residual.
 
-Bar: every shift's FP64 true residual <= refine_tol (1e-10).  The relative
-error of w is then at most kappa_s x 1e-10 plus the oracle's own (tol 1e-13);
-on the 2k workload kappa_s <= 1e5 for the shifts >= 1e-2, so those agree to
-1e-5 with room, and AUC agrees to 4 decimals on every shift.
+Bar: every shift's FP64 true residual <= refine_tol (1e-11); w against the
+FP64 oracle (tol 1e-13) within 1e-6 norm-wise and element-wise on every shift
+whose residual bound kappa_s (rho + rho*) permits it, else within that bound
+(reported); AUC equal to 4 decimals on every shift (parity.py).
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
+import parity
 from paper_1709_04794_gb300 import sda
 
 pytestmark = pytest.mark.gpu
@@ -35,22 +36,24 @@ def _solve(prob, compute, tol, rounds=0, rtol=float("nan"), max_iter=20000):
 
 
 def test_refined_mixed_reaches_fp64_residual(cfg1):
-    rtol = 1e-10
-    code, rep, w = _solve(cfg1, "f16", 1e-4, rounds=8, rtol=rtol)
+    rtol = 1e-11
+    code, rep, w = _solve(cfg1, "f16", 1e-4, rounds=12, rtol=rtol)
     assert code == sda.SDA_OK
     for r in rep:
         assert r["status"] == sda.SDA_OK and r["true_residual"] <= rtol, r
     o = oracle.from_problem(cfg1)
-    ref = o.shifted_cg(o.rhs_canonical(), cfg1.shifts, tol=1e-13, max_iter=50000)
-    X = oracle.dense_x(cfg1.x_ptr, cfg1.x_col, cfg1.x_val, cfg1.d)
+    b = o.rhs_canonical()
+    ref = o.shifted_cg(b, cfg1.shifts, tol=1e-13, max_iter=50000)
+    lam = parity.lambda_max(o)
     rows = cfg1.heldout[0]
     y = cfg1.truth[0][rows]
     for s, beta in enumerate(cfg1.shifts):
-        if beta >= 1e-2:
-            assert _rel(w[s], ref.W[s]) < 1e-5, (s, _rel(w[s], ref.W[s]))
-        auc_gpu = oracle.auc(X[rows] @ w[s], y)
-        auc_ref = oracle.auc(X[rows] @ ref.W[s], y)
-        assert abs(auc_gpu - auc_ref) < 5e-5, (s, auc_gpu, auc_ref)
+        rho, rho_ref = o.true_residual(b, beta, w[s]), o.true_residual(b, beta, ref.W[s])
+        assert rho <= 1.5 * rtol, (s, rho)
+        parity.check(parity.compare(w[s], ref.W[s], beta, lam, rho, rho_ref), s)
+        auc_gpu = oracle.auc(o.project(w[s])[rows], y)
+        auc_ref = oracle.auc(o.project(ref.W[s])[rows], y)
+        assert abs(auc_gpu - auc_ref) < parity.AUC_BAR, (s, auc_gpu, auc_ref)
 
 
 def test_refinement_off_by_default(cfg1):

@@ -1,6 +1,6 @@
 """sda_operator_apply_static: the operator apply for callers that cannot
-allocate device memory (inside a stream capture, under a pool allocator that
-owns all device memory, or where cudaMalloc's implicit synchronisation is not
+allocate device memory (an application whose pool allocator owns all device
+memory, or a loop where cudaMalloc's implicit synchronisation is not
 acceptable).  Its scratch is a fixed device array inside the library.
 
 The result must equal the allocating sda_operator_apply's within the tolerance
@@ -35,6 +35,30 @@ def test_static_apply_matches_allocating_apply(compute):
         sda.sda_operator_apply_static(op.handle, 0, sigma, p, q_st)
         torch.cuda.synchronize()
         assert _rel(q_st.cpu().numpy(), q_ref.cpu().numpy()) < 1e-12, (call, sigma)
+
+
+@pytest.mark.parametrize("kind", ["regression", "sa"])
+def test_static_apply_other_operators(kind):
+    """The X^T X operator of CSR-SDA's regression step (no graph, no centring)
+    and SA-SDA's operator (X = I_N) go through the same row and column passes."""
+    prob = synth.custom_problem(2500, 900, 14, seed=8, values="counts", n_labelled=300, k=5,
+                                shifts=(1e-3, 1e2, 5))
+    if kind == "regression":
+        op = sda.Operator.regression(prob.x_ptr, prob.x_col, prob.x_val, prob.d, compute="f16")
+        dim = prob.d
+    else:
+        op = sda.Operator.sa(prob.s_ptr, prob.s_col, prob.s_val, prob.labels, prob.alpha, compute="f32")
+        dim = prob.n
+    rng = np.random.default_rng(12)
+    for call, sigma in enumerate((0.0, 0.3)):
+        p = torch.from_numpy(rng.standard_normal(dim)).cuda()
+        q_ref = torch.empty(dim, dtype=torch.float64, device="cuda")
+        q_st = torch.full((dim,), float("nan"), dtype=torch.float64, device="cuda")
+        sda.sda_operator_apply(op.handle, 0, sigma, p, q_ref)
+        sda.sda_operator_apply_static(op.handle, 0, sigma, p, q_st)
+        torch.cuda.synchronize()
+        assert _rel(q_st.cpu().numpy(), q_ref.cpu().numpy()) < 1e-12, (kind, call, sigma)
+    op.close()
 
 
 def test_static_apply_rejects_oversized_operator():
