@@ -272,6 +272,37 @@ SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double alpha, dou
                              void *cuda_stream);
 
 /*
+ * sda_adjoint_grad_batched - sda_adjoint_grad for many targets at once (not
+ * in the paper): target targets[i] at (alpha, betas[i]) with the solution
+ * W[i] and the held-out rows rows[row_off[i] .. row_off[i + 1]) with their
+ * loss gradients dloss_ds[same range].  The adjoint solves
+ * (B_t + beta_i I) lambda_i = (X_h - 1 mu_l^T)^T g_i of up to 16 targets share
+ * one batched run (the batched path of sda_solve_shifts, one shift per lane);
+ * the contractions are FP64 per target, as in sda_adjoint_grad.
+ *
+ *   n_targets            number of gradients (0: nothing to do)
+ *   targets, betas       host arrays [n_targets] (targets may repeat)
+ *   alpha                the common alpha (NaN: the operator's)
+ *   W                    [n_targets][D] doubles, device, caller's feature order
+ *   dloss_ds, rows       device arrays of row_off[n_targets] doubles / int64 row ids
+ *   row_off              host int64 [n_targets + 1], row_off[0] = 0, non-decreasing
+ *   opt                  tolerance, cap, fixed_iters, refinement of the adjoint solves
+ *                        (NULL: defaults with tol 1e-10); its alpha/scatter_weight,
+ *                        rhs and target range are ignored
+ *   d_alpha, d_beta      host [n_targets]
+ *   lambda_out           [n_targets][D] doubles (device, caller order), or NULL
+ *   report               host [n_targets] reports of the adjoint solves, or NULL
+ * Errors: INVALID_ARG (a row or target out of range, bad offsets), UNSUPPORTED
+ * (regression operator), BREAKDOWN, CUDA, OOM; SDA_NOT_CONVERGED when an
+ * adjoint solve hit its cap.  Synchronises the stream.
+ */
+SDA_API int sda_adjoint_grad_batched(sda_operator *op, int32_t n_targets, const int32_t *targets, double alpha,
+                                     const double *betas, const double *W, const double *dloss_ds,
+                                     const int64_t *rows, const int64_t *row_off, const sda_solve_opts *opt,
+                                     double *d_alpha, double *d_beta, double *lambda_out,
+                                     sda_shift_report *report, void *cuda_stream);
+
+/*
  * sda_project - ratings s = X w of the samples (Sec. 4, Alg. 7 step 5), or
  * the centred ratings (X - 1 mu_l^T) w when `centred` is 1 (uses mu_l of
  * `target`).  FP64 sums.
@@ -281,6 +312,21 @@ SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double alpha, dou
  */
 SDA_API int sda_project(const sda_operator *op, const double *w, int64_t n_vec, double *scores,
                         int32_t centred, int32_t target, void *cuda_stream);
+
+/*
+ * sda_project_rows - the ratings of a subset of the samples only (Sec. 4,
+ * Alg. 7 step 5 restricted to the rows one scores, e.g. held-out compounds):
+ * scores[v][h] = (X w_v)_{rows[h]}, or the centred (X w_v)_{rows[h]} - mu_l^T w_v
+ * when `centred` is 1 (mu_l of `target`).  FP64 sums.
+ *
+ *   w        [n_vec][D] doubles in the caller's feature order (device)
+ *   rows     n_rows row ids (device int64); repeated ids are allowed
+ *   scores   [n_vec][n_rows] doubles (device)
+ * Errors: INVALID_ARG (a row id outside [0, N), bad argument), CUDA, OOM.
+ * Synchronises the stream.
+ */
+SDA_API int sda_project_rows(const sda_operator *op, const double *w, int32_t n_vec, const int64_t *rows,
+                             int64_t n_rows, double *scores, int32_t centred, int32_t target, void *cuda_stream);
 
 /*
  * sda_operator_apply - q = (B + sigma I) p for one target in FP64 (the

@@ -22,6 +22,8 @@ Functions and what they follow:
   rank-sum formula with average ranks for ties.
 * :func:`adjoint_grad_dense` - d loss / d(alpha, beta) by the adjoint of the
   regularised system (not in the paper; checks the library's adjoint).
+* :func:`adjoint_grad_sparse` - the same through the C oracle's CG and sparse
+  products, for problems too large to densify.
 
 Every function above is pinned by the ``-m "not gpu"`` tests against
 closed forms, dense definitions, special cases and brute force
@@ -319,3 +321,33 @@ def adjoint_grad_dense(X, s_ptr, s_col, s_val, y, alpha, beta, rows, y_rows, b=N
     d_beta = -lam @ w
     d_alpha = -lam @ ((XLX - St) @ w)
     return loss, float(d_alpha), float(d_beta), w
+
+
+def adjoint_grad_sparse(o: Oracle, x_ptr, x_col, x_val, s_ptr, s_col, s_val, rows, y_rows, beta,
+                        tol=1e-12, max_iter=100000):
+    """d loss/d alpha and d loss/d beta of the held-out logistic loss, for
+    problems too large for adjoint_grad_dense: the two solves are the C
+    oracle's CG (Algorithm 2) on its operator, the products sparse.
+
+    w = (B + beta I)^{-1} d, s_h = (X_h - 1 mu_l^T) w, loss = mean log(1 + exp(-y s_h));
+    lambda = (B + beta I)^{-1} (X_h - 1 mu_l^T)^T g,  g = d loss / d s_h;
+    d loss/d beta = -lambda^T w,  d loss/d alpha = -lambda^T (dB/dalpha) w with
+    dB/dalpha = X^T L X - S_t^l (B = (1 - alpha) S_t^l + alpha X^T L X, eq. 7).
+    Returns (loss, d_alpha, d_beta, w)."""
+    import scipy.sparse as sp
+    n, d = o.n, o.d
+    X = sp.csr_matrix((np.asarray(x_val, float), np.asarray(x_col), np.asarray(x_ptr)), shape=(n, d))
+    S = sp.csr_matrix((np.asarray(s_val, float), np.asarray(s_col), np.asarray(s_ptr)), shape=(n, n))
+    L = sp.diags(np.asarray(S.sum(axis=1)).ravel()) - S
+    mu, mp, mn, _ = o.class_means()
+    lab = (np.asarray(o._keep[6]) != 0).astype(float)
+    w, _, _, rc = o.cg(mp - mn, beta, tol=tol, max_iter=max_iter)
+    rows = np.asarray(rows)
+    s = X[rows] @ w - mu @ w
+    loss, g = logistic_loss(s, y_rows)
+    c = X[rows].T @ g - mu * g.sum()
+    lam, _, _, rc2 = o.cg(c, beta, tol=tol, max_iter=max_iter)
+    u = X @ w - mu @ w                      # centred ratings of every sample
+    St_w = X.T @ (lab * u) - mu * (lab * u).sum()
+    XLX_w = X.T @ (L @ (X @ w))
+    return loss, float(-lam @ (XLX_w - St_w)), float(-lam @ w), w

@@ -2,7 +2,8 @@
 
 * ``libsda.so``   - the C-ABI library (CUDA kernels for sm_103a + host runtime),
                      built with nvcc from ``csrc/``.
-* ``_synth_knn.so`` - the input generator's kNN-graph helper, built with gcc.
+* ``_synth_native.so`` - the input generator's native helpers (kNN graph, large
+                     workloads), built with gcc.
 
 Everything is compiled in place next to its sources; nothing is installed.
 """
@@ -17,7 +18,7 @@ from concurrent.futures import ThreadPoolExecutor
 PKG_DIR = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG_DIR, "csrc")
 LIBSDA = os.path.join(PKG_DIR, "libsda.so")
-SYNTH_SO = os.path.join(PKG_DIR, "_synth_knn.so")
+SYNTH_SO = os.path.join(PKG_DIR, "_synth_native.so")
 MACHINE = platform.machine()
 BUILD_DIR = os.path.join(PKG_DIR, "_build", MACHINE)
 
@@ -48,10 +49,10 @@ def _run(cmd: list[str]) -> None:
 
 
 def build_synth(force: bool = False) -> str:
-    src = os.path.join(PKG_DIR, "synth_knn.c")
+    src = os.path.join(PKG_DIR, "synth_native.c")
     if force or _newer(SYNTH_SO, [src]):
         tmp = SYNTH_SO + ".tmp%d" % os.getpid()
-        _run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", src, "-o", tmp])
+        _run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", src, "-o", tmp, "-lm"])
         os.replace(tmp, SYNTH_SO)
         _stamp(SYNTH_SO)
     return SYNTH_SO

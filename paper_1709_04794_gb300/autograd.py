@@ -65,3 +65,62 @@ class HeldOutLoss(torch.autograd.Function):
 def held_out_loss(alpha, beta, op, target, rows, y_rows, tol=1e-10, max_iter=20000):
     """Differentiable held-out logistic loss (see module docstring)."""
     return HeldOutLoss.apply(alpha, beta, op, target, rows, y_rows, tol, max_iter)
+
+
+class HeldOutLossBatched(torch.autograd.Function):
+    """Mean over the targets t0 .. t0 + T - 1 of each one's held-out logistic
+    loss at a common (alpha, beta): the forward solves all T targets in the
+    batched path (sda_solve_shifts with batch_targets, one shift) and scores
+    their held-out rows (sda_project_rows, centred); the backward runs the T
+    adjoint solves batched (sda_adjoint_grad_batched) and sums the gradients."""
+
+    @staticmethod
+    def forward(ctx, alpha, beta, op, t0, T, rows, row_off, y_rows, tol, max_iter, refine_rounds, refine_tol):
+        a, b = float(alpha), float(beta)
+        d = op.info["n_cols"]
+        dev = rows.device
+        w = torch.empty((T, 1, d), dtype=torch.float64, device=dev)
+        o = _solve_opts(op, t0, tol, max_iter, a)
+        o.target_count, o.batch_targets = int(T), 1
+        o.refine_rounds, o.refine_tol = int(refine_rounds), float(refine_tol)
+        sda.sda_solve_shifts(op.handle, [b], o, w_out=w, n_report=T)
+        off = [int(x) for x in row_off]
+        s_h = torch.empty(off[-1], dtype=torch.float64, device=dev)
+        for i in range(T):
+            r = rows[off[i]:off[i + 1]].contiguous()
+            sc = torch.empty((1, r.numel()), dtype=torch.float64, device=dev)
+            sda.sda_project_rows(op.handle, w[i, 0], 1, r, sc, centred=1, target=t0 + i)
+            s_h[off[i]:off[i + 1]] = sc[0]
+        y = y_rows.to(torch.float64)
+        z = -y * s_h
+        counts = torch.tensor([off[i + 1] - off[i] for i in range(T)], dtype=torch.float64, device=dev)
+        per_row = torch.repeat_interleave(1.0 / (counts * T), counts.to(torch.int64))
+        loss = (torch.nn.functional.softplus(z) * per_row).sum()
+        g = (-y * torch.sigmoid(z) * per_row).contiguous()
+        ctx.save_for_backward(w, g, rows)
+        ctx.op, ctx.t0, ctx.T, ctx.off, ctx.a, ctx.b = op, t0, T, off, a, b
+        ctx.opt = (tol, max_iter, refine_rounds, refine_tol)
+        return loss.detach()
+
+    @staticmethod
+    def backward(ctx, grad):
+        w, g, rows = ctx.saved_tensors
+        tol, max_iter, rr, rt = ctx.opt
+        o = _solve_opts(ctx.op, ctx.t0, tol, max_iter)
+        o.refine_rounds, o.refine_tol = int(rr), float(rt)
+        targets = list(range(ctx.t0, ctx.t0 + ctx.T))
+        code, da, db, _ = sda.sda_adjoint_grad_batched(ctx.op.handle, targets, ctx.a, [ctx.b] * ctx.T,
+                                                       w[:, 0].contiguous(), g, rows.to(torch.int64).contiguous(),
+                                                       ctx.off, o)
+        ga = grad * torch.tensor(float(da.sum()), dtype=grad.dtype, device=grad.device)
+        gb = grad * torch.tensor(float(db.sum()), dtype=grad.dtype, device=grad.device)
+        return ga, gb, None, None, None, None, None, None, None, None, None, None
+
+
+def held_out_loss_batched(alpha, beta, op, t0, T, rows, row_off, y_rows, tol=1e-10, max_iter=20000,
+                          refine_rounds=0, refine_tol=float("nan")):
+    """Differentiable mean held-out loss of T targets at a common (alpha, beta)
+    (see HeldOutLossBatched); rows / y_rows concatenate the targets' held-out
+    rows and classes, row_off [T + 1] delimits them."""
+    return HeldOutLossBatched.apply(alpha, beta, op, t0, T, rows, row_off, y_rows, tol, max_iter, refine_rounds,
+                                    refine_tol)

@@ -600,7 +600,8 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
     using R = typename RPair<FT>::T;
     using Part = typename CompSum<FT>::Part;
     __shared__ Part red[kBlock * 3];
-    __shared__ BatchCoef<FT> cf[kMaxShifts * kTB];
+    extern __shared__ __align__(16) unsigned char kb3b_dyn[];   // the ns x kTB coefficients
+    BatchCoef<FT> *cf = reinterpret_cast<BatchCoef<FT> *>(kb3b_dyn);
     __shared__ int any[kMaxShifts];
     __shared__ int s_act[kMaxShifts];
     __shared__ int s_nact;
@@ -819,9 +820,9 @@ __global__ void kb_add_lane(int64_t d, const FT *__restrict__ W, int t, double *
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
-static int grid_for(const void *kernel, int sms) {
+static int grid_for(const void *kernel, int sms, size_t dyn_smem = 0) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, 0) != cudaSuccess || nb <= 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, dyn_smem) != cudaSuccess || nb <= 0) {
         (void)cudaGetLastError();
         nb = 1;
     }
@@ -931,8 +932,9 @@ static int batch_iteration(sda_operator *op, int ns, cudaStream_t s, cudaEvent_t
 
     if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
-    kb_phase3b<FT><<<b.grid, kBlock, 0, s>>>(op->d, b.ldw, ns, bv.s, bv.pairs, bv.W, bv.P, b.st.p, b.ctl.p, bv.coef,
-                                            b.mu32.p, b.mu64.p, b.part.p + (int64_t)P * kTB * 2, b.cnt.p + 1);
+    kb_phase3b<FT><<<b.grid, kBlock, (size_t)ns * kTB * sizeof(BatchCoef<FT>), s>>>(
+        op->d, b.ldw, ns, bv.s, bv.pairs, bv.W, bv.P, b.st.p, b.ctl.p, bv.coef, b.mu32.p, b.mu64.p,
+        b.part.p + (int64_t)P * kTB * 2, b.cnt.p + 1);
     SDA_LAUNCHED();
     if (ev) SDA_CUDA(cudaEventRecord(ev[7], s));
 
@@ -1014,11 +1016,13 @@ static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const dou
     SDA_TRY(ensure_batch<FT>(op, ns));
     BatchWs &b = *op->bws;
     if (!b.grid) {
+        SDA_CUDA(cudaFuncSetAttribute((const void *)kb_phase3b<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kMaxShifts * kTB * sizeof(BatchCoef<FT>))));
         b.grid1 = grid_for((const void *)kb_phase1<BVT<VT>, FT>, op->sm_count);
         b.grid2 = grid_for((const void *)kb_phase2<FT>, op->sm_count);
         b.grid3a = grid_for((const void *)kb_phase3a<VT, FT>, op->sm_count);
-        b.grid = std::min(std::min(b.grid1, b.grid2), std::min(b.grid3a, grid_for((const void *)kb_phase3b<FT>,
-                                                                                    op->sm_count)));
+        b.grid = std::min(std::min(b.grid1, b.grid2), std::min(b.grid3a, grid_for((const void *)kb_phase3b<FT>, op->sm_count,
+                                                                    kMaxShifts * kTB * sizeof(BatchCoef<FT>))));
     }
     const int64_t d = op->d, n = op->n;
     const int ge = grid_elems_b(std::max(b.ldw, b.n8), op->sm_count);
@@ -1080,36 +1084,41 @@ static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const dou
     return SDA_OK;
 }
 
-// One batch: targets t0 .. t0 + nt - 1 (nt <= kTB) share one run; then the
-// FP64 true residual of every (target, shift) and, with refine_rounds > 0,
-// per-pair refinement: while a pair's FP64 true residual exceeds refine_tol,
-// its correction (B_t + beta_s I) c = b_t - (B_t + beta_s I) w_ts is solved in
-// the iteration's precision and added in FP64; the corrections of up to kTB
-// pairs (of any targets and shifts) run as the lanes of one batched run.
+// Outcome of a batched run of lanes, per (lane, shift) pair [lane][shift]: the
+// final solve states of the lanes, FP64 true residuals (-1: not computed) and
+// refinement statuses.
+struct LaneOutcome {
+    std::vector<SolveState> fin;
+    std::vector<double> tres, bn;
+    std::vector<int> pst;
+};
+
+// Lanes l < nl (<= kTB) share one shifted-CG run of the ns relative shifts
+// `deltas`; pair (l, s) solves (B_{t_l} + pshift[l ns + s] I) w = b_l (the run
+// uses sigma0_l + delta_s for it).  Leaves the FP64 solutions in the
+// workspace's wall ([l][s][D], permuted order).  Then the FP64 true residual
+// of every pair and, with refine_rounds > 0, per-pair refinement: while a
+// pair's FP64 true residual exceeds refine_tol, its correction
+// (B_t + beta I) c = b_t - (B_t + beta I) w is solved in the iteration's
+// precision and added in FP64; the corrections of up to kTB pairs (of any
+// lanes and shifts, grouped by shift value) run as the lanes of one batched run.
 template <class VT, class FT>
-static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_perm, const double *shifts, int ns,
-                       const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
-                       cudaStream_t s, int *worst) {
+static int solve_lanes(sda_operator *op, const BatchLane *lanes, int nl, const double *deltas, const double *pshift,
+                       int ns, const sda_solve_opts &o, double alpha, double omega, cudaStream_t s, LaneOutcome &out) {
     const int64_t d = op->d;
     const bool fixed = o.fixed_iters > 0;
-    double sigma0 = shifts[0];
-    for (int i = 1; i < ns; ++i) sigma0 = std::min(sigma0, shifts[i]);
-    std::vector<double> deltas((size_t)ns);
-    for (int i = 0; i < ns; ++i) deltas[(size_t)i] = shifts[i] - sigma0;
-    BatchLane lanes[kTB];
-    for (int i = 0; i < nt; ++i) lanes[i] = BatchLane{t0 + i, b_perm[i], sigma0, o.tol};
-    SDA_TRY((run_lanes<VT, FT>(op, lanes, nt, deltas.data(), ns, fixed, fixed ? o.fixed_iters : o.max_iter, o, alpha,
+    SDA_TRY((run_lanes<VT, FT>(op, lanes, nl, deltas, ns, fixed, fixed ? o.fixed_iters : o.max_iter, o, alpha,
                                omega, s)));
     BatchWs &b = *op->bws;
-    const std::vector<SolveState> fin(b.h_st, b.h_st + kTB);   // later runs reuse h_st
-    for (int i = 0; i < nt; ++i)
+    out.fin.assign(b.h_st, b.h_st + kTB);   // later runs reuse h_st
+    const std::vector<SolveState> &fin = out.fin;
+    for (int i = 0; i < nl; ++i)
         for (int sh = 0; sh < ns; ++sh) op->stats.shift_iterations += fin[(size_t)i].sh[sh].iters;
-    // the FP64 solutions of every (target, shift) of the batch, [i][s][j], permuted order
-    const size_t wall_n = (size_t)nt * ns * d;
+    const size_t wall_n = (size_t)nl * ns * d;
     if (b.wall.n < wall_n) SDA_TRY(b.wall.alloc(wall_n));
     {
         BView<FT> bv = bview<FT>(b);
-        for (int i = 0; i < nt; ++i) {
+        for (int i = 0; i < nl; ++i) {
             kb_take_w<FT><<<grid_elems_b((int64_t)ns * d, op->sm_count), kBlock, 0, s>>>(
                 d, b.ldw, ns, bv.W, i, b.wall.p + (int64_t)i * ns * d);
             SDA_LAUNCHED();
@@ -1118,89 +1127,103 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
     const int rounds = fixed ? 0 : std::max(0, o.refine_rounds);
     const double rtol = std::isnan(o.refine_tol) || o.refine_tol <= 0.0 ? o.tol : o.refine_tol;
     const bool check = o.check_residual != 0 || rounds > 0;
-    std::vector<double> tres((size_t)nt * ns, -1.0), bn((size_t)nt, 0.0);
-    std::vector<int> pst((size_t)nt * ns, SDA_OK);
-    if (check) {
-        // ||b_t|| of every target
+    std::vector<double> &tres = out.tres, &bn = out.bn;
+    std::vector<int> &pst = out.pst;
+    tres.assign((size_t)nl * ns, -1.0);
+    bn.assign((size_t)nl, 0.0);
+    pst.assign((size_t)nl * ns, SDA_OK);
+    if (!check) return SDA_OK;
+    {   // ||b_l|| of every lane
         DevBuf<double> bb;
-        SDA_TRY(bb.alloc((size_t)nt));
-        for (int i = 0; i < nt; ++i) SDA_TRY(dot_f64(op, d, b_perm[i], b_perm[i], bb.p + i, s));
-        std::vector<double> hb((size_t)nt);
-        SDA_CUDA(cudaMemcpyAsync(hb.data(), bb.p, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SDA_TRY(bb.alloc((size_t)nl));
+        for (int i = 0; i < nl; ++i) SDA_TRY(dot_f64(op, d, lanes[i].b, lanes[i].b, bb.p + i, s));
+        SDA_CUDA(cudaMemcpyAsync(bn.data(), bb.p, (size_t)nl * sizeof(double), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
-        for (int i = 0; i < nt; ++i) bn[(size_t)i] = sqrt(hb[(size_t)i]);
-        auto lane_of = [&](int q) {
-            const int i = q / ns, sh = q - i * ns;
-            return ResidLane{t0 + i, shifts[sh], b_perm[i], b.wall.p + (int64_t)q * d};
-        };
-        auto rel = [&](int q, double r2) {
-            const double bq = bn[(size_t)(q / ns)];
-            return bq > 0 ? sqrt(r2) / bq : sqrt(r2);
-        };
-        // FP64 true residual of every pair, kTB pairs per FP64 block pass
-        std::vector<int> all((size_t)nt * ns);
-        for (int q = 0; q < nt * ns; ++q) all[(size_t)q] = q;
-        for (size_t g0 = 0; g0 < all.size(); g0 += kTB) {
-            const int ng = (int)std::min<size_t>(kTB, all.size() - g0);
+        for (int i = 0; i < nl; ++i) bn[(size_t)i] = sqrt(bn[(size_t)i]);
+    }
+    auto lane_of = [&](int q) {
+        const int i = q / ns;
+        return ResidLane{lanes[i].t, pshift[q], lanes[i].b, b.wall.p + (int64_t)q * d};
+    };
+    auto rel = [&](int q, double r2) {
+        const double bq = bn[(size_t)(q / ns)];
+        return bq > 0 ? sqrt(r2) / bq : sqrt(r2);
+    };
+    // FP64 true residual of every pair, kTB pairs per FP64 block pass
+    for (int g0 = 0; g0 < nl * ns; g0 += kTB) {
+        const int ng = std::min(kTB, nl * ns - g0);
+        ResidLane rl[kTB];
+        double r2[kTB];
+        for (int g = 0; g < ng; ++g) rl[g] = lane_of(g0 + g);
+        SDA_TRY(resid_lanes(op, rl, ng, r2, nullptr, alpha, omega, s));
+        for (int g = 0; g < ng; ++g) tres[(size_t)(g0 + g)] = rel(g0 + g, r2[g]);
+    }
+    if (rounds > 0 && b.rbuf.n < (size_t)kTB * d) SDA_TRY(b.rbuf.alloc((size_t)kTB * d));
+    for (int rd = 0; rd < rounds; ++rd) {
+        // pairs still above the target, by shift value: a group's run lasts as long
+        // as its smallest shift needs, so groups of equal shifts waste the least
+        std::vector<int> act;
+        for (int q = 0; q < nl * ns; ++q)
+            if (tres[(size_t)q] > rtol && bn[(size_t)(q / ns)] > 0 && fin[(size_t)(q / ns)].status == SDA_OK &&
+                pst[(size_t)q] == SDA_OK)
+                act.push_back(q);
+        if (act.empty()) break;
+        std::stable_sort(act.begin(), act.end(), [&](int a, int c) { return pshift[a] < pshift[c]; });
+        for (size_t g0 = 0; g0 < act.size(); g0 += kTB) {
+            const int ng = (int)std::min<size_t>(kTB, act.size() - g0);
             ResidLane rl[kTB];
             double r2[kTB];
-            for (int g = 0; g < ng; ++g) rl[g] = lane_of(all[g0 + g]);
-            SDA_TRY(resid_lanes(op, rl, ng, r2, nullptr, alpha, omega, s));
-            for (int g = 0; g < ng; ++g) tres[(size_t)all[g0 + g]] = rel(all[g0 + g], r2[g]);
-        }
-        // refinement rounds
-        if (rounds > 0 && b.rbuf.n < (size_t)kTB * d) SDA_TRY(b.rbuf.alloc((size_t)kTB * d));
-        for (int rd = 0; rd < rounds; ++rd) {
-            // pairs still above the target, shift by shift: a group's run lasts as long
-            // as its smallest shift needs, so groups of equal shifts waste the least
-            std::vector<int> sorder((size_t)ns);
-            for (int sh = 0; sh < ns; ++sh) sorder[(size_t)sh] = sh;
-            std::stable_sort(sorder.begin(), sorder.end(), [&](int a, int c) { return shifts[a] < shifts[c]; });
-            std::vector<int> act;
-            for (int sh : sorder)
-                for (int i = 0; i < nt; ++i) {
-                    const int q = i * ns + sh;
-                    if (tres[(size_t)q] > rtol && bn[(size_t)i] > 0 && fin[(size_t)i].status == SDA_OK &&
-                        pst[(size_t)q] == SDA_OK)
-                        act.push_back(q);
-                }
-            if (act.empty()) break;
-            for (size_t g0 = 0; g0 < act.size(); g0 += kTB) {
-                const int ng = (int)std::min<size_t>(kTB, act.size() - g0);
-                ResidLane rl[kTB];
-                double r2[kTB];
-                BatchLane cl[kTB];
-                for (int g = 0; g < ng; ++g) {
-                    const int q = act[g0 + g];
-                    rl[g] = lane_of(q);
-                    // relative reduction asked of the correction: to the target, but
-                    // not below what the iteration's precision can reach
-                    const double inner = std::min(0.5, std::max(rtol / tres[(size_t)q], 1e-4));
-                    cl[g] = BatchLane{rl[g].t, b.rbuf.p + (int64_t)g * d, rl[g].sigma, inner};
-                }
-                // residual vectors b - (B + beta) w in FP64, then the corrections
-                SDA_TRY(resid_lanes(op, rl, ng, r2, b.rbuf.p, alpha, omega, s));
-                const double zero = 0.0;
-                SDA_TRY((run_lanes<VT, FT>(op, cl, ng, &zero, 1, false, o.max_iter, o, alpha, omega, s)));
-                BView<FT> bv = bview<FT>(*op->bws);
-                for (int g = 0; g < ng; ++g) {
-                    const int q = act[g0 + g];
-                    const SolveState &cs = op->bws->h_st[g];
-                    if (cs.status != SDA_OK) {
-                        pst[(size_t)q] = cs.status;
-                        continue;
-                    }
-                    kb_add_lane<FT><<<grid_elems_b(d, op->sm_count), kBlock, 0, s>>>(d, bv.W, g,
-                                                                                    b.wall.p + (int64_t)q * d);
-                    SDA_LAUNCHED();
-                }
-                SDA_TRY(resid_lanes(op, rl, ng, r2, nullptr, alpha, omega, s));
-                for (int g = 0; g < ng; ++g) tres[(size_t)act[g0 + g]] = rel(act[g0 + g], r2[g]);
+            BatchLane cl[kTB];
+            for (int g = 0; g < ng; ++g) {
+                const int q = act[g0 + g];
+                rl[g] = lane_of(q);
+                // relative reduction asked of the correction: to the target, but
+                // not below what the iteration's precision can reach
+                const double inner = std::min(0.5, std::max(rtol / tres[(size_t)q], 1e-4));
+                cl[g] = BatchLane{rl[g].t, b.rbuf.p + (int64_t)g * d, rl[g].sigma, inner};
             }
+            // residual vectors b - (B + beta) w in FP64, then the corrections
+            SDA_TRY(resid_lanes(op, rl, ng, r2, b.rbuf.p, alpha, omega, s));
+            const double zero = 0.0;
+            SDA_TRY((run_lanes<VT, FT>(op, cl, ng, &zero, 1, false, o.max_iter, o, alpha, omega, s)));
+            BView<FT> bv = bview<FT>(*op->bws);
+            for (int g = 0; g < ng; ++g) {
+                const int q = act[g0 + g];
+                const SolveState &cs = op->bws->h_st[g];
+                if (cs.status != SDA_OK) {
+                    pst[(size_t)q] = cs.status;
+                    continue;
+                }
+                kb_add_lane<FT><<<grid_elems_b(d, op->sm_count), kBlock, 0, s>>>(d, bv.W, g, b.wall.p + (int64_t)q * d);
+                SDA_LAUNCHED();
+            }
+            SDA_TRY(resid_lanes(op, rl, ng, r2, nullptr, alpha, omega, s));
+            for (int g = 0; g < ng; ++g) tres[(size_t)act[g0 + g]] = rel(act[g0 + g], r2[g]);
         }
-        if (!o.check_residual && rounds == 0) std::fill(tres.begin(), tres.end(), -1.0);
     }
-    // solutions out, in the caller's feature order
+    return SDA_OK;
+}
+
+// One batch: targets t0 .. t0 + nt - 1 (nt <= kTB), every shift, as the lanes
+// of one run (solve_lanes); solutions out in the caller's feature order.
+template <class VT, class FT>
+static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_perm, const double *shifts, int ns,
+                       const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
+                       cudaStream_t s, int *worst) {
+    const int64_t d = op->d;
+    const bool fixed = o.fixed_iters > 0;
+    double sigma0 = shifts[0];
+    for (int i = 1; i < ns; ++i) sigma0 = std::min(sigma0, shifts[i]);
+    std::vector<double> deltas((size_t)ns), pshift((size_t)nt * ns);
+    for (int i = 0; i < ns; ++i) deltas[(size_t)i] = shifts[i] - sigma0;
+    BatchLane lanes[kTB];
+    for (int i = 0; i < nt; ++i) {
+        lanes[i] = BatchLane{t0 + i, b_perm[i], sigma0, o.tol};
+        for (int sh = 0; sh < ns; ++sh) pshift[(size_t)i * ns + sh] = shifts[sh];
+    }
+    LaneOutcome out;
+    SDA_TRY((solve_lanes<VT, FT>(op, lanes, nt, deltas.data(), pshift.data(), ns, o, alpha, omega, s, out)));
+    BatchWs &b = *op->bws;
     for (int i = 0; i < nt && w_out; ++i) {
         double *dst = w_out + (int64_t)i * ns * d;
         const double *src = b.wall.p + (int64_t)i * ns * d;
@@ -1214,20 +1237,22 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
             SDA_TRY(permute_to_old(op, src, dst, ns, s));
         }
     }
+    const int rounds = fixed ? 0 : std::max(0, o.refine_rounds);
+    const double rtol = std::isnan(o.refine_tol) || o.refine_tol <= 0.0 ? o.tol : o.refine_tol;
     for (int i = 0; i < nt; ++i) {
         const int t = t0 + i;
-        const SolveState &S = fin[(size_t)i];
+        const SolveState &S = out.fin[(size_t)i];
         if (S.status != SDA_OK) {
             *worst = S.status;
             fail(S.status, "breakdown in the batched shifted CG of target %d at iteration %d", t, S.k);
         }
         for (int sh = 0; sh < ns; ++sh) {
-            const int q = i * ns + sh;
+            const size_t q = (size_t)i * ns + sh;
             const ShiftState &hs = S.sh[sh];
             int st = SDA_OK;
             if (S.status != SDA_OK) st = S.status;
-            else if (pst[(size_t)q] != SDA_OK) st = pst[(size_t)q];
-            else if (rounds > 0) st = tres[(size_t)q] <= rtol ? SDA_OK : SDA_NOT_CONVERGED;
+            else if (out.pst[q] != SDA_OK) st = out.pst[q];
+            else if (rounds > 0) st = out.tres[q] <= rtol ? SDA_OK : SDA_NOT_CONVERGED;
             else if (!fixed && hs.active) st = SDA_NOT_CONVERGED;
             if (st == SDA_NOT_CONVERGED && *worst == SDA_OK) *worst = SDA_NOT_CONVERGED;
             if (st < 0 && *worst >= 0) *worst = st;
@@ -1236,7 +1261,7 @@ static int solve_batch(sda_operator *op, int t0, int nt, const double *const *b_
                 r.iters = hs.iters;
                 r.status = st;
                 r.est_residual = hs.res;
-                r.true_residual = tres[(size_t)q];
+                r.true_residual = out.tres[q];
             }
         }
     }
@@ -1482,6 +1507,62 @@ int solve_batched(sda_operator *op, int t0, int nt, const double *const *b_perm,
         if (rc < 0) return rc;
     }
     return SDA_OK;
+}
+
+// Single-shift solves of nl lanes (lane l: (B_{targets[l]} + betas[l] I) x_l = b[l],
+// all device, permuted order) in runs of kTB lanes; the FP64 solutions go to
+// x [l][D]; per-lane reports (optional).
+template <class VT, class FT>
+static int shift_lanes_t(sda_operator *op, const int *targets, const double *const *b, const double *betas, int nl,
+                         const sda_solve_opts &o, double alpha, double omega, double *x, sda_shift_report *rep,
+                         cudaStream_t s, int *worst) {
+    const int64_t d = op->d;
+    const bool fixed = o.fixed_iters > 0;
+    const int rounds = fixed ? 0 : std::max(0, o.refine_rounds);
+    const double rtol = std::isnan(o.refine_tol) || o.refine_tol <= 0.0 ? o.tol : o.refine_tol;
+    const double zero = 0.0;
+    for (int l0 = 0; l0 < nl; l0 += kTB) {
+        const int ng = std::min(kTB, nl - l0);
+        BatchLane lanes[kTB];
+        for (int g = 0; g < ng; ++g) lanes[g] = BatchLane{targets[l0 + g], b[l0 + g], betas[l0 + g], o.tol};
+        LaneOutcome out;
+        SDA_TRY((solve_lanes<VT, FT>(op, lanes, ng, &zero, betas + l0, 1, o, alpha, omega, s, out)));
+        SDA_CUDA(cudaMemcpyAsync(x + (int64_t)l0 * d, op->bws->wall.p, (size_t)ng * d * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, s));
+        for (int g = 0; g < ng; ++g) {
+            const SolveState &S = out.fin[(size_t)g];
+            int st = SDA_OK;
+            if (S.status != SDA_OK) st = S.status;
+            else if (out.pst[(size_t)g] != SDA_OK) st = out.pst[(size_t)g];
+            else if (rounds > 0) st = out.tres[(size_t)g] <= rtol ? SDA_OK : SDA_NOT_CONVERGED;
+            else if (!fixed && S.sh[0].active) st = SDA_NOT_CONVERGED;
+            if (st == SDA_NOT_CONVERGED && *worst == SDA_OK) *worst = SDA_NOT_CONVERGED;
+            if (st < 0 && *worst >= 0) {
+                *worst = st;
+                fail(st, "breakdown in the solve of lane %d (target %d)", l0 + g, targets[l0 + g]);
+            }
+            if (rep) {
+                sda_shift_report &r = rep[l0 + g];
+                r.iters = S.sh[0].iters;
+                r.status = st;
+                r.est_residual = S.sh[0].res;
+                r.true_residual = out.tres[(size_t)g];
+            }
+        }
+    }
+    SDA_CUDA(cudaStreamSynchronize(s));
+    return SDA_OK;
+}
+
+int solve_shift_lanes(sda_operator *op, const int *targets, const double *const *b, const double *betas, int nl,
+                      const sda_solve_opts &o, double alpha, double omega, double *x, sda_shift_report *rep,
+                      cudaStream_t s, int *worst) {
+    if (op->compute == SDA_F64)
+        return shift_lanes_t<double, double>(op, targets, b, betas, nl, o, alpha, omega, x, rep, s, worst);
+    return with_vt_b(op->compute, [&](auto tag) -> int {
+        using VT = std::remove_pointer_t<decltype(tag)>;
+        return shift_lanes_t<VT, float>(op, targets, b, betas, nl, o, alpha, omega, x, rep, s, worst);
+    });
 }
 
 void release_batch(sda_operator *op) {

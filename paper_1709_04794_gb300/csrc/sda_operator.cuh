@@ -185,6 +185,11 @@ int solve_batched(sda_operator *op, int t0, int nt, const double *const *b_perm,
                   const sda_solve_opts &o, double alpha, double omega, double *w_out, sda_shift_report *rep,
                   cudaStream_t s, int *worst);
 void release_batch(sda_operator *op);
+// single-shift solves of nl lanes (sda_batch.cu): lane l solves (B_{targets[l]} + betas[l] I) x_l = b[l]
+// (device, permuted order), runs of 16 lanes; FP64 solutions to x [nl][D]; per-lane reports (optional)
+int solve_shift_lanes(sda_operator *op, const int *targets, const double *const *b, const double *betas, int nl,
+                      const sda_solve_opts &o, double alpha, double omega, double *x, sda_shift_report *rep,
+                      cudaStream_t s, int *worst);
 // One vector of an FP64 block residual: w (device, permuted order) of target t,
 // against the right-hand side b, shifted by sigma.
 struct ResidLane {

@@ -123,6 +123,69 @@ __global__ void k_mask_labelled(int64_t n, const int8_t *y, const double *u, dou
         out[i] = y[i] != 0 ? u[i] : 0.0;
 }
 
+// WT[j][v] = w_v[old_of_new(j)]: nv vectors of the caller's feature order, transposed
+// into the permuted order so that a row's entry reads its nv values contiguously
+__global__ void k_to_new_t(int64_t d, int nv, const int32_t *new_of_old, const double *w, double *WT) {
+    const int64_t m = d * nv;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = i / d, o = i - v * d;
+        WT[(int64_t)new_of_old[o] * nv + v] = w[i];
+    }
+}
+
+// part[b][v] = sum over the features j = b, b + nb, ... of mu_j WT[j][v] (fixed order)
+__global__ void __launch_bounds__(kBlock) k_mu_dots_part(int64_t d, int nv, const double *__restrict__ mu,
+                                                         const double *__restrict__ WT, double *__restrict__ part) {
+    __shared__ double red[kBlock];
+    for (int v0 = 0; v0 < nv; v0 += kBlock / 32) {
+        const int v = v0 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+        double a = 0.0;
+        if (v < nv)
+            for (int64_t j = (int64_t)blockIdx.x * 32 + lane; j < d; j += (int64_t)gridDim.x * 32) a += mu[j] * WT[j * nv + v];
+        a = warp_sum(a);
+        if (lane == 0) red[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x < kBlock / 32 && v0 + (int)threadIdx.x < nv)
+            part[(int64_t)blockIdx.x * nv + v0 + threadIdx.x] = red[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// c[v] = sum_b part[b][v]
+__global__ void k_mu_dots_sum(int nb, int nv, const double *__restrict__ part, double *__restrict__ c) {
+    const int v = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (v >= nv) return;
+    double a = 0.0;
+    for (int b = 0; b < nb; ++b) a += part[(int64_t)b * nv + v];
+    c[v] = a;
+}
+
+// scores[v][h] = sum over row rows[h] of x_e WT[col_e][v] (- c[v] when c is given):
+// one warp per held row, its lanes over the vectors; a row id outside [0, n) sets *err
+template <class VT>
+__global__ void k_project_rows(int64_t n, int64_t nrows, int nv, const int64_t *__restrict__ rows,
+                               const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                               const VT *__restrict__ val, const double *__restrict__ WT,
+                               const double *__restrict__ c, double *__restrict__ scores, int *err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = warp; h < nrows; h += nwarps) {
+        const int64_t i = rows[h];
+        if (i < 0 || i >= n) {
+            if (lane == 0) atomicOr(err, 1);
+            continue;
+        }
+        for (int v0 = 0; v0 < nv; v0 += 32) {
+            const int v = v0 + lane;
+            double a = 0.0;
+            if (v < nv)
+                for (int64_t e = rp[i]; e < rp[i + 1]; ++e) a += (double)Val<VT>::get(val, e) * WT[(int64_t)col[e] * nv + v];
+            if (v < nv) scores[(int64_t)v * nrows + h] = c ? a - c[v] : a;
+        }
+    }
+}
+
 static int grid_elems(int64_t m, int sms) {
     const int64_t g = (m + kBlock - 1) / kBlock;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
@@ -820,6 +883,29 @@ extern "C" SDA_API int sda_get_solve_stats(const sda_operator *op, sda_solve_sta
 
 extern "C" SDA_API int64_t sda_kernel_launch_count(void) { return launch_count(); }
 
+// The contractions of the adjoint gradient of target t (FP64, permuted order):
+// sc[1] = lambda^T w, sc[4] = (X~ lambda)^T L (X~ w), sc[5] = (X~ lambda)^T P_l (X~ w)
+// (sc[2], sc[3]: mu^T w, mu^T lambda); uw, ul, v, v2: N-vector scratch.
+static int adjoint_dots(const sda_operator *op, int t, const double *wp, const double *lam, double *uw, double *ul,
+                        double *v, double *v2, double *sc, cudaStream_t s) {
+    const int64_t d = op->d, n = op->n;
+    const double *mu = op->mu.p + (int64_t)t * d;
+    const int8_t *y = op->labels.p + (int64_t)t * n;
+    SDA_TRY(dot_f64(op, d, lam, wp, sc + 1, s));
+    SDA_TRY(dot_f64(op, d, mu, wp, sc + 2, s));
+    SDA_TRY(dot_f64(op, d, mu, lam, sc + 3, s));
+    SDA_TRY(op_xmul_f64(op, wp, uw, sc + 2, s));
+    SDA_TRY(op_xmul_f64(op, lam, ul, sc + 3, s));
+    SDA_TRY((rowpass<double, double>(op->s_lanes, n, op->s_rp.p, op->s_col.p, op->s_val64.p,
+                                     GatherVec<double, double>{uw}, EpiLap64{v, uw, op->deg64.p, y, 0.0, 1.0},
+                                     op->sm_count * kMaxBlocksPerSm, s)));
+    SDA_TRY(dot_f64(op, n, ul, v, sc + 4, s));
+    k_mask_labelled<<<grid_elems(n, op->sm_count), kBlock, 0, s>>>(n, y, uw, v2);
+    SDA_LAUNCHED();
+    SDA_TRY(dot_f64(op, n, ul, v2, sc + 5, s));
+    return SDA_OK;
+}
+
 extern "C" SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double alpha, double beta,
                                         const double *w, const double *dloss_ds, const int64_t *rows, int64_t n_rows,
                                         const sda_solve_opts *opt, double *d_alpha, double *d_beta,
@@ -888,25 +974,96 @@ extern "C" SDA_API int sda_adjoint_grad(sda_operator *op, int32_t target, double
     // lambda: the solve's FP64 solution (permuted order)
     SDA_CUDA(cudaMemcpyAsync(lam, ws.w64.p, (size_t)d * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (worst < 0) return worst;
-    // d/d beta = -lambda^T w;  d/d alpha = -[(X~ lambda)^T L (X~ w) - c (X~ lambda)^T P_l (X~ w)]
-    SDA_TRY(dot_f64(op, d, lam, wp, sc.p + 1, s));
-    SDA_TRY(dot_f64(op, d, mu, wp, sc.p + 2, s));
-    SDA_TRY(dot_f64(op, d, mu, lam, sc.p + 3, s));
-    SDA_TRY(op_xmul_f64(op, wp, uw, sc.p + 2, s));
-    SDA_TRY(op_xmul_f64(op, lam, ul, sc.p + 3, s));
-    SDA_TRY((rowpass<double, double>(op->s_lanes, n, op->s_rp.p, op->s_col.p, op->s_val64.p,
-                                     GatherVec<double, double>{uw}, EpiLap64{v, uw, op->deg64.p, y, 0.0, 1.0},
-                                     op->sm_count * kMaxBlocksPerSm, s)));
-    SDA_TRY(dot_f64(op, n, ul, v, sc.p + 4, s));
-    k_mask_labelled<<<grid_elems(n, op->sm_count), kBlock, 0, s>>>(n, y, uw, v2);
-    SDA_LAUNCHED();
-    SDA_TRY(dot_f64(op, n, ul, v2, sc.p + 5, s));
+    SDA_TRY(adjoint_dots(op, target, wp, lam, uw, ul, v, v2, sc.p, s));
     if (lambda_out) SDA_TRY(permute_to_old(op, lam, lambda_out, 1, s));
     double hs[8];
     SDA_CUDA(cudaMemcpyAsync(hs, sc.p, sizeof(hs), cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
     *d_beta = -hs[1];
     *d_alpha = -(hs[4] - (op->omega_follows_alpha ? hs[5] : 0.0));
+    return worst;
+}
+
+extern "C" SDA_API int sda_adjoint_grad_batched(sda_operator *op, int32_t n_targets, const int32_t *targets,
+                                                double alpha, const double *betas, const double *W,
+                                                const double *dloss_ds, const int64_t *rows, const int64_t *row_off,
+                                                const sda_solve_opts *opt, double *d_alpha, double *d_beta,
+                                                double *lambda_out, sda_shift_report *report, void *cuda_stream) {
+    clear_error();
+    if (!op || n_targets < 0) return fail(SDA_ERR_INVALID_ARG, "bad argument");
+    SDA_TRY(check_device(op->device));
+    if (op->regression) return fail(SDA_ERR_UNSUPPORTED, "the adjoint is defined for SDA operators only");
+    if (n_targets == 0) return SDA_OK;
+    if (!targets || !betas || !W || !row_off || !d_alpha || !d_beta) return fail(SDA_ERR_INVALID_ARG, "NULL argument");
+    if (row_off[0] != 0) return fail(SDA_ERR_INVALID_ARG, "row_off[0] must be 0");
+    for (int i = 0; i < n_targets; ++i) {
+        if (targets[i] < 0 || targets[i] >= op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target out of range");
+        if (!(betas[i] > 0.0) || !isfinite(betas[i])) return fail(SDA_ERR_INVALID_ARG, "beta must be finite and > 0");
+        if (row_off[i + 1] < row_off[i]) return fail(SDA_ERR_INVALID_ARG, "row_off must not decrease");
+    }
+    if (row_off[n_targets] > 0 && (!rows || !dloss_ds)) return fail(SDA_ERR_INVALID_ARG, "bad held-out rows");
+    sda_solve_opts o;
+    if (opt) {
+        o = *opt;
+    } else {
+        sda_default_opts(&o);
+        o.tol = 1e-10;
+    }
+    o.alpha = alpha;
+    o.scatter_weight = NAN;
+    o.rhs_mode = SDA_RHS_GIVEN;
+    o.check_residual = 1;
+    double al = 0.0, om = 0.0;
+    SDA_TRY(call_weights(op, o, &al, &om));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t d = op->d, n = op->n, T = n_targets;
+    DevBuf<double> wp, cb, lam, nv, sc;
+    DevBuf<int> err;
+    SDA_TRY(wp.alloc((size_t)(T * d)));
+    SDA_TRY(cb.alloc((size_t)(T * d)));
+    SDA_TRY(lam.alloc((size_t)(T * d)));
+    SDA_TRY(nv.alloc((size_t)(5 * n)));
+    SDA_TRY(sc.alloc((size_t)(8 * T)));
+    SDA_TRY(err.alloc(1));
+    double *G = nv.p, *uw = G + n, *ul = uw + n, *v = ul + n, *v2 = v + n;
+    SDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    SDA_TRY(permute_to_new(op, W, wp.p, T, s));
+    // right-hand sides (X_h - 1 mu^T)^T g = X^T G - mu (1^T G), G = g scattered to the held-out rows
+    std::vector<const double *> bl((size_t)T);
+    for (int64_t i = 0; i < T; ++i) {
+        const int64_t r0 = row_off[i], nr = row_off[i + 1] - row_off[i];
+        double *c = cb.p + i * d;
+        SDA_CUDA(cudaMemsetAsync(G, 0, (size_t)n * sizeof(double), s));
+        if (nr > 0) {
+            k_scatter_rows<<<grid_elems(nr, op->sm_count), kBlock, 0, s>>>(nr, rows + r0, dloss_ds + r0, G, n, err.p);
+            SDA_LAUNCHED();
+        }
+        SDA_TRY(op_xtmul_f64(op, G, c, s));
+        SDA_TRY(dot_f64(op, n, G, nullptr, sc.p + 8 * i, s));
+        k_sub_mu<<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, c, op->mu.p + (int64_t)targets[i] * d,
+                                                               sc.p + 8 * i);
+        SDA_LAUNCHED();
+        bl[(size_t)i] = c;
+    }
+    int herr = 0;
+    SDA_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(SDA_ERR_INVALID_ARG, "a held-out row id is out of range");
+    // the adjoint solves (B_t + beta_t I) lambda_t = c_t, 16 targets per batched run
+    int worst = SDA_OK;
+    memset(&op->stats, 0, sizeof(op->stats));
+    SDA_TRY(solve_shift_lanes(op, targets, bl.data(), betas, n_targets, o, al, om, lam.p, report, s, &worst));
+    if (worst < 0) return worst;
+    for (int64_t i = 0; i < T; ++i)
+        SDA_TRY(adjoint_dots(op, targets[i], wp.p + i * d, lam.p + i * d, uw, ul, v, v2, sc.p + 8 * i, s));
+    if (lambda_out) SDA_TRY(permute_to_old(op, lam.p, lambda_out, T, s));
+    std::vector<double> hs((size_t)(8 * T));
+    SDA_CUDA(cudaMemcpyAsync(hs.data(), sc.p, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < T; ++i) {
+        d_beta[i] = -hs[(size_t)(8 * i + 1)];
+        d_alpha[i] = -(hs[(size_t)(8 * i + 4)] - (op->omega_follows_alpha ? hs[(size_t)(8 * i + 5)] : 0.0));
+    }
     return worst;
 }
 
@@ -942,6 +1099,49 @@ extern "C" SDA_API int sda_project(const sda_operator *op, const double *w, int6
     SDA_TRY(permute_to_new(op, w, wn.p, n_vec, s));
     SDA_TRY(project_block(mop, wn.p, n_vec, scores, centred, target, s));
     SDA_CUDA(cudaStreamSynchronize(s));
+    return SDA_OK;
+}
+
+extern "C" SDA_API int sda_project_rows(const sda_operator *op, const double *w, int32_t n_vec, const int64_t *rows,
+                                        int64_t n_rows, double *scores, int32_t centred, int32_t target,
+                                        void *cuda_stream) {
+    clear_error();
+    if (!op || !w || !scores || n_vec < 0 || n_rows < 0 || (n_rows > 0 && !rows))
+        return fail(SDA_ERR_INVALID_ARG, "bad argument");
+    SDA_TRY(check_device(op->device));
+    if (centred && (target < 0 || target >= op->n_targets)) return fail(SDA_ERR_INVALID_ARG, "target out of range");
+    if (n_vec == 0 || n_rows == 0) return SDA_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int64_t d = op->d;
+    const int nb = std::min<int>(op->sm_count * 2, (int)((d + 31) / 32));
+    DevBuf<double> wt, part, c;
+    DevBuf<int> err;
+    SDA_TRY(wt.alloc((size_t)(n_vec * d)));
+    SDA_TRY(err.alloc(1));
+    SDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    k_to_new_t<<<grid_elems(d * n_vec, op->sm_count), kBlock, 0, s>>>(d, n_vec, op->new_of_old.p, w, wt.p);
+    SDA_LAUNCHED();
+    if (centred) {
+        SDA_TRY(part.alloc((size_t)nb * n_vec));
+        SDA_TRY(c.alloc((size_t)n_vec));
+        k_mu_dots_part<<<nb, kBlock, 0, s>>>(d, n_vec, op->mu.p + (int64_t)target * d, wt.p, part.p);
+        SDA_LAUNCHED();
+        k_mu_dots_sum<<<(n_vec + 127) / 128, 128, 0, s>>>(nb, n_vec, part.p, c.p);
+        SDA_LAUNCHED();
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_rows + 7) / 8, (int64_t)op->sm_count * 16));
+    SDA_TRY(with_vt(op->compute, [&](auto tag) -> int {
+        using VT = std::remove_pointer_t<decltype(tag)>;
+        k_project_rows<VT><<<grid, kBlock, 0, s>>>(op->n, n_rows, n_vec, rows, op->x_rp.p, op->x_col.p,
+                                                   (const VT *)op->x_val_r.p, wt.p, centred ? c.p : nullptr, scores,
+                                                   err.p);
+        SDA_LAUNCHED();
+        return SDA_OK;
+    }));
+    int herr = 0;
+    SDA_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    if (herr) return fail(SDA_ERR_INVALID_ARG, "a row id is out of range");
     return SDA_OK;
 }
 

@@ -87,9 +87,14 @@ _SIGS = {
     "sda_solve_shifts": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(sda_solve_opts), _vp,
                                         ctypes.POINTER(sda_shift_report), _vp]),
     "sda_project": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32, ctypes.c_int32, _vp]),
+    "sda_project_rows": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_int64, _vp, ctypes.c_int32,
+                                        ctypes.c_int32, _vp]),
     "sda_adjoint_grad": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _vp, _vp, _vp,
                                         ctypes.c_int64, ctypes.POINTER(sda_solve_opts), ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), _vp, _vp]),
+    "sda_adjoint_grad_batched": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp,
+                                                ctypes.POINTER(sda_solve_opts), _vp, _vp, _vp,
+                                                ctypes.POINTER(sda_shift_report), _vp]),
     "sda_operator_apply": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
     "sda_operator_apply_static": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
     "sda_get_operator_info": (ctypes.c_int, [_vp, ctypes.POINTER(sda_operator_info)]),
@@ -243,6 +248,11 @@ def sda_solve_shifts(op, shifts, opts: sda_solve_opts | None = None, w_out=None,
     lib = load()
     sh = np.ascontiguousarray(shifts, dtype=np.float64)
     o = opts if opts is not None else sda_default_opts()
+    if n_report:
+        # the report is [target_count][n_shifts]: refuse a buffer the call would overrun
+        count = o.target_count if o.target_count >= 0 else sda_get_operator_info(op)["n_targets"] - o.target_begin
+        if n_report < count:
+            raise ValueError("n_report=%d is smaller than the %d targets this call solves" % (n_report, count))
     keep = [sh]
     if rhs is not None:
         rp, rdev, rk = _ptr(rhs)
@@ -273,6 +283,16 @@ def sda_project(op, w, n_vec, scores, centred=0, target=0, stream=None):
                   "sda_project")
 
 
+def sda_project_rows(op, w, n_vec, rows, scores, centred=0, target=0, stream=None):
+    """Calls sda_project_rows: scores [n_vec][len(rows)] of the given rows only."""
+    lib = load()
+    wp, _, wk = _ptr(w)
+    rp, _, rk = _ptr(rows)
+    sp, _, sk = _ptr(scores)
+    return _check(lib.sda_project_rows(op, wp, int(n_vec), rp, int(rows.shape[0]), sp, int(centred), int(target),
+                                       _stream(stream)), "sda_project_rows")
+
+
 def sda_adjoint_grad(op, target, alpha, beta, w, dloss_ds, rows, opts: sda_solve_opts | None = None,
                      lambda_out=None, stream=None):
     """Calls sda_adjoint_grad; returns (status, d_alpha, d_beta)."""
@@ -286,6 +306,31 @@ def sda_adjoint_grad(op, target, alpha, beta, w, dloss_ds, rows, opts: sda_solve
                                        ctypes.byref(opts) if opts is not None else None, ctypes.byref(da),
                                        ctypes.byref(db), lp, _stream(stream)), "sda_adjoint_grad")
     return code, da.value, db.value
+
+
+def sda_adjoint_grad_batched(op, targets, alpha, betas, W, dloss_ds, rows, row_off, opts=None, lambda_out=None,
+                             stream=None):
+    """Calls sda_adjoint_grad_batched; returns (status, d_alpha [n], d_beta [n], reports)."""
+    lib = load()
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    bt = np.ascontiguousarray(betas, dtype=np.float64)
+    off = np.ascontiguousarray(row_off, dtype=np.int64)
+    n = int(tg.size)
+    if bt.size != n or off.size != n + 1:
+        raise ValueError("targets, betas and row_off must describe the same number of gradients")
+    wp, _, wk = _ptr(W)
+    gp, _, gk = _ptr(dloss_ds)
+    rp, _, rk = _ptr(rows)
+    lp, _, lk = _ptr(lambda_out)
+    da, db = np.zeros(n), np.zeros(n)
+    rep = (sda_shift_report * max(1, n))()
+    code = _check(lib.sda_adjoint_grad_batched(op, n, tg.ctypes.data, float(alpha), bt.ctypes.data, wp, gp, rp,
+                                               off.ctypes.data, ctypes.byref(opts) if opts is not None else None,
+                                               da.ctypes.data, db.ctypes.data, lp, rep, _stream(stream)),
+                  "sda_adjoint_grad_batched")
+    reps = [dict(iters=rep[i].iters, status=rep[i].status, est_residual=rep[i].est_residual,
+                 true_residual=rep[i].true_residual) for i in range(n)]
+    return code, da, db, reps
 
 
 def sda_operator_apply(op, target, sigma, p, q, stream=None):

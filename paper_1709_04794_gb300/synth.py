@@ -22,6 +22,13 @@ the same structure are generated here:
   labelled subset is uniform, with the exact positive share requested.
   A disjoint held-out set of unlabelled rows keeps its true labels for AUC.
 
+The two largest workloads (500,000 and 2,000,000 rows, 64 and 1,000
+targets) are drawn by the native helpers of synth_native.c with the same
+laws: one counter-based random stream per row of X and per target, so that
+they take seconds on many cores; their score spread is measured over each
+target's labelled and held-out rows (the only rows whose scores are drawn),
+and their `truth` holds the classes of those rows only (0 elsewhere).
+
 This module holds none of the solver's arithmetic: no means, no Laplacian,
 no operator.  Both the oracle and the CUDA path consume its arrays.
 """
@@ -59,6 +66,7 @@ class Workload:
     zipf_s: float = 1.1
     knn_cap: int | None = None  # None: exact kNN
     holdout_ratio: float = 0.25  # held-out rows per labelled row (20 % of all known labels)
+    generator: str = "numpy"    # "numpy" | "native" (synth_native.c, the large workloads)
 
     def shift_values(self) -> np.ndarray:
         lo, hi, cnt = self.shifts
@@ -81,12 +89,13 @@ WORKLOADS = {
     "adjoint_64t_500k": Workload(
         name="adjoint_64t_500k", n=500_000, d=262_144, nnz_mean=50, values="binary", n_targets=64,
         labelled=("loguniform", 100, 20_000), pos_frac=("uniform", 0.01, 0.50), knn_k=10,
-        alpha=0.1, shifts=(1e-5, 1e3, 16), seed=17090004, value_dtype="f8e4m3", knn_cap=96),
+        alpha=0.1, shifts=(1e-5, 1e3, 16), seed=17090004, value_dtype="f8e4m3", knn_cap=96,
+        generator="native"),
     "large_1000t_2m": Workload(
         name="large_1000t_2m", n=2_000_000, d=1_048_576, nnz_mean=45, values="binary",
         n_targets=1000, labelled=("loguniform", 50, 50_000), pos_frac=("lognormal_median", 0.02),
         knn_k=8, alpha=0.1, shifts=(1e-5, 1e3, 24), seed=17090005, value_dtype="f8e4m3",
-        knn_cap=96),
+        knn_cap=96, generator="native"),
 }
 
 
@@ -158,10 +167,15 @@ def count_values(rng: np.random.Generator, nnz: int, p: float = 0.7, vmax: int =
 @functools.lru_cache(maxsize=1)
 def _knn_lib():
     lib = ctypes.CDLL(_build.build_synth())
-    lib.synth_knn_jaccard.restype = ctypes.c_int
-    lib.synth_knn_jaccard.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
-                                      ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
-                                      ctypes.c_int32]
+    vp, i64, i32, f64, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64
+    for name, args in (("synth_knn_jaccard", [i64, i64, vp, vp, i32, i64, vp, vp, i32]),
+                       ("synth_row_counts", [i64, i64, f64, u64, vp, i32]),
+                       ("synth_fill_rows", [i64, i64, vp, vp, i32, vp, u64, vp, vp, vp, i32]),
+                       ("synth_planted", [i64, i64, vp, vp, vp, i32, vp, vp, vp, i64, i64, f64, u64, vp, vp,
+                                          vp, i64, vp, i32])):
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = args
     return lib
 
 
@@ -287,13 +301,77 @@ class Problem:
         return self.workload.d
 
 
+def _zipf_cdf(d: int, s: float) -> np.ndarray:
+    w = np.arange(1, d + 1, dtype=np.float64) ** (-s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    cdf[-1] = 1.0
+    return cdf
+
+
+def _geometric_cdf(p: float = 0.7, vmax: int = 8) -> np.ndarray:
+    v = np.arange(1, vmax + 1)
+    pmf = p * (1 - p) ** (v - 1)
+    cdf = np.cumsum(pmf) / pmf.sum()
+    cdf[-1] = 1.0
+    return cdf
+
+
+def native_x(wl: Workload, rng: np.random.Generator):
+    """X of a large workload from synth_native.c: the same laws as zipf_csr and
+    count_values, one random stream per row (seeded from `rng`)."""
+    lib = _knn_lib()
+    seed = int(rng.integers(0, 2**63 - 1))
+    perm = rng.permutation(wl.d).astype(np.int64)
+    cdf = _zipf_cdf(wl.d, wl.zipf_s)
+    counts = np.empty(wl.n, dtype=np.int64)
+    if lib.synth_row_counts(wl.n, wl.d, float(wl.nnz_mean), seed, counts.ctypes.data, 0) != 0:
+        raise RuntimeError("synth_row_counts failed")
+    x_ptr = np.zeros(wl.n + 1, dtype=np.int64)
+    np.cumsum(counts, out=x_ptr[1:])
+    x_col = np.empty(int(x_ptr[-1]), dtype=np.int32)
+    x_val = np.empty(int(x_ptr[-1]), dtype=np.float64)
+    vcdf = _geometric_cdf()
+    rc = lib.synth_fill_rows(wl.n, wl.d, cdf.ctypes.data, perm.ctypes.data, 0 if wl.values == "binary" else 1,
+                             vcdf.ctypes.data, seed, x_ptr.ctypes.data, x_col.ctypes.data, x_val.ctypes.data, 0)
+    if rc != 0:
+        raise RuntimeError("synth_fill_rows failed with code %d" % rc)
+    return x_ptr, x_col, x_val
+
+
 def make_x(wl: Workload, rng: np.random.Generator):
+    if wl.generator == "native":
+        return native_x(wl, rng)
     x_ptr, x_col = zipf_csr(rng, wl.n, wl.d, wl.nnz_mean, wl.zipf_s)
     if wl.values == "binary":
         x_val = np.ones(x_col.size)
     else:
         x_val = count_values(rng, x_col.size)
     return x_ptr, x_col, x_val
+
+
+def native_targets(wl: Workload, trng: np.random.Generator, x_ptr, x_col, x_val, t: int):
+    """Planted targets of a large workload from synth_native.c (the law of
+    planted_target, one random stream per target)."""
+    ell, q = _draw_sizes(trng, wl)
+    ell, q = np.ascontiguousarray(ell[:t], dtype=np.int64), np.ascontiguousarray(q[:t], dtype=np.float64)
+    n, d = wl.n, wl.d
+    n_inf = max(1, int(round(0.01 * d)))
+    freq = np.bincount(x_col, minlength=d)
+    pool = np.ascontiguousarray(np.argsort(-freq, kind="stable")[:max(n_inf, d // 5)], dtype=np.int32)
+    seed = int(trng.integers(0, 2**63 - 1))
+    hmax = int(max(1, np.ceil(wl.holdout_ratio * max(int(ell.max()) if t else 2, 2))))
+    labels = np.zeros((t, n), dtype=np.int8)
+    truth = np.zeros((t, n), dtype=np.int8)
+    held = np.zeros((t, hmax), dtype=np.int64)
+    nheld = np.zeros(t, dtype=np.int64)
+    rc = _knn_lib().synth_planted(n, d, x_ptr.ctypes.data, x_col.ctypes.data, x_val.ctypes.data, t,
+                                  ell.ctypes.data, q.ctypes.data, pool.ctypes.data, pool.size, n_inf,
+                                  float(wl.holdout_ratio), seed, labels.ctypes.data, truth.ctypes.data,
+                                  held.ctypes.data, hmax, nheld.ctypes.data, 0)
+    if rc != 0:
+        raise RuntimeError("synth_planted failed with code %d" % rc)
+    return labels, truth, [held[i, :nheld[i]].copy() for i in range(t)]
 
 
 @functools.lru_cache(maxsize=4)
@@ -306,6 +384,10 @@ def make_problem(name: str, n_targets: int | None = None) -> Problem:
     s_ptr, s_col, s_val = union_graph(nbr, sim)
     t = wl.n_targets if n_targets is None else int(n_targets)
     trng = np.random.default_rng(wl.seed + 7)
+    if wl.generator == "native":
+        labels, truth, held = native_targets(wl, trng, x_ptr, x_col, x_val, t)
+        return Problem(wl, x_ptr, x_col, x_val, s_ptr, s_col, s_val, labels, truth, held,
+                       wl.shift_values(), wl.alpha)
     ell, q = _draw_sizes(trng, wl)
     labels = np.zeros((t, wl.n), dtype=np.int8)
     truth = np.zeros((t, wl.n), dtype=np.int8)

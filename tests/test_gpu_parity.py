@@ -351,3 +351,29 @@ def test_cfg2_converged_mixed_true_residuals(cfg2):
     assert code == sda.SDA_OK
     for r in rep[0]:
         assert r["true_residual"] < 1.5 * tol, r
+
+
+@pytest.mark.parametrize("compute", ["f64", "f16", "pattern"])
+def test_project_rows_matches_oracle(skewed, compute):
+    """Ratings of a subset of the rows (held-out rows, one repeated) against the
+    oracle's X w on those rows; centred ratings subtract mu_l^T w."""
+    prob = skewed if compute != "pattern" else synth.custom_problem(3001, 1201, 15, seed=9, n_labelled=300, k=4)
+    op = sda.Operator(prob, compute=compute)
+    o = oracle.from_problem(prob)
+    rng = np.random.default_rng(4)
+    nv = 37                                      # more vectors than one warp's lanes
+    W = rng.standard_normal((nv, prob.d))
+    rows = np.concatenate([prob.heldout[0], prob.heldout[0][:1]]).astype(np.int64)
+    sc = torch.empty((nv, rows.size), dtype=torch.float64, device="cuda")
+    mu = o.class_means()[0]
+    for centred in (0, 1):
+        sda.sda_project_rows(op.handle, torch.from_numpy(W).cuda(), nv, torch.from_numpy(rows).cuda(), sc,
+                             centred, 0)
+        got = sc.cpu().numpy()
+        for v in range(nv):
+            ref = o.project(W[v])[rows] - (mu @ W[v] if centred else 0.0)
+            assert np.max(np.abs(got[v] - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref))), (centred, v)
+    bad = torch.tensor([0, prob.n], dtype=torch.int64, device="cuda")
+    with pytest.raises(sda.SDAError) as e:
+        sda.sda_project_rows(op.handle, torch.from_numpy(W[:2]).cuda(), 2, bad, sc, 0, 0)
+    assert e.value.code == sda.SDA_ERR_INVALID_ARG

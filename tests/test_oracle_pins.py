@@ -375,6 +375,32 @@ def test_dense_adjoint_gradient_equals_finite_differences(tiny):
     assert abs((lp - lm) / (2 * h) - beta * db) <= 1e-6 * max(1.0, abs(beta * db))
 
 
+def test_sparse_adjoint_equals_dense_adjoint(tiny):
+    """The sparse adjoint gradient (C oracle CG, sparse products) equals the dense
+    one (explicit B, direct solves) at two points and in the finite differences
+    of its own loss; a dropped S_t term in dB/dalpha fails the alpha check."""
+    X = _dense(tiny)
+    y = tiny.labels[0]
+    rows = tiny.heldout[0]
+    yr = tiny.truth[0][rows]
+    for alpha, beta in ((0.3, 0.05), (0.7, 2.0)):
+        o = oracle.from_problem(tiny, alpha=alpha)
+        ls, das, dbs, ws = oracle.adjoint_grad_sparse(o, tiny.x_ptr, tiny.x_col, tiny.x_val, tiny.s_ptr,
+                                                      tiny.s_col, tiny.s_val, rows, yr, beta, tol=1e-14)
+        ld, dad, dbd, wd = oracle.adjoint_grad_dense(X, tiny.s_ptr, tiny.s_col, tiny.s_val, y, alpha, beta, rows, yr)
+        assert np.linalg.norm(ws - wd) <= 1e-10 * np.linalg.norm(wd)
+        assert abs(ls - ld) <= 1e-12 * abs(ld)
+        assert abs(das - dad) <= 1e-8 * abs(dad) and abs(dbs - dbd) <= 1e-8 * abs(dbd)
+    # a plausible mistake, dB/dalpha = X^T L X (dropping the -S_t^l of omega = 1 - alpha),
+    # moves the alpha derivative far beyond the agreement asserted above
+    St, mu = oracle.dense_scatter_labelled(X, y)
+    XLX = oracle.dense_manifold(X, tiny.s_ptr, tiny.s_col, tiny.s_val)
+    A = (1 - alpha) * St + alpha * XLX + beta * np.eye(X.shape[1])
+    _, g = oracle.logistic_loss((X[rows] - mu) @ wd, yr)
+    lam = np.linalg.solve(A, (X[rows] - mu).T @ g)
+    assert abs(-lam @ (XLX @ wd) - dad) > 1e-3 * abs(dad)
+
+
 def test_regression_operator_is_xtx():
     """CSR-SDA's regression step (Algorithm 5, line 5): the oracle's regression
     operator is X^T X + sigma I, and its shifted CG reaches the dense solutions
