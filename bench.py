@@ -1,18 +1,26 @@
 """Benchmark: SDA solves per second (a solve = one binary target, all its
-beta shifts, converged) on the single-target 200,000 x 131,072 workload
-(FP16 count values, 32 shifts 1e-5..1e3, kNN Jaccard graph k=10), plus the
-achieved HBM bandwidth of the dominant kernel against the measured peak.
+beta shifts) on the largest single-GPU workload: X 2,000,000 x 1,048,576
+binary fingerprint-like features stored in FP8 (90M nonzeros, Zipf-popular
+columns), Jaccard kNN graph (k = 8), 1,000 targets with 50..50,000 labelled
+rows, 24 shifts 1e-5..1e3, each solve run for the paper's 70 iterations
+(Sec. 5.2); plus the achieved HBM bandwidth of the dominant kernel and of the
+whole batched iteration against the measured peak.
 
-One step = one pass of the whole hot path over the inputs resident in HBM:
-operator build (CSR->CSC, feature order, degrees, class means), shifted CG
-to tol for every shift, FP64 true-residual check of every shift, and the
-ratings s = X w of every shift.
+One step = one chunk of 32 targets through the whole hot path, inputs
+resident in HBM: operator build with the chunk's labels, the batched
+mixed-precision sweep of every shift with the FP64 true residual of every
+(target, shift), the centred held-out ratings of every shift, the least-loss
+shift per target and the batched adjoint gradient in (alpha, beta) there.
+The line also carries the FP64 GPU path at the same iteration count (equal
+residual), parity against the FP64 CPU oracle, the oracle timed on the host
+cores, and the end-to-end rate from pinned host memory.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+                  [--workload large_1000t_2m|single_mixed_200k|batched_256t_200k|regression_200k|sa_200k]
 
-N > 1 (torchrun, one process per GPU) runs independent replicas: the
-single-target solve does not shard.  --impl reference times the FP64 CPU
-oracle on the host cores instead (rank 0 only).
+N > 1 (torchrun, one process per GPU) shards the targets over the ranks (no
+exchange).  --impl reference times the FP64 CPU oracle on the host cores
+instead (rank 0 only).
 """
 from __future__ import annotations
 
@@ -33,9 +41,13 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOAD = "single_mixed_200k"
+LARGE = "large_1000t_2m"          # the default: the largest single-GPU workload
 METRIC = "SDA solves/s (all shifts)"
 UNIT = "solves/s"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cg_kernels_single_mixed_200k.md")
+LARGE_PROFILE = os.path.join(ROOT, "profiles", "batched_kernels_large_1000t_2m.md")
+FIXED_ITERS = 70                  # iterations per solve in the fixed-iteration protocol (Sec. 5.2)
+CHUNK = 32                        # targets per step of the large workload (two batches of 16)
 
 
 def parse():
@@ -49,13 +61,19 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=500,
-                    help="reference arm: oracle iterations per timed step (a bounded sample of the solve)")
+    ap.add_argument("--cpu-iters", type=int, default=0,
+                    help="reference arm: oracle iterations per timed step (a bounded sample of the solve; "
+                         "default 500 for single_mixed_200k, 10 for the large workload)")
     ap.add_argument("--baseline-iters", type=int, default=0,
                     help="cpu_baseline of our arm: oracle iterations timed once (0: the whole solve, ~10 s on "
                          "16 cores)")
-    ap.add_argument("--workload", default=WORKLOAD,
-                    help="single_mixed_200k (default); batched_256t_200k: 256 targets solved in batches of "
+    ap.add_argument("--fixed-iters", type=int, default=FIXED_ITERS,
+                    help="large workload: shifted-CG iterations per solve (the fixed-iteration protocol)")
+    ap.add_argument("--chunk", type=int, default=CHUNK, help="large workload: targets per step")
+    ap.add_argument("--workload", default=LARGE,
+                    help="large_1000t_2m (default): 2M x 1M, 1,000 targets, 24 shifts, 70 iterations per "
+                         "solve; single_mixed_200k: one target converged to tol; batched_256t_200k: 256 targets "
+                         "solved in batches of "
                          "16 that share every pass over X and S; regression_200k: CSR-SDA's regression step "
                          "(X^T X + beta I) w = X^T z on the same X; sa_200k: SA-SDA, the SDA operator with X = I_N on the "
                          "same graph and labels")
@@ -119,7 +137,7 @@ class ClockSampler:
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
 
-KERNEL_SOURCES = ("sda_common.cuh", "sda_operator.cuh", "sda_kernels.cuh")
+KERNEL_SOURCES = ("sda_common.cuh", "sda_operator.cuh", "sda_kernels.cuh", "sda_batch.cu")
 
 
 def sources_hash() -> str:
@@ -132,12 +150,12 @@ def sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(phase: str):
+def recorded_traffic(phase: str, path: str = PROFILE_SUMMARY):
     """DRAM bytes per launch of the `phase` kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
-    if not os.path.exists(PROFILE_SUMMARY):
+    summary `path`, if it was taken on the current kernel sources (else None)."""
+    if not os.path.exists(path):
         return None
-    txt = open(PROFILE_SUMMARY).read()
+    txt = open(path).read()
     m = re.search(r"sources_sha256:\s*([0-9a-f]+)", txt)
     t = re.search(r"%s_dram_bytes_per_launch:\s*([0-9.eE+]+)" % phase, txt)
     if not m or not t or m.group(1) != sources_hash():
@@ -187,6 +205,52 @@ def load_peaks():
 
 
 # ---------------------------------------------------------------------------
+# the large workload: shared pieces of both arms
+# ---------------------------------------------------------------------------
+
+def heldout_arrays(prob, t0: int, cnt: int):
+    """Held-out rows (concatenated), their offsets [cnt + 1] and classes of targets t0 .. t0 + cnt - 1."""
+    hs = [prob.heldout[t] for t in range(t0, t0 + cnt)]
+    rows = np.concatenate(hs).astype(np.int64)
+    off = np.concatenate([[0], np.cumsum([h.size for h in hs])]).astype(np.int64)
+    y = np.concatenate([prob.truth[t][prob.heldout[t]] for t in range(t0, t0 + cnt)]).astype(np.float64)
+    return rows, off, y
+
+
+def oracle_step(prob, t: int, fixed: int, X=None):
+    """The FP64 oracle's work for one target of a step of the large workload:
+    shifted CG (Algorithm 3) over every shift for `fixed` iterations, the FP64
+    true residual of every shift, the centred held-out ratings of every shift,
+    the shift of least held-out logistic loss and the adjoint gradient there
+    (its solve for `fixed` iterations too).  Returns (W, true residuals, best
+    shift, d_alpha, d_beta, seconds of its parts: setup, sweep, checks, adjoint)."""
+    import scipy.sparse as sp
+    import oracle
+    tm = {}
+    c0 = time.perf_counter()
+    o = oracle.from_problem(prob, target=t)
+    b = o.rhs_canonical()
+    c1 = time.perf_counter()
+    res = o.shifted_cg(b, prob.shifts, fixed_iters=fixed)
+    c2 = time.perf_counter()
+    tres = [o.true_residual(b, beta, res.W[s]) for s, beta in enumerate(prob.shifts)]
+    rows = prob.heldout[t]
+    y = prob.truth[t][rows]
+    X = sp.csr_matrix((prob.x_val, prob.x_col, prob.x_ptr), shape=(prob.n, prob.d)) if X is None else X
+    mu = o.class_means()[0]
+    S = (X[rows] @ res.W.T) - (res.W @ mu)[None, :]
+    losses = [oracle.logistic_loss(S[:, k], y)[0] for k in range(len(prob.shifts))]
+    best = int(np.argmin(losses))
+    c3 = time.perf_counter()
+    _, da, db, _ = oracle.adjoint_grad_sparse(o, prob.x_ptr, prob.x_col, prob.x_val, prob.s_ptr, prob.s_col,
+                                              prob.s_val, rows, y, float(prob.shifts[best]), fixed_iters=fixed,
+                                              w=res.W[best])
+    c4 = time.perf_counter()
+    tm = {"setup": c1 - c0, "sweep": c2 - c1, "checks": c3 - c2, "adjoint": c4 - c3}
+    return res.W, np.array(tres), best, da, db, tm
+
+
+# ---------------------------------------------------------------------------
 # reference arm: the FP64 CPU oracle as it stands
 # ---------------------------------------------------------------------------
 
@@ -200,7 +264,7 @@ def run_reference(args, prob, rank):
     # iterations of the full solve (setup, untimed): the oracle's own run to tol
     full = o.shifted_cg(b, prob.shifts, tol=args.tol, max_iter=args.max_iter)
     iters_full = int(full.total_iters)
-    k = max(1, min(args.cpu_iters, iters_full))
+    k = max(1, min(args.cpu_iters or 500, iters_full))
     for _ in range(args.warmup):
         o.shifted_cg(b, prob.shifts, fixed_iters=k)
     times = []
@@ -217,6 +281,43 @@ def run_reference(args, prob, rank):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d of the %d shifted-CG iterations of the full solve per step, "
                                        "extrapolated linearly" % (k, iters_full)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_large(args, prob, rank):
+    """Reference arm of the large workload: the FP64 oracle as it stands on the
+    host cores, one target per step (oracle_step: its sweep of every shift for
+    70 iterations, true residuals, held-out ratings and adjoint gradient)."""
+    import scipy.sparse as sp
+    import oracle
+    if rank != 0:
+        return
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    X = sp.csr_matrix((prob.x_val, prob.x_col, prob.x_ptr), shape=(prob.n, prob.d))
+    T = prob.labels.shape[0]
+    # a bounded sample per step: one target, its sweep and adjoint solve run for
+    # k = cpu_iters iterations and scaled by fixed_iters / k (the rest as run)
+    k_it = max(1, min(args.cpu_iters or 10, args.fixed_iters))
+    scale = args.fixed_iters / k_it
+    for k in range(args.warmup):
+        oracle_step(prob, k % T, k_it, X)
+    times = []
+    for k in range(args.steps):
+        tm = oracle_step(prob, (args.warmup + k) % T, k_it, X)[-1]
+        times.append(tm["setup"] + tm["checks"] + scale * (tm["sweep"] + tm["adjoint"]))
+    per = statistics.mean(times)
+    value = 1.0 / per
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": LARGE, "n": prob.n, "d": prob.d, "nnz": int(prob.x_ptr[-1]),
+                       "targets": T, "shifts": len(prob.shifts), "fixed_iters": args.fixed_iters},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one target per step: its shifted-CG sweep of all %d shifts and its "
+                                       "adjoint solve run for %d iterations and scaled linearly to %d; FP64 true "
+                                       "residuals, held-out ratings and the operator setup as run"
+                                       % (len(prob.shifts), k_it, args.fixed_iters)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -561,8 +662,295 @@ def run_sa(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_large(args, rank, world, local):
+    """Default workload: 2,000,000 x 1,048,576 binary X (FP8 storage, 90M
+    nonzeros), kNN graph (k = 8), 1,000 targets with 50..50,000 labelled rows,
+    24 shifts 1e-5..1e3, the fixed-iteration protocol of Sec. 5.2 (70
+    iterations per solve).  One step = one chunk of CHUNK targets: operator
+    build with the chunk's labels, the batched sweep of every shift with the
+    FP64 true residual of every (target, shift), the centred held-out ratings
+    of every shift, the shift of least held-out logistic loss per target and
+    the adjoint gradient there (batched, 70 iterations).  Targets are sharded
+    over the ranks with no exchange."""
+    import torch
+    from paper_1709_04794_gb300 import sda, synth
+    prob = synth.make_problem(LARGE)
+    compute = args.compute or prob.workload.value_dtype
+    T_all = prob.labels.shape[0]
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    t_begin, t_mine = shard(T_all, rank, world)
+    stream = torch.cuda.current_stream()
+    ns, d, n = len(prob.shifts), prob.d, prob.n
+    C = max(1, min(args.chunk, t_mine))
+    keys = ("x_ptr", "x_col", "x_val", "s_ptr", "s_col", "s_val", "labels")
+    dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k))).cuda() for k in keys}
+    rows_all, off_all, y_all = heldout_arrays(prob, 0, T_all)
+    held = {"rows": torch.from_numpy(rows_all).cuda(), "y": torch.from_numpy(y_all).cuda()}
+    w = torch.empty((C, ns, d), dtype=torch.float64, device="cuda")
+    chunks = [(t_begin + c0, min(C, t_mine - c0)) for c0 in range(0, t_mine, C)]
+
+    def solve_opts(cnt, profile=0, check=1, fixed=args.fixed_iters):
+        o = sda.sda_default_opts()
+        o.fixed_iters, o.batch_targets, o.check_residual = fixed, 1, check
+        o.target_count, o.profile = cnt, profile
+        return o
+
+    def build(inputs, t0, cnt, comp=compute):
+        return sda.sda_build_operator(inputs["x_ptr"], inputs["x_col"], inputs["x_val"], d, inputs["s_ptr"],
+                                      inputs["s_col"], inputs["s_val"], inputs["labels"][t0:t0 + cnt],
+                                      prob.alpha, float("nan"), comp, stream)
+
+    def step(k, inputs=dev, hold=held):
+        t0, cnt = chunks[k % len(chunks)]
+        h = build(inputs, t0, cnt)
+        try:
+            code, rep = sda.sda_solve_shifts(h, prob.shifts, solve_opts(cnt), w_out=w[:cnt], n_report=cnt,
+                                             stream=stream)
+            r0, r1 = int(off_all[t0]), int(off_all[t0 + cnt])
+            rows = hold["rows"][r0:r1].to("cuda", non_blocking=True)
+            y = hold["y"][r0:r1].to("cuda", non_blocking=True)
+            off = off_all[t0:t0 + cnt + 1] - r0
+            g = torch.empty(r1 - r0, dtype=torch.float64, device="cuda")
+            wb = torch.empty((cnt, d), dtype=torch.float64, device="cuda")
+            losses = torch.empty((cnt, ns), dtype=torch.float64, device="cuda")
+            scs = []
+            for i in range(cnt):
+                ri, yi = rows[off[i]:off[i + 1]], y[off[i]:off[i + 1]]
+                sc = torch.empty((ns, ri.numel()), dtype=torch.float64, device="cuda")
+                sda.sda_project_rows(h, w[i], ns, ri, sc, 1, i, stream)
+                losses[i] = torch.nn.functional.softplus(-yi[None, :] * sc).mean(dim=1)
+                scs.append(sc)
+            best = torch.argmin(losses, dim=1).tolist()
+            for i in range(cnt):
+                yi = y[off[i]:off[i + 1]]
+                g[off[i]:off[i + 1]] = -yi * torch.sigmoid(-yi * scs[i][best[i]]) / yi.numel()
+                wb[i] = w[i, best[i]]
+            oa = sda.sda_default_opts()
+            oa.fixed_iters = args.fixed_iters
+            code_a, da, db, rep_a = sda.sda_adjoint_grad_batched(h, list(range(cnt)), float("nan"),
+                                                                 [float(prob.shifts[b]) for b in best], wb, g,
+                                                                 rows, off, oa, stream=stream)
+            lh = losses.cpu().numpy()
+        finally:
+            sda.sda_destroy_operator(h)
+        return {"code": code, "rep": rep, "best": best, "da": da, "db": db, "losses": lh, "t0": t0, "cnt": cnt}
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sda.sda_kernel_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    outs = [step(args.warmup + k) for k in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = sda.sda_kernel_launch_count() - l0
+    clk = clocks.stop()
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist)
+    solved = sum(o["cnt"] for o in outs)
+    if dist is not None:
+        tot = torch.tensor([float(solved)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tot)
+        solved = int(tot.item())
+    value = solved / t
+
+    # ---- untimed: per-kernel shares, mixed vs FP64, parity, baselines ----------------
+    nb = min(16, chunks[0][1])
+    t0c = chunks[0][0]
+    peak, peak_kind = load_peaks()
+
+    def timed_solve(comp, profile=0, keep_w=False):
+        h = build(dev, t0c, nb, comp)
+        try:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            code, rep = sda.sda_solve_shifts(h, prob.shifts, solve_opts(nb, profile=profile), w_out=w[:nb],
+                                             n_report=nb, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = sda.sda_get_solve_stats(h)
+            w_first = w[:nb].cpu().numpy() if keep_w else None
+            # the same sweep without the residual check (the iteration kernels alone, graphs)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e3 = torch.cuda.Event(enable_timing=True)
+            e2.record(stream)
+            sda.sda_solve_shifts(h, prob.shifts, solve_opts(nb, profile=profile, check=0), w_out=w[:nb],
+                                 n_report=nb, stream=stream)
+            e3.record(stream)
+            torch.cuda.synchronize()
+            st_iter = sda.sda_get_solve_stats(h)
+        finally:
+            sda.sda_destroy_operator(h)
+        return e0.elapsed_time(e1), e2.elapsed_time(e3), rep, st, st_iter, w_first
+
+    ms_mix, ms_mix_iter, rep_mix, _, st_mix, w_mix = timed_solve(compute, keep_w=True)
+    pst = timed_solve(compute, profile=1)[4]
+    ms_64, ms_64_iter, rep_64, _, st_64, w_64 = timed_solve("f64", keep_w=True)
+    bi = max(1, st_mix["iterations"])
+    per = batched_bytes(prob, compute, bi, st_mix["shift_iterations"], nb)
+    prof = {k: pst["ms"][i + 1] for i, k in enumerate(("phase1", "phase2", "phase3a", "phase3b"))}
+    prof_tot = sum(prof.values())
+    it_ms = ms_mix_iter / bi          # one batch iteration of the graph-replayed sweep
+    durs = {k: it_ms * prof[k] / prof_tot for k in prof}
+    dominant = max(durs, key=durs.get)
+    names = {"phase1": "kb_phase1 (rows of X, 16 targets)", "phase2": "kb_phase2 (rows of S, 16 targets)",
+             "phase3a": "kb_phase3a (columns of X, 16 targets)", "phase3b": "kb_phase3b (vector and shift stream)"}
+    achieved = per[dominant] / (durs[dominant] * 1e-3) / 1e9
+    whole = sum(per.values()) / (it_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(dominant, LARGE_PROFILE), "kernel": names[dominant],
+                "peak_kind": peak_kind, "bytes_per_launch": per[dominant], "ms_per_launch": durs[dominant],
+                "whole_iteration": {"GB/s": whole, "frac": whole / peak, "bytes": sum(per.values()),
+                                    "ms": it_ms},
+                "durations": "graph-replayed sweep of one batch of 16 targets / iterations, apportioned by the "
+                             "event-timed shares of the four kernels",
+                "all_kernels": {names[k]: {"ms_per_launch": durs[k], "GB/s": per[k] / (durs[k] * 1e-3) / 1e9,
+                                           "share": prof[k] / prof_tot} for k in durs}}
+    tres_mix = np.array([[r["true_residual"] for r in tr] for tr in rep_mix])
+    tres_64 = np.array([[r["true_residual"] for r in tr] for tr in rep_64])
+    above = tres_64 >= 1e-5
+    mixed_vs_fp64 = {"targets": nb, "fixed_iters": args.fixed_iters,
+                     "mixed_solves_per_s": nb / (ms_mix * 1e-3), "fp64_solves_per_s": nb / (ms_64 * 1e-3),
+                     "speedup": ms_64 / ms_mix, "mixed_iteration_ms": ms_mix_iter / bi,
+                     "fp64_iteration_ms": ms_64_iter / max(1, st_64["iterations"]),
+                     "max_rel_residual_difference": float(np.max((np.abs(tres_mix - tres_64) / tres_64)[above]))
+                     if above.any() else None,
+                     "pairs_compared": "%d of %d" % (int(above.sum()), above.size),
+                     "note": "same Krylov iteration count; FP64 true residual of every (target, shift) of both, "
+                             "compared where the FP64 path's is >= 1e-5 (above that, the FP32 vectors reach the same "
+                             "residual; below it they stop near 1e-6 unless refined)"}
+
+    # parity of the mixed sweep against the FP64 oracle (same 70 iterations), and the
+    # oracle's per-target time as the CPU baseline (rank 0 only)
+    parity, cpu = None, None
+    if rank == 0 and not args.no_cpu:
+        import scipy.sparse as sp
+        import oracle
+        cores = oracle.set_threads(os.cpu_count() or 1)
+        X = sp.csr_matrix((prob.x_val, prob.x_col, prob.x_ptr), shape=(prob.n, prob.d))
+        worst = {"rel": 0.0, "elem": 0.0, "auc": 0.0, "grad": 0.0, "rel_conv": 0.0, "elem_conv": 0.0,
+                 "auc_conv": 0.0, "rel64": 0.0, "elem64": 0.0}
+        times, best_same, n_conv = [], 0, 0
+        first = outs[0] if outs[0]["t0"] == t0c else step(0)
+        nchk = min(2, nb)
+        for i in range(nchk):
+            t = t0c + i
+            c0 = time.perf_counter()
+            W, tres, best, da, db, _ = oracle_step(prob, t, args.fixed_iters, X)
+            times.append(time.perf_counter() - c0)
+            rows = prob.heldout[t]
+            y = prob.truth[t][rows]
+            for s in range(ns):
+                ref = W[s]
+                rel = float(np.linalg.norm(w_mix[i, s] - ref) / np.linalg.norm(ref))
+                elem = float(np.max(np.abs(w_mix[i, s] - ref)) / np.max(np.abs(ref)))
+                dauc = abs(oracle.auc(X[rows] @ w_mix[i, s], y) - oracle.auc(X[rows] @ ref, y))
+                worst["rel"], worst["elem"], worst["auc"] = (max(worst["rel"], rel), max(worst["elem"], elem),
+                                                             max(worst["auc"], dauc))
+                if tres[s] <= 1e-3:        # converged to the paper's tolerance after the fixed iterations
+                    n_conv += 1
+                    worst["rel_conv"], worst["elem_conv"] = max(worst["rel_conv"], rel), max(worst["elem_conv"], elem)
+                    worst["auc_conv"] = max(worst["auc_conv"], dauc)
+                worst["rel64"] = max(worst["rel64"], float(np.linalg.norm(w_64[i, s] - ref) / np.linalg.norm(ref)))
+                worst["elem64"] = max(worst["elem64"],
+                                      float(np.max(np.abs(w_64[i, s] - ref)) / np.max(np.abs(ref))))
+            best_same += int(first["best"][i] == best)
+            worst["grad"] = max(worst["grad"], abs(first["da"][i] - da) / abs(da), abs(first["db"][i] - db) / abs(db))
+        parity = {"oracle": "FP64 CPU oracle, the same %d shifted-CG iterations" % args.fixed_iters,
+                  "targets": nchk, "shifts": ns,
+                  "fp64_gpu": {"max_rel_w_err": worst["rel64"], "max_elem_w_err": worst["elem64"]},
+                  "mixed": {"max_rel_w_err": worst["rel"], "max_elem_w_err": worst["elem"],
+                            "max_abs_dAUC": worst["auc"]},
+                  "mixed_converged_shifts": {"count": n_conv, "max_rel_w_err": worst["rel_conv"],
+                                             "max_elem_w_err": worst["elem_conv"], "max_abs_dAUC": worst["auc_conv"],
+                                             "which": "shifts whose oracle FP64 true residual is <= 1e-3 after the "
+                                                      "fixed iterations"},
+                  "same_best_shift": "%d/%d" % (best_same, nchk), "max_rel_grad_err": worst["grad"],
+                  "note": "mode (ii): iterates after a fixed iteration count; on the shifts far from convergence "
+                          "(kappa up to 1e9) FP32 vectors and FP64 vectors give different iterates; the 1e-6 bar "
+                          "on converged solutions is checked by the refined-solve tests"}
+        per_t = statistics.mean(times)
+        cpu = {"value": 1.0 / per_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d targets of the first chunk, each: shifted-CG sweep of all %d shifts for %d iterations, "
+                         "FP64 true residuals, held-out ratings, adjoint gradient at the best shift" %
+                         (nchk, ns, args.fixed_iters)}
+
+    # end to end through the C ABI with host buffers: X, S, the chunk's labels and
+    # held-out rows from pinned host memory every step; reports, losses and
+    # gradients back to the host
+    e2e = None
+    if not args.no_e2e:
+        host = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k))).pin_memory()
+                for k in keys if k != "labels"}
+        host_lab = torch.from_numpy(prob.labels).pin_memory()
+        host["labels"] = host_lab
+        hold_h = {"rows": torch.from_numpy(rows_all).pin_memory(), "y": torch.from_numpy(y_all).pin_memory()}
+        e_steps = max(1, min(args.steps, 3))
+        h2d = d2h = 0
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        for k in range(e_steps):
+            o = step(k, inputs=host, hold=hold_h)
+            cnt, t0 = o["cnt"], o["t0"]
+            h2d += sum(host[x].numel() * host[x].element_size() for x in keys if x != "labels")
+            h2d += cnt * n + int(off_all[t0 + cnt] - off_all[t0]) * 16
+            d2h += cnt * ns * (24 + 8) + cnt * 16 + cnt * 8
+        el = time.perf_counter() - c0
+        e_solved = sum(chunks[k % len(chunks)][1] for k in range(e_steps))
+        e2e = {"value": world * e_solved / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d / e_steps),
+               "d2h_bytes_per_step": int(d2h / e_steps), "steps": e_steps,
+               "step": "the timed step through the C ABI with X, S, the chunk's labels and held-out rows in "
+                       "pinned host memory (the build copies them in); reports, held-out losses and gradients "
+                       "come back to the host"}
+
+    if rank == 0:
+        last = outs[-1]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak" if world == 1 else "strong", "vs_baseline": None,
+                "dtype": "f32" if compute != "f64" else "f64", "data": "synthetic",
+                "config": {"workload": LARGE, "n": n, "d": d, "nnz": int(prob.x_ptr[-1]),
+                           "graph_nnz": int(prob.s_ptr[-1]), "targets": T_all, "shifts": ns,
+                           "x_storage": compute, "fixed_iters": args.fixed_iters, "chunk": C, "batch": 16,
+                           "targets_per_run": solved, "alpha": prob.alpha,
+                           "parallelism": "targets sharded over %d GPU(s), no exchange" % world,
+                           "status": last["code"],
+                           "max_true_residual_last_step": max(r["true_residual"] for tr in last["rep"] for r in tr),
+                           "step": "operator build with the chunk's labels; batched sweep of every shift "
+                                   "(%d iterations) with the FP64 true residual of every (target, shift); centred "
+                                   "held-out ratings of every shift; least-loss shift per target; batched adjoint "
+                                   "gradient there (%d iterations)" % (args.fixed_iters, args.fixed_iters),
+                           "l2": "no flush: one batch iteration streams > 8 GB (> 126 MB L2)"},
+                "mixed_vs_fp64": mixed_vs_fp64, "parity": parity,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
+    if args.workload == LARGE:
+        rank = int(os.environ.get("RANK", "0"))
+        if args.impl == "reference":
+            from paper_1709_04794_gb300 import synth
+            run_reference_large(args, synth.make_problem(LARGE), rank)
+        else:
+            run_large(args, rank, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0")))
+        return
     if args.workload == "sa_200k" and args.impl == "ours":
         run_sa(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
                int(os.environ.get("LOCAL_RANK", "0")))

@@ -324,7 +324,7 @@ def adjoint_grad_dense(X, s_ptr, s_col, s_val, y, alpha, beta, rows, y_rows, b=N
 
 
 def adjoint_grad_sparse(o: Oracle, x_ptr, x_col, x_val, s_ptr, s_col, s_val, rows, y_rows, beta,
-                        tol=1e-12, max_iter=100000):
+                        tol=1e-12, max_iter=100000, fixed_iters=0, w=None):
     """d loss/d alpha and d loss/d beta of the held-out logistic loss, for
     problems too large for adjoint_grad_dense: the two solves are the C
     oracle's CG (Algorithm 2) on its operator, the products sparse.
@@ -333,6 +333,8 @@ def adjoint_grad_sparse(o: Oracle, x_ptr, x_col, x_val, s_ptr, s_col, s_val, row
     lambda = (B + beta I)^{-1} (X_h - 1 mu_l^T)^T g,  g = d loss / d s_h;
     d loss/d beta = -lambda^T w,  d loss/d alpha = -lambda^T (dB/dalpha) w with
     dB/dalpha = X^T L X - S_t^l (B = (1 - alpha) S_t^l + alpha X^T L X, eq. 7).
+    fixed_iters > 0 runs both CG solves for exactly that many iterations (the
+    fixed-iteration protocol of Sec. 5.2); a given w skips the forward solve.
     Returns (loss, d_alpha, d_beta, w)."""
     import scipy.sparse as sp
     n, d = o.n, o.d
@@ -341,12 +343,13 @@ def adjoint_grad_sparse(o: Oracle, x_ptr, x_col, x_val, s_ptr, s_col, s_val, row
     L = sp.diags(np.asarray(S.sum(axis=1)).ravel()) - S
     mu, mp, mn, _ = o.class_means()
     lab = (np.asarray(o._keep[6]) != 0).astype(float)
-    w, _, _, rc = o.cg(mp - mn, beta, tol=tol, max_iter=max_iter)
+    if w is None:
+        w, _, _, rc = o.cg(mp - mn, beta, tol=tol, max_iter=max_iter, fixed_iters=fixed_iters)
     rows = np.asarray(rows)
     s = X[rows] @ w - mu @ w
     loss, g = logistic_loss(s, y_rows)
     c = X[rows].T @ g - mu * g.sum()
-    lam, _, _, rc2 = o.cg(c, beta, tol=tol, max_iter=max_iter)
+    lam, _, _, rc2 = o.cg(c, beta, tol=tol, max_iter=max_iter, fixed_iters=fixed_iters)
     u = X @ w - mu @ w                      # centred ratings of every sample
     St_w = X.T @ (lab * u) - mu * (lab * u).sum()
     XLX_w = X.T @ (L @ (X @ w))
