@@ -203,11 +203,26 @@ typedef struct {
                                0: one target after another.  With refine_rounds > 0 the correction
                                solves of up to 16 (target, shift) pairs of a batch share one run too */
     double refine_tol;      /* target FP64 true relative residual (NaN or <= 0: tol)                */
+    int32_t shift_form;     /* how the batched path forms every shift's solution: SDA_SHIFTS_*    */
 } sda_solve_opts;
+
+/* Shift forms of the batched path (opts.batch_targets = 1).  The single-target
+ * path always runs the recurrences (SDA_SHIFTS_BASIS there: SDA_ERR_UNSUPPORTED). */
+enum {
+    SDA_SHIFTS_AUTO = 0,        /* the stored basis when every shift is solved at once (n_shifts > 1) and
+                                   (limit + 1) x D x 16 basis values fit in 40 % of the free device
+                                   memory, else the recurrences                                         */
+    SDA_SHIFTS_RECURRENCE = 1,  /* Algorithm 3: every active shift's W and P updated every iteration  */
+    SDA_SHIFTS_BASIS = 2        /* Lanczos form (Sec. 3.2.1, eqs. for T and the shifted solve): the base
+                                   residuals r_0 .. r_{K-1} are kept (the basis V up to scaling), the
+                                   tridiagonal T_K of the base system comes from the CG scalars, each shift
+                                   solves (T_{K_s} + (beta_s - sigma0) I) y = ||b|| e_1 in FP64 and
+                                   W_s = V y is formed once after the run (K_s: the shift's stop)        */
+};
 
 /* Fills *opt with: tol 1e-6, max_iter 10000, fixed_iters 0, canonical RHS,
  * all targets, FP64 residual check on, device output, graphs on, auto batch,
- * the operator's alpha and omega, no refinement. */
+ * the operator's alpha and omega, no refinement, SDA_SHIFTS_AUTO. */
 SDA_API void sda_default_opts(sda_solve_opts *opt);
 
 /* Per target and shift outcome of sda_solve_shifts. */
@@ -376,6 +391,9 @@ typedef struct {
                                   [3] X columns (X^T v), [4] vector and shift-state update          */
     double ms[5];              /* device time of those launches in ms (profile mode, else 0)        */
     double solve_ms;           /* device time of the whole call in ms                               */
+    int32_t shift_form;        /* SDA_SHIFTS_RECURRENCE or SDA_SHIFTS_BASIS: the form the call's first
+                                  batched run used (RECURRENCE on the single-target path)              */
+    int32_t basis_slots;       /* stored-basis form: basis vectors (iterations) kept by that run         */
 } sda_solve_stats;
 
 SDA_API int sda_get_solve_stats(const sda_operator *op, sda_solve_stats *stats);

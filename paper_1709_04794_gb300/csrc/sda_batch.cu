@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "sda_kernels.cuh"
@@ -64,6 +65,23 @@ struct BatchCoef {
     int32_t active;
 };
 
+// Scalars of one iteration k of a lane's base CG run, kept for the stored-basis
+// form: a = -gamma_k (the step), b = alpha_{k+1} = <r_{k+1}, r_{k+1}> / <r_k, r_k>,
+// rr = <r_k, r_k> (all FP64).  They define the tridiagonal T of the base system.
+struct LzStep {
+    double a, b, rr;
+};
+
+// Device view of the stored basis: slot k (iteration k's base residual r_k, all
+// lanes, [ldw][kTB]) lives at tab[k / per_chunk] + (k % per_chunk) * ldw * kTB;
+// NULL tab selects the recurrences.
+template <class FT>
+struct BasisView {
+    FT *const *tab;
+    int per_chunk;
+    LzStep *lz;      // [k][kTB]
+};
+
 struct BatchWs {
     int fp64 = -1;
     int64_t d = 0, n = 0, ldw = 0, n8 = 0;
@@ -80,13 +98,22 @@ struct BatchWs {
     DevBuf<double> sig, r2;    // per-lane shifts and squared residual norms of the FP64 block utilities
     DevBuf<double> wall;       // FP64 solutions of a batch's (target, shift) pairs [target][shift][D]
     DevBuf<double> rbuf;       // residual vectors of up to kTB pairs [lane][D] (refinement right-hand sides)
+    // stored-basis form: chunks of kBasisChunk slots [ldw][kTB] each, their device
+    // pointer table (graphs read it, so new chunks need no recapture), the CG scalars
+    // of every iteration and the per-(lane, shift) basis coefficients
+    std::vector<std::unique_ptr<DevBuf<char>>> bchunks;
+    DevBuf<char> btab;
+    int btab_cap = 0;
+    DevBuf<LzStep> lz;
+    DevBuf<double> coefs;
+    int shift_ns = 0;          // shifts the W, P buffers hold (recurrence form)
     DevBuf<unsigned> cnt, lcount;
     SolveState *h_st = nullptr;
     BatchCtl *h_ctl = nullptr;
     int grid = 0;                          // every kernel but the sparse passes of the batched solve
     int grid1 = 0, grid2 = 0, grid3a = 0;  // their own grids (occupancy of each)
     cudaGraphExec_t graph = nullptr;
-    int graph_iters = 0, graph_ns = 0;
+    int graph_iters = 0, graph_ns = 0, graph_basis = -1;
     cudaStream_t cap_stream = nullptr;
     ~BatchWs() {
         if (graph) cudaGraphExecDestroy(graph);
@@ -194,9 +221,11 @@ __global__ void __launch_bounds__(kBlock) kb_init(int64_t ldw, int ns, const dou
         rp[e] = x;
         x.x = (FT)0;
         rp[m + e] = x;
-        for (int s = 0; s < ns; ++s) {
-            W[(int64_t)s * m + e] = (FT)0;
-            P[(int64_t)s * m + e] = (FT)0;
+        if (W) {   // recurrence form only
+            for (int s = 0; s < ns; ++s) {
+                W[(int64_t)s * m + e] = (FT)0;
+                P[(int64_t)s * m + e] = (FT)0;
+            }
         }
         dd[0].add((double)rj * (double)rj);
         dd[1].add(mu[e] * (double)rj);
@@ -596,7 +625,7 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
                                                     FT *__restrict__ P, SolveState *st, BatchCtl *ctl,
                                                     const BatchCoef<FT> *__restrict__ coef,
                                                     const float *__restrict__ mu32, const double *__restrict__ mu64,
-                                                    double *partials, unsigned *counter) {
+                                                    double *partials, unsigned *counter, BasisView<FT> bvw) {
     using R = typename RPair<FT>::T;
     using Part = typename CompSum<FT>::Part;
     __shared__ Part red[kBlock * 3];
@@ -636,9 +665,12 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
     const int t = threadIdx.x % kTB;
     CompSum<FT> dd[3];
     const int64_t md = d * kTB;
+    // stored-basis form: r_k of every lane goes to basis slot k
+    FT *__restrict__ bslot = bvw.tab ? bvw.tab[ctl->k / bvw.per_chunk] + (int64_t)(ctl->k % bvw.per_chunk) * m : nullptr;
     for (int64_t e = tid; e < md; e += nthr) {
         if (!BOK(e, ctl->bb.ldw * kTB, 41)) continue;
         const R x = a[e];
+        if (bslot) bslot[e] = x.x;
         const FT pk = form_p<FT>(x.x, x.y, s_al[t]);
         CompSum<FT> sj;
         CompSum<FT>::add_part(sj, s[e]);
@@ -664,8 +696,8 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
     // (targets whose shift stopped keep their values).  Items i = q * nch + c over
     // the shifts some target still updates (slot q) and 16-byte chunks c of VW
     // consecutive targets of one feature; (q, c) advance by (nthr / nch, nthr %
-    // nch), two items per thread in flight.
-    {
+    // nch), two items per thread in flight.  The stored-basis form skips it.
+    if (!bvw.tab) {
         using V = typename Vec16<FT>::T;
         constexpr int VW = Vec16<FT>::n;
         constexpr int UNROLL = 2;
@@ -736,6 +768,7 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
             const double c_new = tot[1] + anw * S.c;
             const double pp_new = rr_new + 2.0 * anw * tot[2] + anw * anw * S.pp;
             if (!isfinite(rr_new) || !isfinite(anw)) S.status = SDA_ERR_BREAKDOWN;
+            if (bvw.lz) bvw.lz[(int64_t)S.k * kTB + threadIdx.x] = LzStep{-S.gamma, anw, S.rr};
             S.gamma_prev = S.gamma;
             S.alpha = anw;
             S.c = c_new;
@@ -782,6 +815,116 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
         for (int q = 0; q < kTB; ++q) all &= st[q].done;
         ctl->k = ctl->k + 1;
         ctl->done = all;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// stored-basis (Lanczos) form of the shifted solutions (Sec. 3.2.1)
+// ---------------------------------------------------------------------------
+// Per (lane t, shift s): the solution of the shifted system in the Krylov basis
+// of the lane's run.  With the CG scalars a_j (step), b_j (alpha_{j+1}) and
+// ||r_j||, the Lanczos vectors are v_j = (-1)^j r_j / ||r_j|| and the base
+// system's tridiagonal T has T_jj = 1/a_j + b_{j-1}/a_{j-1} and
+// T_{j,j-1} = T_{j-1,j} = sqrt(b_{j-1}) / a_{j-1}.  The shift solves
+// (T_K + delta_s I) y = ||r_0|| e_1 with K its stop iteration (Thomas
+// algorithm, FP64; T_K + delta I is SPD), so w_s = V_K y; the coefficients of
+// the raw residuals go to coef[t][s][j] = y_j (-1)^j / ||r_j|| (0 for j >= K).
+// `cp` is scratch of coef's size.
+__global__ void kb_lz_solve(int nl, int ns, int kmax, const LzStep *__restrict__ lz, const SolveState *st,
+                            double *__restrict__ coef, double *__restrict__ cp) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nl * ns) return;
+    const int t = q / ns, s = q - t * ns;
+    const SolveState &S = st[t];
+    double *y = coef + (int64_t)q * kmax, *c = cp + (int64_t)q * kmax;
+    const int K = S.status == SDA_OK ? min(S.sh[s].iters, kmax) : 0;
+    for (int j = K; j < kmax; ++j) y[j] = 0.0;
+    if (K <= 0) return;
+    const double delta = S.sh[s].delta;
+    double pa = 1.0, pb = 0.0, cprev = 0.0, dprev = 0.0;   // a_{j-1}, b_{j-1}, forward-sweep values
+    for (int j = 0; j < K; ++j) {
+        const LzStep z = lz[(int64_t)j * kTB + t];
+        const double sub = j > 0 ? sqrt(pb) / pa : 0.0;
+        const double diag = 1.0 / z.a + (j > 0 ? pb / pa : 0.0) + delta;
+        const double m = diag - sub * cprev;
+        cprev = j + 1 < K ? (sqrt(z.b) / z.a) / m : 0.0;
+        dprev = ((j == 0 ? sqrt(z.rr) : 0.0) - sub * dprev) / m;
+        c[j] = cprev;
+        y[j] = dprev;
+        pa = z.a;
+        pb = z.b;
+    }
+    for (int j = K - 2; j >= 0; --j) y[j] -= c[j] * y[j + 1];
+    for (int j = 0; j < K; ++j) y[j] *= ((j & 1) ? -1.0 : 1.0) / sqrt(lz[(int64_t)j * kTB + t].rr);
+}
+
+// W = V Y of every lane: wall[l][s][j] = sum_k coef[l][s][k] r_k[j][l] over the
+// basis slots k < kmax (FP64 out, permuted order).  One thread per (feature,
+// lane) element and EPT features; the shifts in passes of kGemmSG accumulators
+// per element (FMA in the vector type, coefficients rounded to it); a k-chunk of
+// coefficients staged in shared memory; the outputs leave through a transposed
+// tile so that each lane's row of features is written contiguously.
+constexpr int kGemmSG = 16;
+constexpr int kGemmKC = 16;
+template <class FT, int EPT>
+__global__ void __launch_bounds__(kBlock) kb_basis_gemm(int64_t d, int64_t ldw, int nl, int ns, int kmax,
+                                                       FT *const *__restrict__ tab, int per_chunk,
+                                                       const double *__restrict__ coef, double *__restrict__ wall) {
+    constexpr int FR = kBlock / kTB;         // features per row of the block tile
+    constexpr int FPB = FR * EPT;            // features per block tile
+    __shared__ FT cs[kGemmKC][kGemmSG][kTB];
+    __shared__ double tile[kTB][FPB + 1];
+    const int l = threadIdx.x % kTB, f = threadIdx.x / kTB;
+    const int64_t ntiles = (d + FPB - 1) / FPB;
+    for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const int64_t j0 = ti * FPB;
+        for (int s0 = 0; s0 < ns; s0 += kGemmSG) {
+            FT acc[EPT][kGemmSG];
+#pragma unroll
+            for (int u = 0; u < EPT; ++u)
+#pragma unroll
+                for (int g = 0; g < kGemmSG; ++g) acc[u][g] = (FT)0;
+            for (int k0 = 0; k0 < kmax; k0 += kGemmKC) {
+                __syncthreads();
+                for (int q = threadIdx.x; q < kGemmKC * kGemmSG * kTB; q += kBlock) {
+                    const int kk = q / (kGemmSG * kTB), g = (q / kTB) % kGemmSG, ll = q % kTB;
+                    const int k = k0 + kk, sh = s0 + g;
+                    cs[kk][g][ll] = (k < kmax && sh < ns && ll < nl) ? (FT)coef[((int64_t)ll * ns + sh) * kmax + k]
+                                                                     : (FT)0;
+                }
+                __syncthreads();
+                const int kn = min(kGemmKC, kmax - k0);
+                for (int kk = 0; kk < kn; ++kk) {
+                    const int k = k0 + kk;
+                    const FT *slot = tab[k / per_chunk] + (int64_t)(k % per_chunk) * ldw * kTB;
+                    FT r[EPT];
+#pragma unroll
+                    for (int u = 0; u < EPT; ++u) {
+                        const int64_t j = j0 + f + u * FR;
+                        r[u] = j < d ? slot[j * kTB + l] : (FT)0;
+                    }
+#pragma unroll
+                    for (int g = 0; g < kGemmSG; ++g) {
+                        const FT cg = cs[kk][g][l];
+#pragma unroll
+                        for (int u = 0; u < EPT; ++u) acc[u][g] = fma(cg, r[u], acc[u][g]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < kGemmSG; ++g) {
+                if (s0 + g >= ns) break;
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < EPT; ++u) tile[l][f + u * FR] = (double)acc[u][g];
+                __syncthreads();
+                for (int q = threadIdx.x; q < kTB * FPB; q += kBlock) {
+                    const int ll = q / FPB, jj = q % FPB;
+                    const int64_t j = j0 + jj;
+                    if (ll < nl && j < d) wall[((int64_t)ll * ns + s0 + g) * d + j] = tile[ll][jj];
+                }
+            }
+        }
     }
 }
 
@@ -851,7 +994,7 @@ static BView<FT> bview(BatchWs &b) {
     auto *s = (Part *)base;
     base += b.ldw * kTB * sizeof(Part);
     FT *ut = (FT *)base, *v = ut + b.n8 * kTB;
-    FT *W = (FT *)b.shift.p, *P = W + (int64_t)b.ns * b.ldw * kTB;
+    FT *W = (FT *)b.shift.p, *P = W ? W + (int64_t)b.shift_ns * b.ldw * kTB : nullptr;
     return BView<FT>{pairs, s, ut, v, W, P, (BatchCoef<FT> *)b.coef.p, v + b.n8 * kTB};
 }
 
@@ -868,7 +1011,11 @@ static int ensure_batch_ws(sda_operator *op, BatchWs *&slot, int ns) {
     b.graph_iters = 0;
     SDA_TRY(b.vec.alloc((size_t)(2 * ldw * kTB * sizeof(typename RPair<FT>::T) + ldw * kTB * sizeof(Part) +
                                  2 * n8 * kTB * sizeof(FT) + ldw * kTB * sizeof(FT))));
-    SDA_TRY(b.shift.alloc((size_t)(2 * (int64_t)ns * ldw * kTB * sizeof(FT))));
+    b.shift.release();
+    b.shift_ns = 0;
+    b.bchunks.clear();
+    b.btab.release();
+    b.btab_cap = 0;
     SDA_TRY(b.b.alloc((size_t)(ldw * kTB)));
     SDA_TRY(b.mu64.alloc((size_t)(ldw * kTB)));
     SDA_TRY(b.mu32.alloc((size_t)(ldw * kTB)));
@@ -901,11 +1048,55 @@ static int ensure_batch(sda_operator *op, int ns) {
     return ensure_batch_ws<FT>(op, op->bws, ns);
 }
 
+// W, P of ns shifts for the recurrence form (grown on demand; a new buffer
+// invalidates the captured graph, which holds its address)
+template <class FT>
+static int ensure_shift(BatchWs &b, int ns) {
+    if (b.shift_ns >= ns) return SDA_OK;
+    if (b.graph) cudaGraphExecDestroy(b.graph);
+    b.graph = nullptr;
+    SDA_TRY(b.shift.alloc((size_t)(2 * (int64_t)ns * b.ldw * kTB * sizeof(FT))));
+    b.shift_ns = ns;
+    return SDA_OK;
+}
+
+constexpr int kBasisChunk = 64;   // basis slots per allocated chunk
+
+// Basis slots [0, nslots) allocated (whole chunks) and listed in the device table
+// of `cap` entries; the table is (re)allocated for `cap` chunks when smaller.
+template <class FT>
+static int ensure_basis(BatchWs &b, int64_t nslots, int cap, cudaStream_t s) {
+    if (b.btab_cap < cap) {
+        if (b.graph) cudaGraphExecDestroy(b.graph);
+        b.graph = nullptr;
+        SDA_TRY(b.btab.alloc((size_t)cap * sizeof(FT *)));
+        b.btab_cap = cap;
+        std::vector<FT *> h(b.bchunks.size());
+        for (size_t i = 0; i < h.size(); ++i) h[i] = (FT *)b.bchunks[i]->p;
+        if (!h.empty()) {
+            SDA_CUDA(cudaMemcpyAsync(b.btab.p, h.data(), h.size() * sizeof(FT *), cudaMemcpyHostToDevice, s));
+            SDA_CUDA(cudaStreamSynchronize(s));
+        }
+    }
+    const int64_t need = (nslots + kBasisChunk - 1) / kBasisChunk;
+    if (need > b.btab_cap) return fail(SDA_ERR_INVALID_ARG, "basis table too small");
+    while ((int64_t)b.bchunks.size() < need) {
+        std::unique_ptr<DevBuf<char>> c(new DevBuf<char>());
+        SDA_TRY(c->alloc((size_t)kBasisChunk * b.ldw * kTB * sizeof(FT)));
+        FT *ptr = (FT *)c->p;
+        SDA_CUDA(cudaMemcpyAsync((FT **)b.btab.p + b.bchunks.size(), &ptr, sizeof(FT *), cudaMemcpyHostToDevice, s));
+        SDA_CUDA(cudaStreamSynchronize(s));   // `ptr` lives on this stack frame
+        b.bchunks.push_back(std::move(c));
+    }
+    return SDA_OK;
+}
+
 // `ev` (profile mode): a start and an end event around each of the four kernels
 template <class VT, class FT>
-static int batch_iteration(sda_operator *op, int ns, cudaStream_t s, cudaEvent_t *ev = nullptr) {
+static int batch_iteration(sda_operator *op, int ns, bool basis, cudaStream_t s, cudaEvent_t *ev = nullptr) {
     BatchWs &b = *op->bws;
     BView<FT> bv = bview<FT>(b);
+    const BasisView<FT> bvw{basis ? (FT *const *)b.btab.p : nullptr, kBasisChunk, basis ? b.lz.p : nullptr};
     const FT *sv = std::is_same<FT, double>::value ? (const FT *)op->s_val64.p : (const FT *)op->s_val32.p;
     const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
     const int P = kMaxBlocksPerSm * op->sm_count;
@@ -933,8 +1124,8 @@ static int batch_iteration(sda_operator *op, int ns, cudaStream_t s, cudaEvent_t
     if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
     kb_phase3b<FT><<<b.grid, kBlock, (size_t)ns * kTB * sizeof(BatchCoef<FT>), s>>>(
-        op->d, b.ldw, ns, bv.s, bv.pairs, bv.W, bv.P, b.st.p, b.ctl.p, bv.coef, b.mu32.p, b.mu64.p,
-        b.part.p + (int64_t)P * kTB * 2, b.cnt.p + 1);
+        op->d, b.ldw, ns, bv.s, bv.pairs, basis ? nullptr : bv.W, basis ? nullptr : bv.P, b.st.p, b.ctl.p, bv.coef,
+        b.mu32.p, b.mu64.p, b.part.p + (int64_t)P * kTB * 2, b.cnt.p + 1, bvw);
     SDA_LAUNCHED();
     if (ev) SDA_CUDA(cudaEventRecord(ev[7], s));
 
@@ -942,7 +1133,8 @@ static int batch_iteration(sda_operator *op, int ns, cudaStream_t s, cudaEvent_t
 }
 
 template <class VT, class FT>
-static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, bool profile, cudaStream_t s) {
+static int batch_run(sda_operator *op, int ns, bool basis, int nb_iters, bool use_graph, bool profile,
+                     cudaStream_t s) {
     BatchWs &b = *op->bws;
     if (profile) {
         std::vector<cudaEvent_t> &pe = op->ws.prof_ev;
@@ -951,7 +1143,7 @@ static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, boo
             SDA_CUDA(cudaEventCreate(&e));
             pe.push_back(e);
         }
-        for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, s, pe.data() + 8 * i)));
+        for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, basis, s, pe.data() + 8 * i)));
         SDA_CUDA(cudaStreamSynchronize(s));
         for (int i = 0; i < nb_iters; ++i)
             for (int ph = 0; ph < 4; ++ph) {
@@ -963,18 +1155,18 @@ static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, boo
         return SDA_OK;
     }
     if (!use_graph) {
-        for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, s)));
+        for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, basis, s)));
         for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
         return SDA_OK;
     }
-    if (!b.graph || b.graph_iters != nb_iters || b.graph_ns != ns) {
+    if (!b.graph || b.graph_iters != nb_iters || b.graph_ns != ns || b.graph_basis != (int)basis) {
         if (b.graph) cudaGraphExecDestroy(b.graph);
         b.graph = nullptr;
         if (!b.cap_stream) SDA_CUDA(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
         SDA_CUDA(cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal));
         set_capturing(true);
         int rc = SDA_OK;
-        for (int i = 0; i < nb_iters && rc == SDA_OK; ++i) rc = batch_iteration<VT, FT>(op, ns, b.cap_stream);
+        for (int i = 0; i < nb_iters && rc == SDA_OK; ++i) rc = batch_iteration<VT, FT>(op, ns, basis, b.cap_stream);
         set_capturing(false);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(b.cap_stream, &g);
@@ -988,6 +1180,7 @@ static int batch_run(sda_operator *op, int ns, int nb_iters, bool use_graph, boo
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
         b.graph_iters = nb_iters;
         b.graph_ns = ns;
+        b.graph_basis = (int)basis;
     }
     SDA_CUDA(cudaGraphLaunch(b.graph, s));
     note_launch(5 * (int64_t)nb_iters);
@@ -1012,9 +1205,19 @@ struct BatchLane {
 // and the final solve states in the workspace's h_st.
 template <class VT, class FT>
 static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const double *deltas, int ns, bool fixed,
-                     int limit, const sda_solve_opts &o, double alpha, double omega, cudaStream_t s) {
+                     int limit, const sda_solve_opts &o, double alpha, double omega, cudaStream_t s,
+                     bool basis = false) {
     SDA_TRY(ensure_batch<FT>(op, ns));
     BatchWs &b = *op->bws;
+    const int nbi = o.iter_batch > 0 ? o.iter_batch : 32;
+    if (basis) {
+        // slots up to the last launched iteration, CG scalars of every iteration
+        const int64_t max_slots = (int64_t)limit + nbi + 1;
+        SDA_TRY(ensure_basis<FT>(b, 0, (int)((max_slots + kBasisChunk - 1) / kBasisChunk), s));
+        if (b.lz.n < (size_t)max_slots * kTB) SDA_TRY(b.lz.alloc((size_t)max_slots * kTB));
+    } else {
+        SDA_TRY(ensure_shift<FT>(b, ns));
+    }
     if (!b.grid) {
         SDA_CUDA(cudaFuncSetAttribute((const void *)kb_phase3b<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(kMaxShifts * kTB * sizeof(BatchCoef<FT>))));
@@ -1060,15 +1263,15 @@ static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const dou
         *b.h_ctl = hc;
         SDA_CUDA(cudaMemcpyAsync(b.ctl.p, b.h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
     }
-    kb_init<FT><<<b.grid, kBlock, 0, s>>>(b.ldw, ns, b.b.p, b.mu64.p, bv.pairs, bv.W, bv.P, b.st.p, b.ctl.p, b.part.p,
-                                          b.cnt.p + 2);
+    kb_init<FT><<<b.grid, kBlock, 0, s>>>(b.ldw, ns, b.b.p, b.mu64.p, bv.pairs, basis ? nullptr : bv.W,
+                                          basis ? nullptr : bv.P, b.st.p, b.ctl.p, b.part.p, b.cnt.p + 2);
     SDA_LAUNCHED();
     SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
-    const int nbi = o.iter_batch > 0 ? o.iter_batch : 32;
     int launched = 0;
     while (!b.h_ctl->done && launched <= limit) {
-        SDA_TRY((batch_run<VT, FT>(op, ns, nbi, o.use_graph != 0, o.profile != 0, s)));
+        if (basis) SDA_TRY(ensure_basis<FT>(b, (int64_t)launched + nbi, b.btab_cap, s));
+        SDA_TRY((batch_run<VT, FT>(op, ns, basis, nbi, o.use_graph != 0, o.profile != 0, s)));
         launched += nbi;
         SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
@@ -1107,16 +1310,50 @@ static int solve_lanes(sda_operator *op, const BatchLane *lanes, int nl, const d
                        int ns, const sda_solve_opts &o, double alpha, double omega, cudaStream_t s, LaneOutcome &out) {
     const int64_t d = op->d;
     const bool fixed = o.fixed_iters > 0;
-    SDA_TRY((run_lanes<VT, FT>(op, lanes, nl, deltas, ns, fixed, fixed ? o.fixed_iters : o.max_iter, o, alpha,
-                               omega, s)));
+    const int limit = fixed ? o.fixed_iters : o.max_iter;
+    bool basis = o.shift_form == SDA_SHIFTS_BASIS;
+    if (o.shift_form == SDA_SHIFTS_AUTO && ns > 1) {
+        // the stored basis when its worst case fits 40 % of the free memory (chunks held count as free)
+        size_t fr = 0, tot = 0;
+        SDA_CUDA(cudaMemGetInfo(&fr, &tot));
+        size_t held = 0;
+        if (op->bws)
+            for (const auto &c : op->bws->bchunks) held += c->bytes();
+        const double need = (double)(limit + 1) * (double)((op->d + 7) / 8 * 8) * kTB * sizeof(FT);
+        basis = need <= 0.4 * (double)(fr + held);
+    }
+    SDA_TRY((run_lanes<VT, FT>(op, lanes, nl, deltas, ns, fixed, limit, o, alpha, omega, s, basis)));
     BatchWs &b = *op->bws;
+    if (op->stats.shift_form == 0) op->stats.shift_form = basis ? SDA_SHIFTS_BASIS : SDA_SHIFTS_RECURRENCE;
     out.fin.assign(b.h_st, b.h_st + kTB);   // later runs reuse h_st
     const std::vector<SolveState> &fin = out.fin;
+    int kmax = 0;
     for (int i = 0; i < nl; ++i)
-        for (int sh = 0; sh < ns; ++sh) op->stats.shift_iterations += fin[(size_t)i].sh[sh].iters;
+        for (int sh = 0; sh < ns; ++sh) {
+            op->stats.shift_iterations += fin[(size_t)i].sh[sh].iters;
+            kmax = std::max(kmax, fin[(size_t)i].sh[sh].iters);
+        }
     const size_t wall_n = (size_t)nl * ns * d;
     if (b.wall.n < wall_n) SDA_TRY(b.wall.alloc(wall_n));
-    {
+    if (basis) {
+        // every shift's solution from the stored basis: its tridiagonal solve, then W = V Y
+        if (op->stats.basis_slots == 0) op->stats.basis_slots = kmax;
+        if (kmax > 0) {
+            const size_t nc = (size_t)nl * ns * kmax;
+            if (b.coefs.n < 2 * nc) SDA_TRY(b.coefs.alloc(2 * nc));
+            kb_lz_solve<<<(nl * ns + 127) / 128, 128, 0, s>>>(nl, ns, kmax, b.lz.p, b.st.p, b.coefs.p,
+                                                              b.coefs.p + nc);
+            SDA_LAUNCHED();
+            constexpr int EPT = std::is_same<FT, float>::value ? 4 : 2;
+            const int64_t ntiles = (d + (kBlock / kTB) * EPT - 1) / ((kBlock / kTB) * EPT);
+            const int gg = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)op->sm_count * 8));
+            kb_basis_gemm<FT, EPT><<<gg, kBlock, 0, s>>>(d, b.ldw, nl, ns, kmax, (FT *const *)b.btab.p, kBasisChunk,
+                                                         b.coefs.p, b.wall.p);
+            SDA_LAUNCHED();
+        } else {
+            SDA_CUDA(cudaMemsetAsync(b.wall.p, 0, wall_n * sizeof(double), s));
+        }
+    } else {
         BView<FT> bv = bview<FT>(b);
         for (int i = 0; i < nl; ++i) {
             kb_take_w<FT><<<grid_elems_b((int64_t)ns * d, op->sm_count), kBlock, 0, s>>>(

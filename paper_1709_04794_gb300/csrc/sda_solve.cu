@@ -754,6 +754,7 @@ extern "C" SDA_API void sda_default_opts(sda_solve_opts *o) {
     o->refine_rounds = 0;
     o->batch_targets = 0;
     o->refine_tol = NAN;
+    o->shift_form = SDA_SHIFTS_AUTO;
 }
 
 // the (alpha, omega) of a call: overrides from the options, else the operator's
@@ -783,6 +784,10 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
     if (o.fixed_iters <= 0 && (!(o.tol >= 0.0) || o.max_iter < 0))
         return fail(SDA_ERR_INVALID_ARG, "tol must be >= 0 and max_iter >= 0");
     if (o.refine_rounds < 0) return fail(SDA_ERR_INVALID_ARG, "refine_rounds must be >= 0");
+    if (o.shift_form < SDA_SHIFTS_AUTO || o.shift_form > SDA_SHIFTS_BASIS)
+        return fail(SDA_ERR_INVALID_ARG, "bad shift_form");
+    if (o.shift_form == SDA_SHIFTS_BASIS && !o.batch_targets)
+        return fail(SDA_ERR_UNSUPPORTED, "the stored-basis shift form is provided on the batched path");
     const int t0 = o.target_begin;
     const int tc = o.target_count < 0 ? op->n_targets - t0 : o.target_count;
     if (t0 < 0 || tc < 0 || t0 + tc > op->n_targets) return fail(SDA_ERR_INVALID_ARG, "target range out of bounds");
@@ -867,6 +872,7 @@ extern "C" SDA_API int sda_solve_shifts(sda_operator *op, const double *shifts, 
         }
         if (rc < 0) return rc;
     }
+    if (op->stats.shift_form == 0) op->stats.shift_form = SDA_SHIFTS_RECURRENCE;
     SDA_CUDA(cudaEventRecord(w.call_ev[1], s));
     SDA_CUDA(cudaEventSynchronize(w.call_ev[1]));
     float call_ms = 0.f;

@@ -35,6 +35,7 @@ SDA_ERR_UNSUPPORTED = -12
 SDA_F64, SDA_F32, SDA_F16, SDA_F8E4M3, SDA_PATTERN = 0, 1, 2, 3, 4
 DTYPES = {"f64": SDA_F64, "f32": SDA_F32, "f16": SDA_F16, "f8e4m3": SDA_F8E4M3, "pattern": SDA_PATTERN}
 SDA_RHS_CANONICAL, SDA_RHS_FROM_R, SDA_RHS_GIVEN = 0, 1, 2
+SDA_SHIFTS_AUTO, SDA_SHIFTS_RECURRENCE, SDA_SHIFTS_BASIS = 0, 1, 2
 
 
 class sda_csr(ctypes.Structure):
@@ -54,7 +55,8 @@ class sda_solve_opts(ctypes.Structure):
                 ("check_residual", ctypes.c_int32), ("out_on_device", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("iter_batch", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("alpha", ctypes.c_double), ("scatter_weight", ctypes.c_double),
-                ("refine_rounds", ctypes.c_int32), ("batch_targets", ctypes.c_int32), ("refine_tol", ctypes.c_double)]
+                ("refine_rounds", ctypes.c_int32), ("batch_targets", ctypes.c_int32), ("refine_tol", ctypes.c_double),
+                ("shift_form", ctypes.c_int32)]
 
 
 class sda_shift_report(ctypes.Structure):
@@ -64,7 +66,8 @@ class sda_shift_report(ctypes.Structure):
 
 class sda_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("shift_iterations", ctypes.c_int64),
-                ("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5), ("solve_ms", ctypes.c_double)]
+                ("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5), ("solve_ms", ctypes.c_double),
+                ("shift_form", ctypes.c_int32), ("basis_slots", ctypes.c_int32)]
 
 
 class sda_operator_info(ctypes.Structure):
@@ -366,7 +369,8 @@ def sda_get_solve_stats(op) -> dict:
     st = sda_solve_stats()
     _check(load().sda_get_solve_stats(op, ctypes.byref(st)), "sda_get_solve_stats")
     return dict(iterations=st.iterations, shift_iterations=st.shift_iterations,
-                launches=list(st.launches), ms=list(st.ms), solve_ms=st.solve_ms)
+                launches=list(st.launches), ms=list(st.ms), solve_ms=st.solve_ms, shift_form=st.shift_form,
+                basis_slots=st.basis_slots)
 
 
 def sda_kernel_launch_count() -> int:

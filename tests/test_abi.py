@@ -42,6 +42,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sda.sda_csr) == 56
     assert ctypes.sizeof(sda.sda_shift_report) == 24
     assert sda.sda_solve_opts.rhs.offset == 24
-    assert ctypes.sizeof(sda.sda_solve_opts) == 96
-    assert ctypes.sizeof(sda.sda_solve_stats) == 104
+    assert ctypes.sizeof(sda.sda_solve_opts) == 104
+    assert sda.sda_solve_opts.shift_form.offset == 96
+    assert ctypes.sizeof(sda.sda_solve_stats) == 112
     assert ctypes.sizeof(sda.sda_operator_info) == 88

@@ -41,7 +41,7 @@ def multi():
     return p
 
 
-def _solve(prob, compute, batch, tol=1e-10, fixed=0, check=1, begin=0, count=-1):
+def _solve(prob, compute, batch, tol=1e-10, fixed=0, check=1, begin=0, count=-1, form=0, stats=False):
     op = sda.Operator(prob, compute=compute)
     nt = op.info["n_targets"] - begin if count < 0 else count
     ns, d = len(prob.shifts), prob.d
@@ -49,14 +49,19 @@ def _solve(prob, compute, batch, tol=1e-10, fixed=0, check=1, begin=0, count=-1)
     o = sda.sda_default_opts()
     o.tol, o.fixed_iters, o.max_iter = tol, fixed, 20000
     o.batch_targets, o.check_residual = batch, check
-    o.target_begin, o.target_count = begin, count
+    o.target_begin, o.target_count, o.shift_form = begin, count, form
     code, rep = sda.sda_solve_shifts(op.handle, prob.shifts, o, w_out=w, n_report=nt)
+    if stats:
+        return code, rep, w.cpu().numpy(), sda.sda_get_solve_stats(op.handle)
     return code, rep, w.cpu().numpy()
 
 
-def test_batched_fixed_iterations_match_oracle(multi):
+@pytest.mark.parametrize("form", [sda.SDA_SHIFTS_RECURRENCE, sda.SDA_SHIFTS_BASIS])
+def test_batched_fixed_iterations_match_oracle(multi, form):
+    """Both shift forms against the oracle's Algorithm 3 iterates: the recurrences,
+    and the stored basis (W = V y with (T + delta I) y = ||b|| e_1, Sec. 3.2.1)."""
     k = 8
-    code, rep, w = _solve(multi, "f64", 1, fixed=k, check=0)
+    code, rep, w = _solve(multi, "f64", 1, fixed=k, check=0, form=form)
     for t in range(T):
         o = oracle.from_problem(multi, target=t)
         ref = o.shifted_cg(o.rhs_canonical(), multi.shifts, fixed_iters=k)
@@ -85,6 +90,54 @@ def test_batched_mixed_true_residuals(multi):
     for t in range(T):
         for r in rep[t]:
             assert r["status"] == sda.SDA_OK and r["true_residual"] < 20 * tol, (t, r)
+
+
+@pytest.mark.parametrize("compute,tol,bar", [("f64", 1e-8, 1e-8), ("f16", 1e-5, 2e-5)])
+def test_basis_form_equals_recurrences_converged(multi, compute, tol, bar):
+    """Converged with per-shift stops: the stored-basis form gives every shift
+    the Galerkin solution at that shift's own stop iteration, the same iterate as
+    the recurrences (FP64: equal to rounding; FP32 vectors: within the FP32 noise
+    of the two evaluation orders, at a tolerance above the FP32 floor); their FP64
+    true residuals agree."""
+    code_r, rep_r, wr, st_r = _solve(multi, compute, 1, tol=tol, form=sda.SDA_SHIFTS_RECURRENCE, stats=True)
+    code_b, rep_b, wb, st_b = _solve(multi, compute, 1, tol=tol, form=sda.SDA_SHIFTS_BASIS, stats=True)
+    assert st_r["shift_form"] == sda.SDA_SHIFTS_RECURRENCE and st_b["shift_form"] == sda.SDA_SHIFTS_BASIS
+    assert st_b["basis_slots"] == max(r["iters"] for tr in rep_b[:16] for r in tr)
+    for t in range(T):
+        for s in range(len(multi.shifts)):
+            assert rep_b[t][s]["iters"] == rep_r[t][s]["iters"], (t, s)
+            assert _rel(wb[t, s], wr[t, s]) < bar, (t, s, _rel(wb[t, s], wr[t, s]))
+            rb, rr = rep_b[t][s]["true_residual"], rep_r[t][s]["true_residual"]
+            assert abs(rb - rr) <= 0.05 * rr + 1e-9, (t, s, rb, rr)
+
+
+def test_basis_form_is_the_automatic_choice(multi):
+    code, rep, w, st = _solve(multi, "f16", 1, tol=1e-6, stats=True)
+    assert st["shift_form"] == sda.SDA_SHIFTS_BASIS and st["basis_slots"] > 0
+
+
+def test_basis_form_with_refinement(multi):
+    op = sda.Operator(multi, compute="f16")
+    ns, d = len(multi.shifts), multi.d
+    w = torch.empty((T, ns, d), dtype=torch.float64, device="cuda")
+    o = sda.sda_default_opts()
+    o.tol, o.max_iter, o.batch_targets, o.shift_form = 1e-4, 20000, 1, sda.SDA_SHIFTS_BASIS
+    o.refine_rounds, o.refine_tol = 12, 1e-11
+    code, rep = sda.sda_solve_shifts(op.handle, multi.shifts, o, w_out=w, n_report=T)
+    assert code == sda.SDA_OK
+    for t in range(T):
+        for r in rep[t]:
+            assert r["status"] == sda.SDA_OK and r["true_residual"] <= 1e-11, (t, r)
+
+
+def test_basis_form_refused_on_single_target_path(multi):
+    op = sda.Operator(multi, compute="f16")
+    o = sda.sda_default_opts()
+    o.shift_form = sda.SDA_SHIFTS_BASIS
+    w = torch.empty((T, len(multi.shifts), multi.d), dtype=torch.float64, device="cuda")
+    with pytest.raises(sda.SDAError) as e:
+        sda.sda_solve_shifts(op.handle, multi.shifts, o, w_out=w, n_report=T)
+    assert e.value.code == sda.SDA_ERR_UNSUPPORTED
 
 
 def test_batched_target_range(multi):
