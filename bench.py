@@ -346,23 +346,39 @@ def max_over_ranks(t_local: float, dist=None) -> float:
     return float(t.item())
 
 
-def batched_bytes(prob, compute: str, batch_iters: int, shift_iters: int, ntargets: int):
+def batched_bytes(prob, compute: str, batch_iters: int, shift_iters: int, ntargets: int, basis: bool = False,
+                  ns: int = 0, info: dict | None = None):
     """Algorithmic bytes per launch of the batched kernels (16 targets per
     batch), averaged over the solve: X and S streamed once per launch for the
-    batch, the 16 targets' vectors read / written once each, and the active
-    (target, shift) pairs' P and W read and written."""
+    batch, the 16 targets' vectors read / written once each; the recurrence
+    form reads and writes the active (target, shift) pairs' P and W, the
+    stored-basis form writes r_k to its basis instead and, once per run, reads
+    the basis (one pass per 16 shifts) and writes every shift's FP64 solution
+    ("basis_once")."""
     n, d = prob.n, prob.d
     nnz = int(prob.x_ptr[-1])
     snz = int(prob.s_ptr[-1])
     vsz = {"f64": 8, "f32": 4, "f16": 2, "f8e4m3": 1, "pattern": 0}[compute]
     fsz = 8 if compute == "f64" else 4
     tb = 16
-    return {
+    out = {
         "phase1": nnz * (4 + vsz) + (n + 1) * 8 + d * tb * 2 * fsz + n * tb * fsz,
         "phase2": snz * (4 + fsz) + (n + 1) * 8 + n * tb * (2 * fsz + 1) + n * fsz,
         "phase3a": nnz * (4 + vsz) + (d + 1) * 8 + n * tb * fsz + d * tb * 8,
-        "phase3b": d * tb * (8 + 4 * fsz + fsz) + (shift_iters / max(batch_iters, 1)) * d * 4 * fsz,
     }
+    if info and info.get("head_cols"):
+        # head columns from the range layout (16-bit rows + values, V's slices once, the ranges'
+        # parts written and read), the other columns from the CSC
+        H, R = info["head_cols"], info["head_ranges"]
+        nnz_h = int(prob.x_ptr[-1]) - info["tail_nnz"]
+        out["phase3a"] = (nnz_h * (2 + max(vsz, 1)) + R * (H + 1) * 8 + n * tb * fsz + 2 * R * H * tb * 8
+                          + info["tail_nnz"] * (4 + vsz) + (d - H + 1) * 8 + d * tb * 8)
+    if basis:
+        out["phase3b"] = d * tb * (8 + 4 * fsz + 2 * fsz)
+        out["basis_once"] = batch_iters * d * tb * fsz * ((ns + 15) // 16) + ns * d * tb * 8
+    else:
+        out["phase3b"] = d * tb * (8 + 4 * fsz + fsz) + (shift_iters / max(batch_iters, 1)) * d * 4 * fsz
+    return out
 
 
 def run_batched(args, rank, world, local):
@@ -704,12 +720,21 @@ def run_large(args, rank, world, local):
                                       inputs["s_col"], inputs["s_val"], inputs["labels"][t0:t0 + cnt],
                                       prob.alpha, float("nan"), comp, stream)
 
-    def step(k, inputs=dev, hold=held):
+    def mark(marks):
+        if marks is not None:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            marks.append(e)
+
+    def step(k, inputs=dev, hold=held, marks=None):
         t0, cnt = chunks[k % len(chunks)]
+        mark(marks)
         h = build(inputs, t0, cnt)
+        mark(marks)
         try:
             code, rep = sda.sda_solve_shifts(h, prob.shifts, solve_opts(cnt), w_out=w[:cnt], n_report=cnt,
                                              stream=stream)
+            mark(marks)
             r0, r1 = int(off_all[t0]), int(off_all[t0 + cnt])
             rows = hold["rows"][r0:r1].to("cuda", non_blocking=True)
             y = hold["y"][r0:r1].to("cuda", non_blocking=True)
@@ -729,14 +754,17 @@ def run_large(args, rank, world, local):
                 yi = y[off[i]:off[i + 1]]
                 g[off[i]:off[i + 1]] = -yi * torch.sigmoid(-yi * scs[i][best[i]]) / yi.numel()
                 wb[i] = w[i, best[i]]
+            mark(marks)
             oa = sda.sda_default_opts()
             oa.fixed_iters = args.fixed_iters
             code_a, da, db, rep_a = sda.sda_adjoint_grad_batched(h, list(range(cnt)), float("nan"),
                                                                  [float(prob.shifts[b]) for b in best], wb, g,
                                                                  rows, off, oa, stream=stream)
+            mark(marks)
             lh = losses.cpu().numpy()
         finally:
             sda.sda_destroy_operator(h)
+        mark(marks)
         return {"code": code, "rep": rep, "best": best, "da": da, "db": db, "losses": lh, "t0": t0, "cnt": cnt}
 
     for k in range(args.warmup):
@@ -765,13 +793,19 @@ def run_large(args, rank, world, local):
         solved = int(tot.item())
     value = solved / t
 
-    # ---- untimed: per-kernel shares, mixed vs FP64, parity, baselines ----------------
+    # ---- untimed: where a step's time goes, per-kernel shares, mixed vs FP64, parity, baselines
+    marks = []
+    step(0, marks=marks)
+    torch.cuda.synchronize()
+    parts = ("build", "sweep_and_residual_check", "held_out_ratings", "adjoint", "release")
+    breakdown = {parts[i]: marks[i].elapsed_time(marks[i + 1]) for i in range(len(parts))}
     nb = min(16, chunks[0][1])
     t0c = chunks[0][0]
     peak, peak_kind = load_peaks()
 
     def timed_solve(comp, profile=0, keep_w=False):
         h = build(dev, t0c, nb, comp)
+        info = sda.sda_get_operator_info(h)
         try:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -793,27 +827,33 @@ def run_large(args, rank, world, local):
             st_iter = sda.sda_get_solve_stats(h)
         finally:
             sda.sda_destroy_operator(h)
-        return e0.elapsed_time(e1), e2.elapsed_time(e3), rep, st, st_iter, w_first
+        return e0.elapsed_time(e1), e2.elapsed_time(e3), rep, st, st_iter, w_first, info
 
-    ms_mix, ms_mix_iter, rep_mix, _, st_mix, w_mix = timed_solve(compute, keep_w=True)
+    ms_mix, ms_mix_iter, rep_mix, _, st_mix, w_mix, info = timed_solve(compute, keep_w=True)
     pst = timed_solve(compute, profile=1)[4]
-    ms_64, ms_64_iter, rep_64, _, st_64, w_64 = timed_solve("f64", keep_w=True)
+    ms_64, ms_64_iter, rep_64, _, st_64, w_64, _ = timed_solve("f64", keep_w=True)
+    counts = np.sort(np.bincount(prob.x_col, minlength=d))[::-1]
+    info["tail_nnz"] = int(counts[info["head_cols"]:].sum())
     bi = max(1, st_mix["iterations"])
-    per = batched_bytes(prob, compute, bi, st_mix["shift_iterations"], nb)
+    basis = st_mix["shift_form"] == sda.SDA_SHIFTS_BASIS
+    per = batched_bytes(prob, compute, bi, st_mix["shift_iterations"], nb, basis=basis, ns=ns, info=info)
+    once = per.pop("basis_once", 0)
     prof = {k: pst["ms"][i + 1] for i, k in enumerate(("phase1", "phase2", "phase3a", "phase3b"))}
     prof_tot = sum(prof.values())
-    it_ms = ms_mix_iter / bi          # one batch iteration of the graph-replayed sweep
+    it_ms = ms_mix_iter / bi          # one batch iteration of the graph-replayed sweep (W = V Y amortised)
     durs = {k: it_ms * prof[k] / prof_tot for k in prof}
     dominant = max(durs, key=durs.get)
     names = {"phase1": "kb_phase1 (rows of X, 16 targets)", "phase2": "kb_phase2 (rows of S, 16 targets)",
              "phase3a": "kb_phase3a (columns of X, 16 targets)", "phase3b": "kb_phase3b (vector and shift stream)"}
     achieved = per[dominant] / (durs[dominant] * 1e-3) / 1e9
-    whole = sum(per.values()) / (it_ms * 1e-3) / 1e9
+    whole = (sum(per.values()) + once / bi) / (it_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": recorded_traffic(dominant, LARGE_PROFILE), "kernel": names[dominant],
                 "peak_kind": peak_kind, "bytes_per_launch": per[dominant], "ms_per_launch": durs[dominant],
-                "whole_iteration": {"GB/s": whole, "frac": whole / peak, "bytes": sum(per.values()),
-                                    "ms": it_ms},
+                "whole_iteration": {"GB/s": whole, "frac": whole / peak, "bytes": sum(per.values()) + once / bi,
+                                    "ms": it_ms,
+                                    "shift_form": "stored basis (W = V Y once per run, its bytes amortised)"
+                                    if basis else "recurrences"},
                 "durations": "graph-replayed sweep of one batch of 16 targets / iterations, apportioned by the "
                              "event-timed shares of the four kernels",
                 "all_kernels": {names[k]: {"ms_per_launch": durs[k], "GB/s": per[k] / (durs[k] * 1e-3) / 1e9,
@@ -821,6 +861,30 @@ def run_large(args, rank, world, local):
     tres_mix = np.array([[r["true_residual"] for r in tr] for tr in rep_mix])
     tres_64 = np.array([[r["true_residual"] for r in tr] for tr in rep_64])
     above = tres_64 >= 1e-5
+    # equal residual: the mixed path's iterations (and time, with the residual check) to bring every
+    # (target, shift) to the FP64 path's residual after the fixed iterations, where that is above the
+    # FP32 floor
+    eq = None
+    h = build(dev, t0c, nb)
+    try:
+        for k_it in (args.fixed_iters, int(args.fixed_iters * 1.25), int(args.fixed_iters * 1.5),
+                     args.fixed_iters * 2, int(args.fixed_iters * 2.5), args.fixed_iters * 3,
+                     args.fixed_iters * 4):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, rep_k = sda.sda_solve_shifts(h, prob.shifts, solve_opts(nb, fixed=k_it), w_out=w[:nb], n_report=nb,
+                                            stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tk = np.array([[r["true_residual"] for r in tr] for tr in rep_k])
+            ok = bool(np.all(tk[above] <= tres_64[above]))
+            eq = {"mixed_iterations": k_it, "reached": ok, "mixed_ms": e0.elapsed_time(e1), "fp64_ms": ms_64,
+                  "speedup_at_equal_residual": ms_64 / e0.elapsed_time(e1)}
+            if ok:
+                break
+    finally:
+        sda.sda_destroy_operator(h)
     mixed_vs_fp64 = {"targets": nb, "fixed_iters": args.fixed_iters,
                      "mixed_solves_per_s": nb / (ms_mix * 1e-3), "fp64_solves_per_s": nb / (ms_64 * 1e-3),
                      "speedup": ms_64 / ms_mix, "mixed_iteration_ms": ms_mix_iter / bi,
@@ -828,6 +892,7 @@ def run_large(args, rank, world, local):
                      "max_rel_residual_difference": float(np.max((np.abs(tres_mix - tres_64) / tres_64)[above]))
                      if above.any() else None,
                      "pairs_compared": "%d of %d" % (int(above.sum()), above.size),
+                     "equal_residual": eq,
                      "note": "same Krylov iteration count; FP64 true residual of every (target, shift) of both, "
                              "compared where the FP64 path's is >= 1e-5 (above that, the FP32 vectors reach the same "
                              "residual; below it they stop near 1e-6 unless refined)"}
@@ -932,7 +997,8 @@ def run_large(args, rank, world, local):
                                    "(%d iterations) with the FP64 true residual of every (target, shift); centred "
                                    "held-out ratings of every shift; least-loss shift per target; batched adjoint "
                                    "gradient there (%d iterations)" % (args.fixed_iters, args.fixed_iters),
-                           "l2": "no flush: one batch iteration streams > 8 GB (> 126 MB L2)"},
+                           "step_breakdown_ms": breakdown,
+                           "l2": "no flush: one batch iteration streams > 2 GB (> 126 MB L2)"},
                 "mixed_vs_fp64": mixed_vs_fp64, "parity": parity,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches)}

@@ -414,6 +414,10 @@ typedef struct {
     int32_t row_head;       /* leading features the row pass gathers from shared memory */
     int64_t col_entries;    /* entries of the column-pass layout, padding to quads included */
     int64_t row_entries;    /* entries of the row-pass layout, padding to quads included */
+    /* head of the batched column pass (the most frequent columns in ranges of rows): */
+    int32_t head_cols;      /* head columns (0: none; every column takes the tile pass) */
+    int32_t head_ranges;    /* ranges of rows */
+    int64_t head_entries;   /* entries of its layout, padding to quads included */
 } sda_operator_info;
 
 SDA_API int sda_get_operator_info(const sda_operator *op, sda_operator_info *info);

@@ -95,6 +95,7 @@ struct BatchWs {
     DevBuf<BatchCtl> ctl;
     DevBuf<char> coef;
     DevBuf<double> part, slots;
+    DevBuf<double> hparts;     // head column pass: parts [range][head column][kTB] (one 8-byte part each)
     DevBuf<double> sig, r2;    // per-lane shifts and squared residual norms of the FP64 block utilities
     DevBuf<double> wall;       // FP64 solutions of a batch's (target, shift) pairs [target][shift][D]
     DevBuf<double> rbuf;       // residual vectors of up to kTB pairs [lane][D] (refinement right-hand sides)
@@ -112,6 +113,8 @@ struct BatchWs {
     BatchCtl *h_ctl = nullptr;
     int grid = 0;                          // every kernel but the sparse passes of the batched solve
     int grid1 = 0, grid2 = 0, grid3a = 0;  // their own grids (occupancy of each)
+    int grid_head = 0;                     // grid of the head column pass
+    bool head_ready = false;               // its shared-memory attribute set
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0, graph_ns = 0, graph_basis = -1;
     cudaStream_t cap_stream = nullptr;
@@ -615,6 +618,112 @@ __global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase3a(con
     }
 }
 
+// phase 3a, head columns: for every range r of kHeadRows rows the block stages
+// the range's slice of V ([rows][kTB], the vector type) in shared memory; lane
+// groups then take the head columns in turn and sum x_ij V[i] over the column's
+// entries in the range (quads of 16-bit local rows, gathers from shared memory;
+// each quad summed plainly, the quads compensated) into hp[r][h][kTB]
+template <class VT, class FT>
+__global__ void __launch_bounds__(kBlock) kb_head3a(int64_t n, int nr, int H, int nsplit,
+                                                   const int64_t *__restrict__ cp, const uint16_t *__restrict__ idx,
+                                                   const VT *__restrict__ val, const FT *__restrict__ v,
+                                                   typename CompSum<FT>::Part *__restrict__ hp, const BatchCtl *ctl) {
+    using L = BLanes<FT>;
+    using V = typename L::V;
+    using CS = CompSum<FT>;
+    constexpr int TPL = L::TPL, LG = L::LG, GPB = kBlock / LG;
+    extern __shared__ __align__(16) unsigned char kh_dyn[];
+    FT *vs = reinterpret_cast<FT *>(kh_dyn);
+    if (ctl->done) return;
+    const int lg = threadIdx.x % LG, g = threadIdx.x / LG, t0 = lg * TPL;
+    const uint2 *__restrict__ idxq = reinterpret_cast<const uint2 *>(idx);
+    // work items (range r, slice c of the head columns), nsplit slices per range
+    const int hs = (H + nsplit - 1) / nsplit;
+    for (int item = blockIdx.x; item < nr * nsplit; item += gridDim.x) {
+        const int r = item / nsplit, c0 = (item - r * nsplit) * hs, c1 = min(H, c0 + hs);
+        const int64_t row0 = (int64_t)r * kHeadRows;
+        const int rows = (int)min((int64_t)kHeadRows, n - row0);
+        __syncthreads();
+        {
+            const V *__restrict__ src = reinterpret_cast<const V *>(v + row0 * kTB);
+            V *dst = reinterpret_cast<V *>(vs);
+            const int nvec = rows * (kTB / TPL);
+            for (int q = threadIdx.x; q < nvec; q += kBlock) dst[q] = src[q];
+        }
+        __syncthreads();
+        const int64_t *__restrict__ c = cp + (int64_t)r * (H + 1);
+        for (int h = c0 + g; h < c1; h += GPB) {
+            const int64_t q0 = c[h] >> 2, q1 = c[h + 1] >> 2;
+            CS acc[TPL];
+            // four quads per step: their indices and values load first (independent
+            // global loads in flight), then the sixteen gathers from shared memory
+            for (int64_t q = q0; q < q1; q += 4) {
+                uint2 ii[4];
+                FT xv[4][4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    if (q + w < q1) {
+                        ii[w] = idxq[q + w];
+                        Quad<VT, FT>::load(val, q + w, xv[w]);
+                    } else {
+                        ii[w] = make_uint2(0u, 0u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) xv[w][k] = (FT)0;
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int li[4] = {(int)(ii[w].x & 0xffffu), (int)(ii[w].x >> 16), (int)(ii[w].y & 0xffffu),
+                                       (int)(ii[w].y >> 16)};
+                    FT sum[TPL];
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) sum[u] = (FT)0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        FT x[TPL];
+                        *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(vs + li[k] * kTB + t0);
+#pragma unroll
+                        for (int u = 0; u < TPL; ++u) sum[u] += xv[w][k] * x[u];
+                    }
+#pragma unroll
+                    for (int u = 0; u < TPL; ++u) acc[u].add(sum[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TPL; ++u) hp[((int64_t)r * H + h) * kTB + t0 + u] = acc[u].part();
+        }
+    }
+}
+
+// out[e] = sum over the ranges r of hp[r][e] for e < m (fixed order: warp w adds
+// the ranges r = w mod 8, then the eight warps' sums in order)
+template <class FT>
+__global__ void __launch_bounds__(kBlock) kb_head_reduce(int nr, int64_t m, const typename CompSum<FT>::Part *__restrict__ hp,
+                                                        typename CompSum<FT>::Part *__restrict__ out,
+                                                        const BatchCtl *ctl) {
+    using CS = CompSum<FT>;
+    using Part = typename CS::Part;
+    constexpr int NW = kBlock / 32;
+    __shared__ Part red[kBlock];
+    if (ctl->done) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t e0 = (int64_t)blockIdx.x * 32; e0 < m; e0 += (int64_t)gridDim.x * 32) {
+        const int64_t e = e0 + lane;
+        CS acc;
+        if (e < m)
+            for (int r = w; r < nr; r += NW) CS::add_part(acc, hp[(int64_t)r * m + e]);
+        __syncthreads();
+        red[threadIdx.x] = acc.part();
+        __syncthreads();
+        if (w == 0 && e < m) {
+            CS tot;
+#pragma unroll
+            for (int q = 0; q < NW; ++q) CS::add_part(tot, red[q * 32 + lane]);
+            out[e] = tot.part();
+        }
+    }
+}
+
 // phase 3b: base recurrence per (feature, target), shift-state stream over the
 // shifts some target still updates, per-target dots; the last block forms
 // alpha_{k+1}, the shift coefficients and the stop tests of every target
@@ -1026,8 +1135,9 @@ static int ensure_batch_ws(sda_operator *op, BatchWs *&slot, int ns) {
     SDA_TRY(b.part.alloc((size_t)kMaxBlocksPerSm * op->sm_count * kTB * 5));   // phase 2: 2 per target, 3b: 3
     SDA_TRY(b.cnt.alloc(4));
     SDA_CUDA(cudaMemset(b.cnt.p, 0, b.cnt.bytes()));
-    SDA_TRY(b.slots.alloc((size_t)std::max(op->col.nslots, 1) * kTB * 2));
-    SDA_TRY(b.lcount.alloc((size_t)std::max(op->col.nsplits, 1)));
+    SDA_TRY(b.slots.alloc((size_t)std::max(std::max(op->col.nslots, op->col_tail.nslots), 1) * kTB * 2));
+    SDA_TRY(b.lcount.alloc((size_t)std::max(std::max(op->col.nsplits, op->col_tail.nsplits), 1)));
+    SDA_TRY(b.hparts.alloc((size_t)std::max<int64_t>(1, (int64_t)op->hb.nranges * op->hb.nseg * kTB)));
     SDA_CUDA(cudaMemset(b.lcount.p, 0, b.lcount.bytes()));
     SDA_TRY(b.sig.alloc(kTB));
     SDA_TRY(b.r2.alloc(kTB));
@@ -1091,6 +1201,47 @@ static int ensure_basis(BatchWs &b, int64_t nslots, int cap, cudaStream_t s) {
     return SDA_OK;
 }
 
+// S = X^T V for the kTB vectors of a workspace: the head columns from range
+// slices of V in shared memory (kb_head3a, then the fixed-order sum over the
+// ranges), the other columns with the tile pass over the CSC (kb_phase3a)
+template <class VT, class FT>
+static int colpass_b(sda_operator *op, BatchWs &b, const FT *v, typename CompSum<FT>::Part *out, int grid_tail,
+                     cudaStream_t s) {
+    using Part = typename CompSum<FT>::Part;
+    const int64_t H = op->hb.nseg;
+    if (H > 0) {
+        const size_t smem = (size_t)kHeadRows * kTB * sizeof(FT);
+        if (!b.head_ready) {
+            SDA_CUDA(cudaFuncSetAttribute((const void *)kb_head3a<BVT<VT>, FT>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int nb = 0;
+            SDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)kb_head3a<BVT<VT>, FT>, kBlock,
+                                                                   smem));
+            b.grid_head = std::max(1, std::min(nb, kMaxBlocksPerSm)) * op->sm_count;
+            b.head_ready = true;
+        }
+        // slices of the head columns per range: at least four items per resident block
+        const int nr = op->hb.nranges;
+        const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(H / 64, (4LL * b.grid_head + nr - 1) / nr));
+        kb_head3a<BVT<VT>, FT><<<std::min(b.grid_head, nr * nsplit), kBlock, smem, s>>>(
+            op->n, nr, (int)H, nsplit, op->hb.cp.p, op->hb.idx.p, (const BVT<VT> *)op->hb.val.p, v,
+            (Part *)b.hparts.p, b.ctl.p);
+        SDA_LAUNCHED();
+        const int64_t m = H * kTB;
+        kb_head_reduce<FT><<<(int)std::min<int64_t>((m + 31) / 32, (int64_t)op->sm_count * 8), kBlock, 0, s>>>(
+            op->hb.nranges, m, (const Part *)b.hparts.p, out, b.ctl.p);
+        SDA_LAUNCHED();
+    }
+    kb_phase3a<VT, FT><<<grid_tail, kBlock, 0, s>>>(op->col_tail.tiles.p, op->col_tail.ntiles, op->x_cp.p + H,
+                                                    op->x_row.p, (const VT *)op->x_val_c.p, v, out + H * kTB,
+                                                    (Part *)b.slots.p, b.lcount.p, op->col_tail.splits.p, b.ctl.p);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
+// launches of colpass_b
+static int colpass_launches(const sda_operator *op) { return op->hb.nseg > 0 ? 3 : 1; }
+
 // `ev` (profile mode): a start and an end event around each of the four kernels
 template <class VT, class FT>
 static int batch_iteration(sda_operator *op, int ns, bool basis, cudaStream_t s, cudaEvent_t *ev = nullptr) {
@@ -1116,10 +1267,7 @@ static int batch_iteration(sda_operator *op, int ns, bool basis, cudaStream_t s,
     using Part = typename CompSum<FT>::Part;
     if (ev) SDA_CUDA(cudaEventRecord(ev[3], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[4], s));
-    kb_phase3a<VT, FT><<<b.grid3a, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
-                                                (const VT *)op->x_val_c.p, bv.v, bv.s, (Part *)b.slots.p,
-                                                b.lcount.p, op->col.splits.p, b.ctl.p);
-    SDA_LAUNCHED();
+    SDA_TRY((colpass_b<VT, FT>(op, b, bv.v, bv.s, b.grid3a, s)));
 
     if (ev) SDA_CUDA(cudaEventRecord(ev[5], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[6], s));
@@ -1183,7 +1331,7 @@ static int batch_run(sda_operator *op, int ns, bool basis, int nb_iters, bool us
         b.graph_basis = (int)basis;
     }
     SDA_CUDA(cudaGraphLaunch(b.graph, s));
-    note_launch(5 * (int64_t)nb_iters);
+    note_launch((4 + colpass_launches(op)) * (int64_t)nb_iters);
     for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
     return SDA_OK;
 }
@@ -1258,8 +1406,9 @@ static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const dou
     BView<FT> bv = bview<FT>(b);
     {
         BatchCtl hc{};
-        hc.bb = BatchBounds{op->n, op->d, b.ldw, b.n8, op->nnz, op->s_nnz, op->col.ntiles, op->col.nslots,
-                            op->col.nsplits, (int64_t)b.part.n, (int64_t)(op->xr_col.n / 4)};
+        hc.bb = BatchBounds{op->n, op->d, b.ldw, b.n8, op->nnz, op->s_nnz, op->col.ntiles,
+                            std::max(op->col.nslots, op->col_tail.nslots), std::max(op->col.nsplits, op->col_tail.nsplits),
+                            (int64_t)b.part.n, (int64_t)(op->xr_col.n / 4)};
         *b.h_ctl = hc;
         SDA_CUDA(cudaMemcpyAsync(b.ctl.p, b.h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
     }
@@ -1580,6 +1729,34 @@ __global__ void __launch_bounds__(kBlock) kb_resid(int64_t d, int nv, const doub
     }
 }
 
+// per lane l < nv: out[2 l] = sum_i ul[i][l] v[i][l], out[2 l + 1] = the same sum of
+// ul[i][l] uw[i][l] over the lane's labelled rows (y_l(i) != 0)
+__global__ void __launch_bounds__(kBlock) kb_cross_dots(int64_t n, int nv, const double *__restrict__ ul,
+                                                       const double *__restrict__ v, const double *__restrict__ uw,
+                                                       const int8_t *__restrict__ ylab, BatchCtl *ctl, double *out,
+                                                       double *partials, unsigned *counter) {
+    using Part = CompSum<double>::Part;
+    __shared__ Part red[kBlock * 2];
+    CompSum<double> acc[2];
+    const int64_t m = n * kTB;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m; e += (int64_t)gridDim.x * kBlock) {
+        acc[0].add(ul[e] * v[e]);
+        if (ylab[e] != 0) acc[1].add(ul[e] * uw[e]);
+    }
+    Part mine[2];
+    block_tparts<2, double>(acc, mine, red);
+    if (!arrive_last_t<2>(mine, reinterpret_cast<Part *>(partials), counter, ctl)) return;
+    double tot[2];
+    grid_tparts<2, double>(reinterpret_cast<const Part *>(partials), gridDim.x, tot, red);
+    if (threadIdx.x < kTB) {
+        if (threadIdx.x < nv) {
+            out[2 * threadIdx.x] = tot[0];
+            out[2 * threadIdx.x + 1] = tot[1];
+        }
+        if (threadIdx.x == 0) *counter = 0u;
+    }
+}
+
 template <class VT>
 static int block64_setup(sda_operator *op, BatchWs *&B, double alpha, double omega, cudaStream_t s) {
     SDA_TRY(ensure_batch_ws<double>(op, op->bws64, 1));
@@ -1600,8 +1777,9 @@ static int block64_setup(sda_operator *op, BatchWs *&B, double alpha, double ome
     }
     SDA_CUDA(cudaMemcpyAsync(B->st.p, h, sizeof(SolveState) * kTB, cudaMemcpyHostToDevice, s));
     BatchCtl hc{};
-    hc.bb = BatchBounds{op->n, op->d, B->ldw, B->n8, op->nnz, op->s_nnz, op->col.ntiles, op->col.nslots,
-                        op->col.nsplits, (int64_t)B->part.n, (int64_t)(op->xr_col.n / 4)};
+    hc.bb = BatchBounds{op->n, op->d, B->ldw, B->n8, op->nnz, op->s_nnz, op->col.ntiles,
+                        std::max(op->col.nslots, op->col_tail.nslots), std::max(op->col.nsplits, op->col_tail.nsplits),
+                        (int64_t)B->part.n, (int64_t)(op->xr_col.n / 4)};
     *B->h_ctl = hc;
     SDA_CUDA(cudaMemcpyAsync(B->ctl.p, B->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
     return SDA_OK;
@@ -1649,10 +1827,7 @@ static int resid_lanes_t(sda_operator *op, const ResidLane *lanes, int nl, doubl
                                                 B->ylab.p, bv.v, B->st.p, B->ctl.p, bv.coef, 0, B->part.p,
                                                 B->cnt.p + 1);
     SDA_LAUNCHED();
-    kb_phase3a<VT, double><<<B->grid, kBlock, 0, s>>>(op->col.tiles.p, op->col.ntiles, op->x_cp.p, op->x_row.p,
-                                                     (const VT *)op->x_val_c.p, bv.v, bv.s, B->slots.p, B->lcount.p,
-                                                     op->col.splits.p, B->ctl.p);
-    SDA_LAUNCHED();
+    SDA_TRY((colpass_b<VT, double>(op, *B, bv.v, bv.s, B->grid, s)));
     kb_resid<<<B->grid, kBlock, 0, s>>>(d, nl, B->b.p, B->mu64.p, bv.s, bv.p, B->sig.p, B->st.p, B->ctl.p, B->r2.p,
                                        rvec, B->part.p, B->cnt.p + 2);
     SDA_LAUNCHED();
@@ -1690,6 +1865,64 @@ static int project_block_t(sda_operator *op, const double *Wn, int64_t nvec, dou
         SDA_LAUNCHED();
     }
     return block64_check(B, "block projection", s);
+}
+
+// The adjoint contractions of nl <= kTB targets at once (FP64, permuted order):
+// per lane, out[2 l] = (X~ lam_l)^T L (X~ w_l) and out[2 l + 1] =
+// (X~ lam_l)^T P_l (X~ w_l) (host), X~ = X - 1 mu_t^T of the lane's target.
+template <class VT>
+static int adjoint_cross_t(sda_operator *op, const int *targets, int nl, const double *W, const double *Lam,
+                           double *out_host, cudaStream_t s) {
+    BatchWs *B = nullptr;
+    SDA_TRY(block64_setup<VT>(op, B, 1.0, 0.0, s));   // omega 0, alpha 1: phase 2 gives v = L u
+    BView<double> bv = bview<double>(*B);
+    const int64_t d = op->d, n = op->n;
+    const int ge = grid_elems_b(std::max(B->ldw, B->n8), op->sm_count);
+    DevBuf<double> uw, dots;
+    SDA_TRY(uw.alloc((size_t)(B->n8 * kTB)));
+    SDA_TRY(dots.alloc(2 * kTB));
+    SDA_CUDA(cudaMemsetAsync(B->mu64.p, 0, B->mu64.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(B->ylab.p, 0, B->ylab.bytes(), s));
+    for (int pass = 0; pass < 2; ++pass) {
+        const double *src = pass == 0 ? W : Lam;
+        SDA_CUDA(cudaMemsetAsync(bv.p, 0, (size_t)B->ldw * kTB * sizeof(double), s));
+        for (int l = 0; l < nl; ++l) {
+            kb_put<double><<<ge, kBlock, 0, s>>>(d, src + (int64_t)l * d, bv.p, l);
+            if (pass == 0) {
+                kb_put<double><<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)targets[l] * d, B->mu64.p, l);
+                kb_put<int8_t><<<ge, kBlock, 0, s>>>(n, op->labels.p + (int64_t)targets[l] * n, B->ylab.p, l);
+            }
+            SDA_LAUNCHED();
+        }
+        kb_dot_mu<<<B->grid, kBlock, 0, s>>>(d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
+        SDA_LAUNCHED();
+        kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(n, B->ldw, op->xr_rp.p, op->xr_col.p,
+                                                             (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, B->st.p,
+                                                             B->ctl.p);
+        SDA_LAUNCHED();
+        if (pass == 0) {
+            // u_w = X~ w kept; v = L u_w
+            SDA_CUDA(cudaMemcpyAsync(uw.p, bv.ut, (size_t)B->n8 * kTB * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            kb_phase2<double><<<B->grid, kBlock, 0, s>>>(n, op->s_rp.p, op->s_col.p, op->s_val64.p, bv.ut,
+                                                        op->deg64.p, B->ylab.p, bv.v, B->st.p, B->ctl.p, bv.coef, 0,
+                                                        B->part.p, B->cnt.p + 1);
+            SDA_LAUNCHED();
+        }
+    }
+    kb_cross_dots<<<B->grid, kBlock, 0, s>>>(n, nl, bv.ut, bv.v, uw.p, B->ylab.p, B->ctl.p, dots.p, B->part.p,
+                                            B->cnt.p + 3);
+    SDA_LAUNCHED();
+    SDA_CUDA(cudaMemcpyAsync(out_host, dots.p, (size_t)nl * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    return block64_check(B, "adjoint contractions", s);
+}
+
+int adjoint_cross(sda_operator *op, const int *targets, int nl, const double *W, const double *Lam, double *out_host,
+                  cudaStream_t s) {
+    if (nl < 1 || nl > kTB) return fail(SDA_ERR_INVALID_ARG, "adjoint_cross: %d lanes", nl);
+    return with_vt_b(op->compute, [&](auto tag) -> int {
+        using VT = std::remove_pointer_t<decltype(tag)>;
+        return adjoint_cross_t<VT>(op, targets, nl, W, Lam, out_host, s);
+    });
 }
 
 int resid_lanes(sda_operator *op, const ResidLane *lanes, int nl, double *r2_host, double *rvec, double alpha,

@@ -418,6 +418,51 @@ static int build_range_blocks(sda_operator *op, RangeBlocks &out, const int64_t 
     return SDA_OK;
 }
 
+// The head columns of X (the most frequent features: the fewest covering
+// kHeadCover of the nonzeros, at most kHeadMax, each with at least one entry
+// per range on average) split into ranges of kHeadRows rows with 16-bit local
+// row indices, for the batched column pass: a block keeps one range's slice of
+// the 16 targets' vectors in shared memory and gathers from it.
+static int build_head_blocks(sda_operator *op, const char *val, size_t vsz, int64_t n, int64_t d, int sms,
+                             cudaStream_t s) {
+    RangeBlocks &out = op->hb;
+    const int64_t nr = (n + kHeadRows - 1) / kHeadRows;
+    std::vector<int64_t> cp((size_t)std::min<int64_t>(d, kHeadMax) + 1);
+    SDA_CUDA(cudaMemcpyAsync(cp.data(), op->x_cp.p, cp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int64_t nnz_all = 0;
+    SDA_CUDA(cudaMemcpyAsync(&nnz_all, op->x_cp.p + d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    int64_t h = 0;
+    while (h < (int64_t)cp.size() - 1 && cp[(size_t)h] < kHeadCover * (double)nnz_all &&
+           cp[(size_t)h + 1] - cp[(size_t)h] >= nr)
+        ++h;
+    out.nranges = (int)nr;
+    out.rb = kHeadRows;
+    out.nseg = h;
+    if (h == 0) return SDA_OK;
+    const int64_t nnz_h = cp[(size_t)h];
+    SDA_TRY(out.cp.alloc((size_t)(nr * (h + 1))));
+    SDA_CUDA(cudaMemsetAsync(out.cp.p, 0, out.cp.bytes(), s));
+    DevBuf<int64_t> lb;
+    SDA_TRY(lb.alloc((size_t)((nr + 1) * h)));
+    k_range_bounds<<<grid1(h, sms), kBlock, 0, s>>>(h, (int)nr, kHeadRows, op->x_cp.p, op->x_row.p, lb.p, out.cp.p);
+    SDA_LAUNCHED();
+    SDA_TRY(scan_exclusive_i64(out.cp.p, nr * (h + 1), s));
+    int64_t nq = 0;
+    SDA_CUDA(cudaMemcpyAsync(&nq, out.cp.p + nr * (h + 1) - 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaStreamSynchronize(s));
+    nq = std::max<int64_t>(nq, 4);
+    const size_t bvsz = vsz ? vsz : 1;
+    SDA_TRY(out.idx.alloc((size_t)nq));
+    SDA_TRY(out.val.alloc((size_t)nq * bvsz));
+    SDA_CUDA(cudaMemsetAsync(out.idx.p, 0, out.idx.bytes(), s));
+    SDA_CUDA(cudaMemsetAsync(out.val.p, 0, out.val.bytes(), s));
+    k_range_scatter<<<grid1(nnz_h, sms), kBlock, 0, s>>>(nnz_h, h, kHeadRows, op->x_cp.p, op->x_row.p, val,
+                                                         (int)vsz, lb.p, out.cp.p, out.idx.p, out.val.p);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
 // Rows of X padded to whole quads for the row pass of the iteration, and the
 // number of leading (most frequent) features it keeps in shared memory.
 static int build_row_quads(sda_operator *op, bool fp64, size_t vsz, int sms, cudaStream_t s) {
@@ -574,6 +619,7 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
     SDA_TRY(build_range_blocks(op, op->xb, op->x_cp.p, op->x_row.p, op->x_val_c.p, vsz, d, n, nnz,
                                fp64 ? sizeof(double) : sizeof(float), sms, s));
     SDA_TRY(build_row_quads(op, fp64, vsz, sms, s));
+    SDA_TRY(build_head_blocks(op, op->x_val_c.p, vsz, n, d, sms, s));
 
     // ---- S -------------------------------------------------------------------
     DevBuf<int32_t> s_col_in;
@@ -644,6 +690,11 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
         SDA_CUDA(cudaMemcpyAsync(hp.data(), op->x_cp.p, ((size_t)d + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
         SDA_TRY(build_seg_schedule(hp, op->col));
+        // the columns after the head, for the batched column pass (segments from 0 = column hb.nseg)
+        {
+            std::vector<int64_t> tail(hp.begin() + op->hb.nseg, hp.end());
+            SDA_TRY(build_seg_schedule(tail, op->col_tail));
+        }
         hp.resize((size_t)n + 1);
         SDA_CUDA(cudaMemcpyAsync(hp.data(), op->x_rp.p, ((size_t)n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));
@@ -767,7 +818,8 @@ static int build_entry(const sda_csr *X, const sda_csr *S, const sda_labels *y, 
     }
     op->bytes = (int64_t)(op->new_of_old.bytes() + op->old_of_new.bytes() + op->x_rp.bytes() + op->x_cp.bytes() +
                           op->x_col.bytes() + op->x_row.bytes() + op->x_val_r.bytes() + op->x_val_c.bytes() +
-                          op->xb.bytes() + op->xr_rp.bytes() + op->xr_col.bytes() + op->xr_val.bytes() +
+                          op->xb.bytes() + op->hb.cp.bytes() + op->hb.idx.bytes() + op->hb.val.bytes() +
+                          op->xr_rp.bytes() + op->xr_col.bytes() + op->xr_val.bytes() +
                           op->s_rp.bytes() + op->s_col.bytes() + op->s_val64.bytes() + op->s_val32.bytes() +
                           op->deg64.bytes() + op->deg32.bytes() + op->labels.bytes() + op->mu.bytes() +
                           op->mu32.bytes() + op->dvec.bytes() + op->col.tiles.bytes() + op->col.splits.bytes() +

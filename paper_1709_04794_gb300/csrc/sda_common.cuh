@@ -350,6 +350,12 @@ constexpr int kWarpBigSeg = 256;
 constexpr int kWarpChunkNnz = 1024;
 constexpr int kWarpChunkNnz64 = 512;
 constexpr int warp_chunk_nnz(int64_t fsz) { return fsz == 8 ? kWarpChunkNnz64 : kWarpChunkNnz; }
+// Head of the batched column pass: the fewest most frequent columns covering
+// kHeadCover of the nonzeros (at most kHeadMax), in ranges of kHeadRows rows
+// (a range's slice of 16 FP64 vectors fills 192 KB of shared memory).
+constexpr double kHeadCover = 0.7;
+constexpr int64_t kHeadMax = 1024;
+constexpr int64_t kHeadRows = 1536;
 // Shared memory the blocked column pass keeps for itself besides the slice.
 constexpr int kColBlkReserve = 2048;
 // Per-warp scratch of the blocked column pass after the slice: the quad sums of

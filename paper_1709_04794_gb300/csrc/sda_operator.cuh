@@ -124,6 +124,11 @@ struct sda_operator {
     // X in column-major order split into ranges of rows, for the column pass of the
     // iteration (a block keeps its range's slice of v in shared memory)
     sda::RangeBlocks xb;
+    // its head columns (hb.nseg of them, possibly 0) split into ranges of kHeadRows
+    // rows, for the batched column pass (hb.cp is [R][nseg + 1], no schedule)
+    sda::RangeBlocks hb;
+    // the other columns' tiles for the batched column pass (segments counted from hb.nseg)
+    sda::ColSchedule col_tail;
     // X in row-major order with rows padded by zero entries (column 0) to whole
     // quads, for the row pass of the iteration; features [0, xr_head) (the most
     // frequent) are gathered from shared memory there
@@ -202,6 +207,10 @@ struct ResidLane {
 // (host array, written before return); rvec (device, optional): the residual vectors [nl][D]
 int resid_lanes(sda_operator *op, const ResidLane *lanes, int nl, double *r2_host, double *rvec, double alpha,
                 double omega, cudaStream_t s);
+// FP64 block of nl <= 16 targets (sda_batch.cu): per lane l, out_host[2 l] = (X~ lam_l)^T L (X~ w_l),
+// out_host[2 l + 1] = (X~ lam_l)^T P_l (X~ w_l), X~ = X - 1 mu_t^T (W, Lam: [nl][D] device, permuted order)
+int adjoint_cross(sda_operator *op, const int *targets, int nl, const double *W, const double *Lam, double *out_host,
+                  cudaStream_t s);
 // FP64 blocks of 16 vectors (sda_batch.cu): out_r2[v] = ||b - (B + shifts[v] I) W64[v]||^2 of
 // target t for v < ns (all device, permuted order); scores[v] = X Wn[v] (- <mu_t, Wn[v]> if centred)
 int resid_block(sda_operator *op, int t, const double *shifts, int ns, const double *b_perm, const double *W64,

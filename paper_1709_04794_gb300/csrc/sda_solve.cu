@@ -1028,10 +1028,10 @@ extern "C" SDA_API int sda_adjoint_grad_batched(sda_operator *op, int32_t n_targ
     SDA_TRY(wp.alloc((size_t)(T * d)));
     SDA_TRY(cb.alloc((size_t)(T * d)));
     SDA_TRY(lam.alloc((size_t)(T * d)));
-    SDA_TRY(nv.alloc((size_t)(5 * n)));
+    SDA_TRY(nv.alloc((size_t)n));
     SDA_TRY(sc.alloc((size_t)(8 * T)));
     SDA_TRY(err.alloc(1));
-    double *G = nv.p, *uw = G + n, *ul = uw + n, *v = ul + n, *v2 = v + n;
+    double *G = nv.p;   // g scattered to the held-out rows
     SDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     SDA_TRY(permute_to_new(op, W, wp.p, T, s));
     // right-hand sides (X_h - 1 mu^T)^T g = X^T G - mu (1^T G), G = g scattered to the held-out rows
@@ -1060,15 +1060,20 @@ extern "C" SDA_API int sda_adjoint_grad_batched(sda_operator *op, int32_t n_targ
     memset(&op->stats, 0, sizeof(op->stats));
     SDA_TRY(solve_shift_lanes(op, targets, bl.data(), betas, n_targets, o, al, om, lam.p, report, s, &worst));
     if (worst < 0) return worst;
-    for (int64_t i = 0; i < T; ++i)
-        SDA_TRY(adjoint_dots(op, targets[i], wp.p + i * d, lam.p + i * d, uw, ul, v, v2, sc.p + 8 * i, s));
+    // d/d beta = -lambda^T w (per target); the two cross terms of d/d alpha,
+    // (X~ lambda)^T L (X~ w) and (X~ lambda)^T P_l (X~ w), 16 targets per FP64 block pass
+    for (int64_t i = 0; i < T; ++i) SDA_TRY(dot_f64(op, d, lam.p + i * d, wp.p + i * d, sc.p + 8 * i + 1, s));
+    std::vector<double> hs((size_t)(8 * T)), cross((size_t)(2 * T));
+    for (int64_t i0 = 0; i0 < T; i0 += 16) {
+        const int nl = (int)std::min<int64_t>(16, T - i0);
+        SDA_TRY(adjoint_cross(op, targets + i0, nl, wp.p + i0 * d, lam.p + i0 * d, cross.data() + 2 * i0, s));
+    }
     if (lambda_out) SDA_TRY(permute_to_old(op, lam.p, lambda_out, T, s));
-    std::vector<double> hs((size_t)(8 * T));
     SDA_CUDA(cudaMemcpyAsync(hs.data(), sc.p, hs.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
     for (int64_t i = 0; i < T; ++i) {
         d_beta[i] = -hs[(size_t)(8 * i + 1)];
-        d_alpha[i] = -(hs[(size_t)(8 * i + 4)] - (op->omega_follows_alpha ? hs[(size_t)(8 * i + 5)] : 0.0));
+        d_alpha[i] = -(cross[(size_t)(2 * i)] - (op->omega_follows_alpha ? cross[(size_t)(2 * i + 1)] : 0.0));
     }
     return worst;
 }
@@ -1166,6 +1171,9 @@ extern "C" SDA_API int sda_get_operator_info(const sda_operator *op, sda_operato
     info->row_head = op->xr_head;
     info->col_entries = (int64_t)op->xb.idx.n;
     info->row_entries = (int64_t)op->xr_col.n;
+    info->head_cols = (int32_t)op->hb.nseg;
+    info->head_ranges = op->hb.nseg > 0 ? op->hb.nranges : 0;
+    info->head_entries = op->hb.nseg > 0 ? (int64_t)op->hb.idx.n : 0;
     return SDA_OK;
 }
 

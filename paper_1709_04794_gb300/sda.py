@@ -75,7 +75,8 @@ class sda_operator_info(ctypes.Structure):
                 ("graph_nnz", ctypes.c_int64), ("n_targets", ctypes.c_int32), ("compute", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("col_ranges", ctypes.c_int32), ("row_head", ctypes.c_int32), ("col_entries", ctypes.c_int64),
-                ("row_entries", ctypes.c_int64)]
+                ("row_entries", ctypes.c_int64), ("head_cols", ctypes.c_int32), ("head_ranges", ctypes.c_int32),
+                ("head_entries", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p
