@@ -1239,6 +1239,15 @@ static int colpass_b(sda_operator *op, BatchWs &b, const FT *v, typename CompSum
     return SDA_OK;
 }
 
+// U = X P - 1 c^T for the kTB vectors of a workspace (row pass over the quad-padded rows)
+template <class VT, class FT>
+static int rowpass_b(sda_operator *op, BatchWs &b, const FT *p, FT *ut, int grid, cudaStream_t s) {
+    kb_phase1<BVT<VT>, FT><<<grid, kBlock, 0, s>>>(op->n, b.ldw, op->xr_rp.p, op->xr_col.p,
+                                                  (const BVT<VT> *)op->xr_val.p, p, ut, b.st.p, b.ctl.p);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
 // launches of colpass_b
 static int colpass_launches(const sda_operator *op) { return op->hb.nseg > 0 ? 3 : 1; }
 
@@ -1254,9 +1263,7 @@ static int batch_iteration(sda_operator *op, int ns, bool basis, cudaStream_t s,
     if (ev) SDA_CUDA(cudaEventRecord(ev[0], s));
     kb_formp<FT><<<b.grid, kBlock, 0, s>>>(op->d, b.ldw, bv.pairs, bv.p, b.st.p, b.ctl.p);
     SDA_LAUNCHED();
-    kb_phase1<BVT<VT>, FT><<<b.grid1, kBlock, 0, s>>>(op->n, b.ldw, op->xr_rp.p, op->xr_col.p,
-                                                     (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, b.st.p, b.ctl.p);
-    SDA_LAUNCHED();
+    SDA_TRY((rowpass_b<VT, FT>(op, b, bv.p, bv.ut, b.grid1, s)));
 
     if (ev) SDA_CUDA(cudaEventRecord(ev[1], s));
     if (ev) SDA_CUDA(cudaEventRecord(ev[2], s));
@@ -1819,10 +1826,7 @@ static int resid_lanes_t(sda_operator *op, const ResidLane *lanes, int nl, doubl
     SDA_CUDA(cudaMemcpyAsync(B->sig.p, sig, sizeof(sig), cudaMemcpyHostToDevice, s));
     kb_dot_mu<<<B->grid, kBlock, 0, s>>>(d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
     SDA_LAUNCHED();
-    kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(n, B->ldw, op->xr_rp.p, op->xr_col.p,
-                                                         (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, B->st.p,
-                                                         B->ctl.p);
-    SDA_LAUNCHED();
+    SDA_TRY((rowpass_b<VT, double>(op, *B, bv.p, bv.ut, B->grid, s)));
     kb_phase2<double><<<B->grid, kBlock, 0, s>>>(n, op->s_rp.p, op->s_col.p, op->s_val64.p, bv.ut, op->deg64.p,
                                                 B->ylab.p, bv.v, B->st.p, B->ctl.p, bv.coef, 0, B->part.p,
                                                 B->cnt.p + 1);
@@ -1857,10 +1861,7 @@ static int project_block_t(sda_operator *op, const double *Wn, int64_t nvec, dou
             kb_dot_mu<<<B->grid, kBlock, 0, s>>>(op->d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
             SDA_LAUNCHED();
         }
-        kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(op->n, B->ldw, op->xr_rp.p, op->xr_col.p,
-                                                             (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, B->st.p,
-                                                             B->ctl.p);
-        SDA_LAUNCHED();
+        SDA_TRY((rowpass_b<VT, double>(op, *B, bv.p, bv.ut, B->grid, s)));
         kb_unpack<<<ge, kBlock, 0, s>>>(op->n, nv, bv.ut, scores + c0 * op->n);
         SDA_LAUNCHED();
     }
@@ -1896,10 +1897,7 @@ static int adjoint_cross_t(sda_operator *op, const int *targets, int nl, const d
         }
         kb_dot_mu<<<B->grid, kBlock, 0, s>>>(d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
         SDA_LAUNCHED();
-        kb_phase1<BVT<VT>, double><<<B->grid, kBlock, 0, s>>>(n, B->ldw, op->xr_rp.p, op->xr_col.p,
-                                                             (const BVT<VT> *)op->xr_val.p, bv.p, bv.ut, B->st.p,
-                                                             B->ctl.p);
-        SDA_LAUNCHED();
+        SDA_TRY((rowpass_b<VT, double>(op, *B, bv.p, bv.ut, B->grid, s)));
         if (pass == 0) {
             // u_w = X~ w kept; v = L u_w
             SDA_CUDA(cudaMemcpyAsync(uw.p, bv.ut, (size_t)B->n8 * kTB * sizeof(double), cudaMemcpyDeviceToDevice, s));
