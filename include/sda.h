@@ -418,6 +418,11 @@ typedef struct {
     int32_t head_cols;      /* head columns (0: none; every column takes the tile pass) */
     int32_t head_ranges;    /* ranges of rows */
     int64_t head_entries;   /* entries of its layout, padding to quads included */
+    /* schedule of the batched sparse passes picked by the autotuner on the operator's
+       first batched run (0 until then): resident blocks per SM of the row pass, the
+       Laplacian pass and the tail column pass, and work items per resident block of
+       the head column pass */
+    int32_t tuned[4];
 } sda_operator_info;
 
 SDA_API int sda_get_operator_info(const sda_operator *op, sda_operator_info *info);

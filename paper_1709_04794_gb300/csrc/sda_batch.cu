@@ -11,7 +11,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "sda_kernels.cuh"
@@ -46,7 +49,7 @@ struct BatchCtl {
     int32_t k;        // iterations completed
     int32_t done;     // every target of the batch has stopped
     int32_t status;
-    int32_t pad;
+    int32_t bodies;           // loop bodies run by the device-driven loop (bounds it on its own)
     unsigned long long err;   // first index check that failed: (site << 40) | index; 0 if none
     BatchBounds bb;
 };
@@ -115,11 +118,13 @@ struct BatchWs {
     int grid1 = 0, grid2 = 0, grid3a = 0;  // their own grids (occupancy of each)
     int grid_head = 0;                     // grid of the head column pass
     bool head_ready = false;               // its shared-memory attribute set
-    cudaGraphExec_t graph = nullptr;
-    int graph_iters = 0, graph_ns = 0, graph_basis = -1;
+    int head_items = 4;                    // head pass: work items per resident block (tuned)
+    bool tuned = false;                    // the schedule of the sparse passes has been picked
+    cudaGraphExec_t loop = nullptr;        // device-driven loop: a WHILE node over loop_iters iterations
+    int loop_iters = 0, loop_ns = 0, loop_basis = -1, loop_limit = -1;
     cudaStream_t cap_stream = nullptr;
     ~BatchWs() {
-        if (graph) cudaGraphExecDestroy(graph);
+        if (loop) cudaGraphExecDestroy(loop);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (h_st) cudaFreeHost(h_st);
         if (h_ctl) cudaFreeHost(h_ctl);
@@ -1037,6 +1042,16 @@ __global__ void __launch_bounds__(kBlock) kb_basis_gemm(int64_t d, int64_t ldw, 
     }
 }
 
+// Condition of the device-driven iteration loop: keep iterating while some lane
+// of the batch is still running (and the iteration cap is not passed)
+__global__ void kb_loop_cond(BatchCtl *ctl, int limit, int nb_iters, cudaGraphConditionalHandle h) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int bodies = ++ctl->bodies;   // at most (limit + nb_iters) / nb_iters bodies, whatever the state
+        const bool more = !ctl->done && ctl->k <= limit && (int64_t)bodies * nb_iters <= (int64_t)limit + nb_iters;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
 // column t of a [len][kTB] block from / to a plain vector
 template <class T>
 __global__ void kb_put(int64_t len, const T *__restrict__ src, T *__restrict__ dst, int t) {
@@ -1107,6 +1122,13 @@ static BView<FT> bview(BatchWs &b) {
     return BView<FT>{pairs, s, ut, v, W, P, (BatchCoef<FT> *)b.coef.p, v + b.n8 * kTB};
 }
 
+// the captured graphs hold buffer addresses: dropped whenever a buffer is reallocated
+static void drop_graphs(BatchWs &b) {
+    if (b.loop) cudaGraphExecDestroy(b.loop);
+    b.loop = nullptr;
+    b.loop_iters = 0;
+}
+
 template <class FT>
 static int ensure_batch_ws(sda_operator *op, BatchWs *&slot, int ns) {
     if (!slot) slot = new BatchWs();
@@ -1115,9 +1137,7 @@ static int ensure_batch_ws(sda_operator *op, BatchWs *&slot, int ns) {
     const int fp64 = std::is_same<FT, double>::value;
     const int64_t ldw = (op->d + 7) / 8 * 8, n8 = (op->n + 7) / 8 * 8;
     if (b.fp64 == fp64 && b.d == op->d && b.n == op->n && b.ns >= ns) return SDA_OK;
-    if (b.graph) cudaGraphExecDestroy(b.graph);
-    b.graph = nullptr;
-    b.graph_iters = 0;
+    drop_graphs(b);
     SDA_TRY(b.vec.alloc((size_t)(2 * ldw * kTB * sizeof(typename RPair<FT>::T) + ldw * kTB * sizeof(Part) +
                                  2 * n8 * kTB * sizeof(FT) + ldw * kTB * sizeof(FT))));
     b.shift.release();
@@ -1150,6 +1170,7 @@ static int ensure_batch_ws(sda_operator *op, BatchWs *&slot, int ns) {
     b.n8 = n8;
     b.ns = ns;
     b.grid = 0;
+    b.tuned = false;
     return SDA_OK;
 }
 
@@ -1163,8 +1184,7 @@ static int ensure_batch(sda_operator *op, int ns) {
 template <class FT>
 static int ensure_shift(BatchWs &b, int ns) {
     if (b.shift_ns >= ns) return SDA_OK;
-    if (b.graph) cudaGraphExecDestroy(b.graph);
-    b.graph = nullptr;
+    drop_graphs(b);
     SDA_TRY(b.shift.alloc((size_t)(2 * (int64_t)ns * b.ldw * kTB * sizeof(FT))));
     b.shift_ns = ns;
     return SDA_OK;
@@ -1177,8 +1197,7 @@ constexpr int kBasisChunk = 64;   // basis slots per allocated chunk
 template <class FT>
 static int ensure_basis(BatchWs &b, int64_t nslots, int cap, cudaStream_t s) {
     if (b.btab_cap < cap) {
-        if (b.graph) cudaGraphExecDestroy(b.graph);
-        b.graph = nullptr;
+        drop_graphs(b);
         SDA_TRY(b.btab.alloc((size_t)cap * sizeof(FT *)));
         b.btab_cap = cap;
         std::vector<FT *> h(b.bchunks.size());
@@ -1222,7 +1241,8 @@ static int colpass_b(sda_operator *op, BatchWs &b, const FT *v, typename CompSum
         }
         // slices of the head columns per range: at least four items per resident block
         const int nr = op->hb.nranges;
-        const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(H / 64, (4LL * b.grid_head + nr - 1) / nr));
+        const int nsplit =
+            (int)std::max<int64_t>(1, std::min<int64_t>(H / 64, ((int64_t)b.head_items * b.grid_head + nr - 1) / nr));
         kb_head3a<BVT<VT>, FT><<<std::min(b.grid_head, nr * nsplit), kBlock, smem, s>>>(
             op->n, nr, (int)H, nsplit, op->hb.cp.p, op->hb.idx.p, (const BVT<VT> *)op->hb.val.p, v,
             (Part *)b.hparts.p, b.ctl.p);
@@ -1287,10 +1307,10 @@ static int batch_iteration(sda_operator *op, int ns, bool basis, cudaStream_t s,
     return SDA_OK;
 }
 
+// nb_iters iterations launched from the host: with events around every phase
+// (profile mode), else plain launches (graphs off)
 template <class VT, class FT>
-static int batch_run(sda_operator *op, int ns, bool basis, int nb_iters, bool use_graph, bool profile,
-                     cudaStream_t s) {
-    BatchWs &b = *op->bws;
+static int batch_run(sda_operator *op, int ns, bool basis, int nb_iters, bool profile, cudaStream_t s) {
     if (profile) {
         std::vector<cudaEvent_t> &pe = op->ws.prof_ev;
         while (pe.size() < (size_t)nb_iters * 8) {
@@ -1309,37 +1329,186 @@ static int batch_run(sda_operator *op, int ns, bool basis, int nb_iters, bool us
         for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
         return SDA_OK;
     }
-    if (!use_graph) {
-        for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, basis, s)));
-        for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
-        return SDA_OK;
-    }
-    if (!b.graph || b.graph_iters != nb_iters || b.graph_ns != ns || b.graph_basis != (int)basis) {
-        if (b.graph) cudaGraphExecDestroy(b.graph);
-        b.graph = nullptr;
+    for (int i = 0; i < nb_iters; ++i) SDA_TRY((batch_iteration<VT, FT>(op, ns, basis, s)));
+    for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
+    return SDA_OK;
+}
+
+// The whole run of a batch as one graph launch: a WHILE node whose body is
+// nb_iters iterations and kb_loop_cond, so the device decides when the batch
+// is done (no host round trip between iterations).  Returns the bodies run.
+template <class VT, class FT>
+static int batch_loop(sda_operator *op, int ns, bool basis, int nb_iters, int limit, cudaStream_t s) {
+    BatchWs &b = *op->bws;
+    if (!b.loop || b.loop_iters != nb_iters || b.loop_ns != ns || b.loop_basis != (int)basis || b.loop_limit != limit) {
+        if (b.loop) cudaGraphExecDestroy(b.loop);
+        b.loop = nullptr;
         if (!b.cap_stream) SDA_CUDA(cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking));
-        SDA_CUDA(cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t g = nullptr;
+        SDA_CUDA(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {};
+        cudaGraphNode_t node = nullptr;
+        if (e == cudaSuccess) {
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        }
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(e, "conditional graph node", __FILE__, __LINE__);
+        }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(b.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__);
+        }
         set_capturing(true);
         int rc = SDA_OK;
         for (int i = 0; i < nb_iters && rc == SDA_OK; ++i) rc = batch_iteration<VT, FT>(op, ns, basis, b.cap_stream);
-        set_capturing(false);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(b.cap_stream, &g);
-        if (rc != SDA_OK) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
+        if (rc == SDA_OK) {
+            kb_loop_cond<<<1, 32, 0, b.cap_stream>>>(b.ctl.p, limit, nb_iters, h);
+            if (cudaGetLastError() != cudaSuccess) rc = fail(SDA_ERR_CUDA, "loop condition launch failed");
         }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
-        e = cudaGraphInstantiate(&b.graph, g, 0);
+        set_capturing(false);
+        cudaGraph_t cap = nullptr;
+        e = cudaStreamEndCapture(b.cap_stream, &cap);
+        if (rc == SDA_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b.loop, g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
-        b.graph_iters = nb_iters;
-        b.graph_ns = ns;
-        b.graph_basis = (int)basis;
+        if (rc != SDA_OK) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "device-driven loop graph", __FILE__, __LINE__);
+        b.loop_iters = nb_iters;
+        b.loop_ns = ns;
+        b.loop_basis = (int)basis;
+        b.loop_limit = limit;
     }
-    SDA_CUDA(cudaGraphLaunch(b.graph, s));
-    note_launch((4 + colpass_launches(op)) * (int64_t)nb_iters);
-    for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += nb_iters;
+    SDA_CUDA(cudaGraphLaunch(b.loop, s));
+    return SDA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner of the batched sparse passes
+// ---------------------------------------------------------------------------
+// Schedules picked per problem shape (rows, features, nonzeros of X and S, value
+// type, vector type, SMs) and kept for the process: resident blocks per SM of the
+// row pass, the Laplacian pass and the tail column pass, and work items per
+// resident block of the head column pass.
+using TuneKey = std::tuple<int64_t, int64_t, int64_t, int64_t, int, int, int>;
+struct TuneVal {
+    int bpsm1, bpsm2, bpsm3, head_items;
+};
+static std::map<TuneKey, TuneVal> g_tuned;
+static std::mutex g_tune_mu;
+
+// device time of `launch` (ms, the best of three runs of two launches)
+template <class F>
+static int time_launch(cudaStream_t s, F &&launch, float *best) {
+    cudaEvent_t e0, e1;
+    SDA_CUDA(cudaEventCreate(&e0));
+    SDA_CUDA(cudaEventCreate(&e1));
+    *best = 1e30f;
+    int rc = SDA_OK;
+    for (int rep = 0; rep < 3 && rc == SDA_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        rc = launch();
+        if (rc == SDA_OK) rc = launch();
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(SDA_ERR_CUDA, "autotuner timing failed");
+        float ms = 0.f;
+        if (rc == SDA_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) *best = std::min(*best, ms / 2);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+// Picks the schedule of op's batched sparse passes for vector type FT (once per
+// shape in the process) and sets b's grids.  The passes run on the workspace's
+// current vectors; the solve state they touch is reset by the run that follows.
+template <class VT, class FT>
+static int autotune(sda_operator *op, BatchWs &b, cudaStream_t s) {
+    const TuneKey key{op->n, op->d, op->nnz, op->s_nnz, (int)op->compute, (int)sizeof(FT), op->sm_count};
+    TuneVal tv{0, 0, 0, 0};
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            tv = it->second;
+            have = true;
+        }
+    }
+    const int sms = op->sm_count;
+    if (!have) {
+        BatchCtl hc{};
+        hc.bb = BatchBounds{op->n, op->d, b.ldw, b.n8, op->nnz, op->s_nnz, op->col.ntiles,
+                            std::max(op->col.nslots, op->col_tail.nslots), std::max(op->col.nsplits, op->col_tail.nsplits),
+                            (int64_t)b.part.n, (int64_t)(op->xr_col.n / 4)};
+        *b.h_ctl = hc;
+        SDA_CUDA(cudaMemcpyAsync(b.ctl.p, b.h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, s));
+        SDA_CUDA(cudaMemsetAsync(b.vec.p, 0, b.vec.bytes(), s));
+        BView<FT> bv = bview<FT>(b);
+        const FT *sv = std::is_same<FT, double>::value ? (const FT *)op->s_val64.p : (const FT *)op->s_val32.p;
+        const FT *dg = std::is_same<FT, double>::value ? (const FT *)op->deg64.p : (const FT *)op->deg32.p;
+        const int cand[4] = {2, 3, 4, 6};
+        const int m1 = b.grid1 / sms, m2 = b.grid2 / sms, m3 = b.grid3a / sms;   // occupancy caps
+        float best1 = 1e30f, best2 = 1e30f, best3 = 1e30f, t = 0.f;
+        for (int c : cand) {
+            if (c <= m1) {
+                SDA_TRY(time_launch(s, [&] { return rowpass_b<VT, FT>(op, b, bv.p, bv.ut, c * sms, s); }, &t));
+                if (t < best1) best1 = t, tv.bpsm1 = c;
+            }
+            if (c <= m2) {
+                SDA_TRY(time_launch(s, [&]() -> int {
+                    kb_phase2<FT><<<c * sms, kBlock, 0, s>>>(op->n, op->s_rp.p, op->s_col.p, sv, bv.ut, dg, b.ylab.p,
+                                                             bv.v, b.st.p, b.ctl.p, bv.coef, 0, b.part.p, b.cnt.p + 0);
+                    SDA_LAUNCHED();
+                    return SDA_OK;
+                }, &t));
+                if (t < best2) best2 = t, tv.bpsm2 = c;
+            }
+            if (c <= m3) {
+                SDA_TRY(time_launch(s, [&]() -> int {
+                    const int64_t H = op->hb.nseg;
+                    using Part = typename CompSum<FT>::Part;
+                    kb_phase3a<VT, FT><<<c * sms, kBlock, 0, s>>>(op->col_tail.tiles.p, op->col_tail.ntiles,
+                                                                 op->x_cp.p + H, op->x_row.p, (const VT *)op->x_val_c.p,
+                                                                 bv.v, bv.s + H * kTB, (Part *)b.slots.p, b.lcount.p,
+                                                                 op->col_tail.splits.p, b.ctl.p);
+                    SDA_LAUNCHED();
+                    return SDA_OK;
+                }, &t));
+                if (t < best3) best3 = t, tv.bpsm3 = c;
+            }
+        }
+        tv.head_items = 4;
+        if (op->hb.nseg > 0) {
+            float besth = 1e30f;
+            for (int items : {1, 2, 4, 8}) {
+                b.head_items = items;
+                SDA_TRY(time_launch(s, [&] { return colpass_b<VT, FT>(op, b, bv.v, bv.s, b.grid3a, s); }, &t));
+                if (t < besth) besth = t, tv.head_items = items;
+            }
+        }
+        if (tv.bpsm1 == 0) tv.bpsm1 = std::max(1, m1);
+        if (tv.bpsm2 == 0) tv.bpsm2 = std::max(1, m2);
+        if (tv.bpsm3 == 0) tv.bpsm3 = std::max(1, m3);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[key] = tv;
+    }
+    b.grid1 = tv.bpsm1 * sms;
+    b.grid2 = tv.bpsm2 * sms;
+    b.grid3a = tv.bpsm3 * sms;
+    b.head_items = tv.head_items;
+    b.tuned = true;
+    op->tuned[0] = tv.bpsm1;
+    op->tuned[1] = tv.bpsm2;
+    op->tuned[2] = tv.bpsm3;
+    op->tuned[3] = tv.head_items;
     return SDA_OK;
 }
 
@@ -1382,6 +1551,7 @@ static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const dou
         b.grid = std::min(std::min(b.grid1, b.grid2), std::min(b.grid3a, grid_for((const void *)kb_phase3b<FT>, op->sm_count,
                                                                     kMaxShifts * kTB * sizeof(BatchCoef<FT>))));
     }
+    if (!b.tuned) SDA_TRY((autotune<VT, FT>(op, b, s)));
     const int64_t d = op->d, n = op->n;
     const int ge = grid_elems_b(std::max(b.ldw, b.n8), op->sm_count);
     SDA_CUDA(cudaMemsetAsync(b.b.p, 0, b.b.bytes(), s));
@@ -1424,10 +1594,24 @@ static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const dou
     SDA_LAUNCHED();
     SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
-    int launched = 0;
+    const bool device_loop = o.use_graph && !o.profile && !b.h_ctl->done;
+    if (device_loop) {
+        // the device-driven loop: one graph launch runs the batch to its end
+        if (basis) SDA_TRY(ensure_basis<FT>(b, (int64_t)limit + nbi + 1, b.btab_cap, s));
+        SDA_TRY((batch_loop<VT, FT>(op, ns, basis, nbi, limit, s)));
+        SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+        SDA_CUDA(cudaStreamSynchronize(s));
+        if (b.h_ctl->err)
+            return fail(SDA_ERR_INDEX, "batched solve: index check %llu failed at %llu",
+                        (unsigned long long)(b.h_ctl->err >> 40), (unsigned long long)(b.h_ctl->err & 0xffffffffffull));
+        const int64_t bodies = std::max<int64_t>(1, ((int64_t)b.h_ctl->k + nbi - 1) / nbi);
+        note_launch(bodies * ((4 + colpass_launches(op)) * (int64_t)nbi + 1));
+        for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += bodies * nbi;
+    }
+    int launched = device_loop ? limit + 1 : 0;   // the host-driven loop: profile mode and graphs off
     while (!b.h_ctl->done && launched <= limit) {
         if (basis) SDA_TRY(ensure_basis<FT>(b, (int64_t)launched + nbi, b.btab_cap, s));
-        SDA_TRY((batch_run<VT, FT>(op, ns, basis, nbi, o.use_graph != 0, o.profile != 0, s)));
+        SDA_TRY((batch_run<VT, FT>(op, ns, basis, nbi, o.profile != 0, s)));
         launched += nbi;
         SDA_CUDA(cudaMemcpyAsync(b.h_ctl, b.ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
         SDA_CUDA(cudaStreamSynchronize(s));

@@ -129,6 +129,10 @@ struct sda_operator {
     sda::RangeBlocks hb;
     // the other columns' tiles for the batched column pass (segments counted from hb.nseg)
     sda::ColSchedule col_tail;
+    // schedule of the batched sparse passes picked by the autotuner on the first batched
+    // run: resident blocks per SM of the row pass, Laplacian pass and tail column pass,
+    // and work items per resident block of the head column pass (0: not tuned yet)
+    int tuned[4] = {0, 0, 0, 0};
     // X in row-major order with rows padded by zero entries (column 0) to whole
     // quads, for the row pass of the iteration; features [0, xr_head) (the most
     // frequent) are gathered from shared memory there

@@ -1174,6 +1174,7 @@ extern "C" SDA_API int sda_get_operator_info(const sda_operator *op, sda_operato
     info->head_cols = (int32_t)op->hb.nseg;
     info->head_ranges = op->hb.nseg > 0 ? op->hb.nranges : 0;
     info->head_entries = op->hb.nseg > 0 ? (int64_t)op->hb.idx.n : 0;
+    for (int k = 0; k < 4; ++k) info->tuned[k] = op->tuned[k];
     return SDA_OK;
 }
 

@@ -76,7 +76,7 @@ class sda_operator_info(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("col_ranges", ctypes.c_int32), ("row_head", ctypes.c_int32), ("col_entries", ctypes.c_int64),
                 ("row_entries", ctypes.c_int64), ("head_cols", ctypes.c_int32), ("head_ranges", ctypes.c_int32),
-                ("head_entries", ctypes.c_int64)]
+                ("head_entries", ctypes.c_int64), ("tuned", ctypes.c_int32 * 4)]
 
 
 _vp = ctypes.c_void_p
@@ -357,7 +357,9 @@ def sda_operator_apply_static(op, target, sigma, p, q, stream=None):
 def sda_get_operator_info(op) -> dict:
     info = sda_operator_info()
     _check(load().sda_get_operator_info(op, ctypes.byref(info)), "sda_get_operator_info")
-    return {f: getattr(info, f) for f, _ in sda_operator_info._fields_}
+    out = {f: getattr(info, f) for f, _ in sda_operator_info._fields_}
+    out["tuned"] = list(info.tuned)
+    return out
 
 
 def sda_get_target_counts(op, n_targets: int) -> np.ndarray:

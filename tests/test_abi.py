@@ -45,4 +45,4 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sda.sda_solve_opts) == 104
     assert sda.sda_solve_opts.shift_form.offset == 96
     assert ctypes.sizeof(sda.sda_solve_stats) == 112
-    assert ctypes.sizeof(sda.sda_operator_info) == 104
+    assert ctypes.sizeof(sda.sda_operator_info) == 120

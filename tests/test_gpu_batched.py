@@ -216,3 +216,38 @@ def test_batched_full_size_first_batch():
     W0 = w[0].cpu().numpy()
     for s, beta in enumerate(p.shifts):
         assert ob.true_residual(b, beta, W0[s]) < 1.5e-3, s
+
+
+def test_autotuned_schedule_recorded_and_reused(multi):
+    """The first batched run picks the sparse passes' schedule (autotuner) and
+    the operator reports it; an operator of the same shape reuses it."""
+    op = sda.Operator(multi, compute="f16")
+    assert op.info["tuned"] == [0, 0, 0, 0]
+    ns, d = len(multi.shifts), multi.d
+    w = torch.empty((T, ns, d), dtype=torch.float64, device="cuda")
+    o = sda.sda_default_opts()
+    o.fixed_iters, o.batch_targets = 5, 1
+    sda.sda_solve_shifts(op.handle, multi.shifts, o, w_out=w, n_report=T)
+    tuned = sda.sda_get_operator_info(op.handle)["tuned"]
+    assert all(x > 0 for x in tuned), tuned
+    op2 = sda.Operator(multi, compute="f16")
+    sda.sda_solve_shifts(op2.handle, multi.shifts, o, w_out=w, n_report=T)
+    assert sda.sda_get_operator_info(op2.handle)["tuned"] == tuned
+
+
+@pytest.mark.parametrize("fixed", [0, 13])
+def test_device_driven_loop_equals_host_loop(multi, fixed):
+    """With graphs on, one graph launch per batch runs the iterations until the
+    device marks the batch done (a conditional WHILE node); with graphs off the
+    host launches them in groups.  Same kernels, same order: identical results."""
+    ns, d = len(multi.shifts), multi.d
+    out = []
+    for graph in (1, 0):
+        op = sda.Operator(multi, compute="f16")
+        w = torch.empty((T, ns, d), dtype=torch.float64, device="cuda")
+        o = sda.sda_default_opts()
+        o.tol, o.fixed_iters, o.max_iter, o.batch_targets, o.use_graph, o.iter_batch = 1e-6, fixed, 5000, 1, graph, 8
+        code, rep = sda.sda_solve_shifts(op.handle, multi.shifts, o, w_out=w, n_report=T)
+        out.append((w.cpu().numpy(), [[r["iters"] for r in tr] for tr in rep]))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
