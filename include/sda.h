@@ -318,6 +318,32 @@ SDA_API int sda_adjoint_grad_batched(sda_operator *op, int32_t n_targets, const 
                                      sda_shift_report *report, void *cuda_stream);
 
 /*
+ * sda_knn_graph - the similarity graph S of Sec. 2.4 built on the device from
+ * the samples: s_ij = Tanimoto (Jaccard) similarity of the binary supports of
+ * rows i and j of X, |x_i and x_j| / |x_i or x_j| (Tanimoto on fingerprints,
+ * Sec. 5.1); the edges are the union of every row's k nearest rows (the
+ * undirected kNN graph of Sec. 2.4), ranked by (similarity descending, row
+ * index ascending); similarity 0 never makes an edge, and with threshold > 0
+ * neither does a similarity below it (the similarity threshold of Sec. 2.4;
+ * Sec. 5.2 uses Tanimoto >= 0.4).  Candidates of row i are the rows sharing a
+ * feature whose column count is <= cap (cap >= N: every shared feature, the
+ * exact kNN graph).  The result is symmetric with a zero diagonal and is a
+ * valid S for sda_build_operator.
+ *
+ *   X          N x D (values ignored: the binary support counts); host or device arrays
+ *   k          neighbours per row, 1 .. 32
+ *   cap        column-count limit of the features that propose candidates (>= 1)
+ *   threshold  smallest similarity kept, in [0, 1]
+ *   row_ptr    device int64 [N + 1]; col_out, val_out: device int32 / double [capacity]
+ *   nnz_out    host: the entries of S (also when they exceed capacity)
+ * Rows are sorted by column.  Errors: INVALID_ARG, SHAPE (sizes, or an output
+ * smaller than the graph: *nnz_out says how large), INDEX, UNSUPPORTED (a row
+ * of more than 1,024 features), CUDA, OOM.  Synchronises the stream.
+ */
+SDA_API int sda_knn_graph(const sda_csr *X, int32_t k, int64_t cap, double threshold, int64_t *row_ptr,
+                          int32_t *col_out, double *val_out, int64_t capacity, int64_t *nnz_out, void *cuda_stream);
+
+/*
  * sda_project - ratings s = X w of the samples (Sec. 4, Alg. 7 step 5), or
  * the centred ratings (X - 1 mu_l^T) w when `centred` is 1 (uses mu_l of
  * `target`).  FP64 sums.

@@ -24,6 +24,8 @@ Functions and what they follow:
   regularised system (not in the paper; checks the library's adjoint).
 * :func:`adjoint_grad_sparse` - the same through the C oracle's CG and sparse
   products, for problems too large to densify.
+* :func:`knn_graph`          - the similarity graph of Sec. 2.4 (Tanimoto kNN,
+  union of the directed lists) from dense binary supports, small inputs.
 
 Every function above is pinned by the ``-m "not gpu"`` tests against
 closed forms, dense definitions, special cases and brute force
@@ -354,3 +356,42 @@ def adjoint_grad_sparse(o: Oracle, x_ptr, x_col, x_val, s_ptr, s_col, s_val, row
     St_w = X.T @ (lab * u) - mu * (lab * u).sum()
     XLX_w = X.T @ (L @ (X @ w))
     return loss, float(-lam @ (XLX_w - St_w)), float(-lam @ w), w
+
+
+def knn_graph(x_ptr, x_col, d, k, cap=None, threshold=0.0):
+    """The similarity graph of Sec. 2.4 by its definition (small inputs):
+    s_ij = |x_i and x_j| / |x_i or x_j| on the binary supports (Tanimoto,
+    Sec. 5.1); row i's candidates are the rows j != i sharing a feature (only
+    features of column count <= cap when cap is given); its k nearest are the
+    candidates of positive similarity (and >= threshold) ranked by (similarity
+    descending, row index ascending); the edges are the union of the directed
+    lists.  Returns the CSR (row_ptr int64, col int32, val float64), rows sorted."""
+    n = np.asarray(x_ptr).size - 1
+    B = np.zeros((n, d), dtype=np.int64)
+    row = np.repeat(np.arange(n), np.diff(x_ptr))
+    B[row, np.asarray(x_col)] = 1
+    inter = B @ B.T
+    size = B.sum(axis=1)
+    union = size[:, None] + size[None, :] - inter
+    jac = np.where(inter > 0, inter / np.maximum(union, 1), 0.0)
+    if cap is None:
+        cand = inter > 0
+    else:
+        R = B[:, B.sum(axis=0) <= cap]
+        cand = (R @ R.T) > 0
+    np.fill_diagonal(cand, False)
+    edges = {}
+    for i in range(n):
+        js = np.nonzero(cand[i] & (jac[i] > 0) & (jac[i] >= threshold))[0]
+        order = sorted(js.tolist(), key=lambda j: (-jac[i, j], j))[:k]
+        for j in order:
+            edges[(i, j)] = jac[i, j]
+            edges[(j, i)] = jac[i, j]
+    keys = sorted(edges)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    for (i, _) in keys:
+        rp[i + 1] += 1
+    rp = np.cumsum(rp)
+    col = np.array([j for (_, j) in keys], dtype=np.int32)
+    val = np.array([edges[key] for key in keys], dtype=np.float64)
+    return rp, col, val

@@ -101,6 +101,8 @@ _SIGS = {
                                                 ctypes.POINTER(sda_shift_report), _vp]),
     "sda_operator_apply": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
     "sda_operator_apply_static": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
+    "sda_knn_graph": (ctypes.c_int, [ctypes.POINTER(sda_csr), ctypes.c_int32, ctypes.c_int64, ctypes.c_double, _vp,
+                                     _vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _vp]),
     "sda_get_operator_info": (ctypes.c_int, [_vp, ctypes.POINTER(sda_operator_info)]),
     "sda_get_target_counts": (ctypes.c_int, [_vp, _vp]),
     "sda_get_solve_stats": (ctypes.c_int, [_vp, ctypes.POINTER(sda_solve_stats)]),
@@ -352,6 +354,24 @@ def sda_operator_apply_static(op, target, sigma, p, q, stream=None):
     qp, _, qk = _ptr(q)
     return _check(lib.sda_operator_apply_static(op, int(target), float(sigma), pp, qp, _stream(stream)),
                   "sda_operator_apply_static")
+
+
+def sda_knn_graph(x_ptr, x_col, n_cols, k, cap, threshold=0.0, stream=None):
+    """Calls sda_knn_graph; returns (row_ptr, col, val) as CUDA tensors (the
+    output is sized for the union of the directed lists, 2 N k entries)."""
+    import torch
+    lib = load()
+    keep = []
+    n = int(x_ptr.shape[0]) - 1
+    X = _csr(x_ptr, x_col, None, n, n_cols, keep)
+    cap_out = 2 * n * int(k)
+    rp = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(max(cap_out, 1), dtype=torch.int32, device="cuda")
+    val = torch.empty(max(cap_out, 1), dtype=torch.float64, device="cuda")
+    nnz = ctypes.c_int64()
+    _check(lib.sda_knn_graph(ctypes.byref(X), int(k), int(cap), float(threshold), rp.data_ptr(), col.data_ptr(),
+                             val.data_ptr(), cap_out, ctypes.byref(nnz), _stream(stream)), "sda_knn_graph")
+    return rp, col[:nnz.value], val[:nnz.value]
 
 
 def sda_get_operator_info(op) -> dict:

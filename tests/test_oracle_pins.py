@@ -451,3 +451,62 @@ def test_sa_sda_operator_with_identity_data():
     for s, beta in enumerate(p.shifts):
         z = np.linalg.solve(Mt + beta * np.eye(n), d)
         assert np.linalg.norm(res.W[s] - z) < 1e-9 * np.linalg.norm(z)
+
+
+# --------------------------------------------------------------------------
+# Similarity graph (Sec. 2.4; Tanimoto, Sec. 5.1)
+# --------------------------------------------------------------------------
+
+def _knn_by_sets(x_ptr, x_col, k, cap=None, threshold=0.0):
+    """The definition with Python sets and a double loop."""
+    n = x_ptr.size - 1
+    rows = [set(x_col[x_ptr[i]:x_ptr[i + 1]].tolist()) for i in range(n)]
+    cnt = {}
+    for r in rows:
+        for f in r:
+            cnt[f] = cnt.get(f, 0) + 1
+    edges = {}
+    for i in range(n):
+        best = []
+        for j in range(n):
+            if j == i:
+                continue
+            shared = rows[i] & rows[j]
+            if cap is not None:
+                if not any(cnt[f] <= cap for f in shared):
+                    continue
+            if not shared:
+                continue
+            s = len(shared) / len(rows[i] | rows[j])
+            if s < threshold:
+                continue
+            best.append((-s, j, s))
+        best.sort()
+        for _, j, s in best[:k]:
+            edges[(i, j)] = s
+            edges[(j, i)] = s
+    return edges
+
+
+@pytest.mark.parametrize("cap,thr", [(None, 0.0), (3, 0.0), (None, 0.25)])
+def test_knn_graph_oracle_equals_set_definition(cap, thr):
+    from paper_1709_04794_gb300 import synth
+    p = synth.custom_problem(90, 40, 6, seed=13, n_labelled=20, k=3)
+    rp, col, val = oracle.knn_graph(p.x_ptr, p.x_col, p.d, 4, cap=cap, threshold=thr)
+    ref = _knn_by_sets(p.x_ptr, p.x_col, 4, cap=cap, threshold=thr)
+    got = {(i, int(col[e])): float(val[e]) for i in range(p.n) for e in range(rp[i], rp[i + 1])}
+    assert got.keys() == ref.keys() and all(got[key] == ref[key] for key in ref)
+    assert all(i != j for (i, j) in got) and all((j, i) in got for (i, j) in got)
+    assert all(0.0 < v <= 1.0 for v in got.values())
+
+
+def test_knn_graph_oracle_equals_input_generator():
+    """Two independent implementations of the same definition: the oracle's
+    dense one and the input generator's candidate lists in C."""
+    from paper_1709_04794_gb300 import synth
+    p = synth.custom_problem(400, 150, 9, seed=17, n_labelled=40, k=5)
+    for cap in (None, 12):
+        nbr, sim = synth.knn_lists(p.x_ptr, p.x_col, p.d, 5, cap)
+        g_rp, g_col, g_val = synth.union_graph(nbr, sim)
+        o_rp, o_col, o_val = oracle.knn_graph(p.x_ptr, p.x_col, p.d, 5, cap=cap)
+        assert np.array_equal(g_rp, o_rp) and np.array_equal(g_col, o_col) and np.array_equal(g_val, o_val)
