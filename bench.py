@@ -42,6 +42,7 @@ import numpy as np  # noqa: E402
 
 WORKLOAD = "single_mixed_200k"
 LARGE = "large_1000t_2m"          # the default: the largest single-GPU workload
+LARGE_WORKLOADS = (LARGE, "adjoint_64t_500k")   # run by run_large (the same step)
 METRIC = "SDA solves/s (all shifts)"
 UNIT = "solves/s"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cg_kernels_single_mixed_200k.md")
@@ -311,7 +312,7 @@ def run_reference_large(args, prob, rank):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": LARGE, "n": prob.n, "d": prob.d, "nnz": int(prob.x_ptr[-1]),
+            "config": {"workload": args.workload, "n": prob.n, "d": prob.d, "nnz": int(prob.x_ptr[-1]),
                        "targets": T, "shifts": len(prob.shifts), "fixed_iters": args.fixed_iters},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "one target per step: its shifted-CG sweep of all %d shifts and its "
@@ -690,7 +691,7 @@ def run_large(args, rank, world, local):
     over the ranks with no exchange."""
     import torch
     from paper_1709_04794_gb300 import sda, synth
-    prob = synth.make_problem(LARGE)
+    prob = synth.make_problem(args.workload)
     compute = args.compute or prob.workload.value_dtype
     T_all = prob.labels.shape[0]
     torch.cuda.set_device(local)
@@ -986,7 +987,7 @@ def run_large(args, rank, world, local):
                 "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
                 "scaling": "weak" if world == 1 else "strong", "vs_baseline": None,
                 "dtype": "f32" if compute != "f64" else "f64", "data": "synthetic",
-                "config": {"workload": LARGE, "n": n, "d": d, "nnz": int(prob.x_ptr[-1]),
+                "config": {"workload": args.workload, "n": n, "d": d, "nnz": int(prob.x_ptr[-1]),
                            "graph_nnz": int(prob.s_ptr[-1]), "targets": T_all, "shifts": ns,
                            "x_storage": compute, "fixed_iters": args.fixed_iters, "chunk": C, "batch": 16,
                            "targets_per_run": solved, "alpha": prob.alpha,
@@ -1009,11 +1010,11 @@ def run_large(args, rank, world, local):
 
 def main():
     args = parse()
-    if args.workload == LARGE:
+    if args.workload in LARGE_WORKLOADS:
         rank = int(os.environ.get("RANK", "0"))
         if args.impl == "reference":
             from paper_1709_04794_gb300 import synth
-            run_reference_large(args, synth.make_problem(LARGE), rank)
+            run_reference_large(args, synth.make_problem(args.workload), rank)
         else:
             run_large(args, rank, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0")))
         return
