@@ -449,6 +449,13 @@ typedef struct {
        Laplacian pass and the tail column pass, and work items per resident block of
        the head column pass */
     int32_t tuned[4];
+    /* X passes of the FP64 residual checks, projections and block utilities: 1 when
+       they run in exact fixed point (every value of X is x_int 2^-x_frac_bits with
+       |x_int| < 2^x_int_bits, x_frac_bits <= 24, x_int_bits <= 10: products exact in
+       64-bit and sums exact in 128-bit integers, one rounding to FP64 per result),
+       -1 when they run in FP64 arithmetic, 0 until the operator's first such pass */
+    int32_t exact_x_passes;
+    int16_t x_frac_bits, x_int_bits;
 } sda_operator_info;
 
 SDA_API int sda_get_operator_info(const sda_operator *op, sda_operator_info *info);

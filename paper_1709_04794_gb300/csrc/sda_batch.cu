@@ -102,6 +102,12 @@ struct BatchWs {
     DevBuf<double> sig, r2;    // per-lane shifts and squared residual norms of the FP64 block utilities
     DevBuf<double> wall;       // FP64 solutions of a batch's (target, shift) pairs [target][shift][D]
     DevBuf<double> rbuf;       // residual vectors of up to kTB pairs [lane][D] (refinement right-hand sides)
+    // FP64 workspaces, fixed-point X passes: the scaled vector as planes
+    // [kTB / kFxNT][len][kFxNT], the per-lane max |z| (bit patterns) and scale exponents
+    DevBuf<long long> fx_planes;
+    DevBuf<unsigned long long> fx_amax;
+    DevBuf<int> fx_k;
+    int grid_fx1 = 0, grid_fx3 = 0, grid_fx_head = 0;
     // stored-basis form: chunks of kBasisChunk slots [ldw][kTB] each, their device
     // pointer table (graphs read it, so new chunks need no recapture), the CG scalars
     // of every iteration and the per-(lane, shift) basis coefficients
@@ -729,6 +735,353 @@ __global__ void __launch_bounds__(kBlock) kb_head_reduce(int nr, int64_t m, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact fixed-point X passes of the FP64 block utilities
+// ---------------------------------------------------------------------------
+// GB300 runs FP64 arithmetic at a small fraction of its FP32 and integer rates,
+// and an FP64 pass over X costs one FP64 multiply-add per lane and nonzero. When
+// the values of X are small integers times one power of two (binary and count
+// data: x = x_int 2^-sx, |x_int| < 2^bx), the X passes run on integers instead:
+// a lane's vector z is scaled to z_fx = round(z 2^k) with |z_fx| <= 2^(62 - bx),
+// k set by the lane's largest |z|; each product x_int z_fx is exact in 64 bits,
+// the sums are exact in 128 bits, and each result is rounded to FP64 once. The
+// only other error is the rounding of z to multiples of 2^-k: per entry at most
+// 2^-(k+1) sum_j |x_ij|, i.e. about 2^(bx - 63) max|z| sum_j |x_ij|, no larger
+// than the rounding of an FP64 sum of the same terms.
+using i128 = __int128;
+
+constexpr int kFxNT = 8;                  // lanes per fixed-point plane (64-byte rows)
+constexpr int kFxNonFinite = -(1 << 30);  // scale exponent of a lane holding a non-finite value
+
+__device__ __forceinline__ double i128_to_double(i128 a) {
+    const long long hi = (long long)(a >> 64);
+    const unsigned long long lo = (unsigned long long)a;
+    if (hi == ((long long)lo >> 63)) return (double)(long long)lo;   // fits in 64 bits: one rounding
+    return (double)hi * 18446744073709551616.0 + (double)lo;          // |a| >= 2^63: within 2^-52 |a|
+}
+
+// a result scaled back: a 2^-(k + sx), NaN for a non-finite lane
+__device__ __forceinline__ double fx_value(i128 a, int k, int sx) {
+    return k == kFxNonFinite ? (double)NAN : ldexp(i128_to_double(a), -(k + sx));
+}
+
+// x_int = x 2^sx of a stored value read as XF (exact: x has few significant bits)
+template <class XF>
+__device__ __forceinline__ long long fx_int(XF x, XF xs) {
+    return (long long)(x * xs);
+}
+
+// amax[l] = max over i < len of |src[i][l]| as its bit pattern (non-negative
+// doubles order as their bits; a NaN or infinity is at least 0x7ff0...)
+__global__ void __launch_bounds__(kBlock) kb_absmax_lanes(int64_t len, const double *__restrict__ src,
+                                                         unsigned long long *amax) {
+    unsigned long long m = 0;
+    const int64_t total = len * kTB;
+    // kBlock and the grid stride are multiples of kTB: thread x always sees lane x % kTB
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kBlock) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(src[e]));
+        m = b > m ? b : m;
+    }
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, 16);
+    m = o > m ? o : m;
+    if ((threadIdx.x & 31) < kTB) atomicMax(amax + threadIdx.x % kTB, m);
+}
+
+// scale exponent k of a lane from its amax: |z| 2^k < 2^(62 - bx)
+__device__ __forceinline__ int fx_exp(unsigned long long amax_bits, int bx) {
+    if (amax_bits >= 0x7ff0000000000000ull) return kFxNonFinite;
+    if (amax_bits == 0ull) return 0;
+    int e = 0;
+    frexp(__longlong_as_double((long long)amax_bits), &e);   // max |z| < 2^e
+    return 62 - bx - e;
+}
+
+// dst planes [kTB / kFxNT][len][kFxNT] of round(src[i][l] 2^k_l); k_l to kexp
+__global__ void __launch_bounds__(kBlock) kb_to_fixed(int64_t len, const double *__restrict__ src,
+                                                     const unsigned long long *__restrict__ amax, int bx,
+                                                     long long *__restrict__ dst, int *kexp) {
+    const int l = threadIdx.x % kTB;
+    const int k = fx_exp(amax[l], bx);
+    if (blockIdx.x == 0 && threadIdx.x < kTB) kexp[threadIdx.x] = k;
+    const int64_t total = len * kTB;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kBlock) {
+        const int64_t i = e / kTB;
+        const long long q = k == kFxNonFinite ? 0ll : llrint(ldexp(src[e], k));
+        dst[(int64_t)(l / kFxNT) * len * kFxNT + i * kFxNT + (l % kFxNT)] = q;
+    }
+}
+
+// lowest and highest set-bit exponents of the nonzero values of X (for x_int):
+// out[0] = min E, out[1] = max T over x = M 2^E (M odd), 2^T <= |x| < 2^(T+1);
+// out[2] = 1 if a value is not finite
+template <class VT>
+__global__ void __launch_bounds__(kBlock) kb_fx_scan(int64_t nnz, const VT *__restrict__ val, int *out) {
+    int lo = 1 << 30, hi = -(1 << 30), bad = 0;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * kBlock) {
+        const double x = (double)Val<VT>::get(val, e);
+        if (x == 0.0) continue;
+        if (!isfinite(x)) {
+            bad = 1;
+            continue;
+        }
+        int ex = 0;
+        const double m = frexp(fabs(x), &ex);   // |x| = m 2^ex, m in [0.5, 1)
+        const unsigned long long M = (unsigned long long)ldexp(m, 53);
+        lo = min(lo, ex - 53 + (__ffsll((long long)M) - 1));
+        hi = max(hi, ex - 1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out + 0, lo);
+        atomicMax(out + 1, hi);
+        if (bad) atomicOr(out + 2, 1);
+    }
+}
+
+// phase 1 in fixed point: ut[i][t] = (X w_t)_i - c_t for the kFxNT lanes
+// t = lane0 .. lane0 + 7, gathered from one plane wp ([ldw][kFxNT]) of w_fx
+template <class VT>
+__global__ void __launch_bounds__(kBlock) kb_phase1_fx(int64_t n, const int64_t *__restrict__ rp,
+                                                      const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                                      const long long *__restrict__ wp, double *__restrict__ ut,
+                                                      const SolveState *st, const BatchCtl *ctl, int lane0, int sx,
+                                                      const int *__restrict__ kexp) {
+    using XF = std::conditional_t<std::is_same<VT, double>::value, double, float>;
+    constexpr int TPL = 2, LG = kFxNT / TPL;
+    if (ctl->done) return;
+    const int lg = threadIdx.x % LG, t0 = lg * TPL;
+    double c[TPL];
+    int kq[TPL];
+#pragma unroll
+    for (int q = 0; q < TPL; ++q) {
+        c[q] = st[lane0 + t0 + q].c;
+        kq[q] = kexp[lane0 + t0 + q];
+    }
+    const XF xs = (XF)(1ll << sx);
+    const int64_t g = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / LG;
+    const int64_t ng = (int64_t)gridDim.x * (kBlock / LG);
+    const int64_t lim = ctl->bb.ldw * kFxNT;
+    const int4 *__restrict__ colq = reinterpret_cast<const int4 *>(col);
+    for (int64_t i = g; i < n; i += ng) {
+        const int64_t q0 = rp[i] >> 2, q1 = rp[i + 1] >> 2;
+        i128 acc[TPL] = {0, 0};
+        for (int64_t q = q0; q < q1; q += 2) {
+            int4 ci[2];
+            long long xi[2][4];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                ci[u] = make_int4(0, 0, 0, 0);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) xi[u][e] = 0;
+                if (q + u < q1 && BOK(q + u, ctl->bb.nqx, 60)) {
+                    ci[u] = colq[q + u];
+                    XF xv[4];
+                    Quad<VT, XF>::load(val, q + u, xv);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) xi[u][e] = fx_int(xv[e], xs);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int32_t j = e == 0 ? ci[u].x : e == 1 ? ci[u].y : e == 2 ? ci[u].z : ci[u].w;
+                    const int64_t off = (int64_t)j * kFxNT + t0;
+                    if (!BOK(off + TPL - 1, lim, 61)) continue;
+                    const longlong2 w = *reinterpret_cast<const longlong2 *>(wp + off);
+                    acc[0] += (i128)(xi[u][e] * w.x);
+                    acc[1] += (i128)(xi[u][e] * w.y);
+                }
+            }
+        }
+        const int64_t io = i * kTB + lane0 + t0;
+        if (BOK(io + TPL - 1, ctl->bb.n8 * kTB, 62))
+            *reinterpret_cast<double2 *>(ut + io) =
+                make_double2(fx_value(acc[0], kq[0], sx) - c[0], fx_value(acc[1], kq[1], sx) - c[1]);
+    }
+}
+
+// head columns in fixed point: as kb_head3a, the range slice of one plane of v_fx
+// ([n8][kFxNT], lanes hf * kFxNT ..) staged in shared memory; hp[r][h][t] gets
+// the range's sum scaled back to FP64
+template <class VT>
+__global__ void __launch_bounds__(kBlock) kb_head3a_fx(int64_t n, int64_t n8, int nr, int H, int nsplit,
+                                                      const int64_t *__restrict__ cp, const uint16_t *__restrict__ idx,
+                                                      const VT *__restrict__ val, const long long *__restrict__ vpl,
+                                                      double *__restrict__ hp, const BatchCtl *ctl, int sx,
+                                                      const int *__restrict__ kexp) {
+    using XF = std::conditional_t<std::is_same<VT, double>::value, double, float>;
+    constexpr int NH = kTB / kFxNT, TPL = 2, LG = kFxNT / TPL, GPB = kBlock / LG;
+    extern __shared__ __align__(16) unsigned char khx_dyn[];
+    long long *vs = reinterpret_cast<long long *>(khx_dyn);
+    if (ctl->done) return;
+    const int lg = threadIdx.x % LG, g = threadIdx.x / LG, t0 = lg * TPL;
+    const uint2 *__restrict__ idxq = reinterpret_cast<const uint2 *>(idx);
+    const XF xs = (XF)(1ll << sx);
+    const int hs = (H + nsplit - 1) / nsplit;
+    for (int item = blockIdx.x; item < nr * nsplit * NH; item += gridDim.x) {
+        const int r = item / (nsplit * NH), rem = item - r * nsplit * NH;
+        const int sl = rem / NH, hf = rem - sl * NH;
+        const int c0 = sl * hs, c1 = min(H, c0 + hs);
+        const int64_t row0 = (int64_t)r * kHeadRows;
+        const int rows = (int)min((int64_t)kHeadRows, n - row0);
+        __syncthreads();
+        {
+            // the plane's rows are contiguous: rows x kFxNT values
+            const longlong2 *__restrict__ src =
+                reinterpret_cast<const longlong2 *>(vpl + (int64_t)hf * n8 * kFxNT + row0 * kFxNT);
+            longlong2 *dst = reinterpret_cast<longlong2 *>(vs);
+            const int nvec = rows * (kFxNT / 2);
+            for (int q = threadIdx.x; q < nvec; q += kBlock) dst[q] = src[q];
+        }
+        __syncthreads();
+        int kq[TPL];
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) kq[u] = kexp[hf * kFxNT + t0 + u];
+        const int64_t *__restrict__ c = cp + (int64_t)r * (H + 1);
+        for (int h = c0 + g; h < c1; h += GPB) {
+            const int64_t q0 = c[h] >> 2, q1 = c[h + 1] >> 2;
+            i128 acc[TPL] = {0, 0};
+            for (int64_t q = q0; q < q1; q += 4) {
+                uint2 ii[4];
+                long long xi[4][4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    if (q + w < q1) {
+                        ii[w] = idxq[q + w];
+                        XF xv[4];
+                        Quad<VT, XF>::load(val, q + w, xv);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) xi[w][k] = fx_int(xv[k], xs);
+                    } else {
+                        ii[w] = make_uint2(0u, 0u);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) xi[w][k] = 0;
+                    }
+                }
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int li[4] = {(int)(ii[w].x & 0xffffu), (int)(ii[w].x >> 16), (int)(ii[w].y & 0xffffu),
+                                       (int)(ii[w].y >> 16)};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const longlong2 x = *reinterpret_cast<const longlong2 *>(vs + li[k] * kFxNT + t0);
+                        acc[0] += (i128)(xi[w][k] * x.x);
+                        acc[1] += (i128)(xi[w][k] * x.y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TPL; ++u)
+                hp[((int64_t)r * H + h) * kTB + hf * kFxNT + t0 + u] = fx_value(acc[u], kq[u], sx);
+        }
+    }
+}
+
+// tail columns in fixed point: as kb_phase3a for the kFxNT lanes t = lane0 ..,
+// gathered from one plane v ([n8][kFxNT]) of v_fx; the block and split-column
+// sums stay in 128-bit integers (slots: one i128 per lane) until the column's
+// total is scaled back to FP64
+template <class VT>
+__global__ void __launch_bounds__(kBlock) kb_phase3a_fx(const Tile *__restrict__ tiles, int ntiles,
+                                                       const int64_t *__restrict__ cp, const int32_t *__restrict__ row,
+                                                       const VT *__restrict__ val, const long long *__restrict__ v,
+                                                       double *__restrict__ out, i128 *slots, unsigned *lcount,
+                                                       const SplitSeg *__restrict__ splits, const BatchCtl *ctl,
+                                                       int lane0, int sx, const int *__restrict__ kexp) {
+    using XF = std::conditional_t<std::is_same<VT, double>::value, double, float>;
+    constexpr int TPL = 2, LG = kFxNT / TPL, GPB = kBlock / LG;
+    __shared__ i128 red[GPB * kFxNT];
+    __shared__ int last;
+    if (ctl->done) return;
+    const int lg = threadIdx.x % LG, g = threadIdx.x / LG, t0 = lg * TPL;
+    const int64_t lim = ctl->bb.n8 * kFxNT;
+    const XF xs = (XF)(1ll << sx);
+    int kq[TPL];
+#pragma unroll
+    for (int u = 0; u < TPL; ++u) kq[u] = kexp[lane0 + t0 + u];
+    const int lt = lane0 + (int)(threadIdx.x % kFxNT);   // the lane thread x < kFxNT reduces
+    const int kr = kexp[lt];
+    // eight entries (stride `step`) per round: indices and values first, then the gathers
+    auto dot = [&](int64_t e0, int64_t e1, int64_t step, i128 (&acc)[TPL]) {
+        for (int64_t e = e0; e < e1; e += 8 * step) {
+            int32_t ii[8];
+            long long xi[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const bool ok = e + u * step < e1 && BOK(e + u * step, ctl->bb.nnz_x, 63);
+                ii[u] = ok ? row[e + u * step] : 0;
+                xi[u] = ok ? fx_int((XF)Val<VT>::get(val, e + u * step), xs) : 0ll;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t off = (int64_t)ii[u] * kFxNT + t0;
+                if (!BOK(off + TPL - 1, lim, 64)) continue;
+                const longlong2 x = *reinterpret_cast<const longlong2 *>(v + off);
+                acc[0] += (i128)(xi[u] * x.x);
+                acc[1] += (i128)(xi[u] * x.y);
+            }
+        }
+    };
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const Tile tl = tiles[tile];
+        if (tl.lanes > 0) {
+            const int nseg = tl.seg1 - tl.seg0;
+            const int rot = (it * 23 + blockIdx.x) % GPB;
+            for (int sgi = (g - rot + GPB) % GPB; sgi < nseg; sgi += GPB) {
+                const int64_t j = tl.seg0 + sgi;
+                if (!BOK(j, ctl->bb.d, 65)) continue;
+                i128 acc[TPL] = {0, 0};
+                dot(cp[j], cp[j + 1], 1, acc);
+#pragma unroll
+                for (int q = 0; q < TPL; ++q) out[j * kTB + lane0 + t0 + q] = fx_value(acc[q], kq[q], sx);
+            }
+            continue;
+        }
+        i128 acc[TPL] = {0, 0};
+        dot(tl.nz0 + g, tl.nz1, GPB, acc);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TPL; ++q) red[g * kFxNT + t0 + q] = acc[q];
+        __syncthreads();
+        i128 part = 0;
+        if (threadIdx.x < kFxNT)
+            for (int q = 0; q < GPB; ++q) part += red[q * kFxNT + threadIdx.x];
+        if (tl.slot < 0) {
+            if (threadIdx.x < kFxNT && BOK(tl.seg0, ctl->bb.d, 66))
+                out[(int64_t)tl.seg0 * kTB + lt] = fx_value(part, kr, sx);
+            continue;
+        }
+        if (!BOK(tl.slot, ctl->bb.nslots, 67) || !BOK(tl.lseg, ctl->bb.nsplits, 68)) {
+            __syncthreads();
+            continue;
+        }
+        if (threadIdx.x < kFxNT) {
+            slots[(int64_t)tl.slot * kTB + lt] = part;
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) last = (arrive(&lcount[tl.lseg]) == (unsigned)splits[tl.lseg].nchunks - 1u);
+        __syncthreads();
+        if (last && threadIdx.x < kFxNT) {
+            const SplitSeg sp = splits[tl.lseg];
+            i128 tot = 0;
+            for (int q = 0; q < sp.nchunks; ++q) {
+                const long long *p2 = reinterpret_cast<const long long *>(slots + (int64_t)(sp.slot0 + q) * kTB + lt);
+                tot += ((i128)__ldcg(p2 + 1) << 64) | (i128)(unsigned long long)__ldcg(p2);
+            }
+            out[(int64_t)tl.seg0 * kTB + lt] = fx_value(tot, kr, sx);
+            if (threadIdx.x == 0) lcount[tl.lseg] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
 // phase 3b: base recurrence per (feature, target), shift-state stream over the
 // shifts some target still updates, per-target dots; the last block forms
 // alpha_{k+1}, the shift coefficients and the stop tests of every target
@@ -1052,15 +1405,22 @@ __global__ void kb_loop_cond(BatchCtl *ctl, int limit, int nb_iters, cudaGraphCo
     }
 }
 
-// column t of a [len][kTB] block from / to a plain vector
-template <class T>
-__global__ void kb_put(int64_t len, const T *__restrict__ src, T *__restrict__ dst, int t) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i * kTB + t] = src ? src[i] : (T)0;
-}
-__global__ void kb_put_mu32(int64_t len, const double *__restrict__ src, float *__restrict__ dst, int t) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i * kTB + t] = src ? (float)src[i] : 0.f;
+// the source vector of every lane of a [len][kTB] block (NULL: a zero lane)
+template <class S>
+struct LaneSrc {
+    const S *p[kTB];
+};
+
+// dst[i][l] = src.p[l][i] (converted) for i < len, 0 for len <= i < len_dst or a
+// NULL lane: a whole [len_dst][kTB] block in one pass
+template <class S, class T>
+__global__ void __launch_bounds__(kBlock) kb_put_lanes(int64_t len, int64_t len_dst, LaneSrc<S> src, T *__restrict__ dst) {
+    const int64_t m = len_dst * kTB;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m; e += (int64_t)gridDim.x * kBlock) {
+        const int64_t i = e / kTB;
+        const S *q = src.p[e - i * kTB];
+        dst[e] = (q && i < len) ? (T)q[i] : (T)0;
+    }
 }
 // every lane of a [len][kTB] block from one plain vector
 template <class T>
@@ -1098,6 +1458,12 @@ static int grid_for(const void *kernel, int sms, size_t dyn_smem = 0) {
 static int grid_elems_b(int64_t m, int sms) {
     const int64_t g = (m + kBlock - 1) / kBlock;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)sms * 16));
+}
+template <class S, class T>
+static int put_lanes(int64_t len, int64_t len_dst, const LaneSrc<S> &src, T *dst, int sms, cudaStream_t s) {
+    kb_put_lanes<S, T><<<grid_elems_b(len_dst * kTB, sms), kBlock, 0, s>>>(len, len_dst, src, dst);
+    SDA_LAUNCHED();
+    return SDA_OK;
 }
 
 template <class FT>
@@ -1158,6 +1524,12 @@ static int ensure_batch_ws(sda_operator *op, BatchWs *&slot, int ns) {
     SDA_TRY(b.slots.alloc((size_t)std::max(std::max(op->col.nslots, op->col_tail.nslots), 1) * kTB * 2));
     SDA_TRY(b.lcount.alloc((size_t)std::max(std::max(op->col.nsplits, op->col_tail.nsplits), 1)));
     SDA_TRY(b.hparts.alloc((size_t)std::max<int64_t>(1, (int64_t)op->hb.nranges * op->hb.nseg * kTB)));
+    if (fp64) {
+        SDA_TRY(b.fx_planes.alloc((size_t)(std::max(ldw, n8) * kTB)));
+        SDA_TRY(b.fx_amax.alloc(kTB));
+        SDA_TRY(b.fx_k.alloc(kTB));
+    }
+    b.grid_fx1 = b.grid_fx3 = b.grid_fx_head = 0;
     SDA_CUDA(cudaMemset(b.lcount.p, 0, b.lcount.bytes()));
     SDA_TRY(b.sig.alloc(kTB));
     SDA_TRY(b.r2.alloc(kTB));
@@ -1553,18 +1925,19 @@ static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const dou
     }
     if (!b.tuned) SDA_TRY((autotune<VT, FT>(op, b, s)));
     const int64_t d = op->d, n = op->n;
-    const int ge = grid_elems_b(std::max(b.ldw, b.n8), op->sm_count);
-    SDA_CUDA(cudaMemsetAsync(b.b.p, 0, b.b.bytes(), s));
-    SDA_CUDA(cudaMemsetAsync(b.mu64.p, 0, b.mu64.bytes(), s));
-    SDA_CUDA(cudaMemsetAsync(b.mu32.p, 0, b.mu32.bytes(), s));
-    SDA_CUDA(cudaMemsetAsync(b.ylab.p, 0, b.ylab.bytes(), s));
-    for (int i = 0; i < nl; ++i) {
-        const int t = lanes[i].t;
-        kb_put<double><<<ge, kBlock, 0, s>>>(d, lanes[i].b, b.b.p, i);
-        kb_put<double><<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)t * d, b.mu64.p, i);
-        kb_put_mu32<<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)t * d, b.mu32.p, i);
-        kb_put<int8_t><<<ge, kBlock, 0, s>>>(n, op->labels.p + (int64_t)t * n, b.ylab.p, i);
-        SDA_LAUNCHED();
+    {
+        LaneSrc<double> rb{}, mu{};
+        LaneSrc<int8_t> yl{};
+        for (int i = 0; i < nl; ++i) {
+            const int t = lanes[i].t;
+            rb.p[i] = lanes[i].b;
+            mu.p[i] = op->mu.p + (int64_t)t * d;
+            yl.p[i] = op->labels.p + (int64_t)t * n;
+        }
+        SDA_TRY(put_lanes(d, b.ldw, rb, b.b.p, op->sm_count, s));
+        SDA_TRY(put_lanes(d, b.ldw, mu, b.mu64.p, op->sm_count, s));
+        SDA_TRY(put_lanes(d, b.ldw, mu, b.mu32.p, op->sm_count, s));
+        SDA_TRY(put_lanes(n, b.n8, yl, b.ylab.p, op->sm_count, s));
     }
     SolveState *h = b.h_st;
     memset(h, 0, sizeof(SolveState) * kTB);
@@ -1948,6 +2321,111 @@ __global__ void __launch_bounds__(kBlock) kb_cross_dots(int64_t n, int nv, const
     }
 }
 
+// Whether op's X passes can run in fixed point (kb_fx_scan over its values; done
+// once): x = x_int 2^-sx needs sx <= 24 and |x_int| < 2^bx with bx <= 10, so
+// that the scaled vectors keep at least 52 bits
+template <class VT>
+static int fx_examine(sda_operator *op, cudaStream_t s) {
+    if (op->fx_state != 0) return SDA_OK;
+    int lo = 0, hi = 0, bad = 0;
+    if (!std::is_same<VT, Pattern>::value && op->nnz > 0) {
+        DevBuf<int> o;
+        SDA_TRY(o.alloc(3));
+        const int init[3] = {1 << 30, -(1 << 30), 0};
+        SDA_CUDA(cudaMemcpyAsync(o.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+        kb_fx_scan<VT><<<grid_elems_b(op->nnz, op->sm_count), kBlock, 0, s>>>(op->nnz, (const VT *)op->x_val_c.p, o.p);
+        SDA_LAUNCHED();
+        int h[3];
+        SDA_CUDA(cudaMemcpyAsync(h, o.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        SDA_CUDA(cudaStreamSynchronize(s));
+        lo = h[0] == (1 << 30) ? 0 : h[0];
+        hi = h[1] == -(1 << 30) ? 0 : h[1];
+        bad = h[2];
+    }
+    const int sx = std::max(0, -lo), bx = hi + sx + 1;
+    op->fx_sx = sx;
+    op->fx_bx = bx;
+    op->fx_state = (!bad && sx <= 24 && bx <= 10) ? 1 : -1;
+    return SDA_OK;
+}
+
+// z (an FP64 block [len][kTB]) to fixed-point planes in b.fx_planes, scales in b.fx_k
+static int fx_convert(sda_operator *op, BatchWs &b, int64_t len, const double *z, cudaStream_t s) {
+    const int g = grid_elems_b(len * kTB, op->sm_count);
+    SDA_CUDA(cudaMemsetAsync(b.fx_amax.p, 0, kTB * sizeof(unsigned long long), s));
+    kb_absmax_lanes<<<g, kBlock, 0, s>>>(len, z, b.fx_amax.p);
+    SDA_LAUNCHED();
+    kb_to_fixed<<<g, kBlock, 0, s>>>(len, z, b.fx_amax.p, op->fx_bx, b.fx_planes.p, b.fx_k.p);
+    SDA_LAUNCHED();
+    return SDA_OK;
+}
+
+// U = X P - 1 c^T of an FP64 block in fixed point (one launch per plane)
+template <class VT>
+static int fx_rowpass(sda_operator *op, BatchWs &b, const double *p, double *ut, cudaStream_t s) {
+    if (!b.grid_fx1) b.grid_fx1 = grid_for((const void *)kb_phase1_fx<BVT<VT>>, op->sm_count);
+    SDA_TRY(fx_convert(op, b, b.ldw, p, s));
+    for (int h = 0; h < kTB / kFxNT; ++h) {
+        kb_phase1_fx<BVT<VT>><<<b.grid_fx1, kBlock, 0, s>>>(op->n, op->xr_rp.p, op->xr_col.p,
+                                                           (const BVT<VT> *)op->xr_val.p,
+                                                           b.fx_planes.p + h * b.ldw * kFxNT, ut, b.st.p, b.ctl.p,
+                                                           h * kFxNT, op->fx_sx, b.fx_k.p);
+        SDA_LAUNCHED();
+    }
+    return SDA_OK;
+}
+
+// S = X^T V of an FP64 block in fixed point: the head columns from shared-memory
+// slices of the planes, the others with the tile pass (one launch per plane)
+template <class VT>
+static int fx_colpass(sda_operator *op, BatchWs &b, const double *v, double *out, cudaStream_t s) {
+    SDA_TRY(fx_convert(op, b, b.n8, v, s));
+    const long long *pl = b.fx_planes.p;
+    const int64_t H = op->hb.nseg;
+    if (H > 0) {
+        const size_t smem = (size_t)kHeadRows * kFxNT * sizeof(long long);
+        if (!b.grid_fx_head) {
+            SDA_CUDA(cudaFuncSetAttribute((const void *)kb_head3a_fx<BVT<VT>>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            b.grid_fx_head = grid_for((const void *)kb_head3a_fx<BVT<VT>>, op->sm_count, smem);
+        }
+        const int nr = op->hb.nranges;
+        const int nsplit = (int)std::max<int64_t>(
+            1, std::min<int64_t>(H / 64, ((int64_t)b.head_items * b.grid_fx_head + nr - 1) / nr));
+        kb_head3a_fx<BVT<VT>><<<std::min(b.grid_fx_head, nr * nsplit * (kTB / kFxNT)), kBlock, smem, s>>>(
+            op->n, b.n8, nr, (int)H, nsplit, op->hb.cp.p, op->hb.idx.p, (const BVT<VT> *)op->hb.val.p, pl,
+            b.hparts.p, b.ctl.p, op->fx_sx, b.fx_k.p);
+        SDA_LAUNCHED();
+        const int64_t m = H * kTB;
+        kb_head_reduce<double><<<(int)std::min<int64_t>((m + 31) / 32, (int64_t)op->sm_count * 8), kBlock, 0, s>>>(
+            nr, m, b.hparts.p, out, b.ctl.p);
+        SDA_LAUNCHED();
+    }
+    if (!b.grid_fx3) b.grid_fx3 = grid_for((const void *)kb_phase3a_fx<VT>, op->sm_count);
+    for (int h = 0; h < kTB / kFxNT; ++h) {
+        kb_phase3a_fx<VT><<<b.grid_fx3, kBlock, 0, s>>>(op->col_tail.tiles.p, op->col_tail.ntiles, op->x_cp.p + H,
+                                                       op->x_row.p, (const VT *)op->x_val_c.p, pl + h * b.n8 * kFxNT,
+                                                       out + H * kTB, (i128 *)b.slots.p, b.lcount.p,
+                                                       op->col_tail.splits.p, b.ctl.p, h * kFxNT, op->fx_sx, b.fx_k.p);
+        SDA_LAUNCHED();
+    }
+    return SDA_OK;
+}
+
+// the X passes of an FP64 block: fixed point where op's values allow, else FP64
+template <class VT>
+static int rowpass64(sda_operator *op, BatchWs &b, const double *p, double *ut, cudaStream_t s) {
+    SDA_TRY(fx_examine<VT>(op, s));
+    if (op->fx_state > 0) return fx_rowpass<VT>(op, b, p, ut, s);
+    return rowpass_b<VT, double>(op, b, p, ut, b.grid, s);
+}
+template <class VT>
+static int colpass64(sda_operator *op, BatchWs &b, const double *v, double *out, cudaStream_t s) {
+    SDA_TRY(fx_examine<VT>(op, s));
+    if (op->fx_state > 0) return fx_colpass<VT>(op, b, v, out, s);
+    return colpass_b<VT, double>(op, b, v, out, b.grid, s);
+}
+
 template <class VT>
 static int block64_setup(sda_operator *op, BatchWs *&B, double alpha, double omega, cudaStream_t s) {
     SDA_TRY(ensure_batch_ws<double>(op, op->bws64, 1));
@@ -1992,30 +2470,30 @@ static int resid_lanes_t(sda_operator *op, const ResidLane *lanes, int nl, doubl
     SDA_TRY(block64_setup<VT>(op, B, alpha, omega, s));
     BView<double> bv = bview<double>(*B);
     const int64_t d = op->d, n = op->n;
-    const int ge = grid_elems_b(std::max(B->ldw, B->n8), op->sm_count);
-    SDA_CUDA(cudaMemsetAsync(B->b.p, 0, B->b.bytes(), s));
-    SDA_CUDA(cudaMemsetAsync(B->mu64.p, 0, B->mu64.bytes(), s));
-    SDA_CUDA(cudaMemsetAsync(B->ylab.p, 0, B->ylab.bytes(), s));
-    SDA_CUDA(cudaMemsetAsync(bv.p, 0, (size_t)B->ldw * kTB * sizeof(double), s));
     double sig[kTB] = {0};
+    LaneSrc<double> wl{}, rb{}, mu{};
+    LaneSrc<int8_t> yl{};
     for (int l = 0; l < nl; ++l) {
         const int t = lanes[l].t;
         sig[l] = lanes[l].sigma;
-        kb_put<double><<<ge, kBlock, 0, s>>>(d, lanes[l].w, bv.p, l);
-        kb_put<double><<<ge, kBlock, 0, s>>>(d, lanes[l].b, B->b.p, l);
-        kb_put<double><<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)t * d, B->mu64.p, l);
-        kb_put<int8_t><<<ge, kBlock, 0, s>>>(n, op->labels.p + (int64_t)t * n, B->ylab.p, l);
-        SDA_LAUNCHED();
+        wl.p[l] = lanes[l].w;
+        rb.p[l] = lanes[l].b;
+        mu.p[l] = op->mu.p + (int64_t)t * d;
+        yl.p[l] = op->labels.p + (int64_t)t * n;
     }
+    SDA_TRY(put_lanes(d, B->ldw, wl, bv.p, op->sm_count, s));
+    SDA_TRY(put_lanes(d, B->ldw, rb, B->b.p, op->sm_count, s));
+    SDA_TRY(put_lanes(d, B->ldw, mu, B->mu64.p, op->sm_count, s));
+    SDA_TRY(put_lanes(n, B->n8, yl, B->ylab.p, op->sm_count, s));
     SDA_CUDA(cudaMemcpyAsync(B->sig.p, sig, sizeof(sig), cudaMemcpyHostToDevice, s));
     kb_dot_mu<<<B->grid, kBlock, 0, s>>>(d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
     SDA_LAUNCHED();
-    SDA_TRY((rowpass_b<VT, double>(op, *B, bv.p, bv.ut, B->grid, s)));
+    SDA_TRY(rowpass64<VT>(op, *B, bv.p, bv.ut, s));
     kb_phase2<double><<<B->grid, kBlock, 0, s>>>(n, op->s_rp.p, op->s_col.p, op->s_val64.p, bv.ut, op->deg64.p,
                                                 B->ylab.p, bv.v, B->st.p, B->ctl.p, bv.coef, 0, B->part.p,
                                                 B->cnt.p + 1);
     SDA_LAUNCHED();
-    SDA_TRY((colpass_b<VT, double>(op, *B, bv.v, bv.s, B->grid, s)));
+    SDA_TRY(colpass64<VT>(op, *B, bv.v, bv.s, s));
     kb_resid<<<B->grid, kBlock, 0, s>>>(d, nl, B->b.p, B->mu64.p, bv.s, bv.p, B->sig.p, B->st.p, B->ctl.p, B->r2.p,
                                        rvec, B->part.p, B->cnt.p + 2);
     SDA_LAUNCHED();
@@ -2036,16 +2514,14 @@ static int project_block_t(sda_operator *op, const double *Wn, int64_t nvec, dou
     }
     for (int64_t c0 = 0; c0 < nvec; c0 += kTB) {
         const int nv = (int)std::min<int64_t>(kTB, nvec - c0);
-        SDA_CUDA(cudaMemsetAsync(bv.p, 0, (size_t)B->ldw * kTB * sizeof(double), s));
-        for (int v = 0; v < nv; ++v) {
-            kb_put<double><<<ge, kBlock, 0, s>>>(op->d, Wn + (c0 + v) * op->d, bv.p, v);
-            SDA_LAUNCHED();
-        }
+        LaneSrc<double> wl{};
+        for (int v = 0; v < nv; ++v) wl.p[v] = Wn + (c0 + v) * op->d;
+        SDA_TRY(put_lanes(op->d, B->ldw, wl, bv.p, op->sm_count, s));
         if (centred) {
             kb_dot_mu<<<B->grid, kBlock, 0, s>>>(op->d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
             SDA_LAUNCHED();
         }
-        SDA_TRY((rowpass_b<VT, double>(op, *B, bv.p, bv.ut, B->grid, s)));
+        SDA_TRY(rowpass64<VT>(op, *B, bv.p, bv.ut, s));
         kb_unpack<<<ge, kBlock, 0, s>>>(op->n, nv, bv.ut, scores + c0 * op->n);
         SDA_LAUNCHED();
     }
@@ -2062,26 +2538,27 @@ static int adjoint_cross_t(sda_operator *op, const int *targets, int nl, const d
     SDA_TRY(block64_setup<VT>(op, B, 1.0, 0.0, s));   // omega 0, alpha 1: phase 2 gives v = L u
     BView<double> bv = bview<double>(*B);
     const int64_t d = op->d, n = op->n;
-    const int ge = grid_elems_b(std::max(B->ldw, B->n8), op->sm_count);
     DevBuf<double> uw, dots;
     SDA_TRY(uw.alloc((size_t)(B->n8 * kTB)));
     SDA_TRY(dots.alloc(2 * kTB));
-    SDA_CUDA(cudaMemsetAsync(B->mu64.p, 0, B->mu64.bytes(), s));
-    SDA_CUDA(cudaMemsetAsync(B->ylab.p, 0, B->ylab.bytes(), s));
+    {
+        LaneSrc<double> mu{};
+        LaneSrc<int8_t> yl{};
+        for (int l = 0; l < nl; ++l) {
+            mu.p[l] = op->mu.p + (int64_t)targets[l] * d;
+            yl.p[l] = op->labels.p + (int64_t)targets[l] * n;
+        }
+        SDA_TRY(put_lanes(d, B->ldw, mu, B->mu64.p, op->sm_count, s));
+        SDA_TRY(put_lanes(n, B->n8, yl, B->ylab.p, op->sm_count, s));
+    }
     for (int pass = 0; pass < 2; ++pass) {
         const double *src = pass == 0 ? W : Lam;
-        SDA_CUDA(cudaMemsetAsync(bv.p, 0, (size_t)B->ldw * kTB * sizeof(double), s));
-        for (int l = 0; l < nl; ++l) {
-            kb_put<double><<<ge, kBlock, 0, s>>>(d, src + (int64_t)l * d, bv.p, l);
-            if (pass == 0) {
-                kb_put<double><<<ge, kBlock, 0, s>>>(d, op->mu.p + (int64_t)targets[l] * d, B->mu64.p, l);
-                kb_put<int8_t><<<ge, kBlock, 0, s>>>(n, op->labels.p + (int64_t)targets[l] * n, B->ylab.p, l);
-            }
-            SDA_LAUNCHED();
-        }
+        LaneSrc<double> wl{};
+        for (int l = 0; l < nl; ++l) wl.p[l] = src + (int64_t)l * d;
+        SDA_TRY(put_lanes(d, B->ldw, wl, bv.p, op->sm_count, s));
         kb_dot_mu<<<B->grid, kBlock, 0, s>>>(d, B->mu64.p, bv.p, B->st.p, B->ctl.p, B->part.p, B->cnt.p + 0);
         SDA_LAUNCHED();
-        SDA_TRY((rowpass_b<VT, double>(op, *B, bv.p, bv.ut, B->grid, s)));
+        SDA_TRY(rowpass64<VT>(op, *B, bv.p, bv.ut, s));
         if (pass == 0) {
             // u_w = X~ w kept; v = L u_w
             SDA_CUDA(cudaMemcpyAsync(uw.p, bv.ut, (size_t)B->n8 * kTB * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -2096,6 +2573,41 @@ static int adjoint_cross_t(sda_operator *op, const int *targets, int nl, const d
     SDA_LAUNCHED();
     SDA_CUDA(cudaMemcpyAsync(out_host, dots.p, (size_t)nl * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     return block64_check(B, "adjoint contractions", s);
+}
+
+// dst.p[l][j] = s[j][l] for j < len and the lanes with a destination
+__global__ void __launch_bounds__(kBlock) kb_take_lanes(int64_t len, LaneSrc<double> dst, const double *__restrict__ s) {
+    const int64_t m = len * kTB;
+    for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < m; e += (int64_t)gridDim.x * kBlock) {
+        const int64_t j = e / kTB;
+        double *q = const_cast<double *>(dst.p[e - j * kTB]);
+        if (q) q[j] = s[e];
+    }
+}
+
+template <class VT>
+static int xt_lanes_t(sda_operator *op, const double *const *src, int nl, double *const *dst, cudaStream_t s) {
+    BatchWs *B = nullptr;
+    SDA_TRY(block64_setup<VT>(op, B, 0.0, 1.0, s));
+    BView<double> bv = bview<double>(*B);
+    LaneSrc<double> vl{}, dl{};
+    for (int l = 0; l < nl; ++l) {
+        vl.p[l] = src[l];
+        dl.p[l] = dst[l];
+    }
+    SDA_TRY(put_lanes(op->n, B->n8, vl, bv.v, op->sm_count, s));
+    SDA_TRY(colpass64<VT>(op, *B, bv.v, bv.s, s));
+    kb_take_lanes<<<grid_elems_b(op->d * kTB, op->sm_count), kBlock, 0, s>>>(op->d, dl, bv.s);
+    SDA_LAUNCHED();
+    return block64_check(B, "block X^T", s);
+}
+
+int xt_lanes(sda_operator *op, const double *const *src, int nl, double *const *dst, cudaStream_t s) {
+    if (nl < 1 || nl > kTB) return fail(SDA_ERR_INVALID_ARG, "xt_lanes: %d lanes", nl);
+    return with_vt_b(op->compute, [&](auto tag) -> int {
+        using VT = std::remove_pointer_t<decltype(tag)>;
+        return xt_lanes_t<VT>(op, src, nl, dst, s);
+    });
 }
 
 int adjoint_cross(sda_operator *op, const int *targets, int nl, const double *W, const double *Lam, double *out_host,

@@ -735,30 +735,51 @@ static int build(const sda_csr *X, const sda_csr *S, const sda_labels *y, double
         return SDA_OK;
     }
     {
-        DevBuf<double> ip, in_, sp, sn;
+        // class sums X^T 1_+ and X^T 1_- of up to eight targets per FP64 block
+        // column pass (a single target: one plain column pass each)
+        const int tg = T > 1 ? 8 : 1;
+        DevBuf<double> ind, sums;
         DevBuf<unsigned long long> c2;
-        SDA_TRY(ip.alloc((size_t)n));
-        SDA_TRY(in_.alloc((size_t)n));
-        SDA_TRY(sp.alloc((size_t)d));
-        SDA_TRY(sn.alloc((size_t)d));
-        SDA_TRY(c2.alloc(2));
-        for (int64_t t = 0; t < T; ++t) {
-            SDA_CUDA(cudaMemsetAsync(c2.p, 0, 2 * sizeof(unsigned long long), s));
-            k_indicators<<<grid1(n, sms), kBlock, 0, s>>>(n, op->labels.p + t * n, ip.p, in_.p, c2.p);
-            SDA_LAUNCHED();
-            SDA_TRY(op_xtmul_f64(op, ip.p, sp.p, s));
-            SDA_TRY(op_xtmul_f64(op, in_.p, sn.p, s));
-            unsigned long long hc[2];
-            SDA_CUDA(cudaMemcpyAsync(hc, c2.p, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        SDA_TRY(ind.alloc((size_t)(2 * tg * n)));
+        SDA_TRY(sums.alloc((size_t)(2 * tg * d)));
+        SDA_TRY(c2.alloc((size_t)(2 * tg)));
+        for (int64_t t0 = 0; t0 < T; t0 += tg) {
+            const int nt = (int)std::min<int64_t>(tg, T - t0);
+            const double *src[16];
+            double *dst[16];
+            SDA_CUDA(cudaMemsetAsync(c2.p, 0, (size_t)(2 * tg) * sizeof(unsigned long long), s));
+            for (int k = 0; k < nt; ++k) {
+                double *ip = ind.p + (int64_t)(2 * k) * n, *in_ = ip + n;
+                k_indicators<<<grid1(n, sms), kBlock, 0, s>>>(n, op->labels.p + (t0 + k) * n, ip, in_, c2.p + 2 * k);
+                SDA_LAUNCHED();
+                src[2 * k] = ip;
+                src[2 * k + 1] = in_;
+                dst[2 * k] = sums.p + (int64_t)(2 * k) * d;
+                dst[2 * k + 1] = dst[2 * k] + d;
+            }
+            if (T > 1) {
+                SDA_TRY(xt_lanes(op, src, 2 * nt, dst, s));
+            } else {
+                SDA_TRY(op_xtmul_f64(op, src[0], dst[0], s));
+                SDA_TRY(op_xtmul_f64(op, src[1], dst[1], s));
+            }
+            unsigned long long hc[16];
+            SDA_CUDA(cudaMemcpyAsync(hc, c2.p, (size_t)(2 * nt) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
             SDA_CUDA(cudaStreamSynchronize(s));
-            if (hc[0] == 0) return fail(SDA_ERR_NO_POSITIVE, "target %lld has no labelled positive sample", (long long)t);
-            if (hc[1] == 0) return fail(SDA_ERR_NO_NEGATIVE, "target %lld has no labelled negative sample", (long long)t);
-            op->counts[t * 3 + 0] = (double)(hc[0] + hc[1]);
-            op->counts[t * 3 + 1] = (double)hc[0];
-            op->counts[t * 3 + 2] = (double)hc[1];
-            k_means<<<grid1(d, sms), kBlock, 0, s>>>(d, sp.p, sn.p, (double)hc[0], (double)hc[1], op->mu.p + t * d,
-                                                     op->mu32.p + t * d, op->dvec.p + t * d);
-            SDA_LAUNCHED();
+            for (int k = 0; k < nt; ++k) {
+                const int64_t t = t0 + k;
+                if (hc[2 * k] == 0)
+                    return fail(SDA_ERR_NO_POSITIVE, "target %lld has no labelled positive sample", (long long)t);
+                if (hc[2 * k + 1] == 0)
+                    return fail(SDA_ERR_NO_NEGATIVE, "target %lld has no labelled negative sample", (long long)t);
+                op->counts[t * 3 + 0] = (double)(hc[2 * k] + hc[2 * k + 1]);
+                op->counts[t * 3 + 1] = (double)hc[2 * k];
+                op->counts[t * 3 + 2] = (double)hc[2 * k + 1];
+                k_means<<<grid1(d, sms), kBlock, 0, s>>>(d, dst[2 * k], dst[2 * k + 1], (double)hc[2 * k],
+                                                         (double)hc[2 * k + 1], op->mu.p + t * d, op->mu32.p + t * d,
+                                                         op->dvec.p + t * d);
+                SDA_LAUNCHED();
+            }
         }
         SDA_CUDA(cudaStreamSynchronize(s));
     }

@@ -133,6 +133,10 @@ struct sda_operator {
     // run: resident blocks per SM of the row pass, Laplacian pass and tail column pass,
     // and work items per resident block of the head column pass (0: not tuned yet)
     int tuned[4] = {0, 0, 0, 0};
+    // values of X as integers x = x_int 2^-fx_sx with |x_int| < 2^fx_bx, for the
+    // exact fixed-point X passes of the FP64 block utilities; fx_state 0: not
+    // examined yet, 1: they apply, -1: they do not (values too spread; FP64 passes)
+    int fx_state = 0, fx_sx = 0, fx_bx = 0;
     // X in row-major order with rows padded by zero entries (column 0) to whole
     // quads, for the row pass of the iteration; features [0, xr_head) (the most
     // frequent) are gathered from shared memory there
@@ -211,6 +215,9 @@ struct ResidLane {
 // (host array, written before return); rvec (device, optional): the residual vectors [nl][D]
 int resid_lanes(sda_operator *op, const ResidLane *lanes, int nl, double *r2_host, double *rvec, double alpha,
                 double omega, cudaStream_t s);
+// FP64 block of nl <= 16 vectors (sda_batch.cu): dst[l] = X^T src[l] (src: N-vectors, dst:
+// D-vectors, device, permuted order), one column pass for all lanes
+int xt_lanes(sda_operator *op, const double *const *src, int nl, double *const *dst, cudaStream_t s);
 // FP64 block of nl <= 16 targets (sda_batch.cu): per lane l, out_host[2 l] = (X~ lam_l)^T L (X~ w_l),
 // out_host[2 l + 1] = (X~ lam_l)^T P_l (X~ w_l), X~ = X - 1 mu_t^T (W, Lam: [nl][D] device, permuted order)
 int adjoint_cross(sda_operator *op, const int *targets, int nl, const double *W, const double *Lam, double *out_host,

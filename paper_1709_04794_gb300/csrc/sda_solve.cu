@@ -1028,28 +1028,41 @@ extern "C" SDA_API int sda_adjoint_grad_batched(sda_operator *op, int32_t n_targ
     SDA_TRY(wp.alloc((size_t)(T * d)));
     SDA_TRY(cb.alloc((size_t)(T * d)));
     SDA_TRY(lam.alloc((size_t)(T * d)));
-    SDA_TRY(nv.alloc((size_t)n));
+    const int64_t gl = std::min<int64_t>(T, 16);   // targets per FP64 block column pass
+    SDA_TRY(nv.alloc((size_t)(gl * n)));
     SDA_TRY(sc.alloc((size_t)(8 * T)));
     SDA_TRY(err.alloc(1));
-    double *G = nv.p;   // g scattered to the held-out rows
     SDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     SDA_TRY(permute_to_new(op, W, wp.p, T, s));
-    // right-hand sides (X_h - 1 mu^T)^T g = X^T G - mu (1^T G), G = g scattered to the held-out rows
+    // right-hand sides (X_h - 1 mu^T)^T g = X^T G - mu (1^T G), G = g scattered to the
+    // held-out rows; X^T G of up to 16 targets per block column pass
     std::vector<const double *> bl((size_t)T);
-    for (int64_t i = 0; i < T; ++i) {
-        const int64_t r0 = row_off[i], nr = row_off[i + 1] - row_off[i];
-        double *c = cb.p + i * d;
-        SDA_CUDA(cudaMemsetAsync(G, 0, (size_t)n * sizeof(double), s));
-        if (nr > 0) {
-            k_scatter_rows<<<grid_elems(nr, op->sm_count), kBlock, 0, s>>>(nr, rows + r0, dloss_ds + r0, G, n, err.p);
-            SDA_LAUNCHED();
+    for (int64_t i0 = 0; i0 < T; i0 += gl) {
+        const int nl = (int)std::min<int64_t>(gl, T - i0);
+        const double *src[16];
+        double *dst[16];
+        SDA_CUDA(cudaMemsetAsync(nv.p, 0, (size_t)(nl * n) * sizeof(double), s));
+        for (int k = 0; k < nl; ++k) {
+            const int64_t i = i0 + k, r0 = row_off[i], nr = row_off[i + 1] - row_off[i];
+            double *G = nv.p + (int64_t)k * n;   // g scattered to the held-out rows
+            if (nr > 0) {
+                k_scatter_rows<<<grid_elems(nr, op->sm_count), kBlock, 0, s>>>(nr, rows + r0, dloss_ds + r0, G, n,
+                                                                              err.p);
+                SDA_LAUNCHED();
+            }
+            src[k] = G;
+            dst[k] = cb.p + i * d;
         }
-        SDA_TRY(op_xtmul_f64(op, G, c, s));
-        SDA_TRY(dot_f64(op, n, G, nullptr, sc.p + 8 * i, s));
-        k_sub_mu<<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, c, op->mu.p + (int64_t)targets[i] * d,
-                                                               sc.p + 8 * i);
-        SDA_LAUNCHED();
-        bl[(size_t)i] = c;
+        if (nl > 1) SDA_TRY(xt_lanes(op, src, nl, dst, s));
+        else SDA_TRY(op_xtmul_f64(op, src[0], dst[0], s));
+        for (int k = 0; k < nl; ++k) {
+            const int64_t i = i0 + k;
+            SDA_TRY(dot_f64(op, n, src[k], nullptr, sc.p + 8 * i, s));
+            k_sub_mu<<<grid_elems(d, op->sm_count), kBlock, 0, s>>>(d, dst[k], op->mu.p + (int64_t)targets[i] * d,
+                                                                   sc.p + 8 * i);
+            SDA_LAUNCHED();
+            bl[(size_t)i] = dst[k];
+        }
     }
     int herr = 0;
     SDA_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1175,6 +1188,9 @@ extern "C" SDA_API int sda_get_operator_info(const sda_operator *op, sda_operato
     info->head_ranges = op->hb.nseg > 0 ? op->hb.nranges : 0;
     info->head_entries = op->hb.nseg > 0 ? (int64_t)op->hb.idx.n : 0;
     for (int k = 0; k < 4; ++k) info->tuned[k] = op->tuned[k];
+    info->exact_x_passes = op->fx_state;
+    info->x_frac_bits = (int16_t)(op->fx_state != 0 ? op->fx_sx : 0);
+    info->x_int_bits = (int16_t)(op->fx_state != 0 ? op->fx_bx : 0);
     return SDA_OK;
 }
 

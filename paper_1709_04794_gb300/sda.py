@@ -76,7 +76,8 @@ class sda_operator_info(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("omega", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("col_ranges", ctypes.c_int32), ("row_head", ctypes.c_int32), ("col_entries", ctypes.c_int64),
                 ("row_entries", ctypes.c_int64), ("head_cols", ctypes.c_int32), ("head_ranges", ctypes.c_int32),
-                ("head_entries", ctypes.c_int64), ("tuned", ctypes.c_int32 * 4)]
+                ("head_entries", ctypes.c_int64), ("tuned", ctypes.c_int32 * 4), ("exact_x_passes", ctypes.c_int32),
+                ("x_frac_bits", ctypes.c_int16), ("x_int_bits", ctypes.c_int16)]
 
 
 _vp = ctypes.c_void_p

@@ -45,4 +45,5 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sda.sda_solve_opts) == 104
     assert sda.sda_solve_opts.shift_form.offset == 96
     assert ctypes.sizeof(sda.sda_solve_stats) == 112
-    assert ctypes.sizeof(sda.sda_operator_info) == 120
+    assert ctypes.sizeof(sda.sda_operator_info) == 128
+    assert sda.sda_operator_info.exact_x_passes.offset == 120
