@@ -451,9 +451,10 @@ typedef struct {
     int32_t tuned[4];
     /* X passes of the FP64 residual checks, projections and block utilities: 1 when
        they run in exact fixed point (every value of X is x_int 2^-x_frac_bits with
-       |x_int| < 2^x_int_bits, x_frac_bits <= 24, x_int_bits <= 10: products exact in
-       64-bit and sums exact in 128-bit integers, one rounding to FP64 per result),
-       -1 when they run in FP64 arithmetic, 0 until the operator's first such pass */
+       |x_int| < 2^x_int_bits, x_frac_bits <= 24, x_int_bits <= 10, and N, D <
+       2^(32 - x_int_bits): integer products and sums, exact, one rounding to FP64
+       per result), -1 when they run in FP64 arithmetic, 0 until the operator's
+       first such pass */
     int32_t exact_x_passes;
     int16_t x_frac_bits, x_int_bits;
 } sda_operator_info;

@@ -104,7 +104,7 @@ struct BatchWs {
     DevBuf<double> rbuf;       // residual vectors of up to kTB pairs [lane][D] (refinement right-hand sides)
     // FP64 workspaces, fixed-point X passes: the scaled vector as planes
     // [kTB / kFxNT][len][kFxNT], the per-lane max |z| (bit patterns) and scale exponents
-    DevBuf<long long> fx_planes;
+    DevBuf<int2> fx_planes;
     DevBuf<unsigned long long> fx_amax;
     DevBuf<int> fx_k;
     int grid_fx1 = 0, grid_fx3 = 0, grid_fx_head = 0;
@@ -743,14 +743,23 @@ __global__ void __launch_bounds__(kBlock) kb_head_reduce(int nr, int64_t m, cons
 // the values of X are small integers times one power of two (binary and count
 // data: x = x_int 2^-sx, |x_int| < 2^bx), the X passes run on integers instead:
 // a lane's vector z is scaled to z_fx = round(z 2^k) with |z_fx| <= 2^(62 - bx),
-// k set by the lane's largest |z|; each product x_int z_fx is exact in 64 bits,
-// the sums are exact in 128 bits, and each result is rounded to FP64 once. The
-// only other error is the rounding of z to multiples of 2^-k: per entry at most
-// 2^-(k+1) sum_j |x_ij|, i.e. about 2^(bx - 63) max|z| sum_j |x_ij|, no larger
-// than the rounding of an FP64 sum of the same terms.
+// k set by the lane's largest |z|, and stored as two 32-bit halves z_fx =
+// hi 2^31 + lo (0 <= lo < 2^31). Each product is two 32 x 32 -> 64-bit
+// multiply-adds into a 64-bit sum of the lo products and one of the hi products
+// (exact while a sum has fewer than 2^(32 - bx) terms), combined exactly in 128
+// bits and rounded to FP64 once per result. The only other error is the
+// rounding of z to multiples of 2^-k: per entry at most 2^-(k+1) sum_j |x_ij|,
+// i.e. about 2^(bx - 63) max|z| sum_j |x_ij|, no larger than the rounding of an
+// FP64 sum of the same terms.
 using i128 = __int128;
 
-constexpr int kFxNT = 8;                  // lanes per fixed-point plane (64-byte rows)
+// The row and tail column passes gather all 16 lanes of a row of z_fx (128 bytes,
+// one pass; measured against two passes over planes of 8 lanes, 64-byte rows,
+// at 2M x 1M: 988 against 1011 ms per 32-target sweep with its residual check);
+// the head pass stages 8 lanes of a range at a time (96 KB of shared memory)
+constexpr int kFxNT = 16;                 // lanes per row of the scaled block ([len][kFxNT] planes)
+constexpr int kFxHNT = 8;                 // lanes a head work item stages
+constexpr int kFxTPL = 4;                 // lanes per thread in the fixed-point passes
 constexpr int kFxNonFinite = -(1 << 30);  // scale exponent of a lane holding a non-finite value
 
 __device__ __forceinline__ double i128_to_double(i128 a) {
@@ -767,9 +776,19 @@ __device__ __forceinline__ double fx_value(i128 a, int k, int sx) {
 
 // x_int = x 2^sx of a stored value read as XF (exact: x has few significant bits)
 template <class XF>
-__device__ __forceinline__ long long fx_int(XF x, XF xs) {
-    return (long long)(x * xs);
+__device__ __forceinline__ int fx_int(XF x, XF xs) {
+    return (int)(x * xs);
 }
+
+// the two partial sums of a lane: sum x_int lo and sum x_int hi
+struct FxAcc {
+    long long lo = 0, hi = 0;
+    __device__ __forceinline__ void add(int x, int zlo, int zhi) {
+        lo += (long long)x * (long long)zlo;
+        hi += (long long)x * (long long)zhi;
+    }
+    __device__ __forceinline__ i128 total() const { return ((i128)hi << 31) + (i128)lo; }
+};
 
 // amax[l] = max over i < len of |src[i][l]| as its bit pattern (non-negative
 // doubles order as their bits; a NaN or infinity is at least 0x7ff0...)
@@ -796,18 +815,20 @@ __device__ __forceinline__ int fx_exp(unsigned long long amax_bits, int bx) {
     return 62 - bx - e;
 }
 
-// dst planes [kTB / kFxNT][len][kFxNT] of round(src[i][l] 2^k_l); k_l to kexp
+// dst planes [kTB / kFxNT][len][kFxNT] of round(src[i][l] 2^k_l) as {lo, hi}
+// halves; k_l to kexp
 __global__ void __launch_bounds__(kBlock) kb_to_fixed(int64_t len, const double *__restrict__ src,
                                                      const unsigned long long *__restrict__ amax, int bx,
-                                                     long long *__restrict__ dst, int *kexp) {
+                                                     int2 *__restrict__ dst, int *kexp) {
     const int l = threadIdx.x % kTB;
     const int k = fx_exp(amax[l], bx);
     if (blockIdx.x == 0 && threadIdx.x < kTB) kexp[threadIdx.x] = k;
     const int64_t total = len * kTB;
     for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total; e += (int64_t)gridDim.x * kBlock) {
         const int64_t i = e / kTB;
-        const long long q = k == kFxNonFinite ? 0ll : llrint(ldexp(src[e], k));
-        dst[(int64_t)(l / kFxNT) * len * kFxNT + i * kFxNT + (l % kFxNT)] = q;
+        const long long q = k == kFxNonFinite ? 0ll : llrint(ldexp(src[e], k));   // |q| <= 2^(62 - bx)
+        dst[(int64_t)(l / kFxNT) * len * kFxNT + i * kFxNT + (l % kFxNT)] =
+            make_int2((int)(q & 0x7fffffffll), (int)(q >> 31));
     }
 }
 
@@ -842,16 +863,27 @@ __global__ void __launch_bounds__(kBlock) kb_fx_scan(int64_t nnz, const VT *__re
     }
 }
 
+// four lanes' products with one value: z_fx halves of lanes t .. t + 3 at p
+// ({lo, hi} pairs, 32-byte aligned)
+__device__ __forceinline__ void fx_add4(FxAcc (&acc)[4], int x, const int2 *p) {
+    const int4 a = reinterpret_cast<const int4 *>(p)[0];
+    const int4 b = reinterpret_cast<const int4 *>(p)[1];
+    acc[0].add(x, a.x, a.y);
+    acc[1].add(x, a.z, a.w);
+    acc[2].add(x, b.x, b.y);
+    acc[3].add(x, b.z, b.w);
+}
+
 // phase 1 in fixed point: ut[i][t] = (X w_t)_i - c_t for the kFxNT lanes
-// t = lane0 .. lane0 + 7, gathered from one plane wp ([ldw][kFxNT]) of w_fx
+// t = lane0 .., gathered from one plane wp ([ldw][kFxNT]) of w_fx; four lanes per thread
 template <class VT>
-__global__ void __launch_bounds__(kBlock) kb_phase1_fx(int64_t n, const int64_t *__restrict__ rp,
-                                                      const int32_t *__restrict__ col, const VT *__restrict__ val,
-                                                      const long long *__restrict__ wp, double *__restrict__ ut,
-                                                      const SolveState *st, const BatchCtl *ctl, int lane0, int sx,
-                                                      const int *__restrict__ kexp) {
+__global__ void __launch_bounds__(kBlock, 3) kb_phase1_fx(int64_t n, const int64_t *__restrict__ rp,
+                                                         const int32_t *__restrict__ col, const VT *__restrict__ val,
+                                                         const int2 *__restrict__ wp, double *__restrict__ ut,
+                                                         const SolveState *st, const BatchCtl *ctl, int lane0, int sx,
+                                                         const int *__restrict__ kexp) {
     using XF = std::conditional_t<std::is_same<VT, double>::value, double, float>;
-    constexpr int TPL = 2, LG = kFxNT / TPL;
+    constexpr int TPL = kFxTPL, LG = kFxNT / TPL;
     if (ctl->done) return;
     const int lg = threadIdx.x % LG, t0 = lg * TPL;
     double c[TPL];
@@ -868,10 +900,10 @@ __global__ void __launch_bounds__(kBlock) kb_phase1_fx(int64_t n, const int64_t 
     const int4 *__restrict__ colq = reinterpret_cast<const int4 *>(col);
     for (int64_t i = g; i < n; i += ng) {
         const int64_t q0 = rp[i] >> 2, q1 = rp[i + 1] >> 2;
-        i128 acc[TPL] = {0, 0};
+        FxAcc acc[TPL];
         for (int64_t q = q0; q < q1; q += 2) {
             int4 ci[2];
-            long long xi[2][4];
+            int xi[2][4];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 ci[u] = make_int4(0, 0, 0, 0);
@@ -892,32 +924,34 @@ __global__ void __launch_bounds__(kBlock) kb_phase1_fx(int64_t n, const int64_t 
                     const int32_t j = e == 0 ? ci[u].x : e == 1 ? ci[u].y : e == 2 ? ci[u].z : ci[u].w;
                     const int64_t off = (int64_t)j * kFxNT + t0;
                     if (!BOK(off + TPL - 1, lim, 61)) continue;
-                    const longlong2 w = *reinterpret_cast<const longlong2 *>(wp + off);
-                    acc[0] += (i128)(xi[u][e] * w.x);
-                    acc[1] += (i128)(xi[u][e] * w.y);
+                    fx_add4(acc, xi[u][e], wp + off);
                 }
             }
         }
         const int64_t io = i * kTB + lane0 + t0;
-        if (BOK(io + TPL - 1, ctl->bb.n8 * kTB, 62))
-            *reinterpret_cast<double2 *>(ut + io) =
-                make_double2(fx_value(acc[0], kq[0], sx) - c[0], fx_value(acc[1], kq[1], sx) - c[1]);
+        if (BOK(io + TPL - 1, ctl->bb.n8 * kTB, 62)) {
+            double o[TPL];
+#pragma unroll
+            for (int q = 0; q < TPL; ++q) o[q] = fx_value(acc[q].total(), kq[q], sx) - c[q];
+            reinterpret_cast<double2 *>(ut + io)[0] = make_double2(o[0], o[1]);
+            reinterpret_cast<double2 *>(ut + io)[1] = make_double2(o[2], o[3]);
+        }
     }
 }
 
-// head columns in fixed point: as kb_head3a, the range slice of one plane of v_fx
-// ([n8][kFxNT], lanes hf * kFxNT ..) staged in shared memory; hp[r][h][t] gets
-// the range's sum scaled back to FP64
+// head columns in fixed point: as kb_head3a, the range slice of kFxHNT lanes of
+// v_fx (lanes hf * kFxHNT .., from the planes) staged in shared memory; hp[r][h][t]
+// gets the range's sum scaled back to FP64
 template <class VT>
 __global__ void __launch_bounds__(kBlock) kb_head3a_fx(int64_t n, int64_t n8, int nr, int H, int nsplit,
                                                       const int64_t *__restrict__ cp, const uint16_t *__restrict__ idx,
-                                                      const VT *__restrict__ val, const long long *__restrict__ vpl,
+                                                      const VT *__restrict__ val, const int2 *__restrict__ vpl,
                                                       double *__restrict__ hp, const BatchCtl *ctl, int sx,
                                                       const int *__restrict__ kexp) {
     using XF = std::conditional_t<std::is_same<VT, double>::value, double, float>;
-    constexpr int NH = kTB / kFxNT, TPL = 2, LG = kFxNT / TPL, GPB = kBlock / LG;
+    constexpr int NH = kTB / kFxHNT, TPL = kFxTPL, LG = kFxHNT / TPL, GPB = kBlock / LG, VPR = kFxHNT / 2;
     extern __shared__ __align__(16) unsigned char khx_dyn[];
-    long long *vs = reinterpret_cast<long long *>(khx_dyn);
+    int2 *vs = reinterpret_cast<int2 *>(khx_dyn);
     if (ctl->done) return;
     const int lg = threadIdx.x % LG, g = threadIdx.x / LG, t0 = lg * TPL;
     const uint2 *__restrict__ idxq = reinterpret_cast<const uint2 *>(idx);
@@ -931,24 +965,27 @@ __global__ void __launch_bounds__(kBlock) kb_head3a_fx(int64_t n, int64_t n8, in
         const int rows = (int)min((int64_t)kHeadRows, n - row0);
         __syncthreads();
         {
-            // the plane's rows are contiguous: rows x kFxNT values
-            const longlong2 *__restrict__ src =
-                reinterpret_cast<const longlong2 *>(vpl + (int64_t)hf * n8 * kFxNT + row0 * kFxNT);
-            longlong2 *dst = reinterpret_cast<longlong2 *>(vs);
-            const int nvec = rows * (kFxNT / 2);
-            for (int q = threadIdx.x; q < nvec; q += kBlock) dst[q] = src[q];
+            // lanes hf * kFxHNT .. of rows row0 ..: plane pl at offset o within its rows
+            const int pl = (hf * kFxHNT) / kFxNT, o = (hf * kFxHNT) % kFxNT;
+            const int2 *__restrict__ base = vpl + ((int64_t)pl * n8 + row0) * kFxNT + o;
+            int4 *dst = reinterpret_cast<int4 *>(vs);
+            const int nvec = rows * VPR;
+            for (int q = threadIdx.x; q < nvec; q += kBlock) {
+                const int i = q / VPR;
+                dst[q] = reinterpret_cast<const int4 *>(base + (int64_t)i * kFxNT)[q - i * VPR];
+            }
         }
         __syncthreads();
         int kq[TPL];
 #pragma unroll
-        for (int u = 0; u < TPL; ++u) kq[u] = kexp[hf * kFxNT + t0 + u];
+        for (int u = 0; u < TPL; ++u) kq[u] = kexp[hf * kFxHNT + t0 + u];
         const int64_t *__restrict__ c = cp + (int64_t)r * (H + 1);
         for (int h = c0 + g; h < c1; h += GPB) {
             const int64_t q0 = c[h] >> 2, q1 = c[h + 1] >> 2;
-            i128 acc[TPL] = {0, 0};
+            FxAcc acc[TPL];
             for (int64_t q = q0; q < q1; q += 4) {
                 uint2 ii[4];
-                long long xi[4][4];
+                int xi[4][4];
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
                     if (q + w < q1) {
@@ -968,16 +1005,12 @@ __global__ void __launch_bounds__(kBlock) kb_head3a_fx(int64_t n, int64_t n8, in
                     const int li[4] = {(int)(ii[w].x & 0xffffu), (int)(ii[w].x >> 16), (int)(ii[w].y & 0xffffu),
                                        (int)(ii[w].y >> 16)};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const longlong2 x = *reinterpret_cast<const longlong2 *>(vs + li[k] * kFxNT + t0);
-                        acc[0] += (i128)(xi[w][k] * x.x);
-                        acc[1] += (i128)(xi[w][k] * x.y);
-                    }
+                    for (int k = 0; k < 4; ++k) fx_add4(acc, xi[w][k], vs + li[k] * kFxHNT + t0);
                 }
             }
 #pragma unroll
             for (int u = 0; u < TPL; ++u)
-                hp[((int64_t)r * H + h) * kTB + hf * kFxNT + t0 + u] = fx_value(acc[u], kq[u], sx);
+                hp[((int64_t)r * H + h) * kTB + hf * kFxHNT + t0 + u] = fx_value(acc[u].total(), kq[u], sx);
         }
     }
 }
@@ -987,14 +1020,15 @@ __global__ void __launch_bounds__(kBlock) kb_head3a_fx(int64_t n, int64_t n8, in
 // sums stay in 128-bit integers (slots: one i128 per lane) until the column's
 // total is scaled back to FP64
 template <class VT>
-__global__ void __launch_bounds__(kBlock) kb_phase3a_fx(const Tile *__restrict__ tiles, int ntiles,
-                                                       const int64_t *__restrict__ cp, const int32_t *__restrict__ row,
-                                                       const VT *__restrict__ val, const long long *__restrict__ v,
-                                                       double *__restrict__ out, i128 *slots, unsigned *lcount,
-                                                       const SplitSeg *__restrict__ splits, const BatchCtl *ctl,
-                                                       int lane0, int sx, const int *__restrict__ kexp) {
+__global__ void __launch_bounds__(kBlock, 3) kb_phase3a_fx(const Tile *__restrict__ tiles, int ntiles,
+                                                          const int64_t *__restrict__ cp,
+                                                          const int32_t *__restrict__ row, const VT *__restrict__ val,
+                                                          const int2 *__restrict__ v, double *__restrict__ out,
+                                                          i128 *slots, unsigned *lcount,
+                                                          const SplitSeg *__restrict__ splits, const BatchCtl *ctl,
+                                                          int lane0, int sx, const int *__restrict__ kexp) {
     using XF = std::conditional_t<std::is_same<VT, double>::value, double, float>;
-    constexpr int TPL = 2, LG = kFxNT / TPL, GPB = kBlock / LG;
+    constexpr int TPL = kFxTPL, LG = kFxNT / TPL, GPB = kBlock / LG;
     __shared__ i128 red[GPB * kFxNT];
     __shared__ int last;
     if (ctl->done) return;
@@ -1007,23 +1041,21 @@ __global__ void __launch_bounds__(kBlock) kb_phase3a_fx(const Tile *__restrict__
     const int lt = lane0 + (int)(threadIdx.x % kFxNT);   // the lane thread x < kFxNT reduces
     const int kr = kexp[lt];
     // eight entries (stride `step`) per round: indices and values first, then the gathers
-    auto dot = [&](int64_t e0, int64_t e1, int64_t step, i128 (&acc)[TPL]) {
+    auto dot = [&](int64_t e0, int64_t e1, int64_t step, FxAcc (&acc)[TPL]) {
         for (int64_t e = e0; e < e1; e += 8 * step) {
             int32_t ii[8];
-            long long xi[8];
+            int xi[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const bool ok = e + u * step < e1 && BOK(e + u * step, ctl->bb.nnz_x, 63);
                 ii[u] = ok ? row[e + u * step] : 0;
-                xi[u] = ok ? fx_int((XF)Val<VT>::get(val, e + u * step), xs) : 0ll;
+                xi[u] = ok ? fx_int((XF)Val<VT>::get(val, e + u * step), xs) : 0;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int64_t off = (int64_t)ii[u] * kFxNT + t0;
                 if (!BOK(off + TPL - 1, lim, 64)) continue;
-                const longlong2 x = *reinterpret_cast<const longlong2 *>(v + off);
-                acc[0] += (i128)(xi[u] * x.x);
-                acc[1] += (i128)(xi[u] * x.y);
+                fx_add4(acc, xi[u], v + off);
             }
         }
     };
@@ -1036,18 +1068,18 @@ __global__ void __launch_bounds__(kBlock) kb_phase3a_fx(const Tile *__restrict__
             for (int sgi = (g - rot + GPB) % GPB; sgi < nseg; sgi += GPB) {
                 const int64_t j = tl.seg0 + sgi;
                 if (!BOK(j, ctl->bb.d, 65)) continue;
-                i128 acc[TPL] = {0, 0};
+                FxAcc acc[TPL];
                 dot(cp[j], cp[j + 1], 1, acc);
 #pragma unroll
-                for (int q = 0; q < TPL; ++q) out[j * kTB + lane0 + t0 + q] = fx_value(acc[q], kq[q], sx);
+                for (int q = 0; q < TPL; ++q) out[j * kTB + lane0 + t0 + q] = fx_value(acc[q].total(), kq[q], sx);
             }
             continue;
         }
-        i128 acc[TPL] = {0, 0};
+        FxAcc acc[TPL];
         dot(tl.nz0 + g, tl.nz1, GPB, acc);
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < TPL; ++q) red[g * kFxNT + t0 + q] = acc[q];
+        for (int q = 0; q < TPL; ++q) red[g * kFxNT + t0 + q] = acc[q].total();
         __syncthreads();
         i128 part = 0;
         if (threadIdx.x < kFxNT)
@@ -2323,7 +2355,8 @@ __global__ void __launch_bounds__(kBlock) kb_cross_dots(int64_t n, int nv, const
 
 // Whether op's X passes can run in fixed point (kb_fx_scan over its values; done
 // once): x = x_int 2^-sx needs sx <= 24 and |x_int| < 2^bx with bx <= 10, so
-// that the scaled vectors keep at least 52 bits
+// that the scaled vectors keep at least 52 bits, and sums of fewer than
+// 2^(32 - bx) products (rows and columns of X shorter than that)
 template <class VT>
 static int fx_examine(sda_operator *op, cudaStream_t s) {
     if (op->fx_state != 0) return SDA_OK;
@@ -2345,7 +2378,8 @@ static int fx_examine(sda_operator *op, cudaStream_t s) {
     const int sx = std::max(0, -lo), bx = hi + sx + 1;
     op->fx_sx = sx;
     op->fx_bx = bx;
-    op->fx_state = (!bad && sx <= 24 && bx <= 10) ? 1 : -1;
+    const int64_t longest = std::max(op->n, op->d);   // bounds every row and column of X
+    op->fx_state = (!bad && sx <= 24 && bx <= 10 && longest < (int64_t(1) << (32 - bx))) ? 1 : -1;
     return SDA_OK;
 }
 
@@ -2380,10 +2414,10 @@ static int fx_rowpass(sda_operator *op, BatchWs &b, const double *p, double *ut,
 template <class VT>
 static int fx_colpass(sda_operator *op, BatchWs &b, const double *v, double *out, cudaStream_t s) {
     SDA_TRY(fx_convert(op, b, b.n8, v, s));
-    const long long *pl = b.fx_planes.p;
+    const int2 *pl = b.fx_planes.p;
     const int64_t H = op->hb.nseg;
     if (H > 0) {
-        const size_t smem = (size_t)kHeadRows * kFxNT * sizeof(long long);
+        const size_t smem = (size_t)kHeadRows * kFxHNT * sizeof(int2);
         if (!b.grid_fx_head) {
             SDA_CUDA(cudaFuncSetAttribute((const void *)kb_head3a_fx<BVT<VT>>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2392,7 +2426,7 @@ static int fx_colpass(sda_operator *op, BatchWs &b, const double *v, double *out
         const int nr = op->hb.nranges;
         const int nsplit = (int)std::max<int64_t>(
             1, std::min<int64_t>(H / 64, ((int64_t)b.head_items * b.grid_fx_head + nr - 1) / nr));
-        kb_head3a_fx<BVT<VT>><<<std::min(b.grid_fx_head, nr * nsplit * (kTB / kFxNT)), kBlock, smem, s>>>(
+        kb_head3a_fx<BVT<VT>><<<std::min(b.grid_fx_head, nr * nsplit * (kTB / kFxHNT)), kBlock, smem, s>>>(
             op->n, b.n8, nr, (int)H, nsplit, op->hb.cp.p, op->hb.idx.p, (const BVT<VT> *)op->hb.val.p, pl,
             b.hparts.p, b.ctl.p, op->fx_sx, b.fx_k.p);
         SDA_LAUNCHED();
