@@ -48,7 +48,8 @@ UNIT = "solves/s"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cg_kernels_single_mixed_200k.md")
 LARGE_PROFILE = os.path.join(ROOT, "profiles", "batched_kernels_large_1000t_2m.md")
 FIXED_ITERS = 70                  # iterations per solve in the fixed-iteration protocol (Sec. 5.2)
-CHUNK = 32                        # targets per step of the large workload (two batches of 16)
+CHUNK = 32                        # targets per chunk of the large workload (two batches of 16)
+STREAMS = 1                       # chunks of the large workload in flight per step
 
 
 def parse():
@@ -70,7 +71,9 @@ def parse():
                          "16 cores)")
     ap.add_argument("--fixed-iters", type=int, default=FIXED_ITERS,
                     help="large workload: shifted-CG iterations per solve (the fixed-iteration protocol)")
-    ap.add_argument("--chunk", type=int, default=CHUNK, help="large workload: targets per step")
+    ap.add_argument("--chunk", type=int, default=CHUNK, help="large workload: targets per chunk")
+    ap.add_argument("--streams", type=int, default=STREAMS,
+                    help="large workload: chunks in flight at once, one CUDA stream each (a step = that many chunks)")
     ap.add_argument("--workload", default=LARGE,
                     help="large_1000t_2m (default): 2M x 1M, 1,000 targets, 24 shifts, 70 iterations per "
                          "solve; single_mixed_200k: one target converged to tol; batched_256t_200k: 256 targets "
@@ -716,26 +719,30 @@ def run_large(args, rank, world, local):
         o.target_count, o.profile = cnt, profile
         return o
 
-    def build(inputs, t0, cnt, comp=compute):
+    def build(inputs, t0, cnt, comp=compute, st=stream):
         return sda.sda_build_operator(inputs["x_ptr"], inputs["x_col"], inputs["x_val"], d, inputs["s_ptr"],
                                       inputs["s_col"], inputs["s_val"], inputs["labels"][t0:t0 + cnt],
-                                      prob.alpha, float("nan"), comp, stream)
+                                      prob.alpha, float("nan"), comp, st)
 
-    def mark(marks):
+    def mark(marks, st=stream):
         if marks is not None:
             e = torch.cuda.Event(enable_timing=True)
-            e.record(stream)
+            e.record(st)
             marks.append(e)
 
-    def step(k, inputs=dev, hold=held, marks=None):
+    def step(k, inputs=dev, hold=held, marks=None, stream=stream, w=w):
+        with torch.cuda.stream(stream):
+            return step_on(k, inputs, hold, marks, stream, w)
+
+    def step_on(k, inputs, hold, marks, stream, w):
         t0, cnt = chunks[k % len(chunks)]
-        mark(marks)
-        h = build(inputs, t0, cnt)
-        mark(marks)
+        mark(marks, stream)
+        h = build(inputs, t0, cnt, st=stream)
+        mark(marks, stream)
         try:
             code, rep = sda.sda_solve_shifts(h, prob.shifts, solve_opts(cnt), w_out=w[:cnt], n_report=cnt,
                                              stream=stream)
-            mark(marks)
+            mark(marks, stream)
             r0, r1 = int(off_all[t0]), int(off_all[t0 + cnt])
             rows = hold["rows"][r0:r1].to("cuda", non_blocking=True)
             y = hold["y"][r0:r1].to("cuda", non_blocking=True)
@@ -755,21 +762,49 @@ def run_large(args, rank, world, local):
                 yi = y[off[i]:off[i + 1]]
                 g[off[i]:off[i + 1]] = -yi * torch.sigmoid(-yi * scs[i][best[i]]) / yi.numel()
                 wb[i] = w[i, best[i]]
-            mark(marks)
+            mark(marks, stream)
             oa = sda.sda_default_opts()
             oa.fixed_iters = args.fixed_iters
             code_a, da, db, rep_a = sda.sda_adjoint_grad_batched(h, list(range(cnt)), float("nan"),
                                                                  [float(prob.shifts[b]) for b in best], wb, g,
                                                                  rows, off, oa, stream=stream)
-            mark(marks)
+            mark(marks, stream)
             lh = losses.cpu().numpy()
         finally:
             sda.sda_destroy_operator(h)
-        mark(marks)
+        mark(marks, stream)
         return {"code": code, "rep": rep, "best": best, "da": da, "db": db, "losses": lh, "t0": t0, "cnt": cnt}
 
+    # args.streams chunks in flight at once, each on its own CUDA stream and host thread
+    # (the library's calls release the interpreter lock; operators and workspaces are per chunk)
+    S = max(1, args.streams)
+    streams = [stream] + [torch.cuda.Stream() for _ in range(S - 1)]
+    wbufs = [w] + [torch.empty_like(w) for _ in range(S - 1)]
+
+    def steps(k):
+        if S == 1:
+            return [step(k)]
+        res, errs = [None] * S, []
+
+        def run(j):
+            try:
+                res[j] = step(k * S + j, stream=streams[j], w=wbufs[j])
+            except BaseException as e:      # re-raised on the main thread
+                errs.append(e)
+
+        th = [threading.Thread(target=run, args=(j,)) for j in range(S)]
+        for t_ in th:
+            t_.start()
+        for t_ in th:
+            t_.join()
+        if errs:
+            raise errs[0]
+        for st in streams[1:]:
+            stream.wait_stream(st)
+        return res
+
     for k in range(args.warmup):
-        step(k)
+        steps(k)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -779,7 +814,7 @@ def run_large(args, rank, world, local):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    outs = [step(args.warmup + k) for k in range(args.steps)]
+    outs = [o for k in range(args.steps) for o in steps(args.warmup + k)]
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -990,6 +1025,7 @@ def run_large(args, rank, world, local):
                 "config": {"workload": args.workload, "n": n, "d": d, "nnz": int(prob.x_ptr[-1]),
                            "graph_nnz": int(prob.s_ptr[-1]), "targets": T_all, "shifts": ns,
                            "x_storage": compute, "fixed_iters": args.fixed_iters, "chunk": C, "batch": 16,
+                           "streams": S,
                            "targets_per_run": solved, "alpha": prob.alpha,
                            "parallelism": "targets sharded over %d GPU(s), no exchange" % world,
                            "status": last["code"],

@@ -354,15 +354,23 @@ __global__ void __launch_bounds__(kBlock) kb_formp(int64_t d, int64_t ldw, const
     }
 }
 
+// Targets per thread of the batched row pass and its resident-block floor: the
+// per-entry work (index, value, bound check) is shared by a thread's targets, so
+// FP32 takes eight (two 16-byte gathers), FP64 two
+template <class FT>
+struct RowLanes {
+    static constexpr int TPL = sizeof(FT) == 4 ? 8 : 2;
+    static constexpr int min_blocks = sizeof(FT) == 4 ? 4 : 1;
+};
+
 // phase 1: ut[i][t] = (X p_k,t)_i - <mu_t, p_k,t>
 template <class VT, class FT>
-__global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase1(int64_t n, int64_t ldw, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(kBlock, RowLanes<FT>::min_blocks) kb_phase1(int64_t n, int64_t ldw, const int64_t *__restrict__ rp,
                                                    const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                    const FT *__restrict__ p, FT *__restrict__ ut,
                                                    const SolveState *st, const BatchCtl *ctl) {
-    using L = BLanes<FT>;
-    using V = typename L::V;
-    constexpr int TPL = L::TPL, LG = L::LG;
+    using V = typename Vec16<FT>::T;
+    constexpr int TPL = RowLanes<FT>::TPL, VN = Vec16<FT>::n, NV = TPL / VN, LG = kTB / TPL;
     if (ctl->done) return;
     const int lg = threadIdx.x % LG, t0 = lg * TPL;
     FT c[TPL];
@@ -400,7 +408,9 @@ __global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase1(int6
                     const int64_t off = (int64_t)j * kTB + t0;
                     if (!BOK(off + TPL - 1, lim, 12)) continue;
                     FT x[TPL];
-                    *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(p + off);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        *reinterpret_cast<V *>(x + v * VN) = *reinterpret_cast<const V *>(p + off + v * VN);
 #pragma unroll
                     for (int t = 0; t < TPL; ++t) acc[t] += xv[u][e] * x[t];
                 }
@@ -411,7 +421,8 @@ __global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase1(int6
             FT o[TPL];
 #pragma unroll
             for (int q = 0; q < TPL; ++q) o[q] = acc[q] - c[q];
-            *reinterpret_cast<V *>(ut + io) = *reinterpret_cast<const V *>(o);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) *reinterpret_cast<V *>(ut + io + v * VN) = *reinterpret_cast<const V *>(o + v * VN);
         }
     }
 }
@@ -523,17 +534,16 @@ __global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase2(int6
 // long column's chunk); the four products of a step summed plainly, the steps
 // compensated; written as parts
 template <class VT, class FT>
-__global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase3a(const Tile *__restrict__ tiles, int ntiles,
+__global__ void __launch_bounds__(kBlock, RowLanes<FT>::min_blocks) kb_phase3a(const Tile *__restrict__ tiles, int ntiles,
                                                     const int64_t *__restrict__ cp, const int32_t *__restrict__ row,
                                                     const VT *__restrict__ val, const FT *__restrict__ v,
                                                     typename CompSum<FT>::Part *__restrict__ out,
                                                     typename CompSum<FT>::Part *slots, unsigned *lcount,
                                                     const SplitSeg *__restrict__ splits, const BatchCtl *ctl) {
-    using L = BLanes<FT>;
-    using V = typename L::V;
+    using V = typename Vec16<FT>::T;
     using CS = CompSum<FT>;
     using Part = typename CS::Part;
-    constexpr int TPL = L::TPL, LG = L::LG, GPB = kBlock / LG;
+    constexpr int TPL = RowLanes<FT>::TPL, VN = Vec16<FT>::n, NV = TPL / VN, LG = kTB / TPL, GPB = kBlock / LG;
     __shared__ Part red[GPB * kTB];
     __shared__ int last;
     if (ctl->done) return;
@@ -563,7 +573,9 @@ __global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase3a(con
                     const int64_t off = (int64_t)ii[u] * kTB + t0;
                     if (!BOK(off + TPL - 1, lim, 32)) continue;
                     FT x[TPL];
-                    *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(v + off);
+#pragma unroll
+                    for (int w = 0; w < NV; ++w)
+                        *reinterpret_cast<V *>(x + w * VN) = *reinterpret_cast<const V *>(v + off + w * VN);
 #pragma unroll
                     for (int q = 0; q < TPL; ++q) sum[q] += vv[u] * x[q];
                 }
@@ -769,9 +781,14 @@ __device__ __forceinline__ double i128_to_double(i128 a) {
     return (double)hi * 18446744073709551616.0 + (double)lo;          // |a| >= 2^63: within 2^-52 |a|
 }
 
-// a result scaled back: a 2^-(k + sx), NaN for a non-finite lane
+// a result scaled back: a 2^-(k + sx), NaN for a non-finite lane (2^-(k + sx) built
+// from its exponent bits when it is a normal double, as it is for every vector
+// whose largest entry lies between 2^-950 and 2^1000)
 __device__ __forceinline__ double fx_value(i128 a, int k, int sx) {
-    return k == kFxNonFinite ? (double)NAN : ldexp(i128_to_double(a), -(k + sx));
+    if (k == kFxNonFinite) return (double)NAN;
+    const int e = k + sx;
+    if (e > -1000 && e < 1000) return i128_to_double(a) * __longlong_as_double((long long)(1023 - e) << 52);
+    return ldexp(i128_to_double(a), -e);
 }
 
 // x_int = x 2^sx of a stored value read as XF (exact: x has few significant bits)
@@ -941,7 +958,8 @@ __global__ void __launch_bounds__(kBlock, 3) kb_phase1_fx(int64_t n, const int64
 
 // head columns in fixed point: as kb_head3a, the range slice of kFxHNT lanes of
 // v_fx (lanes hf * kFxHNT .., from the planes) staged in shared memory; hp[r][h][t]
-// gets the range's sum scaled back to FP64
+// gets the range's sum scaled back to FP64; two lanes per thread (measured faster
+// here than four: 1.90 against 2.16 ms per launch at 2M x 1M)
 template <class VT>
 __global__ void __launch_bounds__(kBlock) kb_head3a_fx(int64_t n, int64_t n8, int nr, int H, int nsplit,
                                                       const int64_t *__restrict__ cp, const uint16_t *__restrict__ idx,
@@ -949,7 +967,7 @@ __global__ void __launch_bounds__(kBlock) kb_head3a_fx(int64_t n, int64_t n8, in
                                                       double *__restrict__ hp, const BatchCtl *ctl, int sx,
                                                       const int *__restrict__ kexp) {
     using XF = std::conditional_t<std::is_same<VT, double>::value, double, float>;
-    constexpr int NH = kTB / kFxHNT, TPL = kFxTPL, LG = kFxHNT / TPL, GPB = kBlock / LG, VPR = kFxHNT / 2;
+    constexpr int NH = kTB / kFxHNT, TPL = 2, LG = kFxHNT / TPL, GPB = kBlock / LG, VPR = kFxHNT / 2;
     extern __shared__ __align__(16) unsigned char khx_dyn[];
     int2 *vs = reinterpret_cast<int2 *>(khx_dyn);
     if (ctl->done) return;
@@ -1005,7 +1023,11 @@ __global__ void __launch_bounds__(kBlock) kb_head3a_fx(int64_t n, int64_t n8, in
                     const int li[4] = {(int)(ii[w].x & 0xffffu), (int)(ii[w].x >> 16), (int)(ii[w].y & 0xffffu),
                                        (int)(ii[w].y >> 16)};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) fx_add4(acc, xi[w][k], vs + li[k] * kFxHNT + t0);
+                    for (int k = 0; k < 4; ++k) {
+                        const int4 x = *reinterpret_cast<const int4 *>(vs + li[k] * kFxHNT + t0);
+                        acc[0].add(xi[w][k], x.x, x.y);
+                        acc[1].add(xi[w][k], x.z, x.w);
+                    }
                 }
             }
 #pragma unroll
