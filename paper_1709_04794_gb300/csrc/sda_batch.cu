@@ -430,16 +430,15 @@ __global__ void __launch_bounds__(kBlock, RowLanes<FT>::min_blocks) kb_phase1(in
 // phase 2: v = omega P_l ut + alpha (D ut - S ut) per target; <ut, v>, 1^T v;
 // the last block forms gamma_k per target and the (shift, target) coefficients
 template <class FT>
-__global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase2(int64_t n, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(kBlock, RowLanes<FT>::min_blocks) kb_phase2(int64_t n, const int64_t *__restrict__ rp,
                                                    const int32_t *__restrict__ col, const FT *__restrict__ sval,
                                                    const FT *__restrict__ ut, const FT *__restrict__ deg,
                                                    const int8_t *__restrict__ ylab, FT *__restrict__ v,
                                                    SolveState *st, BatchCtl *ctl, BatchCoef<FT> *coef, int ns,
                                                    double *partials, unsigned *counter) {
-    using L = BLanes<FT>;
-    using V = typename L::V;
+    using V = typename Vec16<FT>::T;
     using Part = typename CompSum<FT>::Part;
-    constexpr int TPL = L::TPL, LG = L::LG;
+    constexpr int TPL = RowLanes<FT>::TPL, VN = Vec16<FT>::n, NV = TPL / VN, LG = kTB / TPL;
     __shared__ Part red[kBlock * 2];
     if (ctl->done) return;
     const int lg = threadIdx.x % LG, t0 = lg * TPL;
@@ -467,7 +466,9 @@ __global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase2(int6
                 const int64_t off = (int64_t)jj[u] * kTB + t0;
                 if (!BOK(off + TPL - 1, lim, 22)) continue;
                 FT x[TPL];
-                *reinterpret_cast<V *>(x) = *reinterpret_cast<const V *>(ut + off);
+#pragma unroll
+                for (int w = 0; w < NV; ++w)
+                    *reinterpret_cast<V *>(x + w * VN) = *reinterpret_cast<const V *>(ut + off + w * VN);
 #pragma unroll
                 for (int q = 0; q < TPL; ++q) acc[q] += vv[u] * x[q];
             }
@@ -475,7 +476,8 @@ __global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase2(int6
         const int64_t io = i * kTB + t0;
         if (!BOK(io + TPL - 1, lim, 23)) continue;
         FT u[TPL], vo[TPL];
-        *reinterpret_cast<V *>(u) = *reinterpret_cast<const V *>(ut + io);
+#pragma unroll
+        for (int w = 0; w < NV; ++w) *reinterpret_cast<V *>(u + w * VN) = *reinterpret_cast<const V *>(ut + io + w * VN);
         const FT dg = deg[i];
 #pragma unroll
         for (int q = 0; q < TPL; ++q) {
@@ -484,7 +486,8 @@ __global__ void __launch_bounds__(kBlock, KbMinBlocks<FT>::value) kb_phase2(int6
             dd[0][q].add(u[q] * vo[q]);
             dd[1][q].add(vo[q]);
         }
-        *reinterpret_cast<V *>(v + io) = *reinterpret_cast<const V *>(vo);
+#pragma unroll
+        for (int w = 0; w < NV; ++w) *reinterpret_cast<V *>(v + io + w * VN) = *reinterpret_cast<const V *>(vo + w * VN);
     }
     Part mine[2];
     block_tparts_v<2, TPL, FT>(dd, mine, red);
