@@ -949,12 +949,12 @@ def run_large(args, rank, world, local):
         first = outs[0] if outs[0]["t0"] == t0c else step(0)
         nchk = min(2, nb)
         for i in range(nchk):
-            t = t0c + i
+            tg = t0c + i
             c0 = time.perf_counter()
-            W, tres, best, da, db, _ = oracle_step(prob, t, args.fixed_iters, X)
+            W, tres, best, da, db, _ = oracle_step(prob, tg, args.fixed_iters, X)
             times.append(time.perf_counter() - c0)
-            rows = prob.heldout[t]
-            y = prob.truth[t][rows]
+            rows = prob.heldout[tg]
+            y = prob.truth[tg][rows]
             for s in range(ns):
                 ref = W[s]
                 rel = float(np.linalg.norm(w_mix[i, s] - ref) / np.linalg.norm(ref))
