@@ -46,7 +46,6 @@ LARGE_WORKLOADS = (LARGE, "adjoint_64t_500k")   # run by run_large (the same ste
 METRIC = "SDA solves/s (all shifts)"
 UNIT = "solves/s"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cg_kernels_single_mixed_200k.md")
-LARGE_PROFILE = os.path.join(ROOT, "profiles", "batched_kernels_large_1000t_2m.md")
 FIXED_ITERS = 70                  # iterations per solve in the fixed-iteration protocol (Sec. 5.2)
 CHUNK = 32                        # targets per chunk of the large workload (two batches of 16)
 STREAMS = 2                       # chunks of the large workload in flight per step (own streams)
@@ -843,7 +842,6 @@ def run_large(args, rank, world, local):
 
     def timed_solve(comp, profile=0, keep_w=False):
         h = build(dev, t0c, nb, comp)
-        info = sda.sda_get_operator_info(h)
         try:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -853,6 +851,7 @@ def run_large(args, rank, world, local):
             e1.record(stream)
             torch.cuda.synchronize()
             st = sda.sda_get_solve_stats(h)
+            info = sda.sda_get_operator_info(h)      # after the solve: the schedule it ran
             w_first = w[:nb].cpu().numpy() if keep_w else None
             # the same sweep without the residual check (the iteration kernels alone, graphs)
             e2 = torch.cuda.Event(enable_timing=True)
@@ -886,12 +885,16 @@ def run_large(args, rank, world, local):
     achieved = per[dominant] / (durs[dominant] * 1e-3) / 1e9
     whole = (sum(per.values()) + once / bi) / (it_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(dominant, LARGE_PROFILE), "kernel": names[dominant],
+                "traffic": recorded_traffic(dominant, os.path.join(ROOT, "profiles", "batched_kernels_%s.md" % args.workload)),
+                "kernel": names[dominant],
                 "peak_kind": peak_kind, "bytes_per_launch": per[dominant], "ms_per_launch": durs[dominant],
                 "whole_iteration": {"GB/s": whole, "frac": whole / peak, "bytes": sum(per.values()) + once / bi,
                                     "ms": it_ms,
                                     "shift_form": "stored basis (W = V Y once per run, its bytes amortised)"
                                     if basis else "recurrences"},
+                "schedule": {"blocks_per_sm_rows_of_x": info["tuned"][0], "blocks_per_sm_rows_of_s": info["tuned"][1],
+                             "blocks_per_sm_tail_columns": info["tuned"][2],
+                             "head_items_per_block": info["tuned"][3], "note": "autotuned; head items -1: no head pass"},
                 "durations": "graph-replayed sweep of one batch of 16 targets / iterations, apportioned by the "
                              "event-timed shares of the four kernels",
                 "all_kernels": {names[k]: {"ms_per_launch": durs[k], "GB/s": per[k] / (durs[k] * 1e-3) / 1e9,

@@ -447,7 +447,7 @@ typedef struct {
     /* schedule of the batched sparse passes picked by the autotuner on the operator's
        first batched run (0 until then): resident blocks per SM of the row pass, the
        Laplacian pass and the tail column pass, and work items per resident block of
-       the head column pass */
+       the head column pass (-1: no head pass, every column through the tile pass) */
     int32_t tuned[4];
     /* X passes of the FP64 residual checks, projections and block utilities: 1 when
        they run in exact fixed point (every value of X is x_int 2^-x_frac_bits with

@@ -124,7 +124,7 @@ struct BatchWs {
     int grid1 = 0, grid2 = 0, grid3a = 0;  // their own grids (occupancy of each)
     int grid_head = 0;                     // grid of the head column pass
     bool head_ready = false;               // its shared-memory attribute set
-    int head_items = 4;                    // head pass: work items per resident block (tuned)
+    int head_items = 4;                    // head pass: work items per resident block (tuned; 0: no head pass)
     bool tuned = false;                    // the schedule of the sparse passes has been picked
     cudaGraphExec_t loop = nullptr;        // device-driven loop: a WHILE node over loop_iters iterations
     int loop_iters = 0, loop_ns = 0, loop_basis = -1, loop_limit = -1;
@@ -1656,7 +1656,10 @@ template <class VT, class FT>
 static int colpass_b(sda_operator *op, BatchWs &b, const FT *v, typename CompSum<FT>::Part *out, int grid_tail,
                      cudaStream_t s) {
     using Part = typename CompSum<FT>::Part;
-    const int64_t H = op->hb.nseg;
+    // head_items 0 (the autotuner's choice where the tile pass alone is faster): every
+    // column through the tile pass over the operator's full column schedule
+    const int64_t H = b.head_items > 0 ? op->hb.nseg : 0;
+    const ColSchedule &cs = H > 0 ? op->col_tail : op->col;
     if (H > 0) {
         const size_t smem = (size_t)kHeadRows * kTB * sizeof(FT);
         if (!b.head_ready) {
@@ -1681,9 +1684,9 @@ static int colpass_b(sda_operator *op, BatchWs &b, const FT *v, typename CompSum
             op->hb.nranges, m, (const Part *)b.hparts.p, out, b.ctl.p);
         SDA_LAUNCHED();
     }
-    kb_phase3a<VT, FT><<<grid_tail, kBlock, 0, s>>>(op->col_tail.tiles.p, op->col_tail.ntiles, op->x_cp.p + H,
-                                                    op->x_row.p, (const VT *)op->x_val_c.p, v, out + H * kTB,
-                                                    (Part *)b.slots.p, b.lcount.p, op->col_tail.splits.p, b.ctl.p);
+    kb_phase3a<VT, FT><<<grid_tail, kBlock, 0, s>>>(cs.tiles.p, cs.ntiles, op->x_cp.p + H, op->x_row.p,
+                                                    (const VT *)op->x_val_c.p, v, out + H * kTB, (Part *)b.slots.p,
+                                                    b.lcount.p, cs.splits.p, b.ctl.p);
     SDA_LAUNCHED();
     return SDA_OK;
 }
@@ -1698,7 +1701,9 @@ static int rowpass_b(sda_operator *op, BatchWs &b, const FT *p, FT *ut, int grid
 }
 
 // launches of colpass_b
-static int colpass_launches(const sda_operator *op) { return op->hb.nseg > 0 ? 3 : 1; }
+static int colpass_launches(const sda_operator *op, const BatchWs &b) {
+    return op->hb.nseg > 0 && b.head_items > 0 ? 3 : 1;
+}
 
 // `ev` (profile mode): a start and an end event around each of the four kernels
 template <class VT, class FT>
@@ -1916,8 +1921,10 @@ static int autotune(sda_operator *op, BatchWs &b, cudaStream_t s) {
         }
         tv.head_items = 4;
         if (op->hb.nseg > 0) {
+            // head columns from shared-memory range slices (items per resident block
+            // 1..8), or no head pass at all: every column through the tile pass
             float besth = 1e30f;
-            for (int items : {1, 2, 4, 8}) {
+            for (int items : {1, 2, 4, 8, 0}) {
                 b.head_items = items;
                 SDA_TRY(time_launch(s, [&] { return colpass_b<VT, FT>(op, b, bv.v, bv.s, b.grid3a, s); }, &t));
                 if (t < besth) besth = t, tv.head_items = items;
@@ -1937,7 +1944,7 @@ static int autotune(sda_operator *op, BatchWs &b, cudaStream_t s) {
     op->tuned[0] = tv.bpsm1;
     op->tuned[1] = tv.bpsm2;
     op->tuned[2] = tv.bpsm3;
-    op->tuned[3] = tv.head_items;
+    op->tuned[3] = tv.head_items > 0 ? tv.head_items : -1;
     return SDA_OK;
 }
 
@@ -2035,7 +2042,7 @@ static int run_lanes(sda_operator *op, const BatchLane *lanes, int nl, const dou
             return fail(SDA_ERR_INDEX, "batched solve: index check %llu failed at %llu",
                         (unsigned long long)(b.h_ctl->err >> 40), (unsigned long long)(b.h_ctl->err & 0xffffffffffull));
         const int64_t bodies = std::max<int64_t>(1, ((int64_t)b.h_ctl->k + nbi - 1) / nbi);
-        note_launch(bodies * ((4 + colpass_launches(op)) * (int64_t)nbi + 1));
+        note_launch(bodies * ((4 + colpass_launches(op, b)) * (int64_t)nbi + 1));
         for (int ph = 1; ph <= 4; ++ph) op->stats.launches[ph] += bodies * nbi;
     }
     int launched = device_loop ? limit + 1 : 0;   // the host-driven loop: profile mode and graphs off
