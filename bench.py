@@ -885,7 +885,8 @@ def run_large(args, rank, world, local):
     achieved = per[dominant] / (durs[dominant] * 1e-3) / 1e9
     whole = (sum(per.values()) + once / bi) / (it_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(dominant, os.path.join(ROOT, "profiles", "batched_kernels_%s.md" % args.workload)),
+                "traffic": recorded_traffic(dominant + ("_nohead" if dominant == "phase3a" and info["tuned"][3] == -1 else ""),
+                                           os.path.join(ROOT, "profiles", "batched_kernels_%s.md" % args.workload)),
                 "kernel": names[dominant],
                 "peak_kind": peak_kind, "bytes_per_launch": per[dominant], "ms_per_launch": durs[dominant],
                 "whole_iteration": {"GB/s": whole, "frac": whole / peak, "bytes": sum(per.values()) + once / bi,
