@@ -7,7 +7,11 @@
 // values is one contiguous access.  Per target: its own labels, mu_l, right-hand
 // side, CG scalars and shift states (a SolveState each); the shift list is the
 // call's.  X and S are streamed once per batch iteration instead of once per
-// target.
+// target.  A batch's iterations run as one graph launch with a device-side loop
+// condition; an autotuner picks the passes' schedule.  The same kernels in FP64
+// serve the block utilities (FP64 true residuals, projections, adjoint
+// contractions, class sums, 16 vectors per pass), whose X passes run in exact
+// fixed point where X's values allow it.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -30,15 +34,6 @@ constexpr int kTG = kBlock / kTB;    // lane groups per block
 struct BatchBounds {
     int64_t n, d, ldw, n8, nnz_x, nnz_s, ntiles, nslots, nsplits, npart;
     int64_t nqx;   // quads of the padded row layout of X
-};
-
-// Resident blocks per SM asked of the batched sparse passes: they are bound by
-// gather latency, so the FP32 ones are held to 40 registers for six blocks
-// (measured: 646 against 742 us per batch iteration at four blocks); the FP64
-// ones (block utilities) keep their registers.
-template <class FT>
-struct KbMinBlocks {
-    static constexpr int value = std::is_same<FT, float>::value ? 6 : 1;
 };
 
 // value type of the padded row layout (a pattern X stores FP8 ones there)
@@ -354,9 +349,11 @@ __global__ void __launch_bounds__(kBlock) kb_formp(int64_t d, int64_t ldw, const
     }
 }
 
-// Targets per thread of the batched row pass and its resident-block floor: the
-// per-entry work (index, value, bound check) is shared by a thread's targets, so
-// FP32 takes eight (two 16-byte gathers), FP64 two
+// Targets per thread of the batched row, Laplacian and tail column passes, and
+// their resident-block floor: the per-entry work (index, value, bound check) is
+// shared by a thread's targets, so FP32 takes eight (two 16-byte gathers; the row
+// pass measured 0.81 against 0.98 ms per launch at 2M x 1M with four, at 64
+// against 40 registers), FP64 two; the autotuner picks the resident blocks
 template <class FT>
 struct RowLanes {
     static constexpr int TPL = sizeof(FT) == 4 ? 8 : 2;
