@@ -1161,6 +1161,7 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
     __shared__ float s_sh[kTB], s_sl[kTB];   // each lane's base shift sigma0 as an FP32 pair
     __shared__ double s_sigma0[kTB];
     __shared__ double s_anw[kTB], s_rn[kTB];
+    __shared__ int s_exact[kTB];
     if (ctl->done) return;
     if (threadIdx.x < kTB) {
         const SolveState &S = st[threadIdx.x];
@@ -1283,8 +1284,12 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
         SolveState &S = st[threadIdx.x];
         s_anw[threadIdx.x] = 0.0;
         s_rn[threadIdx.x] = 0.0;
+        s_exact[threadIdx.x] = 0;
         if (!S.done) {
             const double rr_new = tot[0];
+            // an exactly vanished residual ends the lane's run (a fixed-iteration run
+            // would otherwise go on with p = 0 and divide by <p, (B + sigma0) p> = 0)
+            s_exact[threadIdx.x] = rr_new == 0.0;
             const double anw = rr_new / S.rr;
             const double c_new = tot[1] + anw * S.c;
             const double pp_new = rr_new + 2.0 * anw * tot[2] + anw * anw * S.pp;
@@ -1323,7 +1328,7 @@ __global__ void __launch_bounds__(kBlock) kb_phase3b(int64_t d, int64_t ldw, int
             int na = 0;
             for (int sh = 0; sh < ns; ++sh) na += S.sh[sh].active;
             S.nactive = na;
-            if (na == 0 || S.k >= S.limit || S.status != SDA_OK) {
+            if (na == 0 || S.k >= S.limit || S.status != SDA_OK || s_exact[threadIdx.x]) {
                 S.done = 1;
                 S.alpha = 0.0;   // a stopped target's vectors stay put (gamma 0, p = r)
                 S.gamma = 0.0;

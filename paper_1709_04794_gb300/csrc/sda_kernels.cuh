@@ -1067,6 +1067,7 @@ struct StreamSmem {
     double red[kRedDoubles];
     double alpha_new, rnorm;
     float gh, gl, sh, sl, tf;   // gamma_k, sigma0 as FP32 pairs, t in FP32 (mixed path)
+    int exact;                  // r_{k+1} = 0: every shift's solution is exact, the run ends
 };
 
 
@@ -1199,6 +1200,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw,
         st->k = k;
         sm.alpha_new = anw;
         sm.rnorm = sqrt(rr_new);
+        // an exactly vanished residual ends the run (a fixed-iteration run would
+        // otherwise go on with p = 0 and divide by <p, (B + sigma0) p> = 0)
+        sm.exact = rr_new == 0.0;
         *counter = 0u;
     }
     __syncthreads();
@@ -1216,7 +1220,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_phase3b(int64_t d, int64_t ldw,
     const int na = __syncthreads_count(act);
     if (threadIdx.x == 0) {
         st->nactive = na;
-        st->done = (na == 0 || k >= st->limit || st->status != SDA_OK) ? 1 : 0;
+        st->done = (na == 0 || k >= st->limit || st->status != SDA_OK || sm.exact) ? 1 : 0;
     }
 }
 
