@@ -1,0 +1,49 @@
+"""Host logic of bench.py's roofline fields (CPU only): the recorded DRAM
+traffic is taken from a committed profile only while the kernel sources hash
+the same as when it was captured, and per column-pass form; the algorithmic
+bytes of the batched kernels follow their stated model."""
+import os
+
+import bench
+from paper_1709_04794_gb300 import synth
+
+
+def _profile(tmp_path, digest, lines):
+    p = tmp_path / "profile.md"
+    p.write_text("\n\n".join(lines + ["sources_sha256: %s" % digest]) + "\n")
+    return str(p)
+
+
+def test_recorded_traffic_needs_the_current_sources(tmp_path):
+    lines = ["phase3a_dram_bytes_per_launch: 2878539392", "phase3a_nohead_dram_bytes_per_launch: 5200067584"]
+    cur = _profile(tmp_path, bench.sources_hash(), lines)
+    assert bench.recorded_traffic("phase3a", cur) == 2878539392.0
+    assert bench.recorded_traffic("phase3a_nohead", cur) == 5200067584.0
+    assert bench.recorded_traffic("phase1", cur) is None              # no counters for that kernel
+    stale = _profile(tmp_path, "0" * 16, lines)
+    assert bench.recorded_traffic("phase3a", stale) is None          # other kernel sources
+    assert bench.recorded_traffic("phase3a", str(tmp_path / "missing.md")) is None
+
+
+def test_committed_profile_of_the_default_workload_parses():
+    path = os.path.join(bench.ROOT, "profiles", "batched_kernels_large_1000t_2m.md")
+    txt = open(path).read()
+    assert "phase3a_dram_bytes_per_launch:" in txt and "sources_sha256:" in txt
+
+
+def test_batched_bytes_model():
+    p = synth.custom_problem(3000, 2048, 30, seed=21, values="counts", n_targets=2, n_labelled=300, k=5)
+    nnz, snz, n, d = int(p.x_ptr[-1]), int(p.s_ptr[-1]), p.n, p.d
+    per = bench.batched_bytes(p, "f16", 100, 1600, 16)
+    # rows of X: int32 index + FP16 value per entry, row pointers, P read twice, U written (FP32)
+    assert per["phase1"] == nnz * 6 + (n + 1) * 8 + d * 16 * 2 * 4 + n * 16 * 4
+    assert per["phase2"] == snz * 8 + (n + 1) * 8 + n * 16 * 9 + n * 4
+    # recurrence form: 16 active shifts per iteration on average stream P and W (4 values each)
+    assert per["phase3b"] == d * 16 * (8 + 5 * 4) + 16 * d * 4 * 4
+    # the head layout moves the frequent columns' entries to 16-bit local rows
+    info = {"head_cols": 64, "head_ranges": 2, "tail_nnz": nnz // 3}
+    head = bench.batched_bytes(p, "f16", 100, 1600, 16, info=info)
+    assert head["phase3a"] < per["phase3a"] + 2 * 2 * 64 * 16 * 8
+    basis = bench.batched_bytes(p, "f16", 100, 1600, 16, basis=True, ns=24)
+    assert basis["basis_once"] == 100 * d * 16 * 4 * 2 + 24 * d * 16 * 8
+    assert all(v > 0 for v in basis.values())
