@@ -20,12 +20,16 @@ pytestmark = pytest.mark.gpu
 
 
 def _problem(values):
-    p = synth.custom_problem(1800, 900, 16, seed=51, values="counts" if values == "counts" else "binary",
+    p = synth.custom_problem(1800, 900, 16, seed=51, values="counts" if values in ("counts", "signed") else "binary",
                              n_targets=2, n_labelled=150, k=5, shifts=(1e-3, 1e1, 5))
     if values == "real":
         # values spread over many binary digits (exact in FP32): no common power-of-two grid
         x = np.random.default_rng(52).uniform(0.1, 2.0, p.x_val.size).astype(np.float32).astype(np.float64)
         p = dataclasses.replace(p, x_val=x)
+    if values == "signed":
+        # counts with random signs: x_int = x, |x_int| < 2^4, negative products
+        sign = np.where(np.random.default_rng(55).random(p.x_val.size) < 0.5, -1.0, 1.0)
+        p = dataclasses.replace(p, x_val=p.x_val * sign)
     if values == "quarters":
         # multiples of 1/4 up to 7.75: x_int = 4 x < 2^5, two fraction bits
         x = np.random.default_rng(53).integers(1, 32, p.x_val.size) / 4.0
@@ -39,6 +43,7 @@ def _problem(values):
     ("binary", "f64", 1, (0, 1)),
     ("binary", "pattern", 1, (0, 1)),
     ("counts", "f16", 1, (0, 4)),
+    ("signed", "f16", 1, (0, 4)),
     ("quarters", "f16", 1, (2, 5)),
     ("real", "f32", -1, None),
     ("real", "f64", -1, None),
