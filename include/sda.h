@@ -179,13 +179,15 @@ enum {
 typedef struct {
     double tol;             /* shift s stops when |zeta_s| ||r|| < tol ||b|| (Alg. 3, relative)     */
     int32_t max_iter;       /* iteration cap for every shift                                       */
-    int32_t fixed_iters;    /* > 0: run exactly this many iterations, ignore tol (Sec. 5.2: 70)     */
+    int32_t fixed_iters;    /* > 0: run exactly this many iterations, ignore tol (Sec. 5.2: 70);   */
+                            /* a target whose residual vanishes exactly stops there (SDA_OK)       */
     int32_t rhs_mode;       /* SDA_RHS_*                                                           */
     const double *rhs;      /* see rhs_mode; NULL for SDA_RHS_CANONICAL                            */
     int32_t rhs_on_device;  /* 1: `rhs` is a device pointer                                        */
     int32_t target_begin;   /* first target solved by this call                                    */
     int32_t target_count;   /* number of targets solved by this call (-1: all from target_begin)   */
-    int32_t check_residual; /* 1: compute the FP64 true relative residual of every shift           */
+    int32_t check_residual; /* 1: compute the FP64 true relative residual of every shift (its X    */
+                            /* passes exact in integers where X's values allow, see info)          */
     int32_t out_on_device;  /* 1: w_out is a device pointer; 0: host pointer                       */
     int32_t use_graph;      /* 1: replay the iteration loop as captured CUDA graphs                */
     int32_t iter_batch;     /* iterations launched between two host convergence checks (0: auto)   */
