@@ -789,6 +789,7 @@ def run_large(args, rank, world, local):
 
         def run(j):
             try:
+                torch.cuda.set_device(local)     # a new host thread starts on device 0
                 res[j] = step(k * S + j, inputs=inputs, hold=hold, stream=streams[j], w=wbufs[j])
             except BaseException as e:      # re-raised on the main thread
                 errs.append(e)
