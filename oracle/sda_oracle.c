@@ -260,6 +260,8 @@ int oracle_cg(oracle_problem *P, const double *b, double beta, double tol, int m
         for (int64_t j = 0; j < d; ++j) r[j] += gamma * q[j];
         double rr_new = dot(d, r, r);
         if (fixed_iters <= 0 && sqrt(rr_new) < tol * bnorm) { rr = rr_new; ++i; break; }
+        /* a vanished residual: w is exact, nothing is left to iterate on */
+        if (rr_new == 0.0) { rr = rr_new; ++i; break; }
         double a = rr_new / rr;
         for (int64_t j = 0; j < d; ++j) p[j] = r[j] + a * p[j];
         rr = rr_new;
@@ -354,6 +356,9 @@ int oracle_shifted_cg(oracle_problem *P, const double *b, const double *betas, i
         gamma_prev = gamma;
         alpha = alpha_new;
         rr = rr_new;
+        /* a vanished residual: every shift's W_s is exact (its residual is
+           zeta_s r = 0), nothing is left to iterate on */
+        if (rr_new == 0.0) { ++i; break; }
     }
     if (bnorm == 0.0)
         for (int s = 0; s < ns; ++s) res_est[s] = 0.0;

@@ -510,3 +510,24 @@ def test_knn_graph_oracle_equals_input_generator():
         g_rp, g_col, g_val = synth.union_graph(nbr, sim)
         o_rp, o_col, o_val = oracle.knn_graph(p.x_ptr, p.x_col, p.d, 5, cap=cap)
         assert np.array_equal(g_rp, o_rp) and np.array_equal(g_col, o_col) and np.array_equal(g_val, o_val)
+
+
+def test_fixed_run_ends_at_a_vanished_residual(tiny):
+    """Algorithms 2 and 3 iterate while a residual remains: a fixed-iteration
+    run at a shift far above ||B|| converges until <r, r> underflows to exactly
+    zero and ends there (no breakdown on <p, q> = 0), with the exact solution,
+    i.e. the dense solve's."""
+    o = oracle.from_problem(tiny)
+    b = o.rhs_canonical()
+    beta = 1e5
+    X = oracle.dense_x(tiny.x_ptr, tiny.x_col, tiny.x_val, tiny.d)
+    B = oracle.dense_operator(X, tiny.s_ptr, tiny.s_col, tiny.s_val, tiny.labels[0], tiny.alpha)
+    w, it, res, rc = o.cg(b, beta, fixed_iters=2000)
+    assert rc == 0 and it < 2000, (rc, it)
+    sh = o.shifted_cg(b, [beta, 2 * beta], fixed_iters=2000)
+    assert sh.status == 0 and sh.total_iters < 2000, (sh.status, sh.total_iters)
+    for s, bt in enumerate((beta, 2 * beta)):
+        ref = np.linalg.solve(B + bt * np.eye(tiny.d), b)
+        assert np.linalg.norm(sh.W[s] - ref) <= 1e-13 * np.linalg.norm(ref), s
+    ref = np.linalg.solve(B + beta * np.eye(tiny.d), b)
+    assert np.linalg.norm(w - ref) <= 1e-13 * np.linalg.norm(ref)
