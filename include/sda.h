@@ -401,7 +401,7 @@ SDA_API int sda_operator_apply(const sda_operator *op, int32_t target, double si
  * on the GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  The first call on a device looks the array's
  * address up with that device current (which loads the library's device code
- * on that device); make that first call before any stream capture.  p and q
+ * on that device).  p and q
  * are device arrays of D doubles in the caller's feature order; errors as
  * sda_operator_apply.
  */
