@@ -335,6 +335,31 @@ def test_auc_rank_formula_equals_pairwise_bruteforce():
     assert oracle.auc([1, 1, 1, 1], [1, -1, 1, -1]) == 0.5
 
 
+def test_logistic_loss_closed_forms_and_gradient():
+    """The held-out loss of the adjoint gradient (mean log(1 + e^{-y s})):
+    log 2 at s = 0, vanishing for large margins, |y s| for large negative
+    margins, element-wise brute force with math.log1p, and its gradient
+    against central differences of the loss."""
+    import math
+    loss, g = oracle.logistic_loss(np.zeros(4), np.array([1, -1, 1, -1]))
+    assert loss == math.log(2.0) and np.array_equal(g, np.array([-1, 1, -1, 1]) / 8.0)
+    with np.errstate(over="ignore"):        # e^{800} in the gradient's denominator: the gradient is -0
+        assert oracle.logistic_loss(np.array([800.0]), np.array([1]))[0] == 0.0
+    assert oracle.logistic_loss(np.array([800.0]), np.array([-1]))[0] == 800.0
+    rng = np.random.default_rng(9)
+    s = rng.standard_normal(50) * 3.0
+    y = np.where(rng.random(50) < 0.3, 1, -1)
+    loss, g = oracle.logistic_loss(s, y)
+    brute = sum(math.log1p(math.exp(-yi * si)) for si, yi in zip(s, y)) / s.size
+    assert abs(loss - brute) < 1e-15 * max(1.0, brute)
+    h = 1e-6
+    for i in range(0, 50, 7):
+        e = np.zeros(50)
+        e[i] = h
+        fd = (oracle.logistic_loss(s + e, y)[0] - oracle.logistic_loss(s - e, y)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-8, (i, fd, g[i])
+
+
 def test_projection(tiny):
     o = oracle.from_problem(tiny)
     w = np.random.default_rng(8).standard_normal(tiny.d)
