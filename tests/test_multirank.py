@@ -1,7 +1,8 @@
 """Host logic of the multi-GPU benchmark on CPU (gloo, world size 2): the
 batched workload shards its independent targets over the ranks (contiguous
 shares, no exchange in the data path), and the job's time is the slowest
-rank's barrier-to-barrier window."""
+rank's barrier-to-barrier window; the targets solved are summed over the
+ranks."""
 import os
 import socket
 
@@ -36,8 +37,9 @@ def _worker(rank, world, port, out):
     try:
         begin, count = bench.shard(256, rank, world)
         t = bench.max_over_ranks(1.0 + rank, dist)        # rank 1 is the slower one
+        tot = bench.sum_over_ranks(count, dist)           # targets solved by the job
         dist.barrier()
-        out[rank] = (begin, count, t)
+        out[rank] = (begin, count, t, tot)
     finally:
         dist.destroy_process_group()
 
@@ -51,3 +53,4 @@ def test_two_ranks_gloo():
         res = dict(out)
     assert res[0][:2] == (0, 128) and res[1][:2] == (128, 128)
     assert res[0][2] == pytest.approx(2.0) and res[1][2] == pytest.approx(2.0)
+    assert res[0][3] == 256.0 and res[1][3] == 256.0
