@@ -760,20 +760,17 @@ def run_large(args, rank, world, local):
             y = hold["y"][r0:r1].to("cuda", non_blocking=True)
             off = off_all[t0:t0 + cnt + 1] - r0
             g = torch.empty(r1 - r0, dtype=torch.float64, device="cuda")
-            wb = torch.empty((cnt, d), dtype=torch.float64, device="cuda")
             losses = torch.empty((cnt, ns), dtype=torch.float64, device="cuda")
-            scs = []
+            best_d = torch.empty(cnt, dtype=torch.int32, device="cuda")
+            # every target's centred ratings of every shift, target i's at ns * off[i] as [ns][rows_i]
+            sc = torch.empty(ns * (r1 - r0), dtype=torch.float64, device="cuda")
             for i in range(cnt):
-                ri, yi = rows[off[i]:off[i + 1]], y[off[i]:off[i + 1]]
-                sc = torch.empty((ns, ri.numel()), dtype=torch.float64, device="cuda")
-                sda.sda_project_rows(h, w[i], ns, ri, sc, 1, i, stream)
-                losses[i] = torch.nn.functional.softplus(-yi[None, :] * sc).mean(dim=1)
-                scs.append(sc)
-            best = torch.argmin(losses, dim=1).tolist()
-            for i in range(cnt):
-                yi = y[off[i]:off[i + 1]]
-                g[off[i]:off[i + 1]] = -yi * torch.sigmoid(-yi * scs[i][best[i]]) / yi.numel()
-                wb[i] = w[i, best[i]]
+                a, b_ = int(off[i]), int(off[i + 1])
+                sda.sda_project_rows(h, w[i], ns, rows[a:b_], sc[ns * a:ns * b_].view(ns, b_ - a), 1, i, stream)
+            # held-out logistic loss of every (target, shift), least-loss shift, its loss gradient
+            sda.sda_heldout_logistic(ns, off, sc, y, losses, best_d, g, stream)
+            best = best_d.tolist()
+            wb = w[torch.arange(cnt, device="cuda"), best_d.long()]
             mark(marks, stream)
             oa = sda.sda_default_opts()
             oa.fixed_iters = args.fixed_iters

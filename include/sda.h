@@ -34,6 +34,9 @@
  *  - Device work is ordered on the caller's stream (cudaStream_t passed as
  *    void*, NULL = legacy default stream); calls that return host results
  *    synchronise that stream before returning.
+ *  - An operator keeps the scratch of its calls between them, so calls on one
+ *    operator must not overlap (one stream and one host thread at a time);
+ *    different operators share nothing and may be used concurrently.
  */
 #ifndef SDA_H
 #define SDA_H
@@ -320,6 +323,34 @@ SDA_API int sda_adjoint_grad_batched(sda_operator *op, int32_t n_targets, const 
                                      sda_shift_report *report, void *cuda_stream);
 
 /*
+ * sda_heldout_logistic - choose the shift of each target on its held-out rows.
+ * The paper picks the regularisation beta on held-out folds (Sec. 5); the
+ * criterion here is the logistic loss of the ratings, the loss whose
+ * gradient sda_adjoint_grad(_batched) takes:
+ *     loss[t][s] = (1/m_t) sum_h log(1 + exp(-y_h s_{t,s,h}))   (m_t rows of target t)
+ *     best[t]    = the s of least loss[t][s] (the smallest such s on ties; NaN
+ *                  losses are never least unless all are NaN, then 0)
+ *     g_h        = d loss[t][best[t]] / d s_h = -y_h / (1 + exp(y_h s_{t,best,h})) / m_t
+ * FP64; every sum is taken in a fixed order, so repeated calls give the same bits.
+ *
+ *   n_targets, n_shifts  >= 0 and >= 1
+ *   row_off              host int64 [n_targets + 1], row_off[0] = 0, non-decreasing:
+ *                        target t owns held-out rows [row_off[t], row_off[t + 1])
+ *   scores               device doubles [n_shifts * row_off[n_targets]]; target t's ratings
+ *                        start at n_shifts * row_off[t], laid out [n_shifts][m_t] (the
+ *                        layout sda_project_rows writes for one target)
+ *   y                    device doubles [row_off[n_targets]]: the rows' labels (+1 / -1)
+ *   loss                 device doubles [n_targets][n_shifts]
+ *   best                 device int32 [n_targets]
+ *   g                    device doubles [row_off[n_targets]]
+ * A target with no rows gets loss 0 for every shift and best 0.  Errors:
+ * INVALID_ARG (bad sizes or offsets, a NULL array), CUDA.  Does not
+ * synchronise the stream.
+ */
+SDA_API int sda_heldout_logistic(int32_t n_targets, int32_t n_shifts, const int64_t *row_off, const double *scores,
+                                 const double *y, double *loss, int32_t *best, double *g, void *cuda_stream);
+
+/*
  * sda_knn_graph - the similarity graph S of Sec. 2.4 built on the device from
  * the samples: s_ij = Tanimoto (Jaccard) similarity of the binary supports of
  * rows i and j of X, |x_i and x_j| / |x_i or x_j| (Tanimoto on fingerprints,
@@ -365,8 +396,9 @@ SDA_API int sda_project(const sda_operator *op, const double *w, int64_t n_vec, 
  *   w        [n_vec][D] doubles in the caller's feature order (device)
  *   rows     n_rows row ids (device int64); repeated ids are allowed
  *   scores   [n_vec][n_rows] doubles (device)
- * Errors: INVALID_ARG (a row id outside [0, N), bad argument), CUDA, OOM.
- * Synchronises the stream.
+ * The operator keeps the call's scratch (n_vec D doubles and a little more)
+ * for later calls.  Errors: INVALID_ARG (a row id outside [0, N), bad
+ * argument), CUDA, OOM.  Synchronises the stream.
  */
 SDA_API int sda_project_rows(const sda_operator *op, const double *w, int32_t n_vec, const int64_t *rows,
                              int64_t n_rows, double *scores, int32_t centred, int32_t target, void *cuda_stream);

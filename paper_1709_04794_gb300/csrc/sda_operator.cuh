@@ -93,6 +93,7 @@ struct Workspace {
     DevBuf<double> f64;      // FP64 scratch: b (D), w (D), q (D)
     DevBuf<double> dev_b;    // right-hand sides of the call's targets [T][D]
     DevBuf<double> adj;      // adjoint scratch: 3 D + 5 N doubles
+    DevBuf<char> proj;       // scratch of the row-subset projection, grown on demand
     SolveState *h_st = nullptr;   // pinned host mirror of the state
     std::vector<cudaEvent_t> prof_ev;  // profile mode: start/end event of every phase launch of a batch
     cudaEvent_t call_ev[2] = {nullptr, nullptr};

@@ -1138,32 +1138,37 @@ extern "C" SDA_API int sda_project_rows(const sda_operator *op, const double *w,
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int64_t d = op->d;
     const int nb = std::min<int>(op->sm_count * 2, (int)((d + 31) / 32));
-    DevBuf<double> wt, part, c;
-    DevBuf<int> err;
-    SDA_TRY(wt.alloc((size_t)(n_vec * d)));
-    SDA_TRY(err.alloc(1));
-    SDA_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    k_to_new_t<<<grid_elems(d * n_vec, op->sm_count), kBlock, 0, s>>>(d, n_vec, op->new_of_old.p, w, wt.p);
+    // scratch in the operator's workspace (kept between calls, so repeated
+    // calls allocate and free nothing): w permuted [n_vec][D], the centring
+    // partials [nb][n_vec] and sums [n_vec], the row-id error flag
+    const size_t b_wt = (size_t)n_vec * d * sizeof(double), b_part = (size_t)nb * n_vec * sizeof(double),
+                 b_c = (size_t)n_vec * sizeof(double);
+    const size_t need = b_wt + b_part + b_c + 256;
+    sda_operator *mop = const_cast<sda_operator *>(op);
+    if (mop->ws.proj.n < need) SDA_TRY(mop->ws.proj.alloc(need));
+    double *wt = reinterpret_cast<double *>(mop->ws.proj.p), *part = wt + (size_t)n_vec * d,
+           *c = part + (size_t)nb * n_vec;
+    int *err = reinterpret_cast<int *>(c + n_vec);
+    SDA_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    k_to_new_t<<<grid_elems(d * n_vec, op->sm_count), kBlock, 0, s>>>(d, n_vec, op->new_of_old.p, w, wt);
     SDA_LAUNCHED();
     if (centred) {
-        SDA_TRY(part.alloc((size_t)nb * n_vec));
-        SDA_TRY(c.alloc((size_t)n_vec));
-        k_mu_dots_part<<<nb, kBlock, 0, s>>>(d, n_vec, op->mu.p + (int64_t)target * d, wt.p, part.p);
+        k_mu_dots_part<<<nb, kBlock, 0, s>>>(d, n_vec, op->mu.p + (int64_t)target * d, wt, part);
         SDA_LAUNCHED();
-        k_mu_dots_sum<<<(n_vec + 127) / 128, 128, 0, s>>>(nb, n_vec, part.p, c.p);
+        k_mu_dots_sum<<<(n_vec + 127) / 128, 128, 0, s>>>(nb, n_vec, part, c);
         SDA_LAUNCHED();
     }
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_rows + 7) / 8, (int64_t)op->sm_count * 16));
     SDA_TRY(with_vt(op->compute, [&](auto tag) -> int {
         using VT = std::remove_pointer_t<decltype(tag)>;
         k_project_rows<VT><<<grid, kBlock, 0, s>>>(op->n, n_rows, n_vec, rows, op->x_rp.p, op->x_col.p,
-                                                   (const VT *)op->x_val_r.p, wt.p, centred ? c.p : nullptr, scores,
-                                                   err.p);
+                                                   (const VT *)op->x_val_r.p, wt, centred ? c : nullptr, scores,
+                                                   err);
         SDA_LAUNCHED();
         return SDA_OK;
     }));
     int herr = 0;
-    SDA_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SDA_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SDA_CUDA(cudaStreamSynchronize(s));
     if (herr) return fail(SDA_ERR_INVALID_ARG, "a row id is out of range");
     return SDA_OK;

@@ -100,6 +100,7 @@ _SIGS = {
     "sda_adjoint_grad_batched": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp,
                                                 ctypes.POINTER(sda_solve_opts), _vp, _vp, _vp,
                                                 ctypes.POINTER(sda_shift_report), _vp]),
+    "sda_heldout_logistic": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sda_operator_apply": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
     "sda_operator_apply_static": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp]),
     "sda_knn_graph": (ctypes.c_int, [ctypes.POINTER(sda_csr), ctypes.c_int32, ctypes.c_int64, ctypes.c_double, _vp,
@@ -338,6 +339,26 @@ def sda_adjoint_grad_batched(op, targets, alpha, betas, W, dloss_ds, rows, row_o
     reps = [dict(iters=rep[i].iters, status=rep[i].status, est_residual=rep[i].est_residual,
                  true_residual=rep[i].true_residual) for i in range(n)]
     return code, da, db, reps
+
+
+def sda_heldout_logistic(n_shifts, row_off, scores, y, loss, best, g, stream=None):
+    """Calls sda_heldout_logistic: loss [n][n_shifts], best [n] (int32) and g
+    (one entry per held-out row) into the given contiguous device tensors."""
+    lib = load()
+    off = np.ascontiguousarray(row_off, dtype=np.int64)
+    n = int(off.size) - 1
+    if n < 0:
+        raise ValueError("row_off needs n_targets + 1 entries")
+    for a in (loss, best, g):
+        if _is_torch(a) and not a.is_contiguous():
+            raise ValueError("output tensors must be contiguous")
+    sp, _, sk = _ptr(scores)
+    yp, _, yk = _ptr(y)
+    lp, _, lk = _ptr(loss)
+    bp, _, bk = _ptr(best)
+    gp, _, gk = _ptr(g)
+    return _check(lib.sda_heldout_logistic(n, int(n_shifts), off.ctypes.data, sp, yp, lp, bp, gp, _stream(stream)),
+                  "sda_heldout_logistic")
 
 
 def sda_operator_apply(op, target, sigma, p, q, stream=None):

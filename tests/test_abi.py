@@ -47,3 +47,24 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(sda.sda_solve_stats) == 112
     assert ctypes.sizeof(sda.sda_operator_info) == 128
     assert sda.sda_operator_info.exact_x_passes.offset == 120
+
+
+def test_heldout_logistic_rejects_bad_arguments_without_gpu():
+    """The selection call checks its sizes and offsets on the host, before any
+    device work: no targets is a no-op; offsets that do not start at 0 or that
+    decrease, no shifts, and missing outputs are INVALID_ARG."""
+    import numpy as np
+    lib = sda.load()
+
+    def call(n, ns, off, out=True):
+        o = np.ascontiguousarray(off, dtype=np.int64)
+        p = ctypes.c_void_p(8) if out else None            # never dereferenced: the checks come first
+        return lib.sda_heldout_logistic(n, ns, o.ctypes.data, None, None, p, p, None, None)
+
+    assert call(0, 4, [0]) == sda.SDA_OK
+    assert call(2, 4, [1, 2, 3]) == sda.SDA_ERR_INVALID_ARG
+    assert call(2, 4, [0, 3, 2]) == sda.SDA_ERR_INVALID_ARG
+    assert call(2, 0, [0, 1, 2]) == sda.SDA_ERR_INVALID_ARG
+    assert call(-1, 4, [0]) == sda.SDA_ERR_INVALID_ARG
+    assert call(1, 4, [0, 0], out=False) == sda.SDA_ERR_INVALID_ARG
+    assert call(1, 4, [0, 5]) == sda.SDA_ERR_INVALID_ARG        # rows but no scores, y or g
