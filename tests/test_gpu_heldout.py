@@ -20,7 +20,7 @@ NS = 24
 def _case(seed=5, T=300):
     rng = np.random.default_rng(seed)
     m = rng.integers(0, 40, T)
-    m[[3, 7, 9, 10, 100, 299]] = [0, 20, 10, 5, 700, 1]
+    m[[3, 7, 9, 10, T // 3, T - 1]] = [0, 20, 10, 5, 700, 1]
     off = np.concatenate([[0], np.cumsum(m)]).astype(np.int64)
     R = int(off[-1])
     y = np.where(rng.random(R) < 0.3, 1.0, -1.0)
