@@ -1,8 +1,11 @@
 """Host logic of bench.py's roofline fields (CPU only): the recorded DRAM
 traffic is taken from a committed profile only while the kernel sources hash
 the same as when it was captured, and per column-pass form; the algorithmic
-bytes of the batched kernels follow their stated model."""
+bytes of the batched kernels follow their stated model; the oracle leg reports
+the losses its shift choice came from."""
 import os
+
+import numpy as np
 
 import bench
 from paper_1709_04794_gb300 import synth
@@ -47,3 +50,15 @@ def test_batched_bytes_model():
     basis = bench.batched_bytes(p, "f16", 100, 1600, 16, basis=True, ns=24)
     assert basis["basis_once"] == 100 * d * 16 * 4 * 2 + 24 * d * 16 * 8
     assert all(v > 0 for v in basis.values())
+
+
+def test_oracle_step_reports_the_losses_it_chose_from():
+    """The bench's oracle leg returns the held-out loss of every shift beside
+    the least-loss shift it chose, so a parity report can show how close the
+    two shifts are where the mixed sweep chose another one."""
+    p = synth.custom_problem(1500, 600, 12, seed=31, values="counts", n_targets=1, n_labelled=200, k=5,
+                             shifts=(1e-3, 1e2, 5))
+    W, tres, best, da, db, losses, tm = bench.oracle_step(p, 0, 15)
+    assert W.shape == (5, p.d) and tres.shape == (5,) and losses.shape == (5,)
+    assert best == int(np.argmin(losses)) and np.all(np.isfinite(losses))
+    assert set(tm) == {"setup", "sweep", "checks", "adjoint"}
