@@ -9,7 +9,7 @@ FP64 converged to tol 1e-10, batched and sequential solutions within 1e-6 of
 each other, FP64 true residuals below 1e-9 and iteration counts within 3 %;
 the mixed path's true residual within 20 x tol; the mixed path refined per
 (target, shift) to FP64 residuals of 1e-11, against the oracle at the
-spec bar (see parity.py).
+converged-solution parity bar (see parity.py).
 """
 import numpy as np
 import pytest

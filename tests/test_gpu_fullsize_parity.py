@@ -1,5 +1,5 @@
 """Full-size parity of the mixed path with per-shift FP64 refinement against
-the FP64 oracle, at the spec bar (parity.py): 1e-6 relative on w,
+the FP64 oracle, at the converged-solution parity bar (parity.py): 1e-6 relative on w,
 norm-wise and element-wise, on every shift whose residual bound
 kappa_s (rho + rho*) permits it, else the error reported beside that bound;
 AUC of the held-out rows equal to 4 decimals.
