@@ -6,8 +6,9 @@ rows, 24 shifts 1e-5..1e3, each solve run for the paper's 70 iterations
 (Sec. 5.2); plus the achieved HBM bandwidth of the dominant kernel and of the
 whole batched iteration against the measured peak.
 
-One step = one chunk of 32 targets through the whole hot path, inputs
-resident in HBM: operator build with the chunk's labels, the batched
+One step = two chunks of 64 targets in flight, each on its own stream,
+through the whole hot path with inputs resident in HBM.  A chunk is:
+operator build with the chunk's labels, the batched
 mixed-precision sweep of every shift with the FP64 true residual of every
 (target, shift), the centred held-out ratings of every shift, the least-loss
 shift per target and the batched adjoint gradient in (alpha, beta) there.
@@ -47,7 +48,7 @@ METRIC = "SDA solves/s (all shifts)"
 UNIT = "solves/s"
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cg_kernels_single_mixed_200k.md")
 FIXED_ITERS = 70                  # iterations per solve in the fixed-iteration protocol (Sec. 5.2)
-CHUNK = 32                        # targets per chunk of the large workload (two batches of 16)
+CHUNK = 64                        # targets per chunk of the large workload (four batches of 16)
 STREAMS = 2                       # chunks of the large workload in flight per step (own streams)
 
 
@@ -336,6 +337,13 @@ def shard(total: int, rank: int, world: int):
     base, extra = divmod(total, world)
     begin = rank * base + min(rank, extra)
     return begin, base + (1 if rank < extra else 0)
+
+
+def chunk_size(targets: int, chunk: int, streams: int) -> int:
+    """Targets per chunk of the large workload: `chunk`, but at most one
+    stream's share of the rank's targets, so that the chunks in flight at once
+    hold different targets."""
+    return max(1, min(chunk, -(-targets // max(1, streams))))
 
 
 def max_over_ranks(t_local: float, dist=None) -> float:
@@ -718,7 +726,7 @@ def run_large(args, rank, world, local):
     t_begin, t_mine = shard(T_all, rank, world)
     stream = torch.cuda.current_stream()
     ns, d, n = len(prob.shifts), prob.d, prob.n
-    C = max(1, min(args.chunk, t_mine))
+    C = chunk_size(t_mine, args.chunk, args.streams)
     keys = ("x_ptr", "x_col", "x_val", "s_ptr", "s_col", "s_val", "labels")
     dev = {k: torch.from_numpy(np.ascontiguousarray(getattr(prob, k))).cuda() for k in keys}
     rows_all, off_all, y_all = heldout_arrays(prob, 0, T_all)

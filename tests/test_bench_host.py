@@ -62,3 +62,19 @@ def test_oracle_step_reports_the_losses_it_chose_from():
     assert W.shape == (5, p.d) and tres.shape == (5,) and losses.shape == (5,)
     assert best == int(np.argmin(losses)) and np.all(np.isfinite(losses))
     assert set(tm) == {"setup", "sweep", "checks", "adjoint"}
+
+
+def test_chunk_size_keeps_chunks_in_flight_distinct():
+    """The large workload's chunks: the requested size where the rank has
+    enough targets for every stream, else one stream's share (the 64-target
+    workload on two streams: two chunks of 32, never one chunk solved twice)."""
+    assert bench.chunk_size(1000, 64, 2) == 64
+    assert bench.chunk_size(64, 64, 2) == 32
+    assert bench.chunk_size(125, 64, 2) == 63            # 1,000 targets over 8 ranks
+    assert bench.chunk_size(5, 64, 1) == 5
+    assert bench.chunk_size(1, 64, 2) == 1
+    for t in (1, 7, 64, 125, 1000):
+        for s in (1, 2, 3):
+            c = bench.chunk_size(t, 64, s)
+            chunks = -(-t // c)
+            assert chunks >= min(s, t) and 1 <= c <= 64
