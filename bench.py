@@ -346,6 +346,11 @@ def chunk_size(targets: int, chunk: int, streams: int) -> int:
     return max(1, min(chunk, -(-targets // max(1, streams))))
 
 
+def chunk_list(begin: int, count: int, size: int):
+    """(first target, targets) of each chunk of targets [begin, begin + count)."""
+    return [(begin + c0, min(size, count - c0)) for c0 in range(0, count, size)]
+
+
 def max_over_ranks(t_local: float, dist=None) -> float:
     """Slowest rank's time (the barrier-to-barrier window of the whole job)."""
     if dist is None:
@@ -732,7 +737,7 @@ def run_large(args, rank, world, local):
     rows_all, off_all, y_all = heldout_arrays(prob, 0, T_all)
     held = {"rows": torch.from_numpy(rows_all).cuda(), "y": torch.from_numpy(y_all).cuda()}
     w = torch.empty((C, ns, d), dtype=torch.float64, device="cuda")
-    chunks = [(t_begin + c0, min(C, t_mine - c0)) for c0 in range(0, t_mine, C)]
+    chunks = chunk_list(t_begin, t_mine, C)
 
     def solve_opts(cnt, profile=0, check=1, fixed=args.fixed_iters):
         o = sda.sda_default_opts()

@@ -78,3 +78,18 @@ def test_chunk_size_keeps_chunks_in_flight_distinct():
             c = bench.chunk_size(t, 64, s)
             chunks = -(-t // c)
             assert chunks >= min(s, t) and 1 <= c <= 64
+
+
+def test_ranks_and_chunks_cover_every_target_once():
+    """The large workload's 1,000 targets over 1, 2, 3 and 8 ranks: each rank's
+    contiguous share split into its chunks covers every target exactly once,
+    and every rank has at least as many chunks as streams in flight."""
+    for world in (1, 2, 3, 8):
+        seen = []
+        for rank in range(world):
+            begin, count = bench.shard(1000, rank, world)
+            c = bench.chunk_size(count, bench.CHUNK, bench.STREAMS)
+            chunks = bench.chunk_list(begin, count, c)
+            assert len(chunks) >= bench.STREAMS
+            seen += [t for t0, n in chunks for t in range(t0, t0 + n)]
+        assert seen == list(range(1000)), world
