@@ -124,11 +124,18 @@ class ClockSampler:
                 self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        return self.summarise(self.rows)
+
+    @staticmethod
+    def summarise(rows):
+        """Median SM clock, the maximum clock and every throttle reason seen
+        active, from the sampled rows (fields of QUERY; malformed rows and
+        non-numeric clocks are skipped)."""
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for r in rows:
             if len(r) >= 9:
                 for k, name in enumerate(names):
                     if r[5 + k].lower().startswith("active"):

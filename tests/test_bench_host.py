@@ -2,7 +2,8 @@
 traffic is taken from a committed profile only while the kernel sources hash
 the same as when it was captured, and per column-pass form; the algorithmic
 bytes of the batched kernels follow their stated model; the oracle leg reports
-the losses its shift choice came from."""
+the losses its shift choice came from; the chunks cover the targets once;
+the sampled clock rows are summarised as the timing rules read them."""
 import os
 
 import numpy as np
@@ -93,3 +94,17 @@ def test_ranks_and_chunks_cover_every_target_once():
             assert len(chunks) >= bench.STREAMS
             seen += [t for t0, n in chunks for t in range(t0, t0 + n)]
         assert seen == list(range(1000)), world
+
+
+def test_clock_rows_summarised():
+    """nvidia-smi rows (csv, no header, no units) sampled during the timed
+    region: the median SM clock under load, the maximum clock, and every
+    throttle reason seen active; short rows and [N/A] clocks are skipped."""
+    idle = ["0", "2070", "2070", "850.10", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]
+    capped = ["0", "1980", "2070", "1400.00", "0x4", "Not Active", "Not Active", "Not Active", "Active"]
+    hot = ["0", "1500", "2070", "1390.00", "0x48", "Active", "Active", "Not Active", "Not Active"]
+    s = bench.ClockSampler.summarise([idle, idle, capped, ["0", "[N/A]"], ["garbage"]])
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    s = bench.ClockSampler.summarise([idle, hot, hot])
+    assert s["sm_mhz"] == 1500.0 and s["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    assert bench.ClockSampler.summarise([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
