@@ -1,4 +1,4 @@
-"""Host logic of bench.py's roofline fields (CPU only): the recorded DRAM
+"""Host logic of bench.py (CPU only): the recorded DRAM
 traffic is taken from a committed profile only while the kernel sources hash
 the same as when it was captured, and per column-pass form; the algorithmic
 bytes of the batched kernels follow their stated model; the oracle leg reports
